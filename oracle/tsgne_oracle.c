@@ -1,0 +1,372 @@
+/*
+ * tsgne_oracle.c -- plain, slow FP64 CPU reference of the t-SGNE layout loop.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product (the CUDA library and its
+ * Python binding) links, loads or calls this file; only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg do.  It shares no code with the
+ * GPU path.
+ *
+ * Everything is written as the definitions read, in double precision, with
+ * plain loops and no blocking, fusion or reordering.  Section / equation
+ * numbers refer to "Efficiently Visualizing Large Graphs" (Li, Xiao, Zhou,
+ * arXiv 2310.11186):
+ *
+ *   tsgo_structure      neighbour graph G_knn,G of Eq. 7 with the graph's own
+ *                       edges as neighbours (Sec. 2.2); undirected (Sec. 2)
+ *   tsgo_cond_affinity  p_{j|i} of Eq. 2 restricted to N(i), sigma_i by the
+ *                       perplexity binary search of Sec. 2.1
+ *   tsgo_joint_P        p_ij of Eq. 3, normalised by the total so sum P = 1
+ *   tsgo_Z              denominator of Eq. 4 (ordered pairs k != l)
+ *   tsgo_kl             objective of Eq. 5
+ *   tsgo_gradient       derivative of Eq. 5 w.r.t. y_i (not printed in the
+ *                       paper; derived and pinned by finite differences)
+ *   tsgo_repulsion_rows per-row repulsive sums, for sampled checks at size
+ *   tsgo_optimize       gradient descent with gains, momentum and early
+ *                       exaggeration (the paper gives no schedule; the
+ *                       published t-SNE defaults are used)
+ *
+ * Readings of the paper where it is silent (also listed in the design notes):
+ *   - N(i) is the set of graph neighbours (k = graph edges), union of both
+ *     directions, no self loops, sorted by id.
+ *   - the Eq. 2 denominator runs over j in N(i) only;
+ *   - if |N(i)| <= perplexity the target entropy ln(perp) is unreachable and
+ *     the row is uniform, p_{j|i} = 1/|N(i)| ("saturated row");
+ *   - otherwise beta = 1/(2 sigma^2) is bisected from beta = 1 (doubling /
+ *     halving while unbounded, midpoints once bracketed) until
+ *     |H - ln perp| <= tol or max_iter evaluations; p is taken at the last
+ *     evaluated beta; distances are shifted by the row minimum first;
+ *   - Eq. 3's 2n is the total T = sum_ij (p_{j|i} + p_{i|j}), which equals 2n
+ *     when no node is isolated and keeps sum P = 1 otherwise.
+ *
+ * Status codes: 0 ok, -1 invalid argument, -2 malformed CSR, -3 out of memory.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TSGO_OK 0
+#define TSGO_EINVAL -1
+#define TSGO_EBADCSR -2
+#define TSGO_ENOMEM -3
+
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/* Checks a CSR: row_ptr[0] = 0, non-decreasing, cols in [0, n). */
+int tsgo_check_csr(int32_t n, const int64_t* rp, const int32_t* col) {
+  if (n < 0) return TSGO_EINVAL;
+  if (rp[0] != 0) return TSGO_EBADCSR;
+  for (int32_t i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return TSGO_EBADCSR;
+  for (int64_t e = 0; e < rp[n]; ++e)
+    if (col[e] < 0 || col[e] >= n) return TSGO_EBADCSR;
+  return TSGO_OK;
+}
+
+/*
+ * Neighbour structure (Eq. 7, neighbours = graph edges, Sec. 2.2).
+ * N(i) = { j != i : (i,j) or (j,i) is an input entry }, each row sorted and
+ * unique.  Writes out_rp[n+1]; out_col must hold 2*row_ptr[n] entries.
+ * Returns nnz (>= 0) or a negative status.
+ */
+int64_t tsgo_structure(int32_t n, const int64_t* rp, const int32_t* col, int64_t* out_rp, int32_t* out_col) {
+  int st = tsgo_check_csr(n, rp, col);
+  if (st != TSGO_OK) return st;
+  int64_t m = rp[n];
+  int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t* cur = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int32_t* raw = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
+  if (!cnt || !cur || !raw) {
+    free(cnt); free(cur); free(raw);
+    return TSGO_ENOMEM;
+  }
+  /* both directions of every entry, self loops dropped */
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int32_t j = col[e];
+      if (j == i) continue;
+      cnt[i + 1]++;
+      cnt[j + 1]++;
+    }
+  for (int32_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  for (int32_t i = 0; i < n; ++i) cur[i] = cnt[i];
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int32_t j = col[e];
+      if (j == i) continue;
+      raw[cur[i]++] = j;
+      raw[cur[j]++] = i;
+    }
+  /* sort each row, drop repeats */
+  int64_t nnz = 0;
+  out_rp[0] = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int64_t a = cnt[i], b = cnt[i + 1];
+    qsort(raw + a, (size_t)(b - a), sizeof(int32_t), cmp_i32);
+    for (int64_t e = a; e < b; ++e)
+      if (e == a || raw[e] != raw[e - 1]) out_col[nnz++] = raw[e];
+    out_rp[i + 1] = nnz;
+  }
+  free(cnt); free(cur); free(raw);
+  return nnz;
+}
+
+/* Position of column j in sorted row i, or -1. */
+static int64_t find_in_row(const int64_t* rp, const int32_t* col, int32_t i, int32_t j) {
+  int64_t lo = rp[i], hi = rp[i + 1] - 1;
+  while (lo <= hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (col[mid] == j) return mid;
+    if (col[mid] < j) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+/* Position of (j,i) for every entry e = (i,j) of a symmetric structure. */
+int tsgo_transpose_slots(int32_t n, const int64_t* rp, const int32_t* col, int64_t* tslot) {
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int64_t t = find_in_row(rp, col, col[e], i);
+      if (t < 0) return TSGO_EBADCSR;
+      tslot[e] = t;
+    }
+  return TSGO_OK;
+}
+
+/*
+ * Conditional affinities p_{j|i} (Eq. 2 over j in N(i)) with sigma_i from the
+ * perplexity binary search (Sec. 2.1): Perp = 2^{H in bits}, i.e. the target
+ * entropy in nats is ln(perp).
+ *
+ * X is n x d row-major FP64.  Writes pcond[nnz] and beta[n] (beta_i =
+ * 1/(2 sigma_i^2); 0 for saturated rows and isolated nodes) and, if iters is
+ * not NULL, the number of entropy evaluations per row.
+ */
+int tsgo_cond_affinity(int32_t n, const int64_t* rp, const int32_t* col, const double* X, int32_t d,
+                       double perp, double tol, int32_t max_iter, double* pcond, double* beta_out,
+                       int32_t* iters) {
+  if (n < 0 || d < 1 || !(perp > 1.0) || max_iter < 1) return TSGO_EINVAL;
+  const double Hstar = log(perp);
+  for (int32_t i = 0; i < n; ++i) {
+    int64_t a = rp[i], b = rp[i + 1];
+    int64_t k = b - a;
+    if (iters) iters[i] = 0;
+    beta_out[i] = 0.0;
+    if (k == 0) continue;
+    /* squared Euclidean distances in R^d */
+    double* dist = (double*)malloc(sizeof(double) * (size_t)k);
+    if (!dist) return TSGO_ENOMEM;
+    for (int64_t e = a; e < b; ++e) {
+      const double* xi = X + (int64_t)i * d;
+      const double* xj = X + (int64_t)col[e] * d;
+      double s = 0.0;
+      for (int32_t c = 0; c < d; ++c) {
+        double t = xi[c] - xj[c];
+        s += t * t;
+      }
+      dist[e - a] = s;
+    }
+    if ((double)k <= perp) {
+      /* saturated: ln k <= ln perp cannot be reached from above */
+      for (int64_t e = a; e < b; ++e) pcond[e] = 1.0 / (double)k;
+      free(dist);
+      continue;
+    }
+    double dmin = dist[0];
+    for (int64_t t = 1; t < k; ++t)
+      if (dist[t] < dmin) dmin = dist[t];
+    double beta = 1.0, lo = -INFINITY, hi = INFINITY;
+    double S = 0.0;
+    int32_t it;
+    for (it = 0; it < max_iter; ++it) {
+      /* entropy of the row at this beta: H = ln S + beta * E_p[d - dmin] */
+      S = 0.0;
+      double E = 0.0;
+      for (int64_t t = 0; t < k; ++t) {
+        double w = exp(-beta * (dist[t] - dmin));
+        S += w;
+        E += (dist[t] - dmin) * w;
+      }
+      double H = log(S) + beta * E / S;
+      if (fabs(H - Hstar) <= tol || it == max_iter - 1) break;
+      if (H > Hstar) {
+        lo = beta;
+        beta = isinf(hi) ? 2.0 * beta : 0.5 * (beta + hi);
+      } else {
+        hi = beta;
+        beta = isinf(lo) ? 0.5 * beta : 0.5 * (beta + lo);
+      }
+    }
+    if (iters) iters[i] = it + 1;
+    beta_out[i] = beta;
+    for (int64_t t = 0; t < k; ++t) pcond[a + t] = exp(-beta * (dist[t] - dmin)) / S;
+    free(dist);
+  }
+  return TSGO_OK;
+}
+
+/*
+ * Joint affinities (Eq. 3): p_ij = (p_{j|i} + p_{i|j}) / T on the symmetric
+ * structure, T = sum over all entries of the numerator.  Returns T via *total.
+ */
+int tsgo_joint_P(int32_t n, const int64_t* rp, const int32_t* col, const double* pcond, double* P,
+                 double* total) {
+  double T = 0.0;
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int64_t t = find_in_row(rp, col, col[e], i);
+      if (t < 0) return TSGO_EBADCSR;
+      P[e] = pcond[e] + pcond[t];
+      T += P[e];
+    }
+  if (total) *total = T;
+  if (T > 0.0)
+    for (int64_t e = 0; e < rp[n]; ++e) P[e] /= T;
+  return TSGO_OK;
+}
+
+/* Student-t kernel w = (1 + ||y_i - y_j||^2)^-1 (Eq. 4 numerator). */
+static double kernel_w(const double* Y, int64_t i, int64_t j) {
+  double dx = Y[2 * i] - Y[2 * j];
+  double dy = Y[2 * i + 1] - Y[2 * j + 1];
+  return 1.0 / (1.0 + dx * dx + dy * dy);
+}
+
+/* Eq. 4 denominator: Z = sum_k sum_{l != k} w_kl over ordered pairs. */
+double tsgo_Z(int32_t n, const double* Y) {
+  double Z = 0.0;
+  for (int64_t k = 0; k < n; ++k)
+    for (int64_t l = 0; l < n; ++l)
+      if (l != k) Z += kernel_w(Y, k, l);
+  return Z;
+}
+
+/*
+ * Eq. 5: KL(P || Q) = sum_ij p_ij log(p_ij / q_ij), q_ij = w_ij / Z.
+ * Only entries with p_ij > 0 contribute (0 log 0 = 0).
+ */
+double tsgo_kl(int32_t n, const int64_t* rp, const int32_t* col, const double* P, const double* Y,
+               double* Z_out) {
+  double Z = tsgo_Z(n, Y);
+  double kl = 0.0;
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      if (!(P[e] > 0.0)) continue;
+      double q = kernel_w(Y, i, col[e]) / Z;
+      kl += P[e] * log(P[e] / q);
+    }
+  if (Z_out) *Z_out = Z;
+  return kl;
+}
+
+/*
+ * Gradient of Eq. 5 with the affinities multiplied by alpha (early
+ * exaggeration; alpha = 1 is the plain KL gradient):
+ *   g_i = 4 * sum_j (alpha p_ij - q_ij) w_ij (y_i - y_j)
+ *       = 4 * [ alpha sum_{j in N(i)} p_ij w_ij (y_i - y_j)
+ *               - (1/Z) sum_{j != i} w_ij^2 (y_i - y_j) ].
+ * G is n x 2.  Returns Z via *Z_out.
+ */
+int tsgo_gradient(int32_t n, const int64_t* rp, const int32_t* col, const double* P, const double* Y,
+                  double alpha, double* G, double* Z_out) {
+  double Z = tsgo_Z(n, Y);
+  for (int64_t i = 0; i < n; ++i) {
+    double ax = 0.0, ay = 0.0, rx = 0.0, ry = 0.0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int64_t j = col[e];
+      double w = kernel_w(Y, i, j);
+      ax += P[e] * w * (Y[2 * i] - Y[2 * j]);
+      ay += P[e] * w * (Y[2 * i + 1] - Y[2 * j + 1]);
+    }
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double w = kernel_w(Y, i, j);
+      rx += w * w * (Y[2 * i] - Y[2 * j]);
+      ry += w * w * (Y[2 * i + 1] - Y[2 * j + 1]);
+    }
+    G[2 * i] = 4.0 * (alpha * ax - rx / Z);
+    G[2 * i + 1] = 4.0 * (alpha * ay - ry / Z);
+  }
+  if (Z_out) *Z_out = Z;
+  return TSGO_OK;
+}
+
+/*
+ * Rows [i0, i1): F_rep_i = sum_{j != i} w_ij^2 (y_i - y_j) (n x 2 slots i0..i1-1
+ * of Frep) and zrow_i = sum_{j != i} w_ij, so that Z = sum_i zrow_i.  Lets a
+ * caller split the quadratic work over threads or check sampled rows.
+ */
+int tsgo_repulsion_rows(int32_t n, const double* Y, int32_t i0, int32_t i1, double* Frep, double* zrow) {
+  if (i0 < 0 || i1 > n || i0 > i1) return TSGO_EINVAL;
+  for (int64_t i = i0; i < i1; ++i) {
+    double rx = 0.0, ry = 0.0, z = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double w = kernel_w(Y, i, j);
+      z += w;
+      rx += w * w * (Y[2 * i] - Y[2 * j]);
+      ry += w * w * (Y[2 * i + 1] - Y[2 * j + 1]);
+    }
+    Frep[2 * (i - i0)] = rx;
+    Frep[2 * (i - i0) + 1] = ry;
+    zrow[i - i0] = z;
+  }
+  return TSGO_OK;
+}
+
+/* Attractive sums F_attr_i = sum_{j in N(i)} p_ij w_ij (y_i - y_j) for listed rows. */
+int tsgo_attraction_rows(int32_t n, const int64_t* rp, const int32_t* col, const double* P, const double* Y,
+                         const int32_t* rows, int32_t nrows, double* Fattr) {
+  for (int32_t r = 0; r < nrows; ++r) {
+    int64_t i = rows[r];
+    if (i < 0 || i >= n) return TSGO_EINVAL;
+    double ax = 0.0, ay = 0.0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int64_t j = col[e];
+      double w = kernel_w(Y, i, j);
+      ax += P[e] * w * (Y[2 * i] - Y[2 * j]);
+      ay += P[e] * w * (Y[2 * i + 1] - Y[2 * j + 1]);
+    }
+    Fattr[2 * r] = ax;
+    Fattr[2 * r + 1] = ay;
+  }
+  return TSGO_OK;
+}
+
+/*
+ * Gradient descent on Eq. 5 (the paper states only that the iteration count
+ * is a fixed constant, Sec. 3.3).  Schedule, per iteration t (0-based,
+ * counting from t0):
+ *   alpha = ee   if t < ee_iters else 1      (early exaggeration)
+ *   mu    = mom0 if t < ee_iters else mom1   (momentum)
+ *   g = gradient with alpha
+ *   per coordinate: gain += 0.2 if g * upd < 0, else gain *= 0.8;
+ *                   gain = max(gain, min_gain);
+ *                   upd = mu * upd - eta * gain * g;  y += upd
+ * Y, upd, gains are n x 2 and updated in place.
+ */
+int tsgo_optimize(int32_t n, const int64_t* rp, const int32_t* col, const double* P, double* Y, double* upd,
+                  double* gains, int32_t t0, int32_t n_iter, double ee, int32_t ee_iters, double mom0,
+                  double mom1, double eta, double min_gain) {
+  double* G = (double*)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+  if (!G) return TSGO_ENOMEM;
+  for (int32_t t = t0; t < t0 + n_iter; ++t) {
+    double alpha = t < ee_iters ? ee : 1.0;
+    double mu = t < ee_iters ? mom0 : mom1;
+    tsgo_gradient(n, rp, col, P, Y, alpha, G, NULL);
+    for (int64_t c = 0; c < 2 * (int64_t)n; ++c) {
+      if (G[c] * upd[c] < 0.0)
+        gains[c] += 0.2;
+      else
+        gains[c] *= 0.8;
+      if (gains[c] < min_gain) gains[c] = min_gain;
+      upd[c] = mu * upd[c] - eta * gains[c] * G[c];
+      Y[c] += upd[c];
+    }
+  }
+  free(G);
+  return TSGO_OK;
+}

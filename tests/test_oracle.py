@@ -1,0 +1,387 @@
+"""Pins for the FP64 oracle (CPU only).
+
+Each test checks the oracle against something other than itself: brute force
+on tiny inputs, closed forms, finite differences, library routines, or
+invariants that the definitions of the paper fix (Li, Xiao, Zhou, arXiv
+2310.11186, Sec. 2.1-2.2, Eqs. 2-5 and 7).  The cases are chosen so that a
+dropped term, a wrong sign, a wrong index or a transposed operand in the
+oracle fails at least one of them.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import tsgne_synth as synth
+
+
+def _rand_csr(n, m, seed, loops=True, dups=True):
+    """An arbitrary (asymmetric, unsorted, duplicated, looped) CSR."""
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, n, m)
+    dst = rng.integers(0, n, m)
+    if not loops:
+        ok = src != dst
+        src, dst = src[ok], dst[ok]
+    if dups and src.size:
+        src = np.concatenate([src, src[: m // 4]])
+        dst = np.concatenate([dst, dst[: m // 4]])
+    perm = rng.permutation(src.size)
+    src, dst = src[perm], dst[perm]
+    order = np.argsort(src, kind="stable")  # rows grouped, columns unsorted
+    src, dst = src[order], dst[order]
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, src + 1, 1)
+    rp = np.cumsum(rp)
+    return rp, dst.astype(np.int32)
+
+
+def _dense_P(n, rp, col, P):
+    D = np.zeros((n, n))
+    for i in range(n):
+        D[i, col[rp[i]:rp[i + 1]]] = P[rp[i]:rp[i + 1]]
+    return D
+
+
+# ----------------------------------------------------------------- structure
+
+
+@pytest.mark.parametrize("n,m,seed", [(1, 0, 0), (2, 1, 1), (7, 20, 2), (40, 150, 3), (100, 50, 4)])
+def test_structure_is_set_union(n, m, seed):
+    """Eq. 7 with graph-edge neighbours: N(i) = {j != i : (i,j) or (j,i) in G}."""
+    rp, col = _rand_csr(n, m, seed)
+    orp, ocol = oracle.structure(n, rp, col)
+    want = [set() for _ in range(n)]
+    for i in range(n):
+        for j in col[rp[i]:rp[i + 1]]:
+            if j != i:
+                want[i].add(int(j))
+                want[j].add(i)
+    for i in range(n):
+        got = ocol[orp[i]:orp[i + 1]].tolist()
+        assert got == sorted(want[i])
+    assert orp[0] == 0 and orp[-1] == ocol.size
+
+
+def test_structure_rejects_bad_csr():
+    good_rp = np.array([0, 1, 2], np.int64)
+    assert oracle.check_csr(2, good_rp, np.array([1, 0], np.int32)) == 0
+    assert oracle.check_csr(2, np.array([1, 1, 2], np.int64), np.array([1, 0], np.int32)) == -2
+    assert oracle.check_csr(2, np.array([0, 2, 1], np.int64), np.array([1, 0], np.int32)) == -2
+    assert oracle.check_csr(2, good_rp, np.array([1, 2], np.int32)) == -2
+    assert oracle.check_csr(2, good_rp, np.array([-1, 0], np.int32)) == -2
+    with pytest.raises(oracle.OracleError):
+        oracle.structure(2, good_rp, np.array([1, 5], np.int32))
+
+
+def test_transpose_slots():
+    rp, col = _rand_csr(30, 90, 7)
+    srp, scol = oracle.structure(30, rp, col)
+    t = oracle.transpose_slots(30, srp, scol)
+    rows = np.repeat(np.arange(30), np.diff(srp))
+    # entry t[e] sits in row col[e] and points back at row(e)
+    assert np.array_equal(scol[t], rows)
+    assert np.array_equal(rows[t], scol)
+    assert np.array_equal(t[t], np.arange(scol.size))
+
+
+# ------------------------------------------------------ conditional affinity
+
+
+def _graph_and_X(n=60, deg=12.0, d=16, seed=5):
+    g = synth.random_graph(n, deg, seed=seed)
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, d)).astype(np.float32)
+    return g, X
+
+
+@pytest.mark.parametrize("perp", [2.0, 3.0, 5.0, 8.5])
+def test_bisection_reaches_target_entropy(perp):
+    """Sec. 2.1: Perp(P_i) = 2^{H(P_i)} equals the user value, H in bits."""
+    g, X = _graph_and_X()
+    rp, col = oracle.structure(g.n, g.row_ptr, g.col)
+    pc, beta, iters = oracle.cond_affinity(g.n, rp, col, X, perp)
+    checked = 0
+    for i in range(g.n):
+        p = pc[rp[i]:rp[i + 1]]
+        k = p.size
+        if k == 0:
+            continue
+        assert abs(p.sum() - 1.0) < 1e-12
+        if k <= perp:
+            assert np.all(p == 1.0 / k)  # saturated rows are uniform
+            continue
+        H_bits = -(p * np.log2(p)).sum()
+        assert abs(2.0 ** H_bits - perp) / perp < 2e-5
+        checked += 1
+    assert checked > 10
+
+
+def test_affinity_is_gaussian_in_squared_distance():
+    """Eq. 2: ln p_{j|i} - ln p_{k|i} = -beta_i (|x_i-x_j|^2 - |x_i-x_k|^2)."""
+    g, X = _graph_and_X(d=7)
+    rp, col = oracle.structure(g.n, g.row_ptr, g.col)
+    pc, beta, _ = oracle.cond_affinity(g.n, rp, col, X, 3.0)
+    X64 = X.astype(np.float64)
+    for i in range(g.n):
+        nb = col[rp[i]:rp[i + 1]]
+        if nb.size <= 3:
+            continue
+        d2 = ((X64[nb] - X64[i]) ** 2).sum(axis=1)
+        lp = np.log(pc[rp[i]:rp[i + 1]])
+        np.testing.assert_allclose(lp - lp[0], -beta[i] * (d2 - d2[0]), rtol=1e-9, atol=1e-9)
+
+
+def test_bisection_two_level_row_against_brentq():
+    """Row with k1 neighbours at distance a and k2 at distance b: beta solves
+    H(beta) = ln perp, cross-checked with scipy's brentq on the closed form."""
+    brentq = pytest.importorskip("scipy.optimize").brentq
+    k1, k2, perp = 3, 9, 6.0
+    n = 1 + k1 + k2
+    # star graph around node 0; node positions on a line so distances are exact
+    X = np.zeros((n, 1))
+    X[1:1 + k1, 0] = 1.0   # distance^2 = 1
+    X[1 + k1:, 0] = 2.0    # distance^2 = 4
+    rp, col = synth.csr_from_edges(n, np.zeros(k1 + k2, np.int64), np.arange(1, n))
+    pc, beta, _ = oracle.cond_affinity(n, rp, col, X, perp, tol=1e-12, max_iter=200)
+
+    def H(bt):  # two-level row entropy in nats, shift by the smaller distance
+        e = math.exp(-bt * 3.0)
+        S = k1 + k2 * e
+        return math.log(S) + bt * (k2 * 3.0 * e) / S
+
+    root = brentq(lambda bt: H(bt) - math.log(perp), 1e-9, 50.0, xtol=1e-14)
+    assert abs(beta[0] - root) < 1e-8
+    p_near = 1.0 / (k1 + k2 * math.exp(-root * 3.0))
+    np.testing.assert_allclose(pc[rp[0]:rp[0] + k1], p_near, rtol=1e-9)
+
+
+# --------------------------------------------------------------- joint P
+
+
+def test_joint_P_symmetric_normalised():
+    """Eq. 3: p_ij = p_ji, sum P = 1, p > 0 exactly on the structure."""
+    g, X = _graph_and_X(n=80)
+    rp, col, P = oracle.build_P(g.n, g.row_ptr, g.col, X, 3.0)
+    t = oracle.transpose_slots(g.n, rp, col)
+    assert np.all(P > 0)
+    assert np.array_equal(P, P[t])
+    assert abs(P.sum() - 1.0) < 1e-12
+
+
+def test_joint_P_uniform_rows_closed_form():
+    """All rows saturated: p_ij = (1/deg_i + 1/deg_j) / T, T = 2 * #non-isolated."""
+    g = synth.sbm_equal(120, 4, 0.12, 0.01, seed=3)
+    X = synth.block_embedding(g.labels, 8, seed=3)
+    rp, col, P = oracle.build_P(g.n, g.row_ptr, g.col, X, 1000.0)
+    deg = np.diff(rp)
+    T = 2.0 * np.count_nonzero(deg)
+    rows = np.repeat(np.arange(g.n), deg)
+    np.testing.assert_allclose(P, (1.0 / deg[rows] + 1.0 / deg[col]) / T, rtol=1e-13)
+
+
+def test_joint_P_isolated_nodes_keep_sum_one():
+    rp = np.array([0, 1, 2, 2, 2], np.int64)  # 0-1 edge, nodes 2, 3 isolated
+    col = np.array([1, 0], np.int32)
+    X = np.arange(8, dtype=np.float32).reshape(4, 2)
+    srp, scol, P = oracle.build_P(4, rp, col, X, 30.0)
+    assert np.allclose(P, [0.5, 0.5])
+
+
+# ------------------------------------------------------------- Z, KL, grad
+
+
+def test_Z_two_points_and_dense():
+    """Eq. 4 denominator over ordered pairs."""
+    Y = np.array([[0.0, 0.0], [3.0, 4.0]])
+    assert oracle.Z(Y) == pytest.approx(2.0 / 26.0, rel=1e-15)
+    rng = np.random.default_rng(0)
+    Y = rng.normal(scale=3.0, size=(50, 2))
+    D2 = ((Y[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+    W = 1.0 / (1.0 + D2)
+    np.fill_diagonal(W, 0.0)
+    assert oracle.Z(Y) == pytest.approx(W.sum(), rel=1e-13)
+
+
+def test_kl_two_nodes_is_zero():
+    """2-node graph: p = q = 1/2 per ordered pair for any Y, KL = 0, g = 0."""
+    rp, col = np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32)
+    P = np.array([0.5, 0.5])
+    for Y in ([[0.0, 0.0], [1.0, 2.0]], [[5.0, -3.0], [5.0, -3.0]]):
+        v, _ = oracle.kl(2, rp, col, P, np.array(Y))
+        assert abs(v) < 1e-15
+        G, _ = oracle.gradient(2, rp, col, P, np.array(Y))
+        assert np.abs(G).max() < 1e-15
+
+
+def _path3(a):
+    rp, col = synth.csr_from_edges(3, np.array([0, 1]), np.array([1, 2]))
+    Y = np.array([[-a, 0.0], [0.0, 0.0], [a, 0.0]])
+    return rp, col, Y
+
+
+@pytest.mark.parametrize("a", [0.0, 0.3, 1.0, 2.5])
+def test_kl_path3_closed_form(a):
+    """Path 0-1-2, uniform rows: P has four entries 1/4 and
+    KL(a) = ln(1 + (1+a^2) / (2 (1+4a^2))) at Y = (-a,0), (0,0), (a,0)."""
+    rp, col, Y = _path3(a)
+    X = np.zeros((3, 1), np.float32)
+    srp, scol, P = oracle.build_P(3, rp, col, X, 30.0)
+    assert np.allclose(P, 0.25)
+    v, _ = oracle.kl(3, srp, scol, P, Y)
+    assert v == pytest.approx(math.log(1 + (1 + a * a) / (2 * (1 + 4 * a * a))), rel=1e-13, abs=1e-15)
+    G, _ = oracle.gradient(3, srp, scol, P, Y)
+    # middle node: zero by symmetry; end node: half the derivative of KL(a)
+    dkl = (-3 * a / (1 + 4 * a * a) ** 2) / (1 + (1 + a * a) / (2 * (1 + 4 * a * a)))
+    assert np.abs(G[1]).max() < 1e-15
+    assert G[2, 0] == pytest.approx(0.5 * dkl, rel=1e-12, abs=1e-15)
+    assert G[0, 0] == pytest.approx(-0.5 * dkl, rel=1e-12, abs=1e-15)
+    assert abs(G[0, 1]) < 1e-15 and abs(G[2, 1]) < 1e-15
+
+
+def _small_case(n=30, seed=11, perp=3.0, scale=2.0):
+    g = synth.random_graph(n, 6.0, seed=seed)
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, 5)).astype(np.float32)
+    rp, col, P = oracle.build_P(n, g.row_ptr, g.col, X, perp)
+    Y = rng.normal(scale=scale, size=(n, 2))
+    return rp, col, P, Y
+
+
+def test_kl_dense_brute_force_and_invariances():
+    """Eq. 5 from the full dense P and Q; KL >= 0; invariant to rigid motions."""
+    rp, col, P, Y = _small_case()
+    n = Y.shape[0]
+    Pd = _dense_P(n, rp, col, P)
+    D2 = ((Y[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+    W = 1.0 / (1.0 + D2)
+    np.fill_diagonal(W, 0.0)
+    Q = W / W.sum()
+    m = Pd > 0
+    want = (Pd[m] * np.log(Pd[m] / Q[m])).sum()
+    v, _ = oracle.kl(n, rp, col, P, Y)
+    assert v == pytest.approx(want, rel=1e-12)
+    assert v > 0
+    th = 0.7
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    v2, _ = oracle.kl(n, rp, col, P, Y @ R.T + np.array([3.0, -1.5]))
+    assert v2 == pytest.approx(v, rel=1e-12)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 4.0, 12.0])
+def test_gradient_matches_finite_differences(alpha):
+    """g = d f / dY with f(Y) = -alpha sum_e p_e ln w_e + ln Z, which is KL(P||Q)
+    up to a constant when alpha = 1 (Eq. 5); central differences in numpy."""
+    rp, col, P, Y = _small_case()
+    n = Y.shape[0]
+    rows = np.repeat(np.arange(n), np.diff(rp))
+
+    def f(Yv):
+        D2 = ((Yv[:, None, :] - Yv[None, :, :]) ** 2).sum(-1)
+        W = 1.0 / (1.0 + D2)
+        np.fill_diagonal(W, 0.0)
+        return -alpha * (P * np.log(W[rows, col])).sum() + math.log(W.sum())
+
+    G, _ = oracle.gradient(n, rp, col, P, Y, alpha)
+    FD = np.zeros_like(Y)
+    for i in range(n):
+        for c in range(2):
+            h = 1e-6 * max(1.0, abs(Y[i, c]))
+            Yp, Ym = Y.copy(), Y.copy()
+            Yp[i, c] += h
+            Ym[i, c] -= h
+            FD[i, c] = (f(Yp) - f(Ym)) / (2 * h)
+    assert np.linalg.norm(G - FD) / np.linalg.norm(FD) < 1e-6
+    if alpha == 1.0:
+        # the same derivative taken of the oracle's own KL
+        i, c = 3, 1
+        h = 1e-6
+        Yp, Ym = Y.copy(), Y.copy()
+        Yp[i, c] += h
+        Ym[i, c] -= h
+        d = (oracle.kl(n, rp, col, P, Yp)[0] - oracle.kl(n, rp, col, P, Ym)[0]) / (2 * h)
+        assert G[i, c] == pytest.approx(d, rel=1e-6)
+
+
+def test_gradient_sums_to_zero():
+    """Pairwise antisymmetric forces: sum_i g_i = 0."""
+    rp, col, P, Y = _small_case(n=50, seed=2)
+    G, _ = oracle.gradient(50, rp, col, P, Y, 12.0)
+    assert np.abs(G.sum(0)).max() < 1e-12 * np.abs(G).sum()
+
+
+def test_row_splits_agree_with_gradient():
+    """repulsion_rows / attraction_rows recombine into the gradient and Z."""
+    rp, col, P, Y = _small_case(n=40, seed=9)
+    n = 40
+    G1, Z = oracle.gradient(n, rp, col, P, Y, 1.0)
+    Fr, zr = oracle.repulsion_all(Y, threads=3)
+    assert zr.sum() == pytest.approx(Z, rel=1e-14)
+    Fa = oracle.attraction_rows(n, rp, col, P, Y, np.arange(n))
+    np.testing.assert_allclose(4.0 * (Fa - Fr / Z), G1, rtol=1e-12, atol=1e-15)
+    G5, _ = oracle.gradient(n, rp, col, P, Y, 5.0)
+    np.testing.assert_allclose(G5 - G1, 16.0 * Fa, rtol=1e-10, atol=1e-14)
+
+
+# --------------------------------------------------------------- optimiser
+
+
+def test_optimizer_two_nodes_does_not_move():
+    rp, col = np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32)
+    Y0 = np.array([[0.1, -0.2], [0.3, 0.4]])
+    # alpha = 1: p = q, the gradient vanishes up to rounding, nothing moves
+    Y, u, g = oracle.optimize(2, rp, col, np.array([0.5, 0.5]), Y0, 5, ee_iters=0)
+    np.testing.assert_allclose(Y, Y0, rtol=0, atol=1e-12)
+    # alpha = 12: attraction dominates, the two points approach each other
+    Y, u, g = oracle.optimize(2, rp, col, np.array([0.5, 0.5]), Y0, 1, learning_rate=1e-3)
+    assert np.linalg.norm(Y[0] - Y[1]) < np.linalg.norm(Y0[0] - Y0[1])
+
+
+def test_optimizer_hand_trace_path3():
+    """Three iterations on the symmetric 3-node path, traced by hand with the
+    closed-form gradient (alpha = 1 throughout, momentum 0.5, eta = 10):
+        gains start at 1 and updates at 0; g*upd < 0 -> gain + 0.2 else
+        gain * 0.8; upd = mu*upd - eta*gain*g; y += upd."""
+    def g_end(a):  # d KL / d y_2x at half-width a (closed form above)
+        return 0.5 * (-3 * a / (1 + 4 * a * a) ** 2) / (1 + (1 + a * a) / (2 * (1 + 4 * a * a)))
+
+    eta, mu = 10.0, 0.5
+    a0 = 0.05
+    # t = 0: upd = 0 -> product 0 -> gain 0.8
+    g0 = g_end(a0); gain1 = 0.8; u1 = -eta * gain1 * g0; a1 = a0 + u1
+    # t = 1: g1 has the sign of g0 while u1 has the opposite one -> gain 1.0
+    g1 = g_end(a1); assert g1 * u1 < 0; gain2 = gain1 + 0.2
+    u2 = mu * u1 - eta * gain2 * g1; a2 = a1 + u2
+    # t = 2
+    g2 = g_end(a2); gain3 = gain2 + 0.2 if g2 * u2 < 0 else gain2 * 0.8
+    u3 = mu * u2 - eta * gain3 * g2; a3 = a2 + u3
+    rp, col, Y0 = _path3(a0)
+    P = np.full(4, 0.25)
+    Y, u, gains = oracle.optimize(3, rp, col, P, Y0, 3, early_exag=1.0, ee_iters=0, momentum0=mu,
+                                  momentum1=mu, learning_rate=eta)
+    assert Y[2, 0] == pytest.approx(a3, rel=1e-12)
+    assert Y[0, 0] == pytest.approx(-a3, rel=1e-12)
+    assert np.abs(Y[1]).max() < 1e-15 and np.abs(Y[:, 1]).max() < 1e-15
+    assert gains[2, 0] == pytest.approx(gain3, rel=1e-14)
+    assert gains[2, 1] == pytest.approx(0.8 ** 3, rel=1e-14)  # y-gradient stays 0
+    assert u[2, 0] == pytest.approx(u3, rel=1e-12)
+
+
+def test_optimizer_schedule_switches_at_ee_iters():
+    """Splitting a run at any point gives the same trajectory (state = Y, upd,
+    gains, t); the exaggeration phase differs from the plain phase."""
+    rp, col, P, Y = _small_case(n=25, seed=4, scale=1e-2)
+    full = oracle.optimize(25, rp, col, P, Y, 12, ee_iters=5, learning_rate=50.0)
+    a = oracle.optimize(25, rp, col, P, Y, 7, ee_iters=5, learning_rate=50.0)
+    b = oracle.optimize(25, rp, col, P, a[0], 5, upd=a[1], gains=a[2], t0=7, ee_iters=5, learning_rate=50.0)
+    for x, y in zip(full, b):
+        assert np.array_equal(x, y)
+    no_ee = oracle.optimize(25, rp, col, P, Y, 12, ee_iters=0, learning_rate=50.0)
+    assert not np.allclose(no_ee[0], full[0])
+
+
+def test_auto_learning_rate():
+    assert oracle.auto_learning_rate(2000, 12.0) == 50.0
+    assert oracle.auto_learning_rate(300000, 12.0) == 6250.0
