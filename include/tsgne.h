@@ -1,0 +1,208 @@
+/*
+ * tsgne.h -- C ABI of the GB300 t-SGNE layout library (libtsgne.so).
+ *
+ * t-SGNE (Li, Xiao, Zhou, "Efficiently Visualizing Large Graphs",
+ * arXiv 2310.11186) places the nodes of an undirected graph G in 2-D: it runs
+ * t-SNE (Sec. 2.1, Eqs. 2-5) with the neighbour graph taken from G instead of
+ * from the embedding X (Sec. 2.2, Eq. 7).  This library implements the layout
+ * loop on one GPU:
+ *
+ *   tsgne_build_P  neighbour structure (Eq. 7), conditional affinities with
+ *                  the perplexity binary search (Eq. 2, Sec. 2.1) and the
+ *                  joint affinities (Eq. 3);
+ *   tsgne_step     one gradient-descent iteration on KL(P||Q) (Eq. 5): the
+ *                  sparse attraction over P, the exact all-pairs Student-t
+ *                  repulsion with its normaliser Z (Eq. 4), and the
+ *                  gains / momentum / early-exaggeration update;
+ *   tsgne_run      many iterations (CUDA-graph replay);
+ *   tsgne_kl       the objective of Eq. 5 at the current layout.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a tsgne_status; nothing aborts and no C++ exception
+ *     crosses this boundary.  On error, tsgne_last_error(ctx) holds a message.
+ *     TSGNE_ERR_CUDA leaves the context unusable (destroy it); every other
+ *     error leaves it as it was before the call unless stated otherwise.
+ *   - A context is bound to one CUDA device (the current one at creation) and
+ *     one stream; it is not thread-safe.  Distinct contexts are independent.
+ *   - Input pointers are borrowed for the duration of the call and copied.
+ *     ptr_kind says where they live (TSGNE_PTR_HOST or TSGNE_PTR_DEVICE).
+ *     Output buffers are owned by the caller and must have the stated size.
+ *   - Calls that return results to the caller synchronise the context's
+ *     stream; tsgne_step only enqueues work.
+ *   - Layout Y is n x 2 row-major float (x0, y0, x1, y1, ...).  Coordinates
+ *     must stay below 1e18 in magnitude (the repulsion pads ragged tiles with
+ *     points at 1e30 whose kernel value underflows to exactly zero).
+ */
+#ifndef TSGNE_H
+#define TSGNE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsgne_ctx tsgne_ctx;
+
+typedef enum {
+  TSGNE_OK = 0,
+  TSGNE_ERR_INVALID_ARG = 1, /* bad size, NULL pointer, perplexity <= 1, n < 2, ... */
+  TSGNE_ERR_BAD_CSR = 2,     /* row_ptr[0] != 0, decreasing row_ptr, column outside [0, n) */
+  TSGNE_ERR_OOM = 3,         /* device allocation failed; ctx unchanged */
+  TSGNE_ERR_CUDA = 4,        /* CUDA runtime error; ctx must be destroyed */
+  TSGNE_ERR_NOT_BUILT = 5,   /* call needs P (tsgne_build_P / tsgne_set_P) or Y first */
+  TSGNE_ERR_NONFINITE = 6,   /* NaN / Inf met in X, P or the layout */
+  TSGNE_ERR_TIMEOUT = 7,     /* a bounded device-side wait ran out */
+  TSGNE_ERR_CANCELLED = 8    /* work cancelled by the caller */
+} tsgne_status;
+
+typedef enum { TSGNE_PTR_HOST = 0, TSGNE_PTR_DEVICE = 1 } tsgne_ptr_kind;
+
+/*
+ * Parameters.  Only the perplexity comes from the paper (Sec. 2.1: typically
+ * 5-50, default 30); the paper gives no optimiser, so the published t-SNE
+ * schedule is the default: early exaggeration 12 for 250 iterations,
+ * momentum 0.5 then 0.8, learning rate max(n / early_exag / 4, 50), gains
+ * +0.2 / x0.8 with a floor of 0.01.
+ */
+typedef struct {
+  float perplexity;        /* target Perp(P_i) = 2^{H(P_i)} (Sec. 2.1); > 1 */
+  int32_t k_nn;            /* 0: neighbours = graph edges (the only value accepted) */
+  float early_exag;        /* alpha multiplying P in the gradient while t < ee_iters */
+  int32_t ee_iters;        /* length of the early-exaggeration phase */
+  float momentum0;         /* momentum while t < ee_iters */
+  float momentum1;         /* momentum afterwards */
+  float learning_rate;     /* <= 0: max(n / early_exag / 4, 50) */
+  float min_gain;          /* floor of the per-coordinate gains */
+  float bisect_tol;        /* |H_i - ln perp| tolerance of the bisection, nats */
+  int32_t bisect_max_iter; /* max entropy evaluations per row */
+  uint64_t seed;           /* seed of tsgne_init_Y(ctx, NULL, ...) */
+  int32_t precision;       /* 0: FP32 storage of Y and P (the only value accepted) */
+  int32_t profile;         /* 1: time every kernel with CUDA events (see tsgne_kernel_times) */
+  int64_t spin_budget_cycles; /* bound on device-side waits (reserved; > 0) */
+} tsgne_config;
+
+/* Fills *cfg with the defaults listed above (perplexity 30). */
+void tsgne_config_default(tsgne_config* cfg);
+
+/*
+ * Creates a context on the current CUDA device.  cuda_stream is a
+ * cudaStream_t the context will use for all of its work; NULL creates a
+ * private non-blocking stream.  *out receives the context (NULL on error).
+ */
+tsgne_status tsgne_create(tsgne_ctx** out, const tsgne_config* cfg, void* cuda_stream);
+
+/* Frees every device buffer of the context.  NULL is ignored. */
+void tsgne_destroy(tsgne_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Valid until the next call. */
+const char* tsgne_last_error(const tsgne_ctx* ctx);
+
+/* Static name of a status code. */
+const char* tsgne_status_string(tsgne_status s);
+
+/*
+ * Builds the joint affinities P from a graph and its high-dimensional
+ * embedding (the t-SGNE input pair (G, X), Sec. 2.2):
+ *   1. neighbour structure N(i) = { j != i : (i,j) or (j,i) in G } (Eq. 7
+ *      with the graph's edges as neighbours): symmetric, sorted, unique,
+ *      no self loops;
+ *   2. p_{j|i} = exp(-beta_i ||x_i-x_j||^2) / sum_{k in N(i)} exp(...) (Eq. 2
+ *      over N(i)), beta_i by bisection until |H_i - ln perplexity| <=
+ *      bisect_tol (Sec. 2.1); rows with |N(i)| <= perplexity are uniform;
+ *   3. p_ij = (p_{j|i} + p_{i|j}) / T, T the sum of all numerators (Eq. 3;
+ *      T = 2n when no node is isolated), so sum P = 1.
+ * n >= 2 nodes; row_ptr int64[n+1] with row_ptr[0] = 0, non-decreasing;
+ * col_idx int32[row_ptr[n]] in [0, n) (any order, duplicates and self loops
+ * allowed, either direction suffices); X float[n*d] row-major, d >= 1.
+ * All three arrays live where ptr_kind says.  Resets the layout state
+ * (tsgne_init_Y must follow).  Errors: INVALID_ARG, BAD_CSR, NONFINITE (X
+ * produced a non-finite affinity), OOM.
+ */
+tsgne_status tsgne_build_P(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                           const float* X, int32_t d, int32_t ptr_kind);
+
+/*
+ * Installs a joint affinity matrix computed elsewhere.  The structure must
+ * already be symmetric, sorted, unique and loop-free (else BAD_CSR); P float
+ * [row_ptr[n]] holds p_ij per entry (not checked for symmetry or sum).
+ * Resets the layout state like tsgne_build_P.
+ */
+tsgne_status tsgne_set_P(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                         const float* P, int32_t ptr_kind);
+
+/* Number of nodes and of stored affinities (2|E| after symmetrisation). */
+tsgne_status tsgne_get_sizes(tsgne_ctx* ctx, int32_t* n, int64_t* nnz);
+
+/*
+ * Copies the symmetric structure and P out: row_ptr int64[n+1], col int32[nnz],
+ * val float[nnz]; any pointer may be NULL to skip it.
+ */
+tsgne_status tsgne_get_P(tsgne_ctx* ctx, int64_t* row_ptr, int32_t* col, float* val, int32_t ptr_kind);
+
+/*
+ * Sets the initial layout and resets the optimiser (updates 0, gains 1,
+ * iteration 0).  Y0 float[n*2]; NULL draws Y0 ~ N(0, 1e-4^2) on the device
+ * from cfg.seed with SplitMix64 in counter mode and Box-Muller.
+ */
+tsgne_status tsgne_init_Y(tsgne_ctx* ctx, const float* Y0, int32_t ptr_kind);
+
+/*
+ * One iteration, enqueued on the context's stream (no host synchronisation):
+ * repulsion F^r_i = sum_{j != i} w_ij^2 (y_i - y_j) and Z = sum_{k != l} w_kl
+ * (Eq. 4, w = (1 + ||y_k - y_l||^2)^-1, Z accumulated in FP64), attraction
+ * F^a_i = sum_{j in N(i)} p_ij w_ij (y_i - y_j), gradient
+ * g = 4 (alpha F^a - F^r / Z) of Eq. 5, then gains, momentum and y += update.
+ * A non-finite layout is reported by the next synchronising call.
+ */
+tsgne_status tsgne_step(tsgne_ctx* ctx);
+
+/* n_iter iterations by CUDA-graph replay; synchronises at the end. */
+tsgne_status tsgne_run(tsgne_ctx* ctx, int32_t n_iter);
+
+/* KL(P || Q) of Eq. 5 at the current layout (one repulsion pass for Z); synchronises. */
+tsgne_status tsgne_kl(tsgne_ctx* ctx, double* kl_out);
+
+/*
+ * Gradient of Eq. 5 at the current layout with P multiplied by alpha
+ * (alpha = 1: the plain KL gradient), without changing any state.
+ * g_out float[n*2] where ptr_kind says; z_out (host, may be NULL) receives Z.
+ */
+tsgne_status tsgne_gradient(tsgne_ctx* ctx, float alpha, float* g_out, double* z_out, int32_t ptr_kind);
+
+/* Current layout into Y_out float[n*2]. */
+tsgne_status tsgne_get_Y(tsgne_ctx* ctx, float* Y_out, int32_t ptr_kind);
+
+/*
+ * Optimiser state for checkpoint / resume: layout, updates and gains
+ * (float[n*2] each, any may be NULL) and the iteration counter (host).
+ * set_state restores exactly what get_state returned, so a resumed run is
+ * bit-identical to an uninterrupted one.
+ */
+tsgne_status tsgne_get_state(tsgne_ctx* ctx, float* Y, float* update, float* gains, int32_t* iter,
+                             int32_t ptr_kind);
+tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update, const float* gains,
+                             int32_t iter, int32_t ptr_kind);
+
+/*
+ * Profiling (cfg.profile = 1): cumulative device time in ms and launch count
+ * of each kernel class since the last reset, measured with CUDA events on
+ * the context's stream.  Classes: 0 repulsion, 1 attraction+update,
+ * 2 gradient export, 3 KL, 4 build.  ms and launches hold n entries (n <= 5).
+ * reset != 0 clears the counters after reading.  Synchronises.
+ */
+tsgne_status tsgne_kernel_times(tsgne_ctx* ctx, double* ms, int64_t* launches, int32_t n, int32_t reset);
+
+/* Launch geometry of the repulsion pass: grid CTAs, threads per CTA, i per
+ * thread, j-tile, j-chunks, pad length.  Any pointer may be NULL. */
+tsgne_status tsgne_repulsion_shape(tsgne_ctx* ctx, int32_t* grid, int32_t* block, int32_t* i_per_thread,
+                                   int32_t* j_tile, int32_t* j_chunks, int32_t* n_pad);
+
+/* Waits for all work of the context; reports a pending NONFINITE layout. */
+tsgne_status tsgne_sync(tsgne_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSGNE_H */

@@ -1,0 +1,436 @@
+"""GB300-native t-SGNE layout loop: thin Python binding of libtsgne.so.
+
+t-SGNE (Li, Xiao, Zhou, "Efficiently Visualizing Large Graphs", arXiv
+2310.11186, Sec. 2.2) lays out the nodes of a graph G in 2-D by running t-SNE
+(Sec. 2.1) with the neighbour graph taken from G.  All of the computation
+runs in the CUDA kernels of ``libtsgne.so`` (declared in ``include/tsgne.h``);
+this module only marshals arguments through ctypes.  The functions keep the
+C names (``tsgne_build_P``, ``tsgne_step``, ``tsgne_run``, ``tsgne_kl``, ...);
+``Layout`` wraps them in a small class.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA);
+device tensors are passed to the library as device pointers.  There is no
+CPU fallback: if the library is not built, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "TsgneError",
+    "Config",
+    "lib",
+    "library_path",
+    "EXPORTS",
+    "tsgne_config_default",
+    "tsgne_create",
+    "tsgne_destroy",
+    "tsgne_last_error",
+    "tsgne_status_string",
+    "tsgne_build_P",
+    "tsgne_set_P",
+    "tsgne_get_sizes",
+    "tsgne_get_P",
+    "tsgne_init_Y",
+    "tsgne_step",
+    "tsgne_run",
+    "tsgne_kl",
+    "tsgne_gradient",
+    "tsgne_get_Y",
+    "tsgne_get_state",
+    "tsgne_set_state",
+    "tsgne_kernel_times",
+    "tsgne_repulsion_shape",
+    "tsgne_sync",
+    "Layout",
+    "KERNEL_CLASSES",
+]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_PKG, "lib", "libtsgne.so")
+
+PTR_HOST, PTR_DEVICE = 0, 1
+KERNEL_CLASSES = ("repulsion", "attract_update", "gradient", "kl", "build")
+
+STATUS = {
+    0: "TSGNE_OK",
+    1: "TSGNE_ERR_INVALID_ARG",
+    2: "TSGNE_ERR_BAD_CSR",
+    3: "TSGNE_ERR_OOM",
+    4: "TSGNE_ERR_CUDA",
+    5: "TSGNE_ERR_NOT_BUILT",
+    6: "TSGNE_ERR_NONFINITE",
+    7: "TSGNE_ERR_TIMEOUT",
+    8: "TSGNE_ERR_CANCELLED",
+}
+
+
+class TsgneError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{self.name}: {message}")
+
+
+class Config(ctypes.Structure):
+    """Mirror of ``tsgne_config``."""
+
+    _fields_ = [
+        ("perplexity", ctypes.c_float),
+        ("k_nn", ctypes.c_int32),
+        ("early_exag", ctypes.c_float),
+        ("ee_iters", ctypes.c_int32),
+        ("momentum0", ctypes.c_float),
+        ("momentum1", ctypes.c_float),
+        ("learning_rate", ctypes.c_float),
+        ("min_gain", ctypes.c_float),
+        ("bisect_tol", ctypes.c_float),
+        ("bisect_max_iter", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("precision", ctypes.c_int32),
+        ("profile", ctypes.c_int32),
+        ("spin_budget_cycles", ctypes.c_int64),
+    ]
+
+
+_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_st = ctypes.c_int
+
+# name -> (restype, argtypes); the declarations of include/tsgne.h
+EXPORTS = {
+    "tsgne_config_default": (None, [ctypes.POINTER(Config)]),
+    "tsgne_create": (_st, [ctypes.POINTER(_p), ctypes.POINTER(Config), _p]),
+    "tsgne_destroy": (None, [_p]),
+    "tsgne_last_error": (ctypes.c_char_p, [_p]),
+    "tsgne_status_string": (ctypes.c_char_p, [_st]),
+    "tsgne_build_P": (_st, [_p, _i32, _p, _p, _p, _i32, _i32]),
+    "tsgne_set_P": (_st, [_p, _i32, _p, _p, _p, _i32]),
+    "tsgne_get_sizes": (_st, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "tsgne_get_P": (_st, [_p, _p, _p, _p, _i32]),
+    "tsgne_init_Y": (_st, [_p, _p, _i32]),
+    "tsgne_step": (_st, [_p]),
+    "tsgne_run": (_st, [_p, _i32]),
+    "tsgne_kl": (_st, [_p, ctypes.POINTER(ctypes.c_double)]),
+    "tsgne_gradient": (_st, [_p, ctypes.c_float, _p, ctypes.POINTER(ctypes.c_double), _i32]),
+    "tsgne_get_Y": (_st, [_p, _p, _i32]),
+    "tsgne_get_state": (_st, [_p, _p, _p, _p, ctypes.POINTER(_i32), _i32]),
+    "tsgne_set_state": (_st, [_p, _p, _p, _p, _i32, _i32]),
+    "tsgne_kernel_times": (_st, [_p, _p, _p, _i32, _i32]),
+    "tsgne_repulsion_shape": (_st, [_p] + [ctypes.POINTER(_i32)] * 6),
+    "tsgne_sync": (_st, [_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise RuntimeError(
+                f"{library_path} is missing: build it with `python -m paper_2310_11186_gb300.build` "
+                "(there is no CPU fallback)")
+        L = ctypes.CDLL(library_path)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------- marshalling
+
+def _torch():
+    try:
+        import torch  # noqa: F401
+        return torch
+    except Exception:  # pragma: no cover
+        return None
+
+
+def _as_buffer(a, dtype):
+    """(pointer, ptr_kind, keep-alive object) for a numpy array or torch tensor."""
+    if a is None:
+        return None, PTR_HOST, None
+    torch = _torch()
+    if torch is not None and isinstance(a, torch.Tensor):
+        tdt = {np.float32: torch.float32, np.int32: torch.int32, np.int64: torch.int64}[np.dtype(dtype).type]
+        t = a.contiguous()
+        if t.dtype != tdt:
+            t = t.to(tdt)
+        kind = PTR_DEVICE if t.is_cuda else PTR_HOST
+        return ctypes.c_void_p(t.data_ptr()), kind, t
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), PTR_HOST, arr
+
+
+def _check(ctx, status):
+    if status != 0:
+        msg = lib().tsgne_last_error(ctx).decode() if ctx else ""
+        raise TsgneError(status, msg)
+
+
+# ------------------------------------------------------------ C functions
+
+def tsgne_config_default(**overrides) -> Config:
+    c = Config()
+    lib().tsgne_config_default(ctypes.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def tsgne_create(config: Config | None = None, stream=None):
+    """Returns a context handle; stream is a torch.cuda.Stream, a raw handle or None."""
+    handle = ctypes.c_void_p()
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+    st = lib().tsgne_create(ctypes.byref(handle), ctypes.byref(config) if config is not None else None, s)
+    if st != 0:
+        raise TsgneError(st, "tsgne_create failed")
+    return handle
+
+
+def tsgne_destroy(ctx) -> None:
+    lib().tsgne_destroy(ctx)
+
+
+def tsgne_last_error(ctx) -> str:
+    return lib().tsgne_last_error(ctx).decode()
+
+
+def tsgne_status_string(status: int) -> str:
+    return lib().tsgne_status_string(status).decode()
+
+
+def _same_kind(*bufs):
+    kinds = {b[1] for b in bufs if b[0] is not None}
+    if len(kinds) > 1:
+        raise ValueError("inputs of one call must all be on the host or all on the device")
+    return kinds.pop() if kinds else PTR_HOST
+
+
+def tsgne_build_P(ctx, n, row_ptr, col_idx, X):
+    rp = _as_buffer(row_ptr, np.int64)
+    ci = _as_buffer(col_idx, np.int32)
+    x = _as_buffer(X, np.float32)
+    d = int(X.shape[1])
+    kind = _same_kind(rp, ci, x)
+    _check(ctx, lib().tsgne_build_P(ctx, int(n), rp[0], ci[0], x[0], d, kind))
+
+
+def tsgne_set_P(ctx, n, row_ptr, col_idx, P):
+    rp = _as_buffer(row_ptr, np.int64)
+    ci = _as_buffer(col_idx, np.int32)
+    pv = _as_buffer(P, np.float32)
+    kind = _same_kind(rp, ci, pv)
+    _check(ctx, lib().tsgne_set_P(ctx, int(n), rp[0], ci[0], pv[0], kind))
+
+
+def tsgne_get_sizes(ctx):
+    n = _i32()
+    nnz = _i64()
+    _check(ctx, lib().tsgne_get_sizes(ctx, ctypes.byref(n), ctypes.byref(nnz)))
+    return n.value, nnz.value
+
+
+def tsgne_get_P(ctx):
+    """(row_ptr int64[n+1], col int32[nnz], P float32[nnz]) as numpy arrays."""
+    n, nnz = tsgne_get_sizes(ctx)
+    rp = np.zeros(n + 1, np.int64)
+    col = np.zeros(max(nnz, 1), np.int32)
+    val = np.zeros(max(nnz, 1), np.float32)
+    _check(ctx, lib().tsgne_get_P(ctx, rp.ctypes.data_as(_p), col.ctypes.data_as(_p), val.ctypes.data_as(_p),
+                                  PTR_HOST))
+    return rp, col[:nnz], val[:nnz]
+
+
+def tsgne_init_Y(ctx, Y0=None):
+    y = _as_buffer(Y0, np.float32)
+    _check(ctx, lib().tsgne_init_Y(ctx, y[0], y[1]))
+
+
+def tsgne_step(ctx):
+    _check(ctx, lib().tsgne_step(ctx))
+
+
+def tsgne_run(ctx, n_iter: int):
+    _check(ctx, lib().tsgne_run(ctx, int(n_iter)))
+
+
+def tsgne_kl(ctx) -> float:
+    v = ctypes.c_double()
+    _check(ctx, lib().tsgne_kl(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def _out(n, out):
+    if out is None:
+        out = np.zeros((n, 2), np.float32)
+    buf = _as_buffer(out, np.float32)
+    if buf[2] is not out and not (hasattr(out, "data_ptr") and buf[2].data_ptr() == out.data_ptr()):
+        raise ValueError("output must be a contiguous float32 array")
+    return out, buf
+
+
+def tsgne_gradient(ctx, alpha: float = 1.0, out=None):
+    """(g n x 2, Z): gradient of Eq. 5 with P scaled by alpha, and the normaliser."""
+    n, _ = tsgne_get_sizes(ctx)
+    out, buf = _out(n, out)
+    z = ctypes.c_double()
+    _check(ctx, lib().tsgne_gradient(ctx, float(alpha), buf[0], ctypes.byref(z), buf[1]))
+    return out, z.value
+
+
+def tsgne_get_Y(ctx, out=None):
+    n, _ = tsgne_get_sizes(ctx)
+    out, buf = _out(n, out)
+    _check(ctx, lib().tsgne_get_Y(ctx, buf[0], buf[1]))
+    return out
+
+
+def tsgne_get_state(ctx):
+    n, _ = tsgne_get_sizes(ctx)
+    Y = np.zeros((n, 2), np.float32)
+    U = np.zeros((n, 2), np.float32)
+    G = np.zeros((n, 2), np.float32)
+    it = _i32()
+    _check(ctx, lib().tsgne_get_state(ctx, Y.ctypes.data_as(_p), U.ctypes.data_as(_p), G.ctypes.data_as(_p),
+                                      ctypes.byref(it), PTR_HOST))
+    return Y, U, G, it.value
+
+
+def tsgne_set_state(ctx, Y, update=None, gains=None, iteration=0):
+    y = _as_buffer(Y, np.float32)
+    u = _as_buffer(update, np.float32)
+    g = _as_buffer(gains, np.float32)
+    kind = _same_kind(y, u, g)
+    _check(ctx, lib().tsgne_set_state(ctx, y[0], u[0], g[0], int(iteration), kind))
+
+
+def tsgne_kernel_times(ctx, reset: bool = False):
+    """{class: (ms, launches)} accumulated in profile mode."""
+    ms = np.zeros(len(KERNEL_CLASSES))
+    nl = np.zeros(len(KERNEL_CLASSES), np.int64)
+    _check(ctx, lib().tsgne_kernel_times(ctx, ms.ctypes.data_as(_p), nl.ctypes.data_as(_p), len(KERNEL_CLASSES),
+                                         int(bool(reset))))
+    return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def tsgne_repulsion_shape(ctx):
+    vals = [_i32() for _ in range(6)]
+    _check(ctx, lib().tsgne_repulsion_shape(ctx, *[ctypes.byref(v) for v in vals]))
+    keys = ("grid", "block", "i_per_thread", "j_tile", "j_chunks", "n_pad")
+    return {k: v.value for k, v in zip(keys, vals)}
+
+
+def tsgne_sync(ctx):
+    _check(ctx, lib().tsgne_sync(ctx))
+
+
+# ------------------------------------------------------------ convenience
+
+class Layout:
+    """One graph's layout state on the GPU.
+
+    >>> lay = Layout(perplexity=30.0)
+    >>> lay.build_P(row_ptr, col, X)      # CSR + embedding (host or device)
+    >>> lay.init_Y(Y0)                    # or None: N(0, 1e-4^2) from the seed
+    >>> lay.run(1000); Y = lay.get_Y(); kl = lay.kl()
+    """
+
+    def __init__(self, config: Config | None = None, stream=None, **overrides):
+        cfg = config if config is not None else tsgne_config_default()
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.config = cfg
+        self._stream = stream
+        if stream is None:
+            torch = _torch()
+            if torch is not None and torch.cuda.is_available():
+                self._stream = torch.cuda.Stream()
+        self.ctx = tsgne_create(cfg, self._stream)
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def _order_after_torch(self):
+        torch = _torch()
+        if torch is not None and self._stream is not None and hasattr(self._stream, "wait_stream"):
+            self._stream.wait_stream(torch.cuda.current_stream())
+
+    def build_P(self, row_ptr, col, X):
+        self._order_after_torch()
+        tsgne_build_P(self.ctx, len(row_ptr) - 1, row_ptr, col, X)
+
+    def set_P(self, row_ptr, col, P):
+        self._order_after_torch()
+        tsgne_set_P(self.ctx, len(row_ptr) - 1, row_ptr, col, P)
+
+    def init_Y(self, Y0=None):
+        self._order_after_torch()
+        tsgne_init_Y(self.ctx, Y0)
+
+    def step(self):
+        tsgne_step(self.ctx)
+
+    def run(self, n_iter):
+        tsgne_run(self.ctx, n_iter)
+
+    def kl(self):
+        return tsgne_kl(self.ctx)
+
+    def gradient(self, alpha=1.0, out=None):
+        return tsgne_gradient(self.ctx, alpha, out)
+
+    def get_Y(self, out=None):
+        return tsgne_get_Y(self.ctx, out)
+
+    def get_P(self):
+        return tsgne_get_P(self.ctx)
+
+    def get_state(self):
+        return tsgne_get_state(self.ctx)
+
+    def set_state(self, Y, update=None, gains=None, iteration=0):
+        self._order_after_torch()
+        tsgne_set_state(self.ctx, Y, update, gains, iteration)
+
+    def sizes(self):
+        return tsgne_get_sizes(self.ctx)
+
+    def kernel_times(self, reset=False):
+        return tsgne_kernel_times(self.ctx, reset)
+
+    def repulsion_shape(self):
+        return tsgne_repulsion_shape(self.ctx)
+
+    def sync(self):
+        tsgne_sync(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            tsgne_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,680 @@
+// C ABI of libtsgne.so (declared in include/tsgne.h): context ownership,
+// argument validation, host/device copies, CUDA-graph replay of iterations
+// and per-kernel CUDA-event profiling.  All arithmetic runs in the kernels of
+// structure.cu, affinity.cu, repulsion.cu and iterate.cu.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tsgne_internal.cuh"
+
+namespace tsgne {
+
+std::string& last_msg() {
+  thread_local std::string m;
+  return m;
+}
+
+tsgne_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  std::string s = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" + std::to_string(line) + ")";
+  last_msg() = s;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // not sticky: clear it
+    return TSGNE_ERR_OOM;
+  }
+  return TSGNE_ERR_CUDA;
+}
+
+namespace {
+
+__global__ void k_cmp_i64(const int64_t* a, const int64_t* b, int64_t n, uint32_t* neq) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    if (a[k] != b[k]) atomicOr(neq, 1u);
+}
+__global__ void k_cmp_i32(const int32_t* a, const int32_t* b, int64_t n, uint32_t* neq) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    if (a[k] != b[k]) atomicOr(neq, 1u);
+}
+
+constexpr int kClasses = 5;  // repulsion, attraction+update, gradient, KL, build
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+}  // namespace tsgne
+
+using namespace tsgne;
+
+struct tsgne_ctx {
+  tsgne_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int sms = 1;
+  std::string err;
+
+  int n = 0;
+  int64_t nnz = 0;
+  bool have_P = false;
+  bool have_Y = false;
+  bool poisoned = false;
+  float eta = 0.f;
+  RepShape shape;
+
+  DevBuf<int64_t> rp;
+  DevBuf<int32_t> col;
+  DevBuf<float> P;
+  DevBuf<float2> Y[2];
+  int cur = 0;
+  DevBuf<float2> upd, gains, frep, grad;
+  DevBuf<double> zpart, klpart;
+  DevBuf<Sched> sched;
+
+  cudaGraphExec_t g2[2] = {nullptr, nullptr};  // two iterations starting from buffer 0 / 1
+
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> spare;
+  double prof_ms[kClasses] = {0, 0, 0, 0, 0};
+  int64_t prof_n[kClasses] = {0, 0, 0, 0, 0};
+
+  ~tsgne_ctx() {
+    reset_graphs();
+    for (auto& r : pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : spare) cudaEventDestroy(e);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+  void reset_graphs() {
+    for (auto& g : g2)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+  }
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+tsgne_status fail(tsgne_ctx* ctx, tsgne_status st, const std::string& msg = std::string()) {
+  if (ctx) {
+    ctx->err = msg.empty() ? last_msg() : msg;
+    if (st == TSGNE_ERR_CUDA) ctx->poisoned = true;
+  }
+  return st;
+}
+
+#define API_TRY(ctx, call)                        \
+  do {                                            \
+    tsgne_status s__ = (call);                    \
+    if (s__ != TSGNE_OK) return fail((ctx), s__); \
+  } while (0)
+
+#define API_CUDA(ctx, call)                                                          \
+  do {                                                                               \
+    cudaError_t e__ = (call);                                                        \
+    if (e__ != cudaSuccess) return fail((ctx), cuda_fail(e__, #call, __FILE__, __LINE__)); \
+  } while (0)
+
+tsgne_status enter(tsgne_ctx* ctx) {
+  if (!ctx) return TSGNE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  last_msg().clear();
+  if (ctx->poisoned) return fail(ctx, TSGNE_ERR_CUDA, "context is unusable after an earlier CUDA error");
+  return TSGNE_OK;
+}
+
+// Copies count elements from src (host or device) into a new device buffer.
+template <class T>
+tsgne_status to_device(const T* src, size_t count, int ptr_kind, DevBuf<T>& dst, cudaStream_t s) {
+  TS_TRY(dst.alloc(count));
+  if (count == 0) return TSGNE_OK;
+  TS_CUDA(cudaMemcpyAsync(dst.get(), src, count * sizeof(T),
+                          ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  return TSGNE_OK;
+}
+
+tsgne_status copy_out(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t s) {
+  if (bytes == 0) return TSGNE_OK;
+  TS_CUDA(cudaMemcpyAsync(dst, src, bytes, ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          s));
+  return TSGNE_OK;
+}
+
+tsgne_status copy_in(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t s) {
+  if (bytes == 0) return TSGNE_OK;
+  TS_CUDA(cudaMemcpyAsync(dst, src, bytes, ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          s));
+  return TSGNE_OK;
+}
+
+bool valid_kind(int k) { return k == TSGNE_PTR_HOST || k == TSGNE_PTR_DEVICE; }
+
+// ---------------------------------------------------------------- profiling
+
+tsgne_status prof_begin(tsgne_ctx* ctx, int cls, ProfRec* rec) {
+  rec->cls = cls;
+  rec->a = rec->b = nullptr;
+  if (!ctx->cfg.profile) return TSGNE_OK;
+  for (cudaEvent_t* e : {&rec->a, &rec->b}) {
+    if (!ctx->spare.empty()) {
+      *e = ctx->spare.back();
+      ctx->spare.pop_back();
+    } else {
+      TS_CUDA(cudaEventCreate(e));
+    }
+  }
+  TS_CUDA(cudaEventRecord(rec->a, ctx->stream));
+  return TSGNE_OK;
+}
+
+tsgne_status prof_collect(tsgne_ctx* ctx) {
+  if (ctx->pending.empty()) return TSGNE_OK;
+  TS_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (auto& r : ctx->pending) {
+    float ms = 0.f;
+    TS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    ctx->prof_ms[r.cls] += ms;
+    ctx->prof_n[r.cls] += 1;
+    ctx->spare.push_back(r.a);
+    ctx->spare.push_back(r.b);
+  }
+  ctx->pending.clear();
+  return TSGNE_OK;
+}
+
+tsgne_status prof_end(tsgne_ctx* ctx, ProfRec* rec) {
+  if (!ctx->cfg.profile) return TSGNE_OK;
+  TS_CUDA(cudaEventRecord(rec->b, ctx->stream));
+  ctx->pending.push_back(*rec);
+  if (ctx->pending.size() >= 8192) TS_TRY(prof_collect(ctx));
+  return TSGNE_OK;
+}
+
+// ------------------------------------------------------------- iteration
+
+tsgne_status enqueue_repulsion(tsgne_ctx* ctx, int advance) {
+  const tsgne_config& c = ctx->cfg;
+  ProfRec pr;
+  TS_TRY(prof_begin(ctx, 0, &pr));
+  TS_TRY(launch_repulsion(ctx->shape, ctx->n, ctx->Y[ctx->cur].get(), ctx->frep.get(), ctx->zpart.get(),
+                          ctx->sched.get(), advance, c.early_exag, c.ee_iters, c.momentum0, c.momentum1,
+                          ctx->stream));
+  return prof_end(ctx, &pr);
+}
+
+tsgne_status enqueue_step(tsgne_ctx* ctx) {
+  TS_TRY(enqueue_repulsion(ctx, 1));
+  ProfRec pr;
+  TS_TRY(prof_begin(ctx, 1, &pr));
+  const int nxt = ctx->cur ^ 1;
+  TS_TRY(launch_attract_update(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
+                               ctx->Y[nxt].get(), ctx->upd.get(), ctx->gains.get(), ctx->frep.get(),
+                               ctx->shape.chunks, ctx->shape.n_pad, ctx->sched.get(), ctx->eta, ctx->cfg.min_gain,
+                               ctx->stream));
+  TS_TRY(prof_end(ctx, &pr));
+  ctx->cur = nxt;
+  return TSGNE_OK;
+}
+
+tsgne_status read_sched(tsgne_ctx* ctx, Sched* h) {
+  TS_CUDA(cudaMemcpyAsync(h, ctx->sched.get(), sizeof(Sched), cudaMemcpyDeviceToHost, ctx->stream));
+  TS_CUDA(cudaStreamSynchronize(ctx->stream));
+  return TSGNE_OK;
+}
+
+tsgne_status check_flags(tsgne_ctx* ctx) {
+  Sched h;
+  TS_TRY(read_sched(ctx, &h));
+  if (h.flags & kFlagNonfiniteY) {
+    last_msg() = "the layout became non-finite";
+    return TSGNE_ERR_NONFINITE;
+  }
+  return TSGNE_OK;
+}
+
+bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
+tsgne_status ensure_graph(tsgne_ctx* ctx, int start) {
+  if (ctx->g2[start]) return TSGNE_OK;
+  const int saved = ctx->cur;
+  ctx->cur = start;
+  cudaGraph_t g = nullptr;
+  TS_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  tsgne_status st = enqueue_step(ctx);
+  if (st == TSGNE_OK) st = enqueue_step(ctx);
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  ctx->cur = saved;
+  if (st != TSGNE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  e = cudaGraphInstantiate(&ctx->g2[start], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    ctx->g2[start] = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  }
+  return TSGNE_OK;
+}
+
+// Allocates the per-layout buffers for n points (after P is known).
+tsgne_status alloc_layout(tsgne_ctx* ctx) {
+  ctx->shape = repulsion_shape(ctx->n, ctx->sms);
+  const size_t np = (size_t)ctx->shape.n_pad;
+  TS_TRY(ctx->Y[0].alloc(np));
+  TS_TRY(ctx->Y[1].alloc(np));
+  TS_TRY(ctx->upd.alloc(np));
+  TS_TRY(ctx->gains.alloc(np));
+  TS_TRY(ctx->grad.alloc(np));
+  TS_TRY(ctx->frep.alloc(np * (size_t)ctx->shape.chunks));
+  TS_TRY(ctx->zpart.alloc(repulsion_zpart_count(ctx->shape)));
+  TS_TRY(ctx->klpart.alloc(2 * (size_t)kl_partial_count(ctx->sms)));
+  TS_TRY(launch_fill_sentinel(ctx->Y[0].get(), 0, (int)np, ctx->stream));
+  TS_TRY(launch_fill_sentinel(ctx->Y[1].get(), 0, (int)np, ctx->stream));
+  const float ee = ctx->cfg.early_exag > 0.f ? ctx->cfg.early_exag : 1.f;
+  ctx->eta = ctx->cfg.learning_rate > 0.f ? ctx->cfg.learning_rate : std::fmax((float)ctx->n / ee / 4.0f, 50.0f);
+  return TSGNE_OK;
+}
+
+// Installs a built structure + P into the context (commit point of build / set).
+tsgne_status install(tsgne_ctx* ctx, int n, int64_t nnz, DevBuf<int64_t>& rp, DevBuf<int32_t>& col, DevBuf<float>& P) {
+  ctx->reset_graphs();
+  ctx->have_P = false;
+  ctx->have_Y = false;
+  ctx->n = n;
+  ctx->nnz = nnz;
+  ctx->rp = std::move(rp);
+  ctx->col = std::move(col);
+  ctx->P = std::move(P);
+  TS_TRY(alloc_layout(ctx));
+  ctx->have_P = true;
+  return TSGNE_OK;
+}
+
+tsgne_status reset_optimizer(tsgne_ctx* ctx, int32_t t) {
+  TS_TRY(launch_fill2(ctx->upd.get(), ctx->shape.n_pad, 0.f, ctx->stream));
+  TS_TRY(launch_fill2(ctx->gains.get(), ctx->shape.n_pad, 1.f, ctx->stream));
+  Sched h{};
+  h.t = t;
+  TS_CUDA(cudaMemcpyAsync(ctx->sched.get(), &h, sizeof(Sched), cudaMemcpyHostToDevice, ctx->stream));
+  return TSGNE_OK;
+}
+
+tsgne_status read_ends(const int64_t* rp, int32_t n, int ptr_kind, cudaStream_t s, int64_t* first, int64_t* last) {
+  if (ptr_kind == TSGNE_PTR_HOST) {
+    *first = rp[0];
+    *last = rp[n];
+    return TSGNE_OK;
+  }
+  TS_CUDA(cudaMemcpyAsync(first, rp, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TS_CUDA(cudaMemcpyAsync(last, rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TS_CUDA(cudaStreamSynchronize(s));
+  return TSGNE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tsgne_config_default(tsgne_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->perplexity = 30.f;
+  cfg->k_nn = 0;
+  cfg->early_exag = 12.f;
+  cfg->ee_iters = 250;
+  cfg->momentum0 = 0.5f;
+  cfg->momentum1 = 0.8f;
+  cfg->learning_rate = 0.f;
+  cfg->min_gain = 0.01f;
+  cfg->bisect_tol = 1e-5f;
+  cfg->bisect_max_iter = 100;
+  cfg->seed = 0;
+  cfg->precision = 0;
+  cfg->profile = 0;
+  cfg->spin_budget_cycles = 2000000000LL;
+}
+
+const char* tsgne_status_string(tsgne_status s) {
+  switch (s) {
+    case TSGNE_OK: return "TSGNE_OK";
+    case TSGNE_ERR_INVALID_ARG: return "TSGNE_ERR_INVALID_ARG";
+    case TSGNE_ERR_BAD_CSR: return "TSGNE_ERR_BAD_CSR";
+    case TSGNE_ERR_OOM: return "TSGNE_ERR_OOM";
+    case TSGNE_ERR_CUDA: return "TSGNE_ERR_CUDA";
+    case TSGNE_ERR_NOT_BUILT: return "TSGNE_ERR_NOT_BUILT";
+    case TSGNE_ERR_NONFINITE: return "TSGNE_ERR_NONFINITE";
+    case TSGNE_ERR_TIMEOUT: return "TSGNE_ERR_TIMEOUT";
+    case TSGNE_ERR_CANCELLED: return "TSGNE_ERR_CANCELLED";
+  }
+  return "TSGNE_ERR_UNKNOWN";
+}
+
+tsgne_status tsgne_create(tsgne_ctx** out, const tsgne_config* cfg, void* cuda_stream) {
+  if (!out) return TSGNE_ERR_INVALID_ARG;
+  *out = nullptr;
+  tsgne_config c;
+  if (cfg) c = *cfg; else tsgne_config_default(&c);
+  if (!(c.perplexity > 1.f) || c.k_nn != 0 || c.precision != 0 || c.ee_iters < 0 || !(c.min_gain >= 0.f) ||
+      !(c.bisect_tol > 0.f) || c.bisect_max_iter < 1 || !std::isfinite(c.early_exag) || !std::isfinite(c.momentum0) ||
+      !std::isfinite(c.momentum1)) {
+    last_msg() = "invalid configuration (perplexity must exceed 1; k_nn and precision must be 0)";
+    return TSGNE_ERR_INVALID_ARG;
+  }
+  tsgne_ctx* ctx = new (std::nothrow) tsgne_ctx();
+  if (!ctx) return TSGNE_ERR_OOM;
+  ctx->cfg = c;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      ctx->own_stream = (e == cudaSuccess);
+    }
+  }
+  tsgne_status st = TSGNE_OK;
+  if (e != cudaSuccess) st = cuda_fail(e, "tsgne_create", __FILE__, __LINE__);
+  if (st == TSGNE_OK) st = ctx->sched.alloc(1);
+  if (st == TSGNE_OK) {
+    e = cudaMemsetAsync(ctx->sched.get(), 0, sizeof(Sched), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "tsgne_create", __FILE__, __LINE__);
+  }
+  if (st != TSGNE_OK) {
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return TSGNE_OK;
+}
+
+void tsgne_destroy(tsgne_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+}
+
+const char* tsgne_last_error(const tsgne_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+tsgne_status tsgne_build_P(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* X,
+                           int32_t d, int32_t ptr_kind) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (n < 2 || d < 1 || !row_ptr || !X || !valid_kind(ptr_kind))
+    return fail(ctx, TSGNE_ERR_INVALID_ARG, "need n >= 2, d >= 1, non-NULL row_ptr and X, a valid ptr_kind");
+  int64_t first = 0, m = 0;
+  API_TRY(ctx, read_ends(row_ptr, n, ptr_kind, ctx->stream, &first, &m));
+  if (first != 0 || m < 0) return fail(ctx, TSGNE_ERR_BAD_CSR, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+  if (m > 0 && !col_idx) return fail(ctx, TSGNE_ERR_INVALID_ARG, "col_idx is NULL");
+  if (m > (int64_t)1 << 30) return fail(ctx, TSGNE_ERR_INVALID_ARG, "more than 2^30 input entries");
+  ProfRec pr;
+  API_TRY(ctx, prof_begin(ctx, 4, &pr));
+  DevBuf<int64_t> rp_in;
+  DevBuf<int32_t> col_in;
+  DevBuf<float> X_in;
+  const int64_t* rp_d = row_ptr;
+  const int32_t* col_d = col_idx;
+  const float* X_d = X;
+  if (ptr_kind == TSGNE_PTR_HOST) {
+    API_TRY(ctx, to_device(row_ptr, (size_t)n + 1, ptr_kind, rp_in, ctx->stream));
+    API_TRY(ctx, to_device(col_idx, (size_t)m, ptr_kind, col_in, ctx->stream));
+    API_TRY(ctx, to_device(X, (size_t)n * (size_t)d, ptr_kind, X_in, ctx->stream));
+    rp_d = rp_in.get();
+    col_d = col_in.get();
+    X_d = X_in.get();
+  }
+  DevBuf<int64_t> rp, tslot;
+  DevBuf<int32_t> col;
+  DevBuf<float> P;
+  int64_t nnz = 0;
+  API_TRY(ctx, build_structure(n, rp_d, col_d, m, rp, col, tslot, &nnz, ctx->sched.get(), ctx->stream));
+  API_TRY(ctx, P.alloc((size_t)nnz));
+  API_CUDA(ctx, cudaMemsetAsync(ctx->sched.get(), 0, sizeof(Sched), ctx->stream));
+  API_TRY(ctx, build_affinities(n, rp.get(), col.get(), tslot.get(), nnz, X_d, d, ctx->cfg.perplexity,
+                                ctx->cfg.bisect_tol, ctx->cfg.bisect_max_iter, P.get(), ctx->sched.get(), ctx->stream));
+  API_TRY(ctx, prof_end(ctx, &pr));
+  Sched h;
+  API_TRY(ctx, read_sched(ctx, &h));
+  if (h.flags & kFlagNonfiniteP) return fail(ctx, TSGNE_ERR_NONFINITE, "non-finite affinity (check X)");
+  API_TRY(ctx, install(ctx, n, nnz, rp, col, P));
+  API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_set_P(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* Pv,
+                         int32_t ptr_kind) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (n < 2 || !row_ptr || !valid_kind(ptr_kind)) return fail(ctx, TSGNE_ERR_INVALID_ARG, "need n >= 2 and row_ptr");
+  int64_t first = 0, m = 0;
+  API_TRY(ctx, read_ends(row_ptr, n, ptr_kind, ctx->stream, &first, &m));
+  if (first != 0 || m < 0) return fail(ctx, TSGNE_ERR_BAD_CSR, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+  if (m > 0 && (!col_idx || !Pv)) return fail(ctx, TSGNE_ERR_INVALID_ARG, "col_idx or P is NULL");
+  DevBuf<int64_t> rp_in, rp, tslot;
+  DevBuf<int32_t> col_in, col;
+  DevBuf<float> P;
+  API_TRY(ctx, to_device(row_ptr, (size_t)n + 1, ptr_kind, rp_in, ctx->stream));
+  API_TRY(ctx, to_device(col_idx, (size_t)m, ptr_kind, col_in, ctx->stream));
+  API_TRY(ctx, to_device(Pv, (size_t)m, ptr_kind, P, ctx->stream));
+  int64_t nnz = 0;
+  API_TRY(ctx, build_structure(n, rp_in.get(), col_in.get(), m, rp, col, tslot, &nnz, ctx->sched.get(), ctx->stream));
+  if (nnz != m) return fail(ctx, TSGNE_ERR_BAD_CSR, "structure is not symmetric, sorted, unique and loop-free");
+  DevBuf<uint32_t> neq;
+  API_TRY(ctx, neq.alloc(1));
+  API_CUDA(ctx, cudaMemsetAsync(neq.get(), 0, sizeof(uint32_t), ctx->stream));
+  k_cmp_i64<<<64, 256, 0, ctx->stream>>>(rp.get(), rp_in.get(), (int64_t)n + 1, neq.get());
+  if (m > 0) k_cmp_i32<<<256, 256, 0, ctx->stream>>>(col.get(), col_in.get(), m, neq.get());
+  API_CUDA(ctx, cudaGetLastError());
+  uint32_t hneq = 0;
+  API_CUDA(ctx, cudaMemcpyAsync(&hneq, neq.get(), sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (hneq) return fail(ctx, TSGNE_ERR_BAD_CSR, "structure is not symmetric, sorted, unique and loop-free");
+  API_CUDA(ctx, cudaMemsetAsync(ctx->sched.get(), 0, sizeof(Sched), ctx->stream));
+  API_TRY(ctx, install(ctx, n, nnz, rp, col, P));
+  API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_get_sizes(tsgne_ctx* ctx, int32_t* n, int64_t* nnz) {
+  TS_TRY(enter(ctx));
+  if (!ctx->have_P) return fail(ctx, TSGNE_ERR_NOT_BUILT, "no affinities yet");
+  if (n) *n = ctx->n;
+  if (nnz) *nnz = ctx->nnz;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_get_P(tsgne_ctx* ctx, int64_t* row_ptr, int32_t* col, float* val, int32_t ptr_kind) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!valid_kind(ptr_kind)) return fail(ctx, TSGNE_ERR_INVALID_ARG, "bad ptr_kind");
+  if (!ctx->have_P) return fail(ctx, TSGNE_ERR_NOT_BUILT, "no affinities yet");
+  if (row_ptr) API_TRY(ctx, copy_out(row_ptr, ctx->rp.get(), sizeof(int64_t) * ((size_t)ctx->n + 1), ptr_kind, ctx->stream));
+  if (col) API_TRY(ctx, copy_out(col, ctx->col.get(), sizeof(int32_t) * (size_t)ctx->nnz, ptr_kind, ctx->stream));
+  if (val) API_TRY(ctx, copy_out(val, ctx->P.get(), sizeof(float) * (size_t)ctx->nnz, ptr_kind, ctx->stream));
+  API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_init_Y(tsgne_ctx* ctx, const float* Y0, int32_t ptr_kind) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!valid_kind(ptr_kind)) return fail(ctx, TSGNE_ERR_INVALID_ARG, "bad ptr_kind");
+  if (!ctx->have_P) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P first");
+  ctx->cur = 0;
+  if (Y0) {
+    API_TRY(ctx, copy_in(ctx->Y[0].get(), Y0, sizeof(float2) * (size_t)ctx->n, ptr_kind, ctx->stream));
+  } else {
+    API_TRY(ctx, launch_init_Y(ctx->n, ctx->cfg.seed, 1e-4f, ctx->Y[0].get(), ctx->stream));
+  }
+  API_TRY(ctx, reset_optimizer(ctx, 0));
+  API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->have_Y = true;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_step(tsgne_ctx* ctx) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!ctx->have_P || !ctx->have_Y) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P and set Y first");
+  API_TRY(ctx, enqueue_step(ctx));
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_run(tsgne_ctx* ctx, int32_t n_iter) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (n_iter < 0) return fail(ctx, TSGNE_ERR_INVALID_ARG, "n_iter < 0");
+  if (!ctx->have_P || !ctx->have_Y) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P and set Y first");
+  int32_t k = 0;
+  if (!ctx->cfg.profile && capturable(ctx->stream) && n_iter >= 2) {
+    API_TRY(ctx, ensure_graph(ctx, ctx->cur));
+    for (; k + 2 <= n_iter; k += 2) API_CUDA(ctx, cudaGraphLaunch(ctx->g2[ctx->cur], ctx->stream));
+  }
+  for (; k < n_iter; ++k) API_TRY(ctx, enqueue_step(ctx));
+  API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  API_TRY(ctx, check_flags(ctx));
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_sync(tsgne_ctx* ctx) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->have_P) API_TRY(ctx, check_flags(ctx));
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_kl(tsgne_ctx* ctx, double* kl_out) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!kl_out) return fail(ctx, TSGNE_ERR_INVALID_ARG, "kl_out is NULL");
+  if (!ctx->have_P || !ctx->have_Y) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P and set Y first");
+  API_TRY(ctx, enqueue_repulsion(ctx, 0));
+  ProfRec pr;
+  API_TRY(ctx, prof_begin(ctx, 3, &pr));
+  API_TRY(ctx, launch_kl(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
+                         ctx->klpart.get(), kl_partial_count(ctx->sms), ctx->sched.get(), ctx->stream));
+  API_TRY(ctx, prof_end(ctx, &pr));
+  Sched h;
+  API_TRY(ctx, read_sched(ctx, &h));
+  *kl_out = h.red[0] + h.red[1] * std::log(h.Z);
+  if (!std::isfinite(*kl_out)) return fail(ctx, TSGNE_ERR_NONFINITE, "KL is not finite");
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_gradient(tsgne_ctx* ctx, float alpha, float* g_out, double* z_out, int32_t ptr_kind) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!g_out || !valid_kind(ptr_kind)) return fail(ctx, TSGNE_ERR_INVALID_ARG, "g_out is NULL or bad ptr_kind");
+  if (!ctx->have_P || !ctx->have_Y) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P and set Y first");
+  API_TRY(ctx, enqueue_repulsion(ctx, 0));
+  ProfRec pr;
+  API_TRY(ctx, prof_begin(ctx, 2, &pr));
+  API_TRY(ctx, launch_gradient(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
+                               ctx->frep.get(), ctx->shape.chunks, ctx->shape.n_pad, ctx->sched.get(), alpha,
+                               ctx->grad.get(), ctx->stream));
+  API_TRY(ctx, prof_end(ctx, &pr));
+  API_TRY(ctx, copy_out(g_out, ctx->grad.get(), sizeof(float2) * (size_t)ctx->n, ptr_kind, ctx->stream));
+  Sched h;
+  API_TRY(ctx, read_sched(ctx, &h));
+  if (z_out) *z_out = h.Z;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_get_Y(tsgne_ctx* ctx, float* Y_out, int32_t ptr_kind) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!Y_out || !valid_kind(ptr_kind)) return fail(ctx, TSGNE_ERR_INVALID_ARG, "Y_out is NULL or bad ptr_kind");
+  if (!ctx->have_Y) return fail(ctx, TSGNE_ERR_NOT_BUILT, "no layout yet");
+  API_TRY(ctx, copy_out(Y_out, ctx->Y[ctx->cur].get(), sizeof(float2) * (size_t)ctx->n, ptr_kind, ctx->stream));
+  API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_get_state(tsgne_ctx* ctx, float* Y, float* update, float* gains, int32_t* iter, int32_t ptr_kind) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!valid_kind(ptr_kind)) return fail(ctx, TSGNE_ERR_INVALID_ARG, "bad ptr_kind");
+  if (!ctx->have_Y) return fail(ctx, TSGNE_ERR_NOT_BUILT, "no layout yet");
+  const size_t bytes = sizeof(float2) * (size_t)ctx->n;
+  if (Y) API_TRY(ctx, copy_out(Y, ctx->Y[ctx->cur].get(), bytes, ptr_kind, ctx->stream));
+  if (update) API_TRY(ctx, copy_out(update, ctx->upd.get(), bytes, ptr_kind, ctx->stream));
+  if (gains) API_TRY(ctx, copy_out(gains, ctx->gains.get(), bytes, ptr_kind, ctx->stream));
+  Sched h;
+  API_TRY(ctx, read_sched(ctx, &h));
+  if (iter) *iter = h.t;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update, const float* gains, int32_t iter,
+                             int32_t ptr_kind) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!valid_kind(ptr_kind) || iter < 0 || !Y) return fail(ctx, TSGNE_ERR_INVALID_ARG, "need Y, iter >= 0, ptr_kind");
+  if (!ctx->have_P) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P first");
+  const size_t bytes = sizeof(float2) * (size_t)ctx->n;
+  ctx->cur = 0;
+  API_TRY(ctx, reset_optimizer(ctx, iter));
+  API_TRY(ctx, copy_in(ctx->Y[0].get(), Y, bytes, ptr_kind, ctx->stream));
+  if (update) API_TRY(ctx, copy_in(ctx->upd.get(), update, bytes, ptr_kind, ctx->stream));
+  if (gains) API_TRY(ctx, copy_in(ctx->gains.get(), gains, bytes, ptr_kind, ctx->stream));
+  API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->have_Y = true;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_kernel_times(tsgne_ctx* ctx, double* ms, int64_t* launches, int32_t n, int32_t reset) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (n < 0 || n > kClasses) return fail(ctx, TSGNE_ERR_INVALID_ARG, "n outside [0, 5]");
+  API_TRY(ctx, prof_collect(ctx));
+  for (int k = 0; k < n; ++k) {
+    if (ms) ms[k] = ctx->prof_ms[k];
+    if (launches) launches[k] = ctx->prof_n[k];
+  }
+  if (reset)
+    for (int k = 0; k < kClasses; ++k) {
+      ctx->prof_ms[k] = 0.0;
+      ctx->prof_n[k] = 0;
+    }
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_repulsion_shape(tsgne_ctx* ctx, int32_t* grid, int32_t* block, int32_t* i_per_thread,
+                                   int32_t* j_tile, int32_t* j_chunks, int32_t* n_pad) {
+  TS_TRY(enter(ctx));
+  if (!ctx->have_P) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P first");
+  if (grid) *grid = ctx->shape.grid;
+  if (block) *block = ctx->shape.block;
+  if (i_per_thread) *i_per_thread = ctx->shape.R;
+  if (j_tile) *j_tile = ctx->shape.jtile;
+  if (j_chunks) *j_chunks = ctx->shape.chunks;
+  if (n_pad) *n_pad = ctx->shape.n_pad;
+  return TSGNE_OK;
+}
+
+}  // extern "C"

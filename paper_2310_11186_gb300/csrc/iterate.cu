@@ -1,0 +1,218 @@
+// Per-iteration kernels other than the repulsion.
+//
+// k_attract (S3 + S5 fused): G lanes per row i gather the row's neighbours
+//   (float2 loads of Y, int32 columns, FP32 P):
+//     F^a_i = sum_{j in N(i)} p_ij w_ij (y_i - y_j),  w = (1 + ||y_i-y_j||^2)^-1,
+//   add the repulsion partials of the row in a fixed chunk order, and form the
+//   gradient of Eq. 5 with P scaled by alpha (early exaggeration):
+//     g_i = 4 (alpha F^a_i - F^r_i / Z).
+//   In update mode lane 0 then applies the optimiser (the paper gives none;
+//   the published t-SNE rule): per coordinate gain += 0.2 if g and the
+//   previous update have opposite signs, else gain *= 0.8, floored at
+//   min_gain; upd = mu upd - eta gain g; y_next = y + upd.  Reading Y_cur and
+//   writing Y_next (double buffer) keeps every row's neighbours at the old
+//   layout.  In export mode it writes g and changes nothing.
+// k_kl (S6): sum_e p_e ln(p_e / w_e) and sum_e p_e in FP64 (terms in FP32),
+//   fixed-order totals; KL = first + second * ln Z on the host (Eq. 5 with
+//   q = w / Z).
+#include <cmath>
+
+#include "reduce.cuh"
+#include "tsgne_internal.cuh"
+
+namespace tsgne {
+
+namespace {
+
+constexpr int kAttrCta = 256;
+constexpr int kG = 8;  // lanes per row
+
+template <int G, bool EXPORT>
+__global__ void __launch_bounds__(kAttrCta)
+    k_attract(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ P,
+              const float2* __restrict__ Ycur, float2* __restrict__ Ynext, float2* __restrict__ upd,
+              float2* __restrict__ gains, const float2* __restrict__ frep_part, int chunks, int n_pad,
+              Sched* sched, float eta, float min_gain, float alpha_export, float2* __restrict__ g_out) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = gt / G;
+  const int lane = (int)(gt % G);
+  const bool valid = i < n;
+  float ax = 0.f, ay = 0.f, rx = 0.f, ry = 0.f;
+  float2 yi = make_float2(0.f, 0.f);
+  if (valid) {
+    yi = Ycur[i];
+    const int64_t b = rp[i + 1];
+    for (int64_t e = rp[i] + lane; e < b; e += G) {
+      const int32_t j = col[e];
+      const float p = P[e];
+      const float2 yj = Ycur[j];
+      const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+      const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
+      const float pw = p * w;
+      ax = fmaf(pw, dx, ax);
+      ay = fmaf(pw, dy, ay);
+    }
+    for (int c = lane; c < chunks; c += G) {
+      const float2 f = frep_part[(size_t)c * n_pad + i];
+      rx += f.x;
+      ry += f.y;
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o, G);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o, G);
+    rx += __shfl_xor_sync(0xffffffffu, rx, o, G);
+    ry += __shfl_xor_sync(0xffffffffu, ry, o, G);
+  }
+  if (!valid || lane != 0) return;
+  const float invZ = (float)(1.0 / sched->Z);
+  const float alpha = EXPORT ? alpha_export : sched->alpha;
+  const float gx = 4.0f * (alpha * ax - rx * invZ);
+  const float gy = 4.0f * (alpha * ay - ry * invZ);
+  if (EXPORT) {
+    g_out[i] = make_float2(gx, gy);
+    return;
+  }
+  const float mu = sched->mu;
+  float2 u = upd[i], gn = gains[i];
+  const bool incx = (gx > 0.f && u.x < 0.f) || (gx < 0.f && u.x > 0.f);
+  const bool incy = (gy > 0.f && u.y < 0.f) || (gy < 0.f && u.y > 0.f);
+  gn.x = fmaxf(incx ? gn.x + 0.2f : gn.x * 0.8f, min_gain);
+  gn.y = fmaxf(incy ? gn.y + 0.2f : gn.y * 0.8f, min_gain);
+  u.x = mu * u.x - eta * gn.x * gx;
+  u.y = mu * u.y - eta * gn.y * gy;
+  const float2 y = make_float2(yi.x + u.x, yi.y + u.y);
+  upd[i] = u;
+  gains[i] = gn;
+  Ynext[i] = y;
+  if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&sched->flags, kFlagNonfiniteY);
+}
+
+__global__ void __launch_bounds__(kAttrCta)
+    k_kl(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ P,
+         const float2* __restrict__ Y, double* __restrict__ parts, Sched* sched) {
+  double s1 = 0.0, s2 = 0.0;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    const float2 yi = Y[i];
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+      const float p = P[e];
+      if (!(p > 0.f)) continue;
+      const float2 yj = Y[col[e]];
+      const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+      // ln(p / w) = ln p + ln(1 + d^2)
+      s1 += (double)p * ((double)logf(p) + (double)log1pf(fmaf(dy, dy, dx * dx)));
+      s2 += (double)p;
+    }
+  }
+  const double b1 = block_sum_d(s1);
+  const double b2 = block_sum_d(s2);
+  if (threadIdx.x == 0) {
+    parts[2 * blockIdx.x] = b1;
+    parts[2 * blockIdx.x + 1] = b2;
+  }
+  if (arrive_last(&sched->red_done)) {
+    double t1 = 0.0, t2 = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+      t1 += __ldcg(parts + 2 * k);
+      t2 += __ldcg(parts + 2 * k + 1);
+    }
+    t1 = block_sum_d(t1);
+    t2 = block_sum_d(t2);
+    if (threadIdx.x == 0) {
+      sched->red[0] = t1;
+      sched->red[1] = t2;
+    }
+  }
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) in counter mode: draw c of a key.
+__device__ __forceinline__ uint64_t splitmix_at(uint64_t key, uint64_t c) {
+  uint64_t z = key + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_init_Y(int n, uint64_t key, float sigma, float2* __restrict__ Y) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    // Box-Muller on two 53-bit uniforms: u1 in (0, 1], u2 in [0, 1)
+    const double u1 = 1.0 - (double)(splitmix_at(key, 2 * i) >> 11) * (1.0 / 9007199254740992.0);
+    const double u2 = (double)(splitmix_at(key, 2 * i + 1) >> 11) * (1.0 / 9007199254740992.0);
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    Y[i] = make_float2((float)(sigma * r * cs), (float)(sigma * r * sn));
+  }
+}
+
+__global__ void k_fill2(float2* a, int64_t lo, int64_t hi, float v) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < hi; k += stride) a[k] = make_float2(v, v);
+}
+
+int grid_rows(int64_t n, int per_cta) {
+  int64_t g = (n + per_cta - 1) / per_cta;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int kl_partial_count(int sm_count) { return sm_count * 4; }
+
+tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Ycur,
+                                   float2* Ynext, float2* upd, float2* gains, const float2* frep_part, int chunks,
+                                   int n_pad, Sched* sched, float eta, float min_gain, cudaStream_t s) {
+  const int grid = grid_rows((int64_t)n * kG, kAttrCta);
+  k_attract<kG, false><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Ycur, Ynext, upd, gains, frep_part, chunks, n_pad,
+                                                 sched, eta, min_gain, 0.f, nullptr);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+tsgne_status launch_gradient(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
+                             const float2* frep_part, int chunks, int n_pad, const Sched* sched, float alpha,
+                             float2* g, cudaStream_t s) {
+  const int grid = grid_rows((int64_t)n * kG, kAttrCta);
+  k_attract<kG, true><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Y, nullptr, nullptr, nullptr, frep_part, chunks,
+                                                n_pad, const_cast<Sched*>(sched), 0.f, 0.f, alpha, g);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+tsgne_status launch_kl(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
+                       double* partials, int nparts, Sched* sched, cudaStream_t s) {
+  k_kl<<<nparts, kAttrCta, 0, s>>>(n, rp, col, P, Y, partials, sched);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+tsgne_status launch_init_Y(int n, uint64_t seed, float sigma, float2* Y, cudaStream_t s) {
+  // key = SplitMix64 output of the seed itself (stream separation from user seeds)
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  const uint64_t key = z ^ (z >> 31);
+  k_init_Y<<<grid_rows(n, 256) < 4096 ? grid_rows(n, 256) : 4096, 256, 0, s>>>(n, key, sigma, Y);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+tsgne_status launch_fill_sentinel(float2* Y, int lo, int hi, cudaStream_t s) {
+  if (hi <= lo) return TSGNE_OK;
+  k_fill2<<<grid_rows(hi - lo, 256) < 1024 ? grid_rows(hi - lo, 256) : 1024, 256, 0, s>>>(Y, lo, hi, kSentinel);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+tsgne_status launch_fill2(float2* a, int n, float v, cudaStream_t s) {
+  if (n <= 0) return TSGNE_OK;
+  k_fill2<<<grid_rows(n, 256) < 1024 ? grid_rows(n, 256) : 1024, 256, 0, s>>>(a, 0, n, v);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+}  // namespace tsgne

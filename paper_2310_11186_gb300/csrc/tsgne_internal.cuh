@@ -1,0 +1,142 @@
+// Internal declarations shared by the translation units of libtsgne.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "tsgne.h"
+
+namespace tsgne {
+
+// Padding point of the repulsion tiles: its squared distance to any real
+// point overflows to +inf in FP32, so its Student-t kernel value is exactly 0.
+constexpr float kSentinel = 1e30f;
+
+// Device-resident scalars of the iteration (one per context).
+struct Sched {
+  double Z;            // normaliser of the last repulsion pass (ordered pairs, no diagonal)
+  float alpha;         // exaggeration for the update that follows that pass
+  float mu;            // momentum for the update that follows that pass
+  int32_t t;           // index of the next iteration
+  uint32_t flags;      // bit 0: non-finite layout seen; bit 1: non-finite P
+  uint32_t rep_done;   // last-CTA counter of the repulsion pass
+  uint32_t red_done;   // last-CTA counter of the generic reductions
+  double red[4];       // results of the generic reductions
+};
+
+constexpr uint32_t kFlagNonfiniteY = 1u;
+constexpr uint32_t kFlagNonfiniteP = 2u;
+
+// Geometry of one repulsion pass (see repulsion.cu).
+struct RepShape {
+  int grid = 0;      // CTAs (a multiple of the SM count when the work allows)
+  int block = 0;     // threads per CTA
+  int R = 0;         // i-points per thread
+  int jtile = 0;     // j-points staged in shared memory per tile
+  int chunks = 0;    // j-range chunks (partial force slots per point)
+  int n_pad = 0;     // padded length of Y buffers
+  int n_iblk = 0;    // i-blocks of block*R points
+  int n_jtiles = 0;  // j-tiles of jtile points
+};
+
+// Last error message of the calling thread (copied into the context by the API layer).
+std::string& last_msg();
+
+// Returns TSGNE_ERR_OOM or TSGNE_ERR_CUDA for e and records a message.
+tsgne_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define TS_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return ::tsgne::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define TS_TRY(call)                        \
+  do {                                      \
+    tsgne_status s_ = (call);               \
+    if (s_ != TSGNE_OK) return s_;          \
+  } while (0)
+
+// Owning device buffer released with cudaFree.
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { reset(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { reset(); }
+  void reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  tsgne_status alloc(size_t count) {
+    reset();
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) { p = nullptr; return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__); }
+    n = count;
+    return TSGNE_OK;
+  }
+  T* get() const { return p; }
+};
+
+// ---------------------------------------------------------------- scan
+// Exclusive prefix sum of in[0..n) into out[0..n], out[n] = total.
+size_t scan_scratch_bytes(int64_t n);
+tsgne_status scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* scratch, cudaStream_t s);
+
+// ------------------------------------------------------------ structure
+// Symmetric, sorted, unique, loop-free structure of a validated CSR (device
+// pointers).  Allocates *rp_out (n+1), *col_out (nnz) and *tslot_out (nnz).
+// Synchronises the stream.  Returns BAD_CSR when the input is malformed.
+tsgne_status build_structure(int n, const int64_t* rp_in, const int32_t* col_in, int64_t m, DevBuf<int64_t>& rp_out,
+                             DevBuf<int32_t>& col_out, DevBuf<int64_t>& tslot_out, int64_t* nnz_out,
+                             Sched* sched, cudaStream_t s);
+
+// ------------------------------------------------------------- affinity
+// p_{j|i} per entry (Eq. 2 over N(i), bisection of Sec. 2.1) then the joint
+// P of Eq. 3 normalised by the total.  Sets kFlagNonfiniteP on NaN / Inf.
+tsgne_status build_affinities(int n, const int64_t* rp, const int32_t* col, const int64_t* tslot, int64_t nnz,
+                              const float* X, int d, float perplexity, float tol, int max_iter, float* P,
+                              Sched* sched, cudaStream_t s);
+
+// ------------------------------------------------------------ repulsion
+RepShape repulsion_shape(int n, int sm_count);
+size_t repulsion_zpart_count(const RepShape& sh);
+// One pass: partial forces frep_part[chunk][n_pad] (float2), Z into sched;
+// advance != 0 also sets alpha / mu for iteration sched->t and increments t.
+tsgne_status launch_repulsion(const RepShape& sh, int n, const float2* Y, float2* frep_part, double* zpart,
+                              Sched* sched, int advance, float ee, int ee_iters, float mom0, float mom1,
+                              cudaStream_t s);
+
+// ------------------------------------------------------------ iteration
+// Attraction + gradient + optimiser update: reads Ycur, writes Ynext.
+tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Ycur,
+                                   float2* Ynext, float2* upd, float2* gains, const float2* frep_part, int chunks,
+                                   int n_pad, Sched* sched, float eta, float min_gain, cudaStream_t s);
+// Gradient export g = 4 (alpha F^a - F^r / Z) without state change.
+tsgne_status launch_gradient(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
+                             const float2* frep_part, int chunks, int n_pad, const Sched* sched, float alpha,
+                             float2* g, cudaStream_t s);
+// KL terms: sched->red[0] = sum p ln(p / w), sched->red[1] = sum p.
+tsgne_status launch_kl(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
+                       double* partials, int nparts, Sched* sched, cudaStream_t s);
+int kl_partial_count(int sm_count);
+// Y0 ~ N(0, sigma^2) from a seed (SplitMix64 counter mode + Box-Muller).
+tsgne_status launch_init_Y(int n, uint64_t seed, float sigma, float2* Y, cudaStream_t s);
+// Fill y[lo..hi) with the sentinel point.
+tsgne_status launch_fill_sentinel(float2* Y, int lo, int hi, cudaStream_t s);
+// Set every element of a float2 array to (v, v).
+tsgne_status launch_fill2(float2* a, int n, float v, cudaStream_t s);
+
+}  // namespace tsgne

@@ -1,0 +1,59 @@
+"""The C ABI library loads and exports every function include/tsgne.h declares
+(no GPU needed: nothing here launches a kernel)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2310_11186_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tsgne.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tsgne_[a-zA-Z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2310_11186_gb300 import build
+
+    build.build()
+    return pkg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("tsgne_build_P", "tsgne_step", "tsgne_run", "tsgne_kl"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    raw = ctypes.CDLL(pkg.library_path)
+    for name in _declared():
+        assert hasattr(raw, name), name
+    # the binding declares exactly the same set
+    assert sorted(pkg.EXPORTS) == _declared()
+
+
+def test_host_only_calls(built):
+    c = pkg.tsgne_config_default()
+    assert c.perplexity == 30.0 and c.ee_iters == 250 and c.early_exag == 12.0
+    assert abs(c.momentum0 - 0.5) < 1e-7 and abs(c.momentum1 - 0.8) < 1e-7
+    assert pkg.tsgne_status_string(2) == "TSGNE_ERR_BAD_CSR"
+    assert pkg.tsgne_last_error(None) == ""
+    with pytest.raises(pkg.TsgneError) as ei:
+        pkg.tsgne_create(pkg.tsgne_config_default(perplexity=1.0))
+    assert ei.value.status == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    monkeypatch.setattr(pkg, "_lib", None)
+    monkeypatch.setattr(pkg, "library_path", "/nonexistent/libtsgne.so")
+    with pytest.raises(RuntimeError):
+        pkg.lib()
