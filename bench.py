@@ -1,0 +1,398 @@
+"""Benchmark of the t-SGNE layout loop on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (the paper-scale single layout): stochastic block model with 300,000
+nodes in 50 Zipf(1.2)-sized blocks, 1,000,000 edges before 10 % are rewired
+at random, a 128-d embedding of block centres plus noise, perplexity 30,
+exact all-pairs repulsion.  One step = one t-SGNE iteration (attraction over
+P, all-pairs repulsion with FP64 Z, gains / momentum update) through
+``tsgne_step``.  The affinity build runs once before the timed region and is
+reported as ``build_ms``.
+
+Printed: one JSON line (rank 0).  ``value`` = iterations/s over the K timed
+steps (device time, CUDA events on the library's stream, L2 flushed before
+every step); ``e2e`` = the same metric for a whole layout through the C ABI
+from pinned host buffers (build from host CSR + X, K_e2e iterations, layout
+copied back), copies inside the timed region; ``roofline`` = the repulsion
+kernel (the dominant one) against the FP32 ALU peak; ``cpu_baseline`` = the
+FP64 oracle timed on a bounded sample of the same workload.
+
+``--impl reference`` times the oracle itself (there is no runnable reference
+implementation of the paper) on the host cores, each step a bounded sample of
+repulsion rows of the same workload, and prints the same metric.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import tsgne_synth as synth  # noqa: E402
+
+METRIC = "t-SGNE iters/sec @300K nodes/1M edges (% FP32/HBM roofline); served layouts/s + p50/p99"
+UNIT = "iters/s"
+WORKLOAD = "zipf300k"
+WORKLOADS = ("zipf300k", "zipf100k", "sbm2k")
+WORKLOAD_DESC = ("stochastic block model, 300,000 nodes, 50 Zipf(1.2) blocks, 1,000,000 edges before 10% rewiring, "
+                 "128-d FP32 embedding (block centre N(0,4I) + N(0,I)), perplexity 30, Y0 ~ N(0,1e-4^2), "
+                 "exact all-pairs repulsion, FP32 with FP64 Z")
+# FP32 ALU peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FLOPS_PER_UNORDERED_PAIR = 16  # 2 sub, 3 for d^2+1, w^2, Z add, 8 for the two force FMAs pairs
+REPULSION_SRC = os.path.join(ROOT, "paper_2310_11186_gb300", "csrc", "repulsion.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "repulsion_zipf300k.md")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ helpers
+
+class ClockSampler:
+    """Samples nvidia-smi clocks / throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.t:
+                self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "power_w_max": max(pw),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_per_launch():
+    """DRAM bytes per repulsion launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    try:
+        txt = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_b:
+        return None
+    sha = hashlib.sha256(open(REPULSION_SRC, "rb").read()).hexdigest()
+    return float(m_b.group(1)) if sha == m_sha.group(1) else None
+
+
+def oracle_sample(Y, n, target_s: float):
+    """Times the FP64 oracle's repulsion rows on a growing row block until the
+    sample takes about target_s; returns (seconds per iteration extrapolated
+    to all n rows, rows timed, seconds spent)."""
+    import oracle
+
+    oracle.build()
+    Yd = np.ascontiguousarray(Y, np.float64)
+    rows = 16
+    spent = 0.0
+    while True:
+        t = time.perf_counter()
+        oracle.repulsion_rows(Yd, 0, rows)
+        dt = time.perf_counter() - t
+        spent += dt
+        if dt >= target_s or rows >= n:
+            return dt * n / rows, rows, spent
+        rows = min(n, int(rows * max(2.0, min(16.0, 1.2 * target_s / max(dt, 1e-4)))))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    g, X = synth.workload(args.workload)
+    Y = synth.y_init(g.n)
+    import oracle
+
+    oracle.build()
+    # size one step (a block of repulsion rows) to about 1 s of CPU work
+    per_iter, _, _ = oracle_sample(Y, g.n, 0.5)
+    rows = int(min(g.n, max(16, g.n * args.ref_step_seconds / per_iter)))
+    Yd = np.ascontiguousarray(Y, np.float64)
+    for _ in range(args.warmup):
+        oracle.repulsion_rows(Yd, 0, rows)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.repulsion_rows(Yd, 0, rows)
+        times.append(time.perf_counter() - t)
+    s_per_iter = statistics.mean(times) * g.n / rows
+    value = 1.0 / s_per_iter
+    sample = (f"FP64 oracle repulsion rows 0..{rows} of {g.n} (F_rep and row Z sums, {rows * g.n:.3g} pair "
+              f"evaluations per step), extrapolated to all rows; single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_per_iter * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOAD_DESC if args.workload == WORKLOAD else
+                   args.workload, "nodes": g.n, "edges": g.m // 2},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+
+    import paper_2310_11186_gb300 as pkg
+    from paper_2310_11186_gb300 import build as pbuild
+    from paper_2310_11186_gb300 import quality
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    pbuild.build()
+    pkg.lib()
+
+    t0 = time.perf_counter()
+    g, X = synth.workload(args.workload, seed=args.seed)
+    Y0 = synth.y_init(g.n, seed=args.seed)
+    log(f"[bench] workload {WORKLOAD}: n={g.n} edges={g.m // 2} ({time.perf_counter() - t0:.1f}s)")
+
+    # ---- device-timed iterations (profile mode: per-kernel CUDA events)
+    lay = pkg.Layout(profile=1)
+    s = lay.stream
+    tb = time.perf_counter()
+    lay.build_P(g.row_ptr, g.col, X)
+    build_ms = (time.perf_counter() - tb) * 1e3
+    lay.init_Y(Y0)
+    shape = lay.repulsion_shape()
+    for _ in range(args.warmup):
+        lay.step()
+    lay.sync()
+    lay.kernel_times(reset=True)
+    flush = torch.empty(320 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(s):
+                flush.fill_(float(k))
+            starts[k].record(s)
+            lay.step()
+            ends[k].record(s)
+        lay.sync()
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    kt = lay.kernel_times(reset=True)
+    launches = sum(v[1] for v in kt.values())
+    rep_ms = kt["repulsion"][0] / max(kt["repulsion"][1], 1)
+    upd_ms = kt["attract_update"][0] / max(kt["attract_update"][1], 1)
+    n = g.n
+    flops = FLOPS_PER_UNORDERED_PAIR * n * (n - 1) / 2.0
+    achieved = flops / (rep_ms / 1e3) / 1e12
+    Yt = lay.get_Y()
+    nnz_P = lay.sizes()[1]
+    lay.close()
+
+    # max over ranks
+    if ws > 1:
+        tt = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(tt.item())
+    value = ws * args.steps / total_s
+
+    # ---- end to end: whole layout from pinned host buffers through the C ABI
+    e2e_iters = args.e2e_iters
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    X_h = torch.from_numpy(X).pin_memory()
+    Y0_h = torch.from_numpy(Y0).pin_memory()
+    Y_out = torch.empty((n, 2), dtype=torch.float32).pin_memory()
+    lay2 = pkg.Layout()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    te = time.perf_counter()
+    lay2.build_P(rp_h, col_h, X_h)
+    lay2.init_Y(Y0_h)
+    lay2.run(e2e_iters)
+    lay2.get_Y(Y_out)
+    e2e_s = time.perf_counter() - te
+    if ws > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    kl_final = lay2.kl()
+    lay2.close()
+    h2d = rp_h.numel() * 8 + col_h.numel() * 4 + X_h.numel() * 4 + Y0_h.numel() * 4
+    d2h = Y_out.numel() * 4
+    Yf = Y_out.numpy()
+    labels = g.labels
+    q_nmi = quality.layout_nmi(Yf, labels, restarts=2)
+    q_aq = quality.aq(Yf, labels)
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0 only)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        per_iter, rows, spent = oracle_sample(Yt, n, args.cpu_seconds)
+        cpu = {"value": 1.0 / per_iter, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"FP64 oracle repulsion rows 0..{rows} of {n} at the timed layout "
+                          f"({rows * n:.3g} pair evaluations, {spent:.1f} s), extrapolated to all rows; "
+                          f"single thread")}
+
+    if rank != 0:
+        return 0
+    tr = traffic_per_launch()
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_s * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": args.workload,
+            "description": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
+            "nodes": n,
+            "edges": g.m // 2,
+            "nnz_P": int(nnz_P),
+            "l2": "flushed (320 MB write) before every timed step",
+            "parallelism": "replicas" if ws > 1 else "single GPU",
+            "repulsion_launch": shape,
+        },
+        "roofline": {
+            "bound": "alu",
+            "kernel": "repulsion",
+            "achieved": achieved,
+            "peak": FP32_PEAK_TFLOPS,
+            "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS,
+            "traffic": tr,
+            "flops_per_launch": flops,
+            "ms_per_launch": rep_ms,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (unit counts and max clock)",
+        },
+        "kernels_ms_per_step": {"repulsion": rep_ms, "attract_update": upd_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * e2e_iters / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / e2e_iters, "d2h_bytes_per_step": d2h / e2e_iters,
+                "iters": e2e_iters, "wall_s": e2e_s,
+                "note": "build_P from host CSR+X, init_Y from host, run, layout back to host (pinned)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "build_ms": build_ms,
+        "quality": {"kl": kl_final, "nmi": q_nmi, "aq": q_aq, "iters": e2e_iters},
+        "paper_context": "300K nodes / 1M edges in under 5 min (ShortestPath + t-SGNE, 32-core Xeon Gold 6338)",
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-iters", type=int, default=1000)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-step-seconds", type=float, default=1.0)
+    ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOAD,
+                    help="zipf300k is the benchmark; the others are smaller cases for profiling")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -14,6 +14,10 @@
 //     evaluations; p is taken at the last evaluated beta.  A row with
 //     |N(i)| <= perplexity cannot reach ln(perp) (its maximum entropy is
 //     ln |N(i)|) and is set uniform.
+//     Precision: d_ij is accumulated in FP64 (a one-time O(nnz d) cost) and
+//     beta (d - m) is formed in FP64, so that the large beta of small
+//     perplexities does not turn FP32 rounding of d ~ 10^2 into 1e-4 relative
+//     errors in p; exp, the entropy sums and the bisection run in FP32.
 // K2  joint affinities (Eq. 3): p_ij = (p_{j|i} + p_{i|j}) / T with T the
 //     FP64 total of all numerators (T = 2n without isolated nodes), so that
 //     sum P = 1; the total is a fixed-order reduction.
@@ -34,9 +38,15 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-__device__ __forceinline__ float warp_min_f(float v) {
+__device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_min_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
@@ -45,7 +55,7 @@ __global__ void __launch_bounds__(kAffCta) k_cond_affinity(int n, const int64_t*
                                                            const int32_t* __restrict__ col,
                                                            const float* __restrict__ X, int d, float perp,
                                                            float Hstar, float tol, int max_iter,
-                                                           float* __restrict__ dist, float* __restrict__ pcond) {
+                                                           double* __restrict__ dist, float* __restrict__ pcond) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
@@ -55,25 +65,26 @@ __global__ void __launch_bounds__(kAffCta) k_cond_affinity(int n, const int64_t*
     // squared distances in R^d, one neighbour at a time across the warp
     for (int64_t e = a; e < b; ++e) {
       const int64_t j = col[e];
-      float s = 0.f;
+      double s = 0.0;
       if (VEC4) {
         const float4* xi = reinterpret_cast<const float4*>(X + i * d);
         const float4* xj = reinterpret_cast<const float4*>(X + j * d);
         for (int c = lane; c < (d >> 2); c += 32) {
-          float4 u = xi[c], v = xj[c];
-          float t0 = u.x - v.x, t1 = u.y - v.y, t2 = u.z - v.z, t3 = u.w - v.w;
-          s = fmaf(t0, t0, s);
-          s = fmaf(t1, t1, s);
-          s = fmaf(t2, t2, s);
-          s = fmaf(t3, t3, s);
+          const float4 u = xi[c], v = xj[c];
+          const double t0 = (double)u.x - v.x, t1 = (double)u.y - v.y;
+          const double t2 = (double)u.z - v.z, t3 = (double)u.w - v.w;
+          s = fma(t0, t0, s);
+          s = fma(t1, t1, s);
+          s = fma(t2, t2, s);
+          s = fma(t3, t3, s);
         }
       } else {
         for (int c = lane; c < d; c += 32) {
-          float t = X[i * d + c] - X[j * d + c];
-          s = fmaf(t, t, s);
+          const double t = (double)X[i * d + c] - (double)X[j * d + c];
+          s = fma(t, t, s);
         }
       }
-      s = warp_sum_f(s);
+      s = warp_sum_d(s);
       if (lane == 0) dist[e] = s;
     }
     __syncwarp();
@@ -82,17 +93,17 @@ __global__ void __launch_bounds__(kAffCta) k_cond_affinity(int n, const int64_t*
       for (int64_t e = a + lane; e < b; e += 32) pcond[e] = u;
       continue;
     }
-    float m = INFINITY;
-    for (int64_t e = a + lane; e < b; e += 32) m = fminf(m, dist[e]);
-    m = warp_min_f(m);
+    double m = INFINITY;
+    for (int64_t e = a + lane; e < b; e += 32) m = fmin(m, dist[e]);
+    m = warp_min_d(m);
     float beta = 1.f, lo = -INFINITY, hi = INFINITY, S = 1.f;
     for (int it = 0; it < max_iter; ++it) {
       float s = 0.f, E = 0.f;
       for (int64_t e = a + lane; e < b; e += 32) {
-        const float delta = dist[e] - m;
-        const float w = expf(-beta * delta);
+        const double delta = dist[e] - m;
+        const float w = expf(-(float)((double)beta * delta));
         s += w;
-        E = fmaf(delta, w, E);
+        E = fmaf((float)delta, w, E);
       }
       S = warp_sum_f(s);
       E = warp_sum_f(E);
@@ -107,7 +118,7 @@ __global__ void __launch_bounds__(kAffCta) k_cond_affinity(int n, const int64_t*
       }
     }
     const float invS = 1.f / S;
-    for (int64_t e = a + lane; e < b; e += 32) pcond[e] = expf(-beta * (dist[e] - m)) * invS;
+    for (int64_t e = a + lane; e < b; e += 32) pcond[e] = expf(-(float)((double)beta * (dist[e] - m))) * invS;
   }
 }
 
@@ -151,7 +162,8 @@ tsgne_status build_affinities(int n, const int64_t* rp, const int32_t* col, cons
   int dev = 0, sms = 1;
   TS_CUDA(cudaGetDevice(&dev));
   TS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  DevBuf<float> dist, pcond;
+  DevBuf<double> dist;
+  DevBuf<float> pcond;
   TS_TRY(dist.alloc((size_t)nnz));
   TS_TRY(pcond.alloc((size_t)nnz));
   const float Hstar = (float)std::log((double)perplexity);

@@ -290,11 +290,16 @@ def workload(name: str, seed: int = 0):
     ``sbm2k``: 2,000 nodes, 10 equal blocks, p_in 0.05, p_out 0.0005, 128-d X.
     ``zipf300k``: 300,000 nodes, 50 Zipf(1.2) blocks, 1,000,000 edges before
     rewiring, 10 % rewired, 128-d X.
+    ``zipf100k``: the same recipe at 100,000 nodes and 333,333 edges (a
+    smaller case of the same kernels, for profiling).
     """
     if name == "sbm2k":
         g = sbm_equal(2000, 10, 0.05, 0.0005, seed=seed)
         return g, block_embedding(g.labels, 128, seed=seed)
     if name == "zipf300k":
         g = sbm_zipf(300_000, 50, 1_000_000, 1.2, 0.10, seed=seed)
+        return g, block_embedding(g.labels, 128, seed=seed)
+    if name == "zipf100k":
+        g = sbm_zipf(100_000, 50, 333_333, 1.2, 0.10, seed=seed)
         return g, block_embedding(g.labels, 128, seed=seed)
     raise KeyError(name)
