@@ -14,10 +14,11 @@
 //     evaluations; p is taken at the last evaluated beta.  A row with
 //     |N(i)| <= perplexity cannot reach ln(perp) (its maximum entropy is
 //     ln |N(i)|) and is set uniform.
-//     Precision: d_ij is accumulated in FP64 (a one-time O(nnz d) cost) and
-//     beta (d - m) is formed in FP64, so that the large beta of small
-//     perplexities does not turn FP32 rounding of d ~ 10^2 into 1e-4 relative
-//     errors in p; exp, the entropy sums and the bisection run in FP32.
+//     Precision: the whole row computation (distances, exp, entropy sums,
+//     bisection) runs in FP64 and only p is rounded to FP32.  The build runs
+//     once per layout, and FP32 here turns the rounding of d ~ 10^2 into
+//     ~1e-4 relative errors in p at small perplexities (large beta) and can
+//     flip bisection decisions near the stopping tolerance.
 // K2  joint affinities (Eq. 3): p_ij = (p_{j|i} + p_{i|j}) / T with T the
 //     FP64 total of all numerators (T = 2n without isolated nodes), so that
 //     sum P = 1; the total is a fixed-order reduction.
@@ -31,12 +32,6 @@ namespace tsgne {
 namespace {
 
 constexpr int kAffCta = 256;
-
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -54,7 +49,7 @@ template <bool VEC4>
 __global__ void __launch_bounds__(kAffCta) k_cond_affinity(int n, const int64_t* __restrict__ rp,
                                                            const int32_t* __restrict__ col,
                                                            const float* __restrict__ X, int d, float perp,
-                                                           float Hstar, float tol, int max_iter,
+                                                           double Hstar, double tol, int max_iter,
                                                            double* __restrict__ dist, float* __restrict__ pcond) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -62,6 +57,11 @@ __global__ void __launch_bounds__(kAffCta) k_cond_affinity(int n, const int64_t*
     const int64_t a = rp[i], b = rp[i + 1];
     const int64_t k = b - a;
     if (k == 0) continue;
+    if ((float)k <= perp) {  // saturated row: uniform, no distances needed
+      const float u = 1.0f / (float)k;
+      for (int64_t e = a + lane; e < b; e += 32) pcond[e] = u;
+      continue;
+    }
     // squared distances in R^d, one neighbour at a time across the warp
     for (int64_t e = a; e < b; ++e) {
       const int64_t j = col[e];
@@ -88,37 +88,31 @@ __global__ void __launch_bounds__(kAffCta) k_cond_affinity(int n, const int64_t*
       if (lane == 0) dist[e] = s;
     }
     __syncwarp();
-    if ((float)k <= perp) {
-      const float u = 1.0f / (float)k;
-      for (int64_t e = a + lane; e < b; e += 32) pcond[e] = u;
-      continue;
-    }
     double m = INFINITY;
     for (int64_t e = a + lane; e < b; e += 32) m = fmin(m, dist[e]);
     m = warp_min_d(m);
-    float beta = 1.f, lo = -INFINITY, hi = INFINITY, S = 1.f;
+    double beta = 1.0, lo = -INFINITY, hi = INFINITY, S = 1.0;
     for (int it = 0; it < max_iter; ++it) {
-      float s = 0.f, E = 0.f;
+      double s = 0.0, E = 0.0;
       for (int64_t e = a + lane; e < b; e += 32) {
         const double delta = dist[e] - m;
-        const float w = expf(-(float)((double)beta * delta));
+        const double w = exp(-beta * delta);
         s += w;
-        E = fmaf((float)delta, w, E);
+        E += delta * w;
       }
-      S = warp_sum_f(s);
-      E = warp_sum_f(E);
-      const float H = logf(S) + beta * E / S;
-      if (fabsf(H - Hstar) <= tol || it == max_iter - 1) break;
+      S = warp_sum_d(s);
+      E = warp_sum_d(E);
+      const double H = log(S) + beta * E / S;
+      if (fabs(H - Hstar) <= tol || it == max_iter - 1) break;
       if (H > Hstar) {
         lo = beta;
-        beta = isinf(hi) ? 2.f * beta : 0.5f * (beta + hi);
+        beta = isinf(hi) ? 2.0 * beta : 0.5 * (beta + hi);
       } else {
         hi = beta;
-        beta = isinf(lo) ? 0.5f * beta : 0.5f * (beta + lo);
+        beta = isinf(lo) ? 0.5 * beta : 0.5 * (beta + lo);
       }
     }
-    const float invS = 1.f / S;
-    for (int64_t e = a + lane; e < b; e += 32) pcond[e] = expf(-(float)((double)beta * (dist[e] - m))) * invS;
+    for (int64_t e = a + lane; e < b; e += 32) pcond[e] = (float)(exp(-beta * (dist[e] - m)) / S);
   }
 }
 
@@ -166,7 +160,7 @@ tsgne_status build_affinities(int n, const int64_t* rp, const int32_t* col, cons
   DevBuf<float> pcond;
   TS_TRY(dist.alloc((size_t)nnz));
   TS_TRY(pcond.alloc((size_t)nnz));
-  const float Hstar = (float)std::log((double)perplexity);
+  const double Hstar = std::log((double)perplexity);
   int64_t rows_per_cta = kAffCta / 32;
   int64_t g = ((int64_t)n + rows_per_cta - 1) / rows_per_cta;
   int grid = (int)(g < sms * 64 ? (g < 1 ? 1 : g) : sms * 64);
