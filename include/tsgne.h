@@ -201,6 +201,33 @@ tsgne_status tsgne_repulsion_shape(tsgne_ctx* ctx, int32_t* grid, int32_t* block
 /* Waits for all work of the context; reports a pending NONFINITE layout. */
 tsgne_status tsgne_sync(tsgne_ctx* ctx);
 
+/* Largest n accepted by tsgne_repulsion_noalloc. */
+#define TSGNE_NOALLOC_MAX_N 65536
+
+/*
+ * Repulsion pass that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, e.g. code running inside a framework or plugin host that owns
+ * the device-memory budget, or code that must not trigger the device-wide
+ * synchronisation an allocation or free can cause.
+ *
+ * Computes, for the layout Y (device float[n*2], row-major x, y), the
+ * unnormalised repulsive sums F^r_i = sum_{j != i} w_ij^2 (y_i - y_j) into
+ * frep_out (device float[n*2]) and Z = sum_{k != l} w_kl into z_out (one
+ * device double), with w = (1 + ||y_k - y_l||^2)^-1 -- the same quantities as
+ * the repulsion pass of tsgne_step.  Work is enqueued on cuda_stream (NULL =
+ * the legacy default stream); nothing is synchronised.  No context is used.
+ *
+ * Temporaries live in one static device array of about 8.6 MiB that every GPU
+ * loading the library holds until the process exits.  2 <= n <=
+ * TSGNE_NOALLOC_MAX_N, else TSGNE_ERR_INVALID_ARG before any work.  The first
+ * call on a device looks up that array's address with the device current:
+ * make it before any stream capture.  All calls share the array (each call
+ * clears what must start at zero and overwrites what it reads), so calls
+ * that overlap on the GPU race; serialise them on one stream.
+ */
+tsgne_status tsgne_repulsion_noalloc(int32_t n, const float* Y, float* frep_out, double* z_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,8 @@ __all__ = [
     "tsgne_kernel_times",
     "tsgne_repulsion_shape",
     "tsgne_sync",
+    "tsgne_repulsion_noalloc",
+    "NOALLOC_MAX_N",
     "Layout",
     "KERNEL_CLASSES",
 ]
@@ -124,7 +126,10 @@ EXPORTS = {
     "tsgne_kernel_times": (_st, [_p, _p, _p, _i32, _i32]),
     "tsgne_repulsion_shape": (_st, [_p] + [ctypes.POINTER(_i32)] * 6),
     "tsgne_sync": (_st, [_p]),
+    "tsgne_repulsion_noalloc": (_st, [_i32, _p, _p, _p, _p]),
 }
+
+NOALLOC_MAX_N = 65536  # TSGNE_NOALLOC_MAX_N
 
 _lib = None
 
@@ -335,6 +340,41 @@ def tsgne_repulsion_shape(ctx):
 
 def tsgne_sync(ctx):
     _check(ctx, lib().tsgne_sync(ctx))
+
+
+def tsgne_repulsion_noalloc(Y, frep_out=None, z_out=None, stream=None):
+    """Repulsion pass without any device allocation by the library.
+
+    For callers that cannot allocate device memory (a host framework owns the
+    memory budget, or allocation would synchronise the device): Y, frep_out
+    (n x 2 float32) and z_out (1 float64) are CUDA tensors owned by the caller;
+    temporaries live in a static device array of the library.  Returns
+    (frep_out, z_out) with F^r_i = sum_{j != i} w_ij^2 (y_i - y_j) and
+    Z = sum_{k != l} w_kl.  At most NOALLOC_MAX_N points.  Calls that overlap
+    on the GPU share that array and race: keep them on one stream.
+    """
+    torch = _torch()
+    if torch is None or not isinstance(Y, torch.Tensor) or not Y.is_cuda:
+        raise ValueError("Y must be a CUDA tensor")
+    Yc = Y.contiguous().float()
+    n = int(Yc.shape[0])
+    if frep_out is None:
+        frep_out = torch.empty((n, 2), dtype=torch.float32, device=Yc.device)
+    if z_out is None:
+        z_out = torch.empty((1,), dtype=torch.float64, device=Yc.device)
+    if not (frep_out.is_cuda and frep_out.dtype == torch.float32 and frep_out.is_contiguous()):
+        raise ValueError("frep_out must be a contiguous float32 CUDA tensor")
+    if not (z_out.is_cuda and z_out.dtype == torch.float64):
+        raise ValueError("z_out must be a float64 CUDA tensor")
+    s = stream if stream is not None else torch.cuda.current_stream(Yc.device)
+    handle = ctypes.c_void_p(getattr(s, "cuda_stream", s))
+    st = lib().tsgne_repulsion_noalloc(n, ctypes.c_void_p(Yc.data_ptr()), ctypes.c_void_p(frep_out.data_ptr()),
+                                       ctypes.c_void_p(z_out.data_ptr()), handle)
+    if st != 0:
+        why = (f"n = {n} exceeds the no-allocation maximum of {NOALLOC_MAX_N} points" if n > NOALLOC_MAX_N
+               else "tsgne_repulsion_noalloc failed")
+        raise TsgneError(st, why)
+    return frep_out, z_out
 
 
 # ------------------------------------------------------------ convenience
