@@ -216,9 +216,9 @@ tsgne_status enqueue_repulsion(tsgne_ctx* ctx, int advance) {
   const tsgne_config& c = ctx->cfg;
   ProfRec pr;
   TS_TRY(prof_begin(ctx, 0, &pr));
-  TS_TRY(launch_repulsion(ctx->shape, ctx->n, ctx->Y[ctx->cur].get(), ctx->frep.get(), ctx->zpart.get(),
-                          ctx->sched.get(), advance, c.early_exag, c.ee_iters, c.momentum0, c.momentum1,
-                          ctx->stream));
+  TS_TRY(launch_repulsion_sym(ctx->shape, ctx->n, ctx->Y[ctx->cur].get(), ctx->frep.get(), ctx->zpart.get(),
+                              ctx->sched.get(), advance, c.early_exag, c.ee_iters, c.momentum0, c.momentum1,
+                              ctx->stream));
   return prof_end(ctx, &pr);
 }
 
@@ -280,7 +280,8 @@ tsgne_status ensure_graph(tsgne_ctx* ctx, int start) {
 
 // Allocates the per-layout buffers for n points (after P is known).
 tsgne_status alloc_layout(tsgne_ctx* ctx) {
-  ctx->shape = repulsion_shape(ctx->n, ctx->sms);
+  ctx->shape = repulsion_shape_sym(ctx->n, ctx->sms);
+  TS_TRY(repulsion_sym_prepare(ctx->shape));
   const size_t np = (size_t)ctx->shape.n_pad;
   TS_TRY(ctx->Y[0].alloc(np));
   TS_TRY(ctx->Y[1].alloc(np));
@@ -288,7 +289,7 @@ tsgne_status alloc_layout(tsgne_ctx* ctx) {
   TS_TRY(ctx->gains.alloc(np));
   TS_TRY(ctx->grad.alloc(np));
   TS_TRY(ctx->frep.alloc(np * (size_t)ctx->shape.chunks));
-  TS_TRY(ctx->zpart.alloc(repulsion_zpart_count(ctx->shape)));
+  TS_TRY(ctx->zpart.alloc((size_t)ctx->shape.units));
   TS_TRY(ctx->klpart.alloc(2 * (size_t)kl_partial_count(ctx->sms)));
   TS_TRY(launch_fill_sentinel(ctx->Y[0].get(), 0, (int)np, ctx->stream));
   TS_TRY(launch_fill_sentinel(ctx->Y[1].get(), 0, (int)np, ctx->stream));

@@ -1,0 +1,305 @@
+// Symmetric exact repulsion (Sec. 2.1, Eq. 4): each unordered pair {i, j} is
+// evaluated once and its force is applied to both points,
+//   w = (1 + ||y_i - y_j||^2)^-1,  F^r_i += w^2 (y_i - y_j),  F^r_j -= w^2 (y_i - y_j),
+//   Z += 2 w  (Z sums ordered pairs k != l).
+// Per unordered pair this is 10 FP32 lane-ops and one MUFU reciprocal, i.e.
+// 5 lane-ops and half a reciprocal per ordered pair (the ordered kernel in
+// repulsion.cu spends 8 and 1).
+//
+// Decomposition.  Points are padded to n_pad = nt * T (T = 256 W) with the
+// sentinel point.  A unit of work is a tile pair (a, b), a <= b; the units
+// are enumerated row by row and taken from a global work queue by a
+// persistent grid (16 warps per SM).  Unit (a, b), a < b, writes the forces
+// of tile a's points into slot b and those of tile b's points into slot a of
+// part[slot][point]; the diagonal unit (t, t) evaluates its ordered pairs
+// with the i-side only and writes slot t.  Every slot of every point is
+// written exactly once per pass, so the update kernel's fixed-order sum over
+// the nt slots gives bit-reproducible forces whatever CTA ran which unit.
+// Each unit also writes its own FP64 Z partial; the last CTA adds them in unit
+// order, removes the n self terms w_ii = 1 and sets the iteration schedule.
+//
+// Inside a unit (a < b).  Each of the W warps holds 256 points of tile a in
+// registers (8 per lane, as four FP32x2 pairs).  Tile b sits in shared
+// memory as {-x, -x, -y, -y} plus an FP32 force accumulator per point, cut
+// into 4W groups of 64 points.  In phase p warp w works on group (w + p) mod
+// 4W, so no two warps touch the same accumulators at once and no atomics are
+// needed.  Within a warp, lane l starts with the accumulators of the group's
+// points 2l and 2l+1; each of 32 steps evaluates the lane's 8 i-points
+// against those 2 j-points, then passes the j accumulators one lane down the
+// ring (shuffle); after 32 steps every j has met all 256 i of the warp and
+// its accumulators are back home.  Only sentinel points lie in the last tile,
+// and a < b means tile a never holds any, so sentinel-sentinel pairs (w = 1)
+// occur only in the diagonal unit, where they are masked out of Z.
+#include "f32x2.cuh"
+#include "reduce.cuh"
+#include "tsgne_internal.cuh"
+
+namespace tsgne {
+
+namespace {
+
+constexpr int kRI = 8;              // i-points per lane
+constexpr int kH = kRI / 2;         // FP32x2 pairs of i-points per lane
+constexpr int kWarpsPerSm = 16;     // resident warps per SM the grid is sized for
+constexpr int kGroup = 64;          // j-points per ring group (32 lanes x 2)
+
+__device__ __forceinline__ int row_start(int a, int nt) { return a * nt - (a * (a - 1)) / 2; }
+
+// One j-point against the lane's 8 i-points; acc (x, y) is the running sum
+// of w^2 (y_i - y_j) over i for this j.
+__device__ __forceinline__ void ring_pair(const float4 q, float& accx, float& accy, const u64 (&X2)[kH],
+                                          const u64 (&Y2)[kH], u64 (&FX)[kH], u64 (&FY)[kH], u64 (&Z2)[kH],
+                                          const u64 one2) {
+  const u64 nx = pk(q.x, q.y);
+  const u64 ny = pk(q.z, q.w);
+  u64 PX = pk(accx, 0.f), PY = pk(accy, 0.f);
+#pragma unroll
+  for (int h = 0; h < kH; ++h) {
+    const u64 dx = add2(X2[h], nx);
+    const u64 dy = add2(Y2[h], ny);
+    u64 qq = fma2(dx, dx, one2);
+    qq = fma2(dy, dy, qq);
+    float q0, q1;
+    upk(qq, q0, q1);
+    const u64 w = pk(rcp_approx(q0), rcp_approx(q1));
+    Z2[h] = add2(Z2[h], w);
+    const u64 w2 = mul2(w, w);
+    FX[h] = fma2(w2, dx, FX[h]);
+    FY[h] = fma2(w2, dy, FY[h]);
+    PX = fma2(w2, dx, PX);
+    PY = fma2(w2, dy, PY);
+  }
+  float a0, a1;
+  upk(PX, a0, a1);
+  accx = a0 + a1;
+  upk(PY, a0, a1);
+  accy = a0 + a1;
+}
+
+template <int W>
+__global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
+    k_repulsion_sym(const float2* __restrict__ Y, int n, int nt, int n_pad, float2* __restrict__ part,
+                    double* __restrict__ zunit, Sched* sched, int advance, float ee, int ee_iters, float mom0,
+                    float mom1) {
+  constexpr int T = W * 32 * kRI;
+  constexpr int G = T / kGroup;  // = 4W groups
+  extern __shared__ float4 smem[];
+  float4* sj = smem;                                   // T x {-x, -x, -y, -y}
+  float2* sacc = reinterpret_cast<float2*>(smem + T);  // T x force accumulator
+  __shared__ int s_unit, s_a, s_b;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u64 one2 = pk(1.f, 1.f);
+  const int units = nt * (nt + 1) / 2;
+
+  for (;;) {
+    if (tid == 0) {
+      const int u = (int)atomicAdd(&sched->work_next, 1u);
+      int a = 0;
+      if (u < units) {
+        int lo = 0, hi = nt - 1;  // largest a with row_start(a) <= u
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (row_start(mid, nt) <= u) lo = mid; else hi = mid - 1;
+        }
+        a = lo;
+      }
+      s_unit = u;
+      s_a = a;
+      s_b = u < units ? a + (u - row_start(a, nt)) : 0;
+    }
+    __syncthreads();
+    const int u = s_unit, a = s_a, b = s_b;
+    if (u >= units) break;
+
+    // j tile b into shared memory
+    for (int k = tid; k < T; k += W * 32) {
+      const float2 p = Y[(size_t)b * T + k];
+      sj[k] = make_float4(-p.x, -p.x, -p.y, -p.y);
+      sacc[k] = make_float2(0.f, 0.f);
+    }
+    // i points of tile a: lane holds i = a*T + warp*256 + r*32 + lane, r = 0..7
+    const int ibase = a * T + warp * (32 * kRI) + lane;
+    u64 X2[kH], Y2[kH], FX[kH], FY[kH], Z2[kH];
+#pragma unroll
+    for (int h = 0; h < kH; ++h) {
+      const float2 p0 = Y[ibase + (2 * h) * 32];
+      const float2 p1 = Y[ibase + (2 * h + 1) * 32];
+      X2[h] = pk(p0.x, p1.x);
+      Y2[h] = pk(p0.y, p1.y);
+      FX[h] = FY[h] = Z2[h] = 0ull;
+    }
+    __syncthreads();
+
+    double zt = 0.0;
+    if (a != b) {
+      for (int ph = 0; ph < G; ++ph) {
+        const int g = (warp + ph) & (G - 1);
+        const float4* gj = sj + g * kGroup;
+        float2* ga = sacc + g * kGroup;
+        float2 c0 = ga[2 * lane], c1 = ga[2 * lane + 1];
+        float ax0 = c0.x, ay0 = c0.y, ax1 = c1.x, ay1 = c1.y;
+        const int src = (lane + 1) & 31;
+#pragma unroll 2
+        for (int s = 0; s < 32; ++s) {
+          const int jj = (lane + s) & 31;
+          const float4 q0 = gj[2 * jj];
+          const float4 q1 = gj[2 * jj + 1];
+          ring_pair(q0, ax0, ay0, X2, Y2, FX, FY, Z2, one2);
+          ring_pair(q1, ax1, ay1, X2, Y2, FX, FY, Z2, one2);
+          ax0 = __shfl_sync(0xffffffffu, ax0, src);
+          ay0 = __shfl_sync(0xffffffffu, ay0, src);
+          ax1 = __shfl_sync(0xffffffffu, ax1, src);
+          ay1 = __shfl_sync(0xffffffffu, ay1, src);
+        }
+        ga[2 * lane] = make_float2(ax0, ay0);
+        ga[2 * lane + 1] = make_float2(ax1, ay1);
+        __syncthreads();
+      }
+#pragma unroll
+      for (int h = 0; h < kH; ++h) {
+        float z0, z1;
+        upk(Z2[h], z0, z1);
+        zt += 2.0 * ((double)z0 + (double)z1);  // tile a holds no padding
+      }
+      // j side: F_j = -sum_i w^2 (y_i - y_j), into slot a of tile b's points
+      float2* outj = part + (size_t)a * n_pad + (size_t)b * T;
+      for (int k = tid; k < T; k += W * 32) {
+        const float2 v = sacc[k];
+        outj[k] = make_float2(-v.x, -v.y);
+      }
+    } else {
+      // diagonal unit: ordered pairs within the tile, i side only
+#pragma unroll 2
+      for (int j = 0; j < T; ++j) {
+        const float4 q = sj[j];
+        const u64 nx = pk(q.x, q.y);
+        const u64 ny = pk(q.z, q.w);
+#pragma unroll
+        for (int h = 0; h < kH; ++h) {
+          const u64 dx = add2(X2[h], nx);
+          const u64 dy = add2(Y2[h], ny);
+          u64 qq = fma2(dx, dx, one2);
+          qq = fma2(dy, dy, qq);
+          float q0, q1;
+          upk(qq, q0, q1);
+          const u64 w = pk(rcp_approx(q0), rcp_approx(q1));
+          Z2[h] = add2(Z2[h], w);
+          const u64 w2 = mul2(w, w);
+          FX[h] = fma2(w2, dx, FX[h]);
+          FY[h] = fma2(w2, dy, FY[h]);
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < kH; ++h) {
+        float z0, z1;
+        upk(Z2[h], z0, z1);
+        if (ibase + (2 * h) * 32 < n) zt += (double)z0;
+        if (ibase + (2 * h + 1) * 32 < n) zt += (double)z1;
+      }
+    }
+    // i side of tile a into slot b
+    float2* outi = part + (size_t)b * n_pad;
+#pragma unroll
+    for (int h = 0; h < kH; ++h) {
+      float fx0, fx1, fy0, fy1;
+      upk(FX[h], fx0, fx1);
+      upk(FY[h], fy0, fy1);
+      outi[ibase + (2 * h) * 32] = make_float2(fx0, fy0);
+      outi[ibase + (2 * h + 1) * 32] = make_float2(fx1, fy1);
+    }
+    const double zb = block_sum_d(zt);
+    if (tid == 0) zunit[u] = zb;
+    __syncthreads();  // shared tiles are rewritten by the next unit
+  }
+
+  if (arrive_last(&sched->rep_done)) {
+    const double total = sum_partials(zunit, units);
+    if (tid == 0) {
+      sched->work_next = 0u;
+      sched->Z = total - (double)n;
+      const int t = sched->t;
+      sched->alpha = t < ee_iters ? ee : 1.0f;
+      sched->mu = t < ee_iters ? mom0 : mom1;
+      if (advance) sched->t = t + 1;
+    }
+  }
+}
+
+template <int W>
+size_t smem_bytes() {
+  constexpr int T = W * 32 * kRI;
+  return (size_t)T * (sizeof(float4) + sizeof(float2));
+}
+
+template <int W>
+tsgne_status prepare() {
+  TS_CUDA(cudaFuncSetAttribute(k_repulsion_sym<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_bytes<W>()));
+  return TSGNE_OK;
+}
+
+template <int W>
+tsgne_status launch(const RepShape& sh, int n, const float2* Y, float2* part, double* zunit, Sched* sched,
+                    int advance, float ee, int ee_iters, float mom0, float mom1, cudaStream_t s) {
+  k_repulsion_sym<W><<<sh.grid, W * 32, sh.smem, s>>>(Y, n, sh.chunks, sh.n_pad, part, zunit, sched, advance, ee,
+                                                      ee_iters, mom0, mom1);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+}  // namespace
+
+RepShape repulsion_shape_sym(int n, int sm_count) {
+  RepShape sh;
+  int W = 8;
+  for (int w : {8, 4, 2, 1}) {
+    W = w;
+    const long T = 32L * kRI * w;
+    const long nt = (n + T - 1) / T;
+    const long units = nt * (nt + 1) / 2;
+    const long slots = (long)sm_count * (kWarpsPerSm / w);
+    if (units >= 4 * slots) break;
+  }
+  const int T = 32 * kRI * W;
+  const int nt = (n + T - 1) / T;
+  sh.warps = W;
+  sh.block = 32 * W;
+  sh.R = kRI;
+  sh.jtile = T;
+  sh.chunks = nt;
+  sh.n_pad = nt * T;
+  sh.n_iblk = nt;
+  sh.n_jtiles = nt;
+  sh.units = nt * (nt + 1) / 2;
+  const int slots = sm_count * (kWarpsPerSm / W);
+  sh.grid = sh.units < slots ? sh.units : slots;
+  switch (W) {
+    case 8: sh.smem = smem_bytes<8>(); break;
+    case 4: sh.smem = smem_bytes<4>(); break;
+    case 2: sh.smem = smem_bytes<2>(); break;
+    default: sh.smem = smem_bytes<1>(); break;
+  }
+  return sh;
+}
+
+tsgne_status repulsion_sym_prepare(const RepShape& sh) {
+  switch (sh.warps) {
+    case 8: return prepare<8>();
+    case 4: return prepare<4>();
+    case 2: return prepare<2>();
+    default: return prepare<1>();
+  }
+}
+
+tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const float2* Y, float2* frep_part, double* zpart,
+                                  Sched* sched, int advance, float ee, int ee_iters, float mom0, float mom1,
+                                  cudaStream_t s) {
+  switch (sh.warps) {
+    case 8: return launch<8>(sh, n, Y, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+    case 4: return launch<4>(sh, n, Y, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+    case 2: return launch<2>(sh, n, Y, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+    default: return launch<1>(sh, n, Y, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+  }
+}
+
+}  // namespace tsgne

@@ -24,22 +24,26 @@ struct Sched {
   uint32_t flags;      // bit 0: non-finite layout seen; bit 1: non-finite P
   uint32_t rep_done;   // last-CTA counter of the repulsion pass
   uint32_t red_done;   // last-CTA counter of the generic reductions
+  uint32_t work_next;  // work-queue head of the symmetric repulsion pass
   double red[4];       // results of the generic reductions
 };
 
 constexpr uint32_t kFlagNonfiniteY = 1u;
 constexpr uint32_t kFlagNonfiniteP = 2u;
 
-// Geometry of one repulsion pass (see repulsion.cu).
+// Geometry of one repulsion pass (see repulsion.cu and repulsion_sym.cu).
 struct RepShape {
   int grid = 0;      // CTAs (a multiple of the SM count when the work allows)
   int block = 0;     // threads per CTA
   int R = 0;         // i-points per thread
   int jtile = 0;     // j-points staged in shared memory per tile
-  int chunks = 0;    // j-range chunks (partial force slots per point)
+  int chunks = 0;    // partial force slots per point (ordered: j-chunks; symmetric: tiles)
   int n_pad = 0;     // padded length of Y buffers
   int n_iblk = 0;    // i-blocks of block*R points
   int n_jtiles = 0;  // j-tiles of jtile points
+  int units = 0;     // work units of one pass (symmetric: tile pairs a <= b)
+  int warps = 0;     // warps per CTA (symmetric)
+  size_t smem = 0;   // dynamic shared memory per CTA (symmetric)
 };
 
 // Last error message of the calling thread (copied into the context by the API layer).
@@ -118,6 +122,16 @@ size_t repulsion_zpart_count(const RepShape& sh);
 tsgne_status launch_repulsion(const RepShape& sh, int n, const float2* Y, float2* frep_part, double* zpart,
                               Sched* sched, int advance, float ee, int ee_iters, float mom0, float mom1,
                               cudaStream_t s);
+
+// Symmetric pass: every unordered pair once (repulsion_sym.cu).  Same
+// outputs as launch_repulsion with chunks = number of tiles; zpart needs
+// sh.units doubles.  repulsion_sym_prepare sets kernel attributes (call it
+// outside stream capture, once per shape).
+RepShape repulsion_shape_sym(int n, int sm_count);
+tsgne_status repulsion_sym_prepare(const RepShape& sh);
+tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const float2* Y, float2* frep_part, double* zpart,
+                                  Sched* sched, int advance, float ee, int ee_iters, float mom0, float mom1,
+                                  cudaStream_t s);
 
 // ------------------------------------------------------------ iteration
 // Attraction + gradient + optimiser update: reads Ycur, writes Ynext.
