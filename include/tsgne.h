@@ -188,7 +188,8 @@ tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update
  * Profiling (cfg.profile = 1): cumulative device time in ms and launch count
  * of each kernel class since the last reset, measured with CUDA events on
  * the context's stream.  Classes: 0 repulsion, 1 attraction+update,
- * 2 gradient export, 3 KL, 4 build.  ms and launches hold n entries (n <= 5).
+ * 2 gradient export, 3 KL, 4 build, 5 repulsion slot reduction.  ms and
+ * launches hold n entries (n <= 6).
  * reset != 0 clears the counters after reading.  Synchronises.
  */
 tsgne_status tsgne_kernel_times(tsgne_ctx* ctx, double* ms, int64_t* launches, int32_t n, int32_t reset);
@@ -200,6 +201,65 @@ tsgne_status tsgne_repulsion_shape(tsgne_ctx* ctx, int32_t* grid, int32_t* block
 
 /* Waits for all work of the context; reports a pending NONFINITE layout. */
 tsgne_status tsgne_sync(tsgne_ctx* ctx);
+
+/*
+ * ---------------------------------------------------------------- batches
+ * Many layouts advanced together: every iteration of every member runs in
+ * four kernel launches (replayed as one CUDA graph per membership) instead of
+ * two launches per member.  Each member keeps its own P, layout, optimiser
+ * state and iteration counter on the device, may be added or removed between
+ * runs (continuous batching), and evolves exactly as it would in a batch of
+ * its own: the per-member arithmetic, including the order of every
+ * reduction, does not depend on the other members.  All members share one
+ * repulsion tile of 256 * tile_warps points (1, 2, 4 or 8; smaller tiles pad
+ * small graphs less, larger tiles amortise more per unit).  The same
+ * conventions as the context API apply (status codes, one stream, not
+ * thread-safe); the batch API has its own error string.
+ */
+typedef struct tsgne_batch tsgne_batch;
+
+/* Creates an empty batch; tile_warps 0 means 1 until tsgne_batch_autotune runs. */
+tsgne_status tsgne_batch_create(tsgne_batch** out, const tsgne_config* cfg, int32_t tile_warps, void* cuda_stream);
+void tsgne_batch_destroy(tsgne_batch* b);
+const char* tsgne_batch_last_error(const tsgne_batch* b);
+
+/*
+ * Adds a layout: builds its P exactly as tsgne_build_P does (same arguments)
+ * and sets its initial layout Y0 (float[n*2]; NULL: N(0, 1e-4^2) from
+ * cfg.seed), updates 0, gains 1, iteration 0.  *id_out receives the member id.
+ */
+tsgne_status tsgne_batch_add(tsgne_batch* b, int32_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* X,
+                             int32_t d, const float* Y0, int32_t ptr_kind, int32_t* id_out);
+
+/* Removes a member and frees its device memory. */
+tsgne_status tsgne_batch_remove(tsgne_batch* b, int32_t id);
+
+/* Members, tile warps and total repulsion work units of one iteration. */
+tsgne_status tsgne_batch_size(tsgne_batch* b, int32_t* members, int32_t* tile_warps, int64_t* units);
+
+/* n_iter iterations of every member; synchronises; NONFINITE if any layout diverged. */
+tsgne_status tsgne_batch_run(tsgne_batch* b, int32_t n_iter);
+
+/* Current layout of a member (float[n*2]) and its iteration count (host, may be NULL). */
+tsgne_status tsgne_batch_get_Y(tsgne_batch* b, int32_t id, float* Y_out, int32_t* iter, int32_t ptr_kind);
+
+/* Changes the repulsion tile of the batch (members' states are kept). */
+tsgne_status tsgne_batch_set_tile(tsgne_batch* b, int32_t tile_warps);
+
+/* Resets every member to its initial layout, updates 0, gains 1, iteration 0. */
+tsgne_status tsgne_batch_reset(tsgne_batch* b);
+
+/*
+ * Tile autotuner: times trial_iters iterations of the current membership
+ * with each tile (1, 2, 4, 8 warps), keeps the fastest, records it in a
+ * process-wide cache keyed by (SM count, log2 of the pair count, log2 of the
+ * member count), and resets every member (tsgne_batch_reset).  *chosen gets
+ * the tile; ms_per_iter (may be NULL) gets the 4 measured times.
+ */
+tsgne_status tsgne_batch_autotune(tsgne_batch* b, int32_t trial_iters, int32_t* chosen, float* ms_per_iter);
+
+/* Cached tile for the current membership's key, 0 if none was tuned yet. */
+tsgne_status tsgne_batch_cached_tile(tsgne_batch* b, int32_t* tile_warps);
 
 /* Largest n accepted by tsgne_repulsion_noalloc. */
 #define TSGNE_NOALLOC_MAX_N 65536

@@ -49,6 +49,7 @@ __all__ = [
     "tsgne_repulsion_noalloc",
     "NOALLOC_MAX_N",
     "Layout",
+    "Batch",
     "KERNEL_CLASSES",
 ]
 
@@ -56,7 +57,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_PKG, "lib", "libtsgne.so")
 
 PTR_HOST, PTR_DEVICE = 0, 1
-KERNEL_CLASSES = ("repulsion", "attract_update", "gradient", "kl", "build")
+KERNEL_CLASSES = ("repulsion", "attract_update", "gradient", "kl", "build", "reduce_slots")
 
 STATUS = {
     0: "TSGNE_OK",
@@ -127,6 +128,18 @@ EXPORTS = {
     "tsgne_repulsion_shape": (_st, [_p] + [ctypes.POINTER(_i32)] * 6),
     "tsgne_sync": (_st, [_p]),
     "tsgne_repulsion_noalloc": (_st, [_i32, _p, _p, _p, _p]),
+    "tsgne_batch_create": (_st, [ctypes.POINTER(_p), ctypes.POINTER(Config), _i32, _p]),
+    "tsgne_batch_destroy": (None, [_p]),
+    "tsgne_batch_last_error": (ctypes.c_char_p, [_p]),
+    "tsgne_batch_add": (_st, [_p, _i32, _p, _p, _p, _i32, _p, _i32, ctypes.POINTER(_i32)]),
+    "tsgne_batch_remove": (_st, [_p, _i32]),
+    "tsgne_batch_size": (_st, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "tsgne_batch_run": (_st, [_p, _i32]),
+    "tsgne_batch_get_Y": (_st, [_p, _i32, _p, ctypes.POINTER(_i32), _i32]),
+    "tsgne_batch_set_tile": (_st, [_p, _i32]),
+    "tsgne_batch_reset": (_st, [_p]),
+    "tsgne_batch_autotune": (_st, [_p, _i32, ctypes.POINTER(_i32), _p]),
+    "tsgne_batch_cached_tile": (_st, [_p, ctypes.POINTER(_i32)]),
 }
 
 NOALLOC_MAX_N = 65536  # TSGNE_NOALLOC_MAX_N
@@ -462,6 +475,106 @@ class Layout:
         if getattr(self, "ctx", None):
             tsgne_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batches
+
+class Batch:
+    """Many layouts advanced together (the ``tsgne_batch_*`` C calls).
+
+    >>> b = Batch(tile_warps=2)
+    >>> ids = [b.add(g.row_ptr, g.col, X, Y0) for g, X, Y0 in graphs]
+    >>> b.run(100); Y, it = b.get_Y(ids[0])
+    """
+
+    def __init__(self, config: Config | None = None, tile_warps: int = 0, stream=None, **overrides):
+        cfg = config if config is not None else tsgne_config_default()
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.config = cfg
+        self._stream = stream
+        if stream is None:
+            torch = _torch()
+            if torch is not None and torch.cuda.is_available():
+                self._stream = torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(getattr(self._stream, "cuda_stream", self._stream)) if self._stream is not None else None
+        st = lib().tsgne_batch_create(ctypes.byref(h), ctypes.byref(cfg), int(tile_warps), s)
+        if st != 0:
+            raise TsgneError(st, "tsgne_batch_create failed")
+        self.h = h
+        self.sizes = {}
+
+    def _check(self, st):
+        if st != 0:
+            raise TsgneError(st, lib().tsgne_batch_last_error(self.h).decode())
+
+    def add(self, row_ptr, col, X, Y0=None) -> int:
+        rp = _as_buffer(row_ptr, np.int64)
+        ci = _as_buffer(col, np.int32)
+        x = _as_buffer(X, np.float32)
+        y = _as_buffer(Y0, np.float32)
+        kind = _same_kind(rp, ci, x, y)
+        out = _i32()
+        n = len(row_ptr) - 1
+        self._check(lib().tsgne_batch_add(self.h, n, rp[0], ci[0], x[0], int(X.shape[1]), y[0], kind,
+                                          ctypes.byref(out)))
+        self.sizes[out.value] = n
+        return out.value
+
+    def remove(self, mid: int):
+        self._check(lib().tsgne_batch_remove(self.h, int(mid)))
+        self.sizes.pop(mid, None)
+
+    def size(self):
+        m, w, u = _i32(), _i32(), _i64()
+        self._check(lib().tsgne_batch_size(self.h, ctypes.byref(m), ctypes.byref(w), ctypes.byref(u)))
+        return {"members": m.value, "tile_warps": w.value, "units": u.value}
+
+    def run(self, n_iter: int):
+        self._check(lib().tsgne_batch_run(self.h, int(n_iter)))
+
+    def get_Y(self, mid: int, out=None):
+        n = self.sizes[mid]
+        out, buf = _out(n, out)
+        it = _i32()
+        self._check(lib().tsgne_batch_get_Y(self.h, int(mid), buf[0], ctypes.byref(it), buf[1]))
+        return out, it.value
+
+    def set_tile(self, tile_warps: int):
+        self._check(lib().tsgne_batch_set_tile(self.h, int(tile_warps)))
+
+    def reset(self):
+        self._check(lib().tsgne_batch_reset(self.h))
+
+    def autotune(self, trial_iters: int = 3):
+        chosen = _i32()
+        ms = np.zeros(4, np.float32)
+        self._check(lib().tsgne_batch_autotune(self.h, int(trial_iters), ctypes.byref(chosen),
+                                               ms.ctypes.data_as(_p)))
+        return chosen.value, dict(zip((1, 2, 4, 8), ms.tolist()))
+
+    def cached_tile(self) -> int:
+        w = _i32()
+        self._check(lib().tsgne_batch_cached_tile(self.h, ctypes.byref(w)))
+        return w.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tsgne_batch_destroy(self.h)
+            self.h = None
 
     def __enter__(self):
         return self

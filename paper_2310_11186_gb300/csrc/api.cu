@@ -38,7 +38,7 @@ __global__ void k_cmp_i32(const int32_t* a, const int32_t* b, int64_t n, uint32_
     if (a[k] != b[k]) atomicOr(neq, 1u);
 }
 
-constexpr int kClasses = 5;  // repulsion, attraction+update, gradient, KL, build
+constexpr int kClasses = 6;  // repulsion, attraction+update, gradient, KL, build, slot reduction
 
 struct ProfRec {
   int cls;
@@ -71,7 +71,7 @@ struct tsgne_ctx {
   DevBuf<float> P;
   DevBuf<float2> Y[2];
   int cur = 0;
-  DevBuf<float2> upd, gains, frep, grad;
+  DevBuf<float2> upd, gains, frep, fsum, grad;
   DevBuf<double> zpart, klpart;
   DevBuf<Sched> sched;
 
@@ -79,8 +79,8 @@ struct tsgne_ctx {
 
   std::vector<ProfRec> pending;
   std::vector<cudaEvent_t> spare;
-  double prof_ms[kClasses] = {0, 0, 0, 0, 0};
-  int64_t prof_n[kClasses] = {0, 0, 0, 0, 0};
+  double prof_ms[kClasses] = {0, 0, 0, 0, 0, 0};
+  int64_t prof_n[kClasses] = {0, 0, 0, 0, 0, 0};
 
   ~tsgne_ctx() {
     reset_graphs();
@@ -219,7 +219,12 @@ tsgne_status enqueue_repulsion(tsgne_ctx* ctx, int advance) {
   TS_TRY(launch_repulsion_sym(ctx->shape, ctx->n, ctx->Y[ctx->cur].get(), ctx->frep.get(), ctx->zpart.get(),
                               ctx->sched.get(), advance, c.early_exag, c.ee_iters, c.momentum0, c.momentum1,
                               ctx->stream));
-  return prof_end(ctx, &pr);
+  TS_TRY(prof_end(ctx, &pr));
+  ProfRec pr2;
+  TS_TRY(prof_begin(ctx, 5, &pr2));
+  TS_TRY(launch_reduce_slots(ctx->n, ctx->frep.get(), ctx->shape.chunks, ctx->shape.n_pad, ctx->fsum.get(),
+                             ctx->stream));
+  return prof_end(ctx, &pr2);
 }
 
 tsgne_status enqueue_step(tsgne_ctx* ctx) {
@@ -228,8 +233,8 @@ tsgne_status enqueue_step(tsgne_ctx* ctx) {
   TS_TRY(prof_begin(ctx, 1, &pr));
   const int nxt = ctx->cur ^ 1;
   TS_TRY(launch_attract_update(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
-                               ctx->Y[nxt].get(), ctx->upd.get(), ctx->gains.get(), ctx->frep.get(),
-                               ctx->shape.chunks, ctx->shape.n_pad, ctx->sched.get(), ctx->eta, ctx->cfg.min_gain,
+                               ctx->Y[nxt].get(), ctx->upd.get(), ctx->gains.get(), ctx->fsum.get(), 1,
+                               ctx->shape.n_pad, ctx->sched.get(), ctx->eta, ctx->cfg.min_gain,
                                ctx->stream));
   TS_TRY(prof_end(ctx, &pr));
   ctx->cur = nxt;
@@ -288,6 +293,7 @@ tsgne_status alloc_layout(tsgne_ctx* ctx) {
   TS_TRY(ctx->upd.alloc(np));
   TS_TRY(ctx->gains.alloc(np));
   TS_TRY(ctx->grad.alloc(np));
+  TS_TRY(ctx->fsum.alloc(np));
   TS_TRY(ctx->frep.alloc(np * (size_t)ctx->shape.chunks));
   TS_TRY(ctx->zpart.alloc((size_t)ctx->shape.units));
   TS_TRY(ctx->klpart.alloc(2 * (size_t)kl_partial_count(ctx->sms)));
@@ -596,7 +602,7 @@ tsgne_status tsgne_gradient(tsgne_ctx* ctx, float alpha, float* g_out, double* z
   ProfRec pr;
   API_TRY(ctx, prof_begin(ctx, 2, &pr));
   API_TRY(ctx, launch_gradient(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
-                               ctx->frep.get(), ctx->shape.chunks, ctx->shape.n_pad, ctx->sched.get(), alpha,
+                               ctx->fsum.get(), 1, ctx->shape.n_pad, ctx->sched.get(), alpha,
                                ctx->grad.get(), ctx->stream));
   API_TRY(ctx, prof_end(ctx, &pr));
   API_TRY(ctx, copy_out(g_out, ctx->grad.get(), sizeof(float2) * (size_t)ctx->n, ptr_kind, ctx->stream));
@@ -651,7 +657,7 @@ tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update
 tsgne_status tsgne_kernel_times(tsgne_ctx* ctx, double* ms, int64_t* launches, int32_t n, int32_t reset) {
   TS_TRY(enter(ctx));
   DeviceGuard dg(ctx->device);
-  if (n < 0 || n > kClasses) return fail(ctx, TSGNE_ERR_INVALID_ARG, "n outside [0, 5]");
+  if (n < 0 || n > kClasses) return fail(ctx, TSGNE_ERR_INVALID_ARG, "n outside [0, 6]");
   API_TRY(ctx, prof_collect(ctx));
   for (int k = 0; k < n; ++k) {
     if (ms) ms[k] = ctx->prof_ms[k];

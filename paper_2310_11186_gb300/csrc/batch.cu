@@ -1,0 +1,650 @@
+// Many layouts per launch: the t-SGNE iteration of every member of a batch
+// runs in four launches, whatever the number and sizes of the members.
+//
+//   k_batch_repulsion  one global work queue over the tile pairs of all
+//                      members (prefix offsets per member); each unit is the
+//                      same device code as the single-layout pass (sym_unit)
+//                      on that member's buffers, so every member's forces and
+//                      Z partials are the same bits as when it runs alone
+//   k_batch_finalize   one CTA per member: Z = fixed-order sum of its unit
+//                      partials minus n, schedule (alpha, mu) from its own
+//                      iteration counter t, t += 1
+//   k_batch_reduce     fixed-order sum of each point's partial-force slots
+//   k_batch_attract    attraction + gradient + optimiser step per row
+//
+// Members keep their P, layout and optimiser state resident on the device
+// and may differ in size and in iteration count (each has its own t); the
+// current layout of a member is Y[t & 1], so one captured CUDA graph of the
+// four launches serves every iteration of a given membership.  All members of
+// a batch use the same tile size T = 256 W; tsgne_batch_autotune picks W.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "reduce.cuh"
+#include "row_update.cuh"
+#include "sym_unit.cuh"
+#include "tsgne_internal.cuh"
+
+namespace tsgne {
+
+struct GraphDesc {
+  const int64_t* rp;
+  const int32_t* col;
+  const float* P;
+  float2* Y[2];
+  float2* upd;
+  float2* gains;
+  float2* part;
+  float2* fsum;
+  double* zunit;
+  Sched* sched;
+  int n, nt, n_pad, units;
+  float eta;
+  int pad_;
+};
+
+struct BatchCtr {
+  uint32_t work_next;
+  uint32_t rep_done;
+};
+
+namespace {
+
+constexpr int kMaxT = 2048;  // largest tile (W = 8); member buffers are padded to it
+constexpr int kBG = 8;       // lanes per row in the update
+
+// Largest k with off[k] <= v over off[0..count) (off non-decreasing, off[0] = 0).
+__device__ __forceinline__ int find_owner(const int* __restrict__ off, int count, int v) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= v) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int W>
+__global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
+    k_batch_repulsion(const GraphDesc* __restrict__ descs, const int* __restrict__ unit_off, int members, int U,
+                      BatchCtr* ctr) {
+  constexpr int T = W * 32 * kRI;
+  extern __shared__ float4 smem[];
+  float4* sj = smem;
+  float2* sacc = reinterpret_cast<float2*>(smem + T);
+  __shared__ int s_unit, s_g, s_a, s_b;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      const int u = (int)atomicAdd(&ctr->work_next, 1u);
+      int g = 0, a = 0, b = 0;
+      if (u < U) {
+        g = find_owner(unit_off, members, u);
+        unit_tiles(u - unit_off[g], descs[g].nt, &a, &b);
+      }
+      s_unit = u;
+      s_g = g;
+      s_a = a;
+      s_b = b;
+    }
+    __syncthreads();
+    const int u = s_unit, g = s_g, a = s_a, b = s_b;
+    if (u >= U) break;
+    const GraphDesc& d = descs[g];
+    const float2* Y = d.Y[d.sched->t & 1];
+    const double zt = sym_unit<W>(Y, d.n, d.n_pad, d.part, a, b, sj, sacc);
+    const double zb = block_sum_d(zt);
+    if (tid == 0) d.zunit[u - unit_off[g]] = zb;
+    __syncthreads();
+  }
+  if (arrive_last(&ctr->rep_done) && tid == 0) ctr->work_next = 0u;
+}
+
+__global__ void k_batch_finalize(const GraphDesc* __restrict__ descs, float ee, int ee_iters, float mom0,
+                                 float mom1) {
+  const GraphDesc& d = descs[blockIdx.x];
+  const double total = sum_partials(d.zunit, d.units);
+  if (threadIdx.x == 0) {
+    Sched* s = d.sched;
+    s->Z = total - (double)d.n;
+    const int t = s->t;
+    s->alpha = t < ee_iters ? ee : 1.0f;
+    s->mu = t < ee_iters ? mom0 : mom1;
+    s->t = t + 1;
+  }
+}
+
+__global__ void k_batch_reduce(const GraphDesc* __restrict__ descs, const int* __restrict__ row_off, int members,
+                               int R) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += stride) {
+    const int g = find_owner(row_off, members, r);
+    const GraphDesc& d = descs[g];
+    const int i = r - row_off[g];
+    float fx = 0.f, fy = 0.f;
+    for (int k = 0; k < d.nt; ++k) {
+      const float2 f = d.part[(size_t)k * d.n_pad + i];
+      fx += f.x;
+      fy += f.y;
+    }
+    d.fsum[i] = make_float2(fx, fy);
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_batch_attract(const GraphDesc* __restrict__ descs,
+                                                       const int* __restrict__ row_off, int members, int R,
+                                                       float min_gain) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r = gt / G;
+  const int lane = (int)(gt % G);
+  const bool valid = r < R;
+  const int g = valid ? find_owner(row_off, members, (int)r) : 0;
+  const GraphDesc& d = descs[g];
+  const int64_t i = valid ? r - row_off[g] : 0;
+  float ax = 0.f, ay = 0.f;
+  float2 yi = make_float2(0.f, 0.f);
+  int t = 0;
+  if (valid) {
+    t = d.sched->t;  // already advanced by k_batch_finalize
+    const float2* Ycur = d.Y[(t - 1) & 1];
+    yi = Ycur[i];
+    attract_row<G>(d.rp, d.col, d.P, Ycur, i, lane, yi, ax, ay);
+  }
+  ax = group_sum<G>(ax);
+  ay = group_sum<G>(ay);
+  if (!valid || lane != 0) return;
+  const Sched* s = d.sched;
+  const float2 fr = d.fsum[i];
+  const float invZ = (float)(1.0 / s->Z);
+  const float gx = 4.0f * (s->alpha * ax - fr.x * invZ);
+  const float gy = 4.0f * (s->alpha * ay - fr.y * invZ);
+  float2 u = d.upd[i], gn = d.gains[i];
+  const float2 y = optimizer_step(gx, gy, u, gn, s->mu, d.eta, min_gain, yi);
+  d.upd[i] = u;
+  d.gains[i] = gn;
+  d.Y[t & 1][i] = y;
+  if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&d.sched->flags, kFlagNonfiniteY);
+}
+
+template <int W>
+size_t batch_smem() {
+  return (size_t)(W * 32 * kRI) * (sizeof(float4) + sizeof(float2));
+}
+
+size_t smem_for(int W) {
+  switch (W) {
+    case 8: return batch_smem<8>();
+    case 4: return batch_smem<4>();
+    case 2: return batch_smem<2>();
+    default: return batch_smem<1>();
+  }
+}
+
+tsgne_status prepare_w(int W) {
+  const int bytes = (int)smem_for(W);
+  switch (W) {
+    case 8: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
+    case 4: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
+    case 2: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
+    default: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
+  }
+  return TSGNE_OK;
+}
+
+// One member: affinities, layout, optimiser state and repulsion scratch.
+struct Member {
+  int id = -1;
+  int n = 0;
+  int64_t nnz = 0;
+  int n_pad_max = 0;  // buffers sized for T = kMaxT
+  float eta = 0.f;
+  DevBuf<int64_t> rp;
+  DevBuf<int32_t> col;
+  DevBuf<float> P;
+  DevBuf<float2> Y[2], upd, gains, fsum;
+  DevBuf<float2> part;
+  DevBuf<double> zunit;
+  DevBuf<Sched> sched;
+  int nt = 0, n_pad = 0, units = 0;  // for the batch's current tile
+  DevBuf<float2> Y0;                 // initial layout (autotune restores it)
+};
+
+std::mutex g_cache_mu;
+std::map<std::tuple<int, int, int>, int> g_tile_cache;  // (SMs, log2 pairs, log2 members) -> W
+
+}  // namespace
+}  // namespace tsgne
+
+using namespace tsgne;
+
+struct tsgne_batch {
+  tsgne_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0, sms = 1;
+  int W = 1;
+  std::string err;
+  int next_id = 0;
+  std::vector<std::unique_ptr<Member>> members;
+  DevBuf<GraphDesc> d_desc;
+  DevBuf<int> d_unit_off, d_row_off;
+  DevBuf<BatchCtr> d_ctr;
+  int U = 0, R = 0;
+  bool dirty = true;
+  cudaGraphExec_t graph = nullptr;
+  ~tsgne_batch() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+tsgne_status bfail(tsgne_batch* b, tsgne_status st, const std::string& msg = std::string()) {
+  if (b) b->err = msg.empty() ? last_msg() : msg;
+  return st;
+}
+
+#define B_TRY(b, call)                             \
+  do {                                             \
+    tsgne_status s__ = (call);                     \
+    if (s__ != TSGNE_OK) return bfail((b), s__);   \
+  } while (0)
+
+#define B_CUDA(b, call)                                                                    \
+  do {                                                                                     \
+    cudaError_t e__ = (call);                                                              \
+    if (e__ != cudaSuccess) return bfail((b), cuda_fail(e__, #call, __FILE__, __LINE__));  \
+  } while (0)
+
+void shape_member(Member& m, int W) {
+  const int T = 256 * W;
+  m.nt = (m.n + T - 1) / T;
+  m.n_pad = m.nt * T;
+  m.units = m.nt * (m.nt + 1) / 2;
+}
+
+tsgne_status alloc_scratch(Member& m, int W) {
+  shape_member(m, W);
+  TS_TRY(m.part.alloc((size_t)m.nt * m.n_pad));
+  TS_TRY(m.zunit.alloc((size_t)m.units));
+  return TSGNE_OK;
+}
+
+void invalidate(tsgne_batch* b) {
+  b->dirty = true;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+// Uploads descriptors and prefix offsets for the current membership.
+tsgne_status refresh(tsgne_batch* b) {
+  if (!b->dirty) return TSGNE_OK;
+  const int G = (int)b->members.size();
+  std::vector<GraphDesc> h(G > 0 ? G : 1);
+  std::vector<int> uo(G + 1, 0), ro(G + 1, 0);
+  for (int k = 0; k < G; ++k) {
+    Member& m = *b->members[k];
+    GraphDesc d{};
+    d.rp = m.rp.get();
+    d.col = m.col.get();
+    d.P = m.P.get();
+    d.Y[0] = m.Y[0].get();
+    d.Y[1] = m.Y[1].get();
+    d.upd = m.upd.get();
+    d.gains = m.gains.get();
+    d.part = m.part.get();
+    d.fsum = m.fsum.get();
+    d.zunit = m.zunit.get();
+    d.sched = m.sched.get();
+    d.n = m.n;
+    d.nt = m.nt;
+    d.n_pad = m.n_pad;
+    d.units = m.units;
+    d.eta = m.eta;
+    h[k] = d;
+    uo[k + 1] = uo[k] + m.units;
+    ro[k + 1] = ro[k] + m.n;
+  }
+  b->U = uo[G];
+  b->R = ro[G];
+  TS_TRY(b->d_desc.alloc(h.size()));
+  TS_TRY(b->d_unit_off.alloc(uo.size()));
+  TS_TRY(b->d_row_off.alloc(ro.size()));
+  TS_CUDA(cudaMemcpyAsync(b->d_desc.get(), h.data(), sizeof(GraphDesc) * h.size(), cudaMemcpyHostToDevice, b->stream));
+  TS_CUDA(cudaMemcpyAsync(b->d_unit_off.get(), uo.data(), sizeof(int) * uo.size(), cudaMemcpyHostToDevice, b->stream));
+  TS_CUDA(cudaMemcpyAsync(b->d_row_off.get(), ro.data(), sizeof(int) * ro.size(), cudaMemcpyHostToDevice, b->stream));
+  TS_CUDA(cudaStreamSynchronize(b->stream));
+  b->dirty = false;
+  return TSGNE_OK;
+}
+
+tsgne_status enqueue_iteration(tsgne_batch* b) {
+  const int G = (int)b->members.size();
+  if (G == 0) return TSGNE_OK;
+  const int W = b->W;
+  const int slots = b->sms * (kWarpsPerSm / W);
+  const int grid = b->U < slots ? b->U : slots;
+  const size_t sm = smem_for(W);
+  switch (W) {
+    case 8: k_batch_repulsion<8><<<grid, 256, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
+    case 4: k_batch_repulsion<4><<<grid, 128, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
+    case 2: k_batch_repulsion<2><<<grid, 64, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
+    default: k_batch_repulsion<1><<<grid, 32, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
+  }
+  const tsgne_config& c = b->cfg;
+  // 32 W threads: the same reduction tree as the single-layout pass's last CTA
+  k_batch_finalize<<<G, 32 * W, 0, b->stream>>>(b->d_desc.get(), c.early_exag, c.ee_iters, c.momentum0, c.momentum1);
+  const int rgrid = std::max(1, std::min((b->R + 255) / 256, b->sms * 16));
+  k_batch_reduce<<<rgrid, 256, 0, b->stream>>>(b->d_desc.get(), b->d_row_off.get(), G, b->R);
+  const int64_t threads = (int64_t)b->R * kBG;
+  const int agrid = (int)std::max<int64_t>(1, (threads + 255) / 256);
+  k_batch_attract<kBG><<<agrid, 256, 0, b->stream>>>(b->d_desc.get(), b->d_row_off.get(), G, b->R, c.min_gain);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+tsgne_status run_iterations(tsgne_batch* b, int n_iter, bool use_graph) {
+  TS_TRY(refresh(b));
+  if (b->members.empty() || n_iter <= 0) return TSGNE_OK;
+  if (use_graph && !b->graph) {
+    cudaGraph_t g = nullptr;
+    TS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    tsgne_status st = enqueue_iteration(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (st != TSGNE_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->graph = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    }
+  }
+  for (int k = 0; k < n_iter; ++k) {
+    if (use_graph) {
+      TS_CUDA(cudaGraphLaunch(b->graph, b->stream));
+    } else {
+      TS_TRY(enqueue_iteration(b));
+    }
+  }
+  return TSGNE_OK;
+}
+
+Member* find_member(tsgne_batch* b, int id, size_t* pos = nullptr) {
+  for (size_t k = 0; k < b->members.size(); ++k)
+    if (b->members[k]->id == id) {
+      if (pos) *pos = k;
+      return b->members[k].get();
+    }
+  return nullptr;
+}
+
+tsgne_status reset_member_state(Member& m, cudaStream_t s) {
+  TS_CUDA(cudaMemcpyAsync(m.Y[0].get(), m.Y0.get(), sizeof(float2) * m.n, cudaMemcpyDeviceToDevice, s));
+  TS_TRY(launch_fill2(m.upd.get(), m.n_pad_max, 0.f, s));
+  TS_TRY(launch_fill2(m.gains.get(), m.n_pad_max, 1.f, s));
+  Sched h{};
+  TS_CUDA(cudaMemcpyAsync(m.sched.get(), &h, sizeof(Sched), cudaMemcpyHostToDevice, s));
+  return TSGNE_OK;
+}
+
+bool capturable_stream(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
+}  // namespace
+
+extern "C" {
+
+tsgne_status tsgne_batch_create(tsgne_batch** out, const tsgne_config* cfg, int32_t tile_warps, void* cuda_stream) {
+  if (!out) return TSGNE_ERR_INVALID_ARG;
+  *out = nullptr;
+  tsgne_config c;
+  if (cfg) c = *cfg; else tsgne_config_default(&c);
+  if (!(c.perplexity > 1.f) || c.k_nn != 0 || c.precision != 0 || c.ee_iters < 0)
+    return TSGNE_ERR_INVALID_ARG;
+  if (!(tile_warps == 0 || tile_warps == 1 || tile_warps == 2 || tile_warps == 4 || tile_warps == 8))
+    return TSGNE_ERR_INVALID_ARG;
+  tsgne_batch* b = new (std::nothrow) tsgne_batch();
+  if (!b) return TSGNE_ERR_OOM;
+  b->cfg = c;
+  b->W = tile_warps ? tile_warps : 1;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      b->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+      b->own_stream = (e == cudaSuccess);
+    }
+  }
+  tsgne_status st = e == cudaSuccess ? TSGNE_OK : cuda_fail(e, "tsgne_batch_create", __FILE__, __LINE__);
+  if (st == TSGNE_OK) st = b->d_ctr.alloc(1);
+  if (st == TSGNE_OK && cudaMemsetAsync(b->d_ctr.get(), 0, sizeof(BatchCtr), b->stream) != cudaSuccess)
+    st = TSGNE_ERR_CUDA;
+  for (int w : {1, 2, 4, 8})
+    if (st == TSGNE_OK) st = prepare_w(w);
+  if (st == TSGNE_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = TSGNE_ERR_CUDA;
+  if (st != TSGNE_OK) {
+    delete b;
+    return st;
+  }
+  *out = b;
+  return TSGNE_OK;
+}
+
+void tsgne_batch_destroy(tsgne_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  delete b;
+}
+
+const char* tsgne_batch_last_error(const tsgne_batch* b) { return b ? b->err.c_str() : ""; }
+
+tsgne_status tsgne_batch_add(tsgne_batch* b, int32_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* X,
+                             int32_t d, const float* Y0, int32_t ptr_kind, int32_t* id_out) {
+  if (!b) return TSGNE_ERR_INVALID_ARG;
+  b->err.clear();
+  if (n < 2 || d < 1 || !row_ptr || !X || !(ptr_kind == TSGNE_PTR_HOST || ptr_kind == TSGNE_PTR_DEVICE))
+    return bfail(b, TSGNE_ERR_INVALID_ARG, "need n >= 2, d >= 1, row_ptr, X and a valid ptr_kind");
+  const cudaMemcpyKind kin = ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  int64_t first = 0, m = 0;
+  if (ptr_kind == TSGNE_PTR_HOST) {
+    first = row_ptr[0];
+    m = row_ptr[n];
+  } else {
+    B_CUDA(b, cudaMemcpy(&first, row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    B_CUDA(b, cudaMemcpy(&m, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  }
+  if (first != 0 || m < 0) return bfail(b, TSGNE_ERR_BAD_CSR, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+  if (m > 0 && !col_idx) return bfail(b, TSGNE_ERR_INVALID_ARG, "col_idx is NULL");
+  auto mem = std::make_unique<Member>();
+  Member& mb = *mem;
+  mb.n = n;
+  DevBuf<int64_t> rp_in, tslot;
+  DevBuf<int32_t> col_in;
+  DevBuf<float> X_in;
+  B_TRY(b, rp_in.alloc((size_t)n + 1));
+  B_TRY(b, col_in.alloc((size_t)m));
+  B_TRY(b, X_in.alloc((size_t)n * d));
+  B_CUDA(b, cudaMemcpyAsync(rp_in.get(), row_ptr, sizeof(int64_t) * ((size_t)n + 1), kin, b->stream));
+  if (m > 0) B_CUDA(b, cudaMemcpyAsync(col_in.get(), col_idx, sizeof(int32_t) * (size_t)m, kin, b->stream));
+  B_CUDA(b, cudaMemcpyAsync(X_in.get(), X, sizeof(float) * (size_t)n * d, kin, b->stream));
+  B_TRY(b, mb.sched.alloc(1));
+  B_CUDA(b, cudaMemsetAsync(mb.sched.get(), 0, sizeof(Sched), b->stream));
+  B_TRY(b, build_structure(n, rp_in.get(), col_in.get(), m, mb.rp, mb.col, tslot, &mb.nnz, mb.sched.get(), b->stream));
+  B_TRY(b, mb.P.alloc((size_t)mb.nnz));
+  B_TRY(b, build_affinities(n, mb.rp.get(), mb.col.get(), tslot.get(), mb.nnz, X_in.get(), d, b->cfg.perplexity,
+                            b->cfg.bisect_tol, b->cfg.bisect_max_iter, mb.P.get(), mb.sched.get(), b->stream));
+  Sched hs;
+  B_CUDA(b, cudaMemcpyAsync(&hs, mb.sched.get(), sizeof(Sched), cudaMemcpyDeviceToHost, b->stream));
+  B_CUDA(b, cudaStreamSynchronize(b->stream));
+  if (hs.flags & kFlagNonfiniteP) return bfail(b, TSGNE_ERR_NONFINITE, "non-finite affinity (check X)");
+  mb.n_pad_max = ((n + kMaxT - 1) / kMaxT) * kMaxT;
+  const size_t np = (size_t)mb.n_pad_max;
+  B_TRY(b, mb.Y[0].alloc(np));
+  B_TRY(b, mb.Y[1].alloc(np));
+  B_TRY(b, mb.upd.alloc(np));
+  B_TRY(b, mb.gains.alloc(np));
+  B_TRY(b, mb.fsum.alloc(np));
+  B_TRY(b, mb.Y0.alloc((size_t)n));
+  B_TRY(b, launch_fill_sentinel(mb.Y[0].get(), 0, (int)np, b->stream));
+  B_TRY(b, launch_fill_sentinel(mb.Y[1].get(), 0, (int)np, b->stream));
+  if (Y0) {
+    B_CUDA(b, cudaMemcpyAsync(mb.Y0.get(), Y0, sizeof(float2) * (size_t)n, kin, b->stream));
+  } else {
+    B_TRY(b, launch_init_Y(n, b->cfg.seed, 1e-4f, mb.Y0.get(), b->stream));
+  }
+  B_TRY(b, alloc_scratch(mb, b->W));
+  B_TRY(b, reset_member_state(mb, b->stream));
+  const float ee = b->cfg.early_exag > 0.f ? b->cfg.early_exag : 1.f;
+  mb.eta = b->cfg.learning_rate > 0.f ? b->cfg.learning_rate : std::fmax((float)n / ee / 4.0f, 50.0f);
+  B_CUDA(b, cudaStreamSynchronize(b->stream));
+  mb.id = b->next_id++;
+  if (id_out) *id_out = mb.id;
+  b->members.push_back(std::move(mem));
+  invalidate(b);
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_remove(tsgne_batch* b, int32_t id) {
+  if (!b) return TSGNE_ERR_INVALID_ARG;
+  b->err.clear();
+  size_t pos = 0;
+  if (!find_member(b, id, &pos)) return bfail(b, TSGNE_ERR_INVALID_ARG, "unknown member id");
+  B_CUDA(b, cudaStreamSynchronize(b->stream));
+  b->members.erase(b->members.begin() + (long)pos);
+  invalidate(b);
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_size(tsgne_batch* b, int32_t* members, int32_t* tile_warps, int64_t* units) {
+  if (!b) return TSGNE_ERR_INVALID_ARG;
+  B_TRY(b, refresh(b));
+  if (members) *members = (int32_t)b->members.size();
+  if (tile_warps) *tile_warps = b->W;
+  if (units) *units = b->U;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_run(tsgne_batch* b, int32_t n_iter) {
+  if (!b) return TSGNE_ERR_INVALID_ARG;
+  b->err.clear();
+  if (n_iter < 0) return bfail(b, TSGNE_ERR_INVALID_ARG, "n_iter < 0");
+  B_TRY(b, run_iterations(b, n_iter, capturable_stream(b->stream)));
+  B_CUDA(b, cudaStreamSynchronize(b->stream));
+  for (auto& m : b->members) {
+    Sched h;
+    B_CUDA(b, cudaMemcpyAsync(&h, m->sched.get(), sizeof(Sched), cudaMemcpyDeviceToHost, b->stream));
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    if (h.flags & kFlagNonfiniteY) return bfail(b, TSGNE_ERR_NONFINITE, "a member's layout became non-finite");
+  }
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_get_Y(tsgne_batch* b, int32_t id, float* Y_out, int32_t* iter, int32_t ptr_kind) {
+  if (!b || !Y_out) return TSGNE_ERR_INVALID_ARG;
+  b->err.clear();
+  Member* m = find_member(b, id);
+  if (!m) return bfail(b, TSGNE_ERR_INVALID_ARG, "unknown member id");
+  Sched h;
+  B_CUDA(b, cudaMemcpyAsync(&h, m->sched.get(), sizeof(Sched), cudaMemcpyDeviceToHost, b->stream));
+  B_CUDA(b, cudaStreamSynchronize(b->stream));
+  B_CUDA(b, cudaMemcpyAsync(Y_out, m->Y[h.t & 1].get(), sizeof(float2) * (size_t)m->n,
+                            ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->stream));
+  B_CUDA(b, cudaStreamSynchronize(b->stream));
+  if (iter) *iter = h.t;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_set_tile(tsgne_batch* b, int32_t tile_warps) {
+  if (!b) return TSGNE_ERR_INVALID_ARG;
+  if (!(tile_warps == 1 || tile_warps == 2 || tile_warps == 4 || tile_warps == 8))
+    return bfail(b, TSGNE_ERR_INVALID_ARG, "tile_warps must be 1, 2, 4 or 8");
+  if (tile_warps == b->W) return TSGNE_OK;
+  B_CUDA(b, cudaStreamSynchronize(b->stream));
+  for (auto& m : b->members) B_TRY(b, alloc_scratch(*m, tile_warps));
+  b->W = tile_warps;
+  invalidate(b);
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_reset(tsgne_batch* b) {
+  if (!b) return TSGNE_ERR_INVALID_ARG;
+  for (auto& m : b->members) B_TRY(b, reset_member_state(*m, b->stream));
+  B_CUDA(b, cudaStreamSynchronize(b->stream));
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_autotune(tsgne_batch* b, int32_t trial_iters, int32_t* chosen, float* ms_per_iter) {
+  if (!b || trial_iters < 1) return TSGNE_ERR_INVALID_ARG;
+  b->err.clear();
+  B_TRY(b, refresh(b));
+  double pairs = 0.0;
+  for (auto& m : b->members) pairs += 0.5 * (double)m->n * (double)m->n;
+  const auto key = std::make_tuple(b->sms, (int)std::log2(pairs + 1.0), (int)std::log2((double)b->members.size() + 1.0));
+  int best = -1;
+  float best_ms = 0.f;
+  const int cand[4] = {1, 2, 4, 8};
+  cudaEvent_t e0, e1;
+  B_CUDA(b, cudaEventCreate(&e0));
+  B_CUDA(b, cudaEventCreate(&e1));
+  for (int k = 0; k < 4; ++k) {
+    const int w = cand[k];
+    tsgne_status st = tsgne_batch_set_tile(b, w);
+    if (st == TSGNE_OK) st = run_iterations(b, 1, false);  // warm-up
+    if (st == TSGNE_OK) st = cudaEventRecord(e0, b->stream) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
+    if (st == TSGNE_OK) st = run_iterations(b, trial_iters, false);
+    if (st == TSGNE_OK) st = cudaEventRecord(e1, b->stream) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
+    if (st == TSGNE_OK) st = cudaEventSynchronize(e1) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
+    float ms = 0.f;
+    if (st == TSGNE_OK) st = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
+    if (st != TSGNE_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return bfail(b, st);
+    }
+    ms /= (float)trial_iters;
+    if (ms_per_iter) ms_per_iter[k] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = w;
+      best_ms = ms;
+    }
+    B_TRY(b, tsgne_batch_reset(b));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  B_TRY(b, tsgne_batch_set_tile(b, best));
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_tile_cache[key] = best;
+  }
+  if (chosen) *chosen = best;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_cached_tile(tsgne_batch* b, int32_t* tile_warps) {
+  if (!b || !tile_warps) return TSGNE_ERR_INVALID_ARG;
+  double pairs = 0.0;
+  for (auto& m : b->members) pairs += 0.5 * (double)m->n * (double)m->n;
+  const auto key = std::make_tuple(b->sms, (int)std::log2(pairs + 1.0), (int)std::log2((double)b->members.size() + 1.0));
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_tile_cache.find(key);
+  *tile_warps = it == g_tile_cache.end() ? 0 : it->second;
+  return TSGNE_OK;
+}
+
+}  // extern "C"

@@ -12,12 +12,15 @@
 //   min_gain; upd = mu upd - eta gain g; y_next = y + upd.  Reading Y_cur and
 //   writing Y_next (double buffer) keeps every row's neighbours at the old
 //   layout.  In export mode it writes g and changes nothing.
+// k_reduce_slots (end of S4): adds the repulsion's partial-force slots of each
+//   point in slot order into F^r (the update then reads one float2 per row).
 // k_kl (S6): sum_e p_e ln(p_e / w_e) and sum_e p_e in FP64 (terms in FP32),
 //   fixed-order totals; KL = first + second * ln Z on the host (Eq. 5 with
 //   q = w / Z).
 #include <cmath>
 
 #include "reduce.cuh"
+#include "row_update.cuh"
 #include "tsgne_internal.cuh"
 
 namespace tsgne {
@@ -41,30 +44,17 @@ __global__ void __launch_bounds__(kAttrCta)
   float2 yi = make_float2(0.f, 0.f);
   if (valid) {
     yi = Ycur[i];
-    const int64_t b = rp[i + 1];
-    for (int64_t e = rp[i] + lane; e < b; e += G) {
-      const int32_t j = col[e];
-      const float p = P[e];
-      const float2 yj = Ycur[j];
-      const float dx = yi.x - yj.x, dy = yi.y - yj.y;
-      const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
-      const float pw = p * w;
-      ax = fmaf(pw, dx, ax);
-      ay = fmaf(pw, dy, ay);
-    }
+    attract_row<G>(rp, col, P, Ycur, i, lane, yi, ax, ay);
     for (int c = lane; c < chunks; c += G) {
       const float2 f = frep_part[(size_t)c * n_pad + i];
       rx += f.x;
       ry += f.y;
     }
   }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    ax += __shfl_xor_sync(0xffffffffu, ax, o, G);
-    ay += __shfl_xor_sync(0xffffffffu, ay, o, G);
-    rx += __shfl_xor_sync(0xffffffffu, rx, o, G);
-    ry += __shfl_xor_sync(0xffffffffu, ry, o, G);
-  }
+  ax = group_sum<G>(ax);
+  ay = group_sum<G>(ay);
+  rx = group_sum<G>(rx);
+  ry = group_sum<G>(ry);
   if (!valid || lane != 0) return;
   const float invZ = (float)(1.0 / sched->Z);
   const float alpha = EXPORT ? alpha_export : sched->alpha;
@@ -76,17 +66,27 @@ __global__ void __launch_bounds__(kAttrCta)
   }
   const float mu = sched->mu;
   float2 u = upd[i], gn = gains[i];
-  const bool incx = (gx > 0.f && u.x < 0.f) || (gx < 0.f && u.x > 0.f);
-  const bool incy = (gy > 0.f && u.y < 0.f) || (gy < 0.f && u.y > 0.f);
-  gn.x = fmaxf(incx ? gn.x + 0.2f : gn.x * 0.8f, min_gain);
-  gn.y = fmaxf(incy ? gn.y + 0.2f : gn.y * 0.8f, min_gain);
-  u.x = mu * u.x - eta * gn.x * gx;
-  u.y = mu * u.y - eta * gn.y * gy;
-  const float2 y = make_float2(yi.x + u.x, yi.y + u.y);
+  const float2 y = optimizer_step(gx, gy, u, gn, mu, eta, min_gain, yi);
   upd[i] = u;
   gains[i] = gn;
   Ynext[i] = y;
   if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&sched->flags, kFlagNonfiniteY);
+}
+
+// F^r_i = sum over the partial-force slots in slot order (fixed order, so the
+// forces are bit-reproducible); one thread per point, coalesced per slot.
+__global__ void __launch_bounds__(kAttrCta)
+    k_reduce_slots(int n, const float2* __restrict__ part, int slots, int n_pad, float2* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    float fx = 0.f, fy = 0.f;
+    for (int k = 0; k < slots; ++k) {
+      const float2 f = part[(size_t)k * n_pad + i];
+      fx += f.x;
+      fy += f.y;
+    }
+    out[i] = make_float2(fx, fy);
+  }
 }
 
 __global__ void __launch_bounds__(kAttrCta)
@@ -162,6 +162,13 @@ int grid_rows(int64_t n, int per_cta) {
 }  // namespace
 
 int kl_partial_count(int sm_count) { return sm_count * 4; }
+
+tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad, float2* out, cudaStream_t s) {
+  const int g = grid_rows(n, kAttrCta);
+  k_reduce_slots<<<g, kAttrCta, 0, s>>>(n, part, slots, n_pad, out);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
 
 tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Ycur,
                                    float2* Ynext, float2* upd, float2* gains, const float2* frep_part, int chunks,

@@ -9,7 +9,7 @@
 // Decomposition.  Points are padded to n_pad = nt * T (T = 256 W) with the
 // sentinel point.  A unit of work is a tile pair (a, b), a <= b; the units
 // are enumerated row by row and taken from a global work queue by a
-// persistent grid (16 warps per SM).  Unit (a, b), a < b, writes the forces
+// persistent grid (24 warps per SM).  Unit (a, b), a < b, writes the forces
 // of tile a's points into slot b and those of tile b's points into slot a of
 // part[slot][point]; the diagonal unit (t, t) evaluates its ordered pairs
 // with the i-side only and writes slot t.  Every slot of every point is
@@ -32,49 +32,12 @@
 // occur only in the diagonal unit, where they are masked out of Z.
 #include "f32x2.cuh"
 #include "reduce.cuh"
+#include "sym_unit.cuh"
 #include "tsgne_internal.cuh"
 
 namespace tsgne {
 
 namespace {
-
-constexpr int kRI = 8;              // i-points per lane
-constexpr int kH = kRI / 2;         // FP32x2 pairs of i-points per lane
-constexpr int kWarpsPerSm = 16;     // resident warps per SM the grid is sized for
-constexpr int kGroup = 64;          // j-points per ring group (32 lanes x 2)
-
-__device__ __forceinline__ int row_start(int a, int nt) { return a * nt - (a * (a - 1)) / 2; }
-
-// One j-point against the lane's 8 i-points; acc (x, y) is the running sum
-// of w^2 (y_i - y_j) over i for this j.
-__device__ __forceinline__ void ring_pair(const float4 q, float& accx, float& accy, const u64 (&X2)[kH],
-                                          const u64 (&Y2)[kH], u64 (&FX)[kH], u64 (&FY)[kH], u64 (&Z2)[kH],
-                                          const u64 one2) {
-  const u64 nx = pk(q.x, q.y);
-  const u64 ny = pk(q.z, q.w);
-  u64 PX = pk(accx, 0.f), PY = pk(accy, 0.f);
-#pragma unroll
-  for (int h = 0; h < kH; ++h) {
-    const u64 dx = add2(X2[h], nx);
-    const u64 dy = add2(Y2[h], ny);
-    u64 qq = fma2(dx, dx, one2);
-    qq = fma2(dy, dy, qq);
-    float q0, q1;
-    upk(qq, q0, q1);
-    const u64 w = pk(rcp_approx(q0), rcp_approx(q1));
-    Z2[h] = add2(Z2[h], w);
-    const u64 w2 = mul2(w, w);
-    FX[h] = fma2(w2, dx, FX[h]);
-    FY[h] = fma2(w2, dy, FY[h]);
-    PX = fma2(w2, dx, PX);
-    PY = fma2(w2, dy, PY);
-  }
-  float a0, a1;
-  upk(PX, a0, a1);
-  accx = a0 + a1;
-  upk(PY, a0, a1);
-  accy = a0 + a1;
-}
 
 template <int W>
 __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
@@ -82,131 +45,26 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
                     double* __restrict__ zunit, Sched* sched, int advance, float ee, int ee_iters, float mom0,
                     float mom1) {
   constexpr int T = W * 32 * kRI;
-  constexpr int G = T / kGroup;  // = 4W groups
   extern __shared__ float4 smem[];
   float4* sj = smem;                                   // T x {-x, -x, -y, -y}
   float2* sacc = reinterpret_cast<float2*>(smem + T);  // T x force accumulator
   __shared__ int s_unit, s_a, s_b;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const u64 one2 = pk(1.f, 1.f);
+  const int tid = threadIdx.x;
   const int units = nt * (nt + 1) / 2;
 
   for (;;) {
     if (tid == 0) {
       const int u = (int)atomicAdd(&sched->work_next, 1u);
-      int a = 0;
-      if (u < units) {
-        int lo = 0, hi = nt - 1;  // largest a with row_start(a) <= u
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (row_start(mid, nt) <= u) lo = mid; else hi = mid - 1;
-        }
-        a = lo;
-      }
+      int a = 0, b = 0;
+      if (u < units) unit_tiles(u, nt, &a, &b);
       s_unit = u;
       s_a = a;
-      s_b = u < units ? a + (u - row_start(a, nt)) : 0;
+      s_b = b;
     }
     __syncthreads();
     const int u = s_unit, a = s_a, b = s_b;
     if (u >= units) break;
-
-    // j tile b into shared memory
-    for (int k = tid; k < T; k += W * 32) {
-      const float2 p = Y[(size_t)b * T + k];
-      sj[k] = make_float4(-p.x, -p.x, -p.y, -p.y);
-      sacc[k] = make_float2(0.f, 0.f);
-    }
-    // i points of tile a: lane holds i = a*T + warp*256 + r*32 + lane, r = 0..7
-    const int ibase = a * T + warp * (32 * kRI) + lane;
-    u64 X2[kH], Y2[kH], FX[kH], FY[kH], Z2[kH];
-#pragma unroll
-    for (int h = 0; h < kH; ++h) {
-      const float2 p0 = Y[ibase + (2 * h) * 32];
-      const float2 p1 = Y[ibase + (2 * h + 1) * 32];
-      X2[h] = pk(p0.x, p1.x);
-      Y2[h] = pk(p0.y, p1.y);
-      FX[h] = FY[h] = Z2[h] = 0ull;
-    }
-    __syncthreads();
-
-    double zt = 0.0;
-    if (a != b) {
-      for (int ph = 0; ph < G; ++ph) {
-        const int g = (warp + ph) & (G - 1);
-        const float4* gj = sj + g * kGroup;
-        float2* ga = sacc + g * kGroup;
-        float2 c0 = ga[2 * lane], c1 = ga[2 * lane + 1];
-        float ax0 = c0.x, ay0 = c0.y, ax1 = c1.x, ay1 = c1.y;
-        const int src = (lane + 1) & 31;
-#pragma unroll 2
-        for (int s = 0; s < 32; ++s) {
-          const int jj = (lane + s) & 31;
-          const float4 q0 = gj[2 * jj];
-          const float4 q1 = gj[2 * jj + 1];
-          ring_pair(q0, ax0, ay0, X2, Y2, FX, FY, Z2, one2);
-          ring_pair(q1, ax1, ay1, X2, Y2, FX, FY, Z2, one2);
-          ax0 = __shfl_sync(0xffffffffu, ax0, src);
-          ay0 = __shfl_sync(0xffffffffu, ay0, src);
-          ax1 = __shfl_sync(0xffffffffu, ax1, src);
-          ay1 = __shfl_sync(0xffffffffu, ay1, src);
-        }
-        ga[2 * lane] = make_float2(ax0, ay0);
-        ga[2 * lane + 1] = make_float2(ax1, ay1);
-        __syncthreads();
-      }
-#pragma unroll
-      for (int h = 0; h < kH; ++h) {
-        float z0, z1;
-        upk(Z2[h], z0, z1);
-        zt += 2.0 * ((double)z0 + (double)z1);  // tile a holds no padding
-      }
-      // j side: F_j = -sum_i w^2 (y_i - y_j), into slot a of tile b's points
-      float2* outj = part + (size_t)a * n_pad + (size_t)b * T;
-      for (int k = tid; k < T; k += W * 32) {
-        const float2 v = sacc[k];
-        outj[k] = make_float2(-v.x, -v.y);
-      }
-    } else {
-      // diagonal unit: ordered pairs within the tile, i side only
-#pragma unroll 2
-      for (int j = 0; j < T; ++j) {
-        const float4 q = sj[j];
-        const u64 nx = pk(q.x, q.y);
-        const u64 ny = pk(q.z, q.w);
-#pragma unroll
-        for (int h = 0; h < kH; ++h) {
-          const u64 dx = add2(X2[h], nx);
-          const u64 dy = add2(Y2[h], ny);
-          u64 qq = fma2(dx, dx, one2);
-          qq = fma2(dy, dy, qq);
-          float q0, q1;
-          upk(qq, q0, q1);
-          const u64 w = pk(rcp_approx(q0), rcp_approx(q1));
-          Z2[h] = add2(Z2[h], w);
-          const u64 w2 = mul2(w, w);
-          FX[h] = fma2(w2, dx, FX[h]);
-          FY[h] = fma2(w2, dy, FY[h]);
-        }
-      }
-#pragma unroll
-      for (int h = 0; h < kH; ++h) {
-        float z0, z1;
-        upk(Z2[h], z0, z1);
-        if (ibase + (2 * h) * 32 < n) zt += (double)z0;
-        if (ibase + (2 * h + 1) * 32 < n) zt += (double)z1;
-      }
-    }
-    // i side of tile a into slot b
-    float2* outi = part + (size_t)b * n_pad;
-#pragma unroll
-    for (int h = 0; h < kH; ++h) {
-      float fx0, fx1, fy0, fy1;
-      upk(FX[h], fx0, fx1);
-      upk(FY[h], fy0, fy1);
-      outi[ibase + (2 * h) * 32] = make_float2(fx0, fy0);
-      outi[ibase + (2 * h + 1) * 32] = make_float2(fx1, fy1);
-    }
+    const double zt = sym_unit<W>(Y, n, n_pad, part, a, b, sj, sacc);
     const double zb = block_sum_d(zt);
     if (tid == 0) zunit[u] = zb;
     __syncthreads();  // shared tiles are rewritten by the next unit

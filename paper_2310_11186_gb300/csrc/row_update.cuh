@@ -1,0 +1,54 @@
+// Device code shared by the single-layout and multi-layout update kernels:
+// the attraction of one row and the optimiser step of one point.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace tsgne {
+
+// This lane's share of F^a_i = sum_{j in N(i)} p_ij w_ij (y_i - y_j),
+// w = (1 + ||y_i - y_j||^2)^-1, over entries rp[i] + lane, + G, ...
+template <int G>
+__device__ __forceinline__ void attract_row(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                            const float* __restrict__ P, const float2* __restrict__ Y, int64_t i,
+                                            int lane, float2 yi, float& ax, float& ay) {
+  const int64_t b = rp[i + 1];
+  for (int64_t e = rp[i] + lane; e < b; e += G) {
+    const int32_t j = col[e];
+    const float p = P[e];
+    const float2 yj = Y[j];
+    const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+    const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
+    const float pw = p * w;
+    ax = fmaf(pw, dx, ax);
+    ay = fmaf(pw, dy, ay);
+  }
+}
+
+// Sum over the G lanes of a row group (xor butterfly: every lane gets the
+// same value, so later decisions are uniform).
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+
+// Optimiser step (the published t-SNE rule; the paper gives none): per
+// coordinate gain += 0.2 if g and the previous update have opposite signs,
+// else gain *= 0.8, floored at min_gain; upd = mu upd - eta gain g.
+// Returns y + upd and updates u, gn in place.
+__device__ __forceinline__ float2 optimizer_step(float gx, float gy, float2& u, float2& gn, float mu, float eta,
+                                                 float min_gain, float2 yi) {
+  const bool incx = (gx > 0.f && u.x < 0.f) || (gx < 0.f && u.x > 0.f);
+  const bool incy = (gy > 0.f && u.y < 0.f) || (gy < 0.f && u.y > 0.f);
+  gn.x = fmaxf(incx ? gn.x + 0.2f : gn.x * 0.8f, min_gain);
+  gn.y = fmaxf(incy ? gn.y + 0.2f : gn.y * 0.8f, min_gain);
+  u.x = mu * u.x - eta * gn.x * gx;
+  u.y = mu * u.y - eta * gn.y * gy;
+  return make_float2(yi.x + u.x, yi.y + u.y);
+}
+
+}  // namespace tsgne

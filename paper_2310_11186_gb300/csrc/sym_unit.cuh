@@ -1,0 +1,173 @@
+// Device code shared by the single-layout and the multi-layout symmetric
+// repulsion kernels: the work of one tile pair (see repulsion_sym.cu for the
+// decomposition and the ring schedule).
+#pragma once
+
+#include "f32x2.cuh"
+#include "tsgne_internal.cuh"
+
+namespace tsgne {
+
+constexpr int kRI = 8;              // i-points per lane
+constexpr int kH = kRI / 2;         // FP32x2 pairs of i-points per lane
+constexpr int kWarpsPerSm = 24;     // resident warps per SM the grid is sized for
+constexpr int kGroup = 64;          // j-points per ring group (32 lanes x 2)
+
+__device__ __forceinline__ int row_start(int a, int nt) { return a * nt - (a * (a - 1)) / 2; }
+
+// One j-point against the lane's 8 i-points; acc (x, y) is the running sum
+// of w^2 (y_i - y_j) over i for this j.
+__device__ __forceinline__ void ring_pair(const float4 q, float& accx, float& accy, const u64 (&X2)[kH],
+                                          const u64 (&Y2)[kH], u64 (&FX)[kH], u64 (&FY)[kH], u64 (&Z2)[kH],
+                                          const u64 one2) {
+  const u64 nx = pk(q.x, q.y);
+  const u64 ny = pk(q.z, q.w);
+  u64 PX = pk(accx, 0.f), PY = pk(accy, 0.f);
+#pragma unroll
+  for (int h = 0; h < kH; ++h) {
+    const u64 dx = add2(X2[h], nx);
+    const u64 dy = add2(Y2[h], ny);
+    u64 qq = fma2(dx, dx, one2);
+    qq = fma2(dy, dy, qq);
+    float q0, q1;
+    upk(qq, q0, q1);
+    const u64 w = pk(rcp_approx(q0), rcp_approx(q1));
+    Z2[h] = add2(Z2[h], w);
+    const u64 w2 = mul2(w, w);
+    FX[h] = fma2(w2, dx, FX[h]);
+    FY[h] = fma2(w2, dy, FY[h]);
+    PX = fma2(w2, dx, PX);
+    PY = fma2(w2, dy, PY);
+  }
+  float a0, a1;
+  upk(PX, a0, a1);
+  accx = a0 + a1;
+  upk(PY, a0, a1);
+  accy = a0 + a1;
+}
+
+// One tile pair (a, b), a <= b, of one layout: stages tile b, evaluates the
+// pairs and writes tile a's forces into slot b and (a < b) tile b's forces
+// into slot a of part[slot * n_pad + point].  Returns this thread's share of
+// the unit's Z (ordered pairs; the diagonal unit includes the w_ii = 1 terms
+// of its real points).  Every thread of the CTA must call it; it ends with the
+// shared tiles free for reuse only after a __syncthreads by the caller.
+template <int W>
+__device__ __forceinline__ double sym_unit(const float2* __restrict__ Y, int n, int n_pad, float2* __restrict__ part,
+                                           int a, int b, float4* sj, float2* sacc) {
+  constexpr int T = W * 32 * kRI;
+  constexpr int G = T / kGroup;  // = 4W groups
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u64 one2 = pk(1.f, 1.f);
+
+  // j tile b into shared memory
+  for (int k = tid; k < T; k += W * 32) {
+    const float2 p = Y[(size_t)b * T + k];
+    sj[k] = make_float4(-p.x, -p.x, -p.y, -p.y);
+    sacc[k] = make_float2(0.f, 0.f);
+  }
+  // i points of tile a: lane holds i = a*T + warp*256 + r*32 + lane, r = 0..7
+  const int ibase = a * T + warp * (32 * kRI) + lane;
+  u64 X2[kH], Y2[kH], FX[kH], FY[kH], Z2[kH];
+#pragma unroll
+  for (int h = 0; h < kH; ++h) {
+    const float2 p0 = Y[ibase + (2 * h) * 32];
+    const float2 p1 = Y[ibase + (2 * h + 1) * 32];
+    X2[h] = pk(p0.x, p1.x);
+    Y2[h] = pk(p0.y, p1.y);
+    FX[h] = FY[h] = Z2[h] = 0ull;
+  }
+  __syncthreads();
+
+  double zt = 0.0;
+  if (a != b) {
+    for (int ph = 0; ph < G; ++ph) {
+      const int g = (warp + ph) & (G - 1);
+      const float4* gj = sj + g * kGroup;
+      float2* ga = sacc + g * kGroup;
+      float2 c0 = ga[2 * lane], c1 = ga[2 * lane + 1];
+      float ax0 = c0.x, ay0 = c0.y, ax1 = c1.x, ay1 = c1.y;
+      const int src = (lane + 1) & 31;
+#pragma unroll 4
+      for (int s = 0; s < 32; ++s) {
+        const int jj = (lane + s) & 31;
+        const float4 q0 = gj[2 * jj];
+        const float4 q1 = gj[2 * jj + 1];
+        ring_pair(q0, ax0, ay0, X2, Y2, FX, FY, Z2, one2);
+        ring_pair(q1, ax1, ay1, X2, Y2, FX, FY, Z2, one2);
+        ax0 = __shfl_sync(0xffffffffu, ax0, src);
+        ay0 = __shfl_sync(0xffffffffu, ay0, src);
+        ax1 = __shfl_sync(0xffffffffu, ax1, src);
+        ay1 = __shfl_sync(0xffffffffu, ay1, src);
+      }
+      ga[2 * lane] = make_float2(ax0, ay0);
+      ga[2 * lane + 1] = make_float2(ax1, ay1);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int h = 0; h < kH; ++h) {
+      float z0, z1;
+      upk(Z2[h], z0, z1);
+      zt += 2.0 * ((double)z0 + (double)z1);  // tile a holds no padding
+    }
+    // j side: F_j = -sum_i w^2 (y_i - y_j), into slot a of tile b's points
+    float2* outj = part + (size_t)a * n_pad + (size_t)b * T;
+    for (int k = tid; k < T; k += W * 32) {
+      const float2 v = sacc[k];
+      outj[k] = make_float2(-v.x, -v.y);
+    }
+  } else {
+    // diagonal unit: ordered pairs within the tile, i side only
+#pragma unroll 2
+    for (int j = 0; j < T; ++j) {
+      const float4 q = sj[j];
+      const u64 nx = pk(q.x, q.y);
+      const u64 ny = pk(q.z, q.w);
+#pragma unroll
+      for (int h = 0; h < kH; ++h) {
+        const u64 dx = add2(X2[h], nx);
+        const u64 dy = add2(Y2[h], ny);
+        u64 qq = fma2(dx, dx, one2);
+        qq = fma2(dy, dy, qq);
+        float q0, q1;
+        upk(qq, q0, q1);
+        const u64 w = pk(rcp_approx(q0), rcp_approx(q1));
+        Z2[h] = add2(Z2[h], w);
+        const u64 w2 = mul2(w, w);
+        FX[h] = fma2(w2, dx, FX[h]);
+        FY[h] = fma2(w2, dy, FY[h]);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < kH; ++h) {
+      float z0, z1;
+      upk(Z2[h], z0, z1);
+      if (ibase + (2 * h) * 32 < n) zt += (double)z0;
+      if (ibase + (2 * h + 1) * 32 < n) zt += (double)z1;
+    }
+  }
+  // i side of tile a into slot b
+  float2* outi = part + (size_t)b * n_pad;
+#pragma unroll
+  for (int h = 0; h < kH; ++h) {
+    float fx0, fx1, fy0, fy1;
+    upk(FX[h], fx0, fx1);
+    upk(FY[h], fy0, fy1);
+    outi[ibase + (2 * h) * 32] = make_float2(fx0, fy0);
+    outi[ibase + (2 * h + 1) * 32] = make_float2(fx1, fy1);
+  }
+  return zt;
+}
+
+// (a, b) of unit u of a layout with nt tiles (row-major upper triangle).
+__device__ __forceinline__ void unit_tiles(int u, int nt, int* a_out, int* b_out) {
+  int lo = 0, hi = nt - 1;  // largest a with row_start(a) <= u
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (row_start(mid, nt) <= u) lo = mid; else hi = mid - 1;
+  }
+  *a_out = lo;
+  *b_out = lo + (u - row_start(lo, nt));
+}
+
+}  // namespace tsgne

@@ -134,6 +134,8 @@ tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const float2* Y, fl
                                   cudaStream_t s);
 
 // ------------------------------------------------------------ iteration
+// F^r[i] = sum_k part[k * n_pad + i] for k < slots, in slot order.
+tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad, float2* out, cudaStream_t s);
 // Attraction + gradient + optimiser update: reads Ycur, writes Ynext.
 tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Ycur,
                                    float2* Ynext, float2* upd, float2* gains, const float2* frep_part, int chunks,

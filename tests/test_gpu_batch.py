@@ -1,0 +1,151 @@
+"""Batched layouts and the serving loop (GPU, through the C ABI).
+
+A member of a batch must evolve exactly as it does alone: the batched kernels
+keep every member's arithmetic (including reduction orders) independent of the
+other members, so these comparisons are bit-exact.  The batch of one is also
+compared with the single-layout context path at the same tile size.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2310_11186_gb300 as pkg  # noqa: E402
+import tsgne_synth as synth  # noqa: E402
+from paper_2310_11186_gb300 import serve  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2310_11186_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+    yield
+
+
+def _graphs(sizes, seed=0, d=16):
+    out = []
+    for k, n in enumerate(sizes):
+        g = synth.sbm_zipf(n, max(2, n // 400), n * 3, zipf_s=0.0, rewire=0.1, seed=seed + k)
+        X = synth.block_embedding(g.labels, d, seed=seed + k)
+        Y0 = synth.y_init(n, seed=seed + k)
+        out.append((g, X, Y0))
+    return out
+
+
+def _alone(g, X, Y0, tile, iters, perp=30.0):
+    with pkg.Batch(tile_warps=tile, perplexity=perp) as b:
+        mid = b.add(g.row_ptr, g.col, X, Y0)
+        b.run(iters)
+        Y, it = b.get_Y(mid)
+    assert it == iters
+    return Y
+
+
+def test_batch_of_one_equals_context_path():
+    (g, X, Y0), = _graphs([2000], seed=3)
+    with pkg.Layout() as lay:
+        lay.build_P(g.row_ptr, g.col, X)
+        lay.init_Y(Y0)
+        tile = lay.repulsion_shape()["block"] // 32
+        lay.run(30)
+        Yc = lay.get_Y()
+    Yb = _alone(g, X, Y0, tile, 30)
+    assert np.array_equal(Yb, Yc)
+
+
+@pytest.mark.parametrize("tile", [1, 2, 8])
+def test_members_in_a_mix_equal_alone(tile):
+    gs = _graphs([700, 2000, 3500, 5003], seed=10)
+    late = _graphs([1200], seed=40)[0]
+    with pkg.Batch(tile_warps=tile) as b:
+        ids = [b.add(g.row_ptr, g.col, X, Y0) for g, X, Y0 in gs]
+        b.run(10)
+        late_id = b.add(late[0].row_ptr, late[0].col, late[1], late[2])  # joins at iteration 10
+        b.run(15)
+        assert b.size()["members"] == 5
+        mixed = [b.get_Y(i) for i in ids]
+        late_Y, late_it = b.get_Y(late_id)
+    for (g, X, Y0), (Y, it) in zip(gs, mixed):
+        assert it == 25
+        assert np.array_equal(Y, _alone(g, X, Y0, tile, 25))
+    assert late_it == 15
+    assert np.array_equal(late_Y, _alone(*late, tile, 15))
+
+
+def test_remove_keeps_others_unchanged():
+    gs = _graphs([900, 1500, 2600], seed=20)
+    with pkg.Batch(tile_warps=2) as b:
+        ids = [b.add(g.row_ptr, g.col, X, Y0) for g, X, Y0 in gs]
+        b.run(8)
+        b.remove(ids[1])
+        b.run(12)
+        Y0_, it0 = b.get_Y(ids[0])
+        Y2_, it2 = b.get_Y(ids[2])
+        with pytest.raises(pkg.TsgneError):
+            b.get_Y(ids[1])
+    assert it0 == it2 == 20
+    assert np.array_equal(Y0_, _alone(*gs[0], 2, 20))
+    assert np.array_equal(Y2_, _alone(*gs[2], 2, 20))
+
+
+def test_batched_layout_matches_oracle_short_horizon():
+    """A batch member after 10 iterations against the FP64 oracle (1e-4 rel L2)."""
+    (g, X, Y0), = _graphs([1800], seed=30)
+    Y = _alone(g, X, Y0, 1, 10)
+    rp, col, P = oracle.build_P(g.n, g.row_ptr, g.col, X, 30.0)
+    oY, _, _ = oracle.optimize(g.n, rp, col, P, Y0, 10)
+    assert np.linalg.norm(Y - oY) / np.linalg.norm(oY) < 1e-4
+
+
+def test_autotune_resets_and_caches():
+    gs = _graphs([1000, 3000, 6000], seed=50)
+    with pkg.Batch() as b:
+        for g, X, Y0 in gs:
+            b.add(g.row_ptr, g.col, X, Y0)
+        chosen, times = b.autotune(trial_iters=2)
+        assert chosen in (1, 2, 4, 8) and all(t > 0 for t in times.values())
+        assert b.size()["tile_warps"] == chosen
+        assert b.cached_tile() == chosen
+        Y, it = b.get_Y(0)
+        assert it == 0 and np.array_equal(Y, gs[0][2])
+
+
+def test_serving_results_equal_alone():
+    """Requests arriving while others run are admitted between ticks; each
+    result equals the same request run alone (same tile, same iterations)."""
+    gs = _graphs([800, 2500, 1300, 4000, 600], seed=60)
+    arrivals = [0.0, 0.0, 0.02, 0.05, 0.05]
+    reqs = [serve.Request(k, a, g.row_ptr, g.col, X, Y0) for k, (a, (g, X, Y0)) in enumerate(zip(arrivals, gs))]
+    srv = serve.LayoutServer(iters=40, tick_iters=10, tile_warps=2)
+    try:
+        summary = srv.serve(reqs)
+    finally:
+        srv.close()
+    assert summary["layouts"] == 5 and summary["p99_s"] >= summary["p50_s"] > 0
+    for r, (g, X, Y0) in zip(reqs, gs):
+        assert r.meta["device_iterations"] == 40
+        assert np.array_equal(r.Y, _alone(g, X, Y0, 2, 40))
+
+
+def test_serving_respects_memory_budget():
+    gs = _graphs([3000, 3000, 3000], seed=70)
+    reqs = [serve.Request(k, 0.0, g.row_ptr, g.col, X, Y0) for k, (g, X, Y0) in enumerate(gs)]
+    one = serve.estimate_bytes(3000, int(gs[0][0].row_ptr[-1]) * 2, 2)
+    srv = serve.LayoutServer(iters=20, tick_iters=10, tile_warps=2, budget_bytes=int(one * 1.5))
+    try:
+        summary = srv.serve(reqs)
+    finally:
+        srv.close()
+    # only one layout fits at a time: admissions are staggered
+    adm = sorted(r.admitted for r in reqs)
+    fin = sorted(r.finished for r in reqs)
+    assert summary["layouts"] == 3
+    assert adm[1] >= fin[0] - 1e-9 and adm[2] >= fin[1] - 1e-9

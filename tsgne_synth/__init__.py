@@ -41,6 +41,9 @@ __all__ = [
     "spread_layout",
     "random_graph",
     "workload",
+    "poisson_arrivals",
+    "log_uniform_ints",
+    "sbm_mixed_batch",
 ]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -303,3 +306,37 @@ def workload(name: str, seed: int = 0):
         g = sbm_zipf(100_000, 50, 333_333, 1.2, 0.10, seed=seed)
         return g, block_embedding(g.labels, 128, seed=seed)
     raise KeyError(name)
+
+
+S_ARRIVAL, S_SIZES = 97, 98
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 0) -> np.ndarray:
+    """Arrival times (s) of a Poisson process: cumulative exponential gaps of mean 1/rate."""
+    u = uniform(seed, S_ARRIVAL, 0, count)
+    return np.cumsum(-np.log1p(-u) / rate)
+
+
+def log_uniform_ints(count: int, lo: int, hi: int, seed: int = 0, stream: int = S_SIZES) -> np.ndarray:
+    """Integers log-uniform in [lo, hi]."""
+    u = uniform(seed, stream, 0, count)
+    return np.floor(np.exp(np.log(lo) + u * (np.log(hi + 1) - np.log(lo)))).astype(np.int64).clip(lo, hi)
+
+
+def sbm_mixed_batch(count: int, n_lo: int, n_hi: int, deg_lo: float, deg_hi: float, blocks_lo: int, blocks_hi: int,
+                    d: int, seed: int = 0):
+    """``count`` block-model graphs for batched runs: n log-uniform in
+    [n_lo, n_hi], mean degree uniform in [deg_lo, deg_hi], blocks uniform in
+    [blocks_lo, blocks_hi] (equal sizes), 10 % of edges rewired, d-dimensional
+    block-centre embeddings.  Returns a list of (Graph, X)."""
+    ns = log_uniform_ints(count, n_lo, n_hi, seed=seed)
+    degs = deg_lo + (deg_hi - deg_lo) * uniform(seed, S_SIZES + 1, 0, count)
+    nbs = blocks_lo + np.floor((blocks_hi - blocks_lo + 1) * uniform(seed, S_SIZES + 2, 0, count)).astype(int)
+    out = []
+    for k in range(count):
+        n = int(ns[k])
+        nb = int(min(nbs[k], max(1, n // 8)))
+        edges = int(round(n * degs[k] / 2))
+        g = sbm_zipf(n, nb, edges, zipf_s=0.0, rewire=0.10, seed=seed * 100003 + k)
+        out.append((g, block_embedding(g.labels, d, seed=seed * 100003 + k)))
+    return out
