@@ -316,6 +316,13 @@ def run_ours(args):
                           f"({rows * n:.3g} pair evaluations, {spent:.1f} s), extrapolated to all rows; "
                           f"single thread")}
 
+    batched = None
+    serving = None
+    if rank == 0 and not args.no_batched:
+        batched = bench_batched(args, pkg)
+    if rank == 0 and not args.no_serving:
+        serving = bench_serving(args, pkg)
+
     if rank != 0:
         return 0
     tr = traffic_per_launch()
@@ -365,12 +372,96 @@ def run_ours(args):
         "clocks": clocks,
         "build_ms": build_ms,
         "quality": {"kl": kl_final, "nmi": q_nmi, "aq": q_aq, "iters": e2e_iters},
+        "serving": serving,
+        "batched": batched,
         "paper_context": "300K nodes / 1M edges in under 5 min (ShortestPath + t-SGNE, 32-core Xeon Gold 6338)",
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_batched(args, pkg, log_fn=log):
+    """256 block-model graphs advanced together (one batch, autotuned tile)
+    against one context per graph run one after the other."""
+    import time as _t
+
+    graphs = synth.sbm_mixed_batch(args.batch_graphs, 500, 50_000, 4, 12, 5, 40, 64, seed=args.seed)
+    Y0s = [synth.y_init(g.n, seed=args.seed * 7919 + k) for k, (g, _) in enumerate(graphs)]
+    n_tot = sum(g.n for g, _ in graphs)
+    pairs = sum(0.5 * g.n * (g.n - 1) for g, _ in graphs)
+    log_fn(f"[bench] batched: {len(graphs)} graphs, {n_tot} nodes, {pairs:.3g} pairs/iter")
+    iters = args.batch_iters
+    with pkg.Batch() as b:
+        for (g, X), Y0 in zip(graphs, Y0s):
+            b.add(g.row_ptr, g.col, X, Y0)
+        chosen, tune = b.autotune(trial_iters=2)
+        b.run(2)
+        t0 = _t.perf_counter()
+        b.run(iters)
+        batched_s = (_t.perf_counter() - t0) / iters
+    per_graph = 0.0
+    for (g, X), Y0 in zip(graphs, Y0s):
+        with pkg.Layout() as lay:
+            lay.build_P(g.row_ptr, g.col, X)
+            lay.init_Y(Y0)
+            lay.run(2)
+            t0 = _t.perf_counter()
+            lay.run(iters)
+            per_graph += (_t.perf_counter() - t0) / iters
+    L = len(graphs)
+    return {
+        "workload": (f"{L} stochastic block models, n log-uniform in [500, 50000] (total {n_tot}), mean degree "
+                     f"U[4, 12], 5-40 equal blocks, 10% rewired, 64-d embeddings, perplexity 30"),
+        "iters_timed": iters,
+        "tile_warps": chosen,
+        "autotune_ms_per_iter": tune,
+        "batched_ms_per_iter": batched_s * 1e3,
+        "one_context_per_graph_ms_per_iter": per_graph * 1e3,
+        "speedup": per_graph / batched_s,
+        "layouts_per_s_at_1000_iters": {"batched": L / (1000 * batched_s), "one_per_graph": L / (1000 * per_graph)},
+        "pairs_per_s_batched": pairs / batched_s,
+        "note": "wall-clock per iteration after warm-up, both arms synchronised; layouts/s = members / (1000 x s/iter)",
+    }
+
+
+def bench_serving(args, pkg, log_fn=log):
+    """Poisson arrivals of block-model layout requests served by continuous
+    batching, against the same trace served one layout at a time."""
+    from paper_2310_11186_gb300 import serve
+
+    count = args.serve_requests
+    arr = synth.poisson_arrivals(count, args.serve_rate, seed=args.seed + 11)
+    ns = synth.log_uniform_ints(count, 1_000, 300_000, seed=args.seed + 12)
+    reqs, spec = [], []
+    for k in range(count):
+        n = int(ns[k])
+        blocks = int(min(50, max(5, n // 5000)))
+        g = synth.sbm_zipf(n, blocks, 3 * n, zipf_s=0.0, rewire=0.10, seed=args.seed * 1000 + 500 + k)
+        X = synth.block_embedding(g.labels, 128, seed=args.seed * 1000 + 500 + k)
+        spec.append((g, X))
+    mk = lambda: [serve.Request(k, float(arr[k]), spec[k][0].row_ptr, spec[k][0].col, spec[k][1],
+                                synth.y_init(spec[k][0].n, seed=k)) for k in range(count)]
+    log_fn(f"[bench] serving: {count} requests at {args.serve_rate}/s, n in [{ns.min()}, {ns.max()}]")
+    srv = serve.LayoutServer(iters=args.serve_iters, tick_iters=10, budget_bytes=80 * 2 ** 30, tile_warps=4,
+                             policy="srpt")
+    try:
+        served = srv.serve(mk())
+    finally:
+        srv.close()
+    serial = serve.serial_baseline(mk(), args.serve_iters)
+    return {
+        "workload": (f"{count} requests, Poisson arrivals at {args.serve_rate}/s, stochastic block models with n "
+                     f"log-uniform in [1000, 300000], mean degree 6, 128-d embeddings, {args.serve_iters} "
+                     f"iterations each, 80 GB admission budget"),
+        "policy": "continuous batching, shortest remaining work first, tile 4 warps",
+        "layouts_per_s": served["layouts_per_s"],
+        "p50_s": served["p50_s"],
+        "p99_s": served["p99_s"],
+        "wall_s": served["wall_s"],
+        "serial_one_at_a_time": serial,
+    }
 
 
 def main():
@@ -384,6 +475,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-step-seconds", type=float, default=1.0)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=256)
+    ap.add_argument("--batch-iters", type=int, default=20)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-iters", type=int, default=500)
     ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOAD,
                     help="zipf300k is the benchmark; the others are smaller cases for profiling")
     args = ap.parse_args()

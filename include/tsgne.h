@@ -234,7 +234,7 @@ tsgne_status tsgne_batch_add(tsgne_batch* b, int32_t n, const int64_t* row_ptr, 
 /* Removes a member and frees its device memory. */
 tsgne_status tsgne_batch_remove(tsgne_batch* b, int32_t id);
 
-/* Members, tile warps and total repulsion work units of one iteration. */
+/* Members, tile warps and the repulsion work units of one iteration of the active members. */
 tsgne_status tsgne_batch_size(tsgne_batch* b, int32_t* members, int32_t* tile_warps, int64_t* units);
 
 /* n_iter iterations of every member; synchronises; NONFINITE if any layout diverged. */
@@ -242,6 +242,13 @@ tsgne_status tsgne_batch_run(tsgne_batch* b, int32_t n_iter);
 
 /* Current layout of a member (float[n*2]) and its iteration count (host, may be NULL). */
 tsgne_status tsgne_batch_get_Y(tsgne_batch* b, int32_t id, float* Y_out, int32_t* iter, int32_t ptr_kind);
+
+/*
+ * Marks a member active (default) or inactive.  tsgne_batch_run advances
+ * only active members; inactive ones keep their state untouched (schedulers
+ * use this to run short jobs first without evicting long ones).
+ */
+tsgne_status tsgne_batch_set_active(tsgne_batch* b, int32_t id, int32_t active);
 
 /* Changes the repulsion tile of the batch (members' states are kept). */
 tsgne_status tsgne_batch_set_tile(tsgne_batch* b, int32_t tile_warps);

@@ -137,6 +137,7 @@ EXPORTS = {
     "tsgne_batch_run": (_st, [_p, _i32]),
     "tsgne_batch_get_Y": (_st, [_p, _i32, _p, ctypes.POINTER(_i32), _i32]),
     "tsgne_batch_set_tile": (_st, [_p, _i32]),
+    "tsgne_batch_set_active": (_st, [_p, _i32, _i32]),
     "tsgne_batch_reset": (_st, [_p]),
     "tsgne_batch_autotune": (_st, [_p, _i32, ctypes.POINTER(_i32), _p]),
     "tsgne_batch_cached_tile": (_st, [_p, ctypes.POINTER(_i32)]),
@@ -547,11 +548,17 @@ class Batch:
         self._check(lib().tsgne_batch_run(self.h, int(n_iter)))
 
     def get_Y(self, mid: int, out=None):
+        if mid not in self.sizes:
+            raise TsgneError(1, f"unknown member id {mid}")
         n = self.sizes[mid]
         out, buf = _out(n, out)
         it = _i32()
         self._check(lib().tsgne_batch_get_Y(self.h, int(mid), buf[0], ctypes.byref(it), buf[1]))
         return out, it.value
+
+    def set_active(self, mid: int, active: bool = True):
+        """Inactive members keep their state and are skipped by run()."""
+        self._check(lib().tsgne_batch_set_active(self.h, int(mid), int(bool(active))))
 
     def set_tile(self, tile_warps: int):
         self._check(lib().tsgne_batch_set_tile(self.h, int(tile_warps)))

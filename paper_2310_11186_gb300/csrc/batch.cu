@@ -215,6 +215,7 @@ struct Member {
   DevBuf<Sched> sched;
   int nt = 0, n_pad = 0, units = 0;  // for the batch's current tile
   DevBuf<float2> Y0;                 // initial layout (autotune restores it)
+  bool active = true;
 };
 
 std::mutex g_cache_mu;
@@ -237,7 +238,7 @@ struct tsgne_batch {
   DevBuf<GraphDesc> d_desc;
   DevBuf<int> d_unit_off, d_row_off;
   DevBuf<BatchCtr> d_ctr;
-  int U = 0, R = 0;
+  int U = 0, R = 0, G = 0;  // of the active members
   bool dirty = true;
   cudaGraphExec_t graph = nullptr;
   ~tsgne_batch() {
@@ -290,11 +291,15 @@ void invalidate(tsgne_batch* b) {
 // Uploads descriptors and prefix offsets for the current membership.
 tsgne_status refresh(tsgne_batch* b) {
   if (!b->dirty) return TSGNE_OK;
-  const int G = (int)b->members.size();
+  std::vector<Member*> act;
+  for (auto& m : b->members)
+    if (m->active) act.push_back(m.get());
+  const int G = (int)act.size();
+  b->G = G;
   std::vector<GraphDesc> h(G > 0 ? G : 1);
   std::vector<int> uo(G + 1, 0), ro(G + 1, 0);
   for (int k = 0; k < G; ++k) {
-    Member& m = *b->members[k];
+    Member& m = *act[k];
     GraphDesc d{};
     d.rp = m.rp.get();
     d.col = m.col.get();
@@ -330,7 +335,7 @@ tsgne_status refresh(tsgne_batch* b) {
 }
 
 tsgne_status enqueue_iteration(tsgne_batch* b) {
-  const int G = (int)b->members.size();
+  const int G = b->G;
   if (G == 0) return TSGNE_OK;
   const int W = b->W;
   const int slots = b->sms * (kWarpsPerSm / W);
@@ -356,7 +361,7 @@ tsgne_status enqueue_iteration(tsgne_batch* b) {
 
 tsgne_status run_iterations(tsgne_batch* b, int n_iter, bool use_graph) {
   TS_TRY(refresh(b));
-  if (b->members.empty() || n_iter <= 0) return TSGNE_OK;
+  if (b->G == 0 || n_iter <= 0) return TSGNE_OK;
   if (use_graph && !b->graph) {
     cudaGraph_t g = nullptr;
     TS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -567,6 +572,18 @@ tsgne_status tsgne_batch_get_Y(tsgne_batch* b, int32_t id, float* Y_out, int32_t
                             ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->stream));
   B_CUDA(b, cudaStreamSynchronize(b->stream));
   if (iter) *iter = h.t;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_set_active(tsgne_batch* b, int32_t id, int32_t active) {
+  if (!b) return TSGNE_ERR_INVALID_ARG;
+  b->err.clear();
+  Member* m = find_member(b, id);
+  if (!m) return bfail(b, TSGNE_ERR_INVALID_ARG, "unknown member id");
+  if (m->active != (active != 0)) {
+    m->active = active != 0;
+    invalidate(b);
+  }
   return TSGNE_OK;
 }
 

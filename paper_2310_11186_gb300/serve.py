@@ -65,10 +65,23 @@ def estimate_bytes(n: int, nnz: int, tile_warps: int) -> int:
 
 
 class LayoutServer:
+    """Policies: ``"all"`` advances every resident layout at every tick;
+    ``"srpt"`` (shortest remaining processing time first) advances, at each
+    tick, the resident layouts with the least remaining work (remaining
+    iterations x n^2) until their pairs per iteration reach ``fill_pairs``
+    (enough tile pairs to keep every SM busy), so small requests are not held
+    behind large ones while the GPU stays full; the others wait, resident."""
+
     def __init__(self, iters: int = 500, tick_iters: int = 10, budget_bytes: int = 80 * 2 ** 30,
-                 max_members: int = 256, tile_warps: int = 2, config=None, stream=None):
+                 max_members: int = 256, tile_warps: int = 2, config=None, stream=None, policy: str = "srpt",
+                 fill_pairs: float = 4e9):
         if iters % tick_iters != 0:
             raise ValueError("iters must be a multiple of tick_iters (layouts join and leave between ticks)")
+        if policy not in ("all", "srpt"):
+            raise ValueError("policy must be 'all' or 'srpt'")
+        self.policy = policy
+        self.fill_pairs = fill_pairs
+        self.active: set[int] = set()
         self.iters = iters
         self.tick_iters = tick_iters
         self.budget = budget_bytes
@@ -95,6 +108,7 @@ class LayoutServer:
                               or need > self._free_device_bytes()):
             return False
         mid = self.batch.add(req.row_ptr, req.col, req.X, req.Y0)
+        self.active.add(mid)
         self.resident[mid] = (req, need)
         self.used += need
         req.admitted = now
@@ -118,9 +132,20 @@ class LayoutServer:
                 if k < len(pending):  # idle until the next arrival
                     time.sleep(max(0.0, min(0.05, pending[k].arrival - (clock() - t0))))
                 continue
+            chosen = self._select()
+            for mid in self.resident:
+                want = mid in chosen
+                if want != (mid in self.active):
+                    self.batch.set_active(mid, want)
+                    if want:
+                        self.active.add(mid)
+                    else:
+                        self.active.discard(mid)
             self.batch.run(self.tick_iters)
             self.ticks += 1
             for mid in list(self.resident):
+                if mid not in chosen:
+                    continue
                 req, nbytes = self.resident[mid]
                 req.iterations += self.tick_iters
                 if req.iterations >= self.iters:
@@ -130,10 +155,27 @@ class LayoutServer:
                     req.finished = clock() - t0
                     self.batch.remove(mid)
                     del self.resident[mid]
+                    self.active.discard(mid)
                     self.used -= nbytes
                     done.append(req)
         wall = clock() - t0
         return summarize(done, wall)
+
+    def _select(self) -> set[int]:
+        if self.policy == "all":
+            return set(self.resident)
+
+        def remaining(mid):
+            req = self.resident[mid][0]
+            return (self.iters - req.iterations) * float(req.n) ** 2
+
+        chosen, pairs = set(), 0.0
+        for mid in sorted(self.resident, key=lambda m: (remaining(m), m)):
+            chosen.add(mid)
+            pairs += 0.5 * float(self.resident[mid][0].n) ** 2
+            if pairs >= self.fill_pairs:
+                break
+        return chosen
 
     def close(self):
         self.batch.close()

@@ -149,3 +149,19 @@ def test_serving_respects_memory_budget():
     fin = sorted(r.finished for r in reqs)
     assert summary["layouts"] == 3
     assert adm[1] >= fin[0] - 1e-9 and adm[2] >= fin[1] - 1e-9
+
+
+def test_srpt_runs_short_jobs_first_and_results_stay_exact():
+    """With room for one layout per tick, shortest-remaining-work-first lets
+    the small requests overtake a large one that arrived first; inactive
+    members keep their state, so every result still equals its run alone."""
+    gs = _graphs([6000, 700, 900], seed=80)
+    reqs = [serve.Request(k, 0.0, g.row_ptr, g.col, X, Y0) for k, (g, X, Y0) in enumerate(gs)]
+    srv = serve.LayoutServer(iters=30, tick_iters=10, tile_warps=2, policy="srpt", fill_pairs=1.0)
+    try:
+        srv.serve(reqs)
+    finally:
+        srv.close()
+    assert reqs[1].finished < reqs[0].finished and reqs[2].finished < reqs[0].finished
+    for r, (g, X, Y0) in zip(reqs, gs):
+        assert np.array_equal(r.Y, _alone(g, X, Y0, 2, 30))
