@@ -72,6 +72,16 @@ struct tsgne_ctx {
   DevBuf<float2> Y[2];
   int cur = 0;
   DevBuf<float2> upd, gains, frep, fsum, grad;
+  DevBuf<int32_t> heavy_rows;
+  DevBuf<float2> heavy_fa;
+  int heavy_count = 0;
+  HeavyRows heavy() const {
+    HeavyRows h;
+    h.rows = heavy_rows.get();
+    h.fa = heavy_fa.get();
+    h.count = heavy_count;
+    return h;
+  }
   DevBuf<double> zpart, klpart;
   DevBuf<Sched> sched;
 
@@ -234,7 +244,7 @@ tsgne_status enqueue_step(tsgne_ctx* ctx) {
   const int nxt = ctx->cur ^ 1;
   TS_TRY(launch_attract_update(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
                                ctx->Y[nxt].get(), ctx->upd.get(), ctx->gains.get(), ctx->fsum.get(), 1,
-                               ctx->shape.n_pad, ctx->sched.get(), ctx->eta, ctx->cfg.min_gain,
+                               ctx->shape.n_pad, ctx->sched.get(), ctx->eta, ctx->cfg.min_gain, ctx->heavy(),
                                ctx->stream));
   TS_TRY(prof_end(ctx, &pr));
   ctx->cur = nxt;
@@ -315,6 +325,7 @@ tsgne_status install(tsgne_ctx* ctx, int n, int64_t nnz, DevBuf<int64_t>& rp, De
   ctx->col = std::move(col);
   ctx->P = std::move(P);
   TS_TRY(alloc_layout(ctx));
+  TS_TRY(find_heavy_rows(n, ctx->rp.get(), ctx->heavy_rows, ctx->heavy_fa, &ctx->heavy_count, ctx->stream));
   ctx->have_P = true;
   return TSGNE_OK;
 }
@@ -602,7 +613,7 @@ tsgne_status tsgne_gradient(tsgne_ctx* ctx, float alpha, float* g_out, double* z
   ProfRec pr;
   API_TRY(ctx, prof_begin(ctx, 2, &pr));
   API_TRY(ctx, launch_gradient(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
-                               ctx->fsum.get(), 1, ctx->shape.n_pad, ctx->sched.get(), alpha,
+                               ctx->fsum.get(), 1, ctx->shape.n_pad, ctx->sched.get(), alpha, ctx->heavy(),
                                ctx->grad.get(), ctx->stream));
   API_TRY(ctx, prof_end(ctx, &pr));
   API_TRY(ctx, copy_out(g_out, ctx->grad.get(), sizeof(float2) * (size_t)ctx->n, ptr_kind, ctx->stream));

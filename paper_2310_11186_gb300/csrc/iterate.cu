@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(kAttrCta)
     k_attract(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ P,
               const float2* __restrict__ Ycur, float2* __restrict__ Ynext, float2* __restrict__ upd,
               float2* __restrict__ gains, const float2* __restrict__ frep_part, int chunks, int n_pad,
-              Sched* sched, float eta, float min_gain, float alpha_export, float2* __restrict__ g_out) {
+              Sched* sched, float eta, float min_gain, float alpha_export, float2* __restrict__ g_out,
+              const int32_t* __restrict__ heavy_rows, int heavy_count, const float2* __restrict__ heavy_fa) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = gt / G;
   const int lane = (int)(gt % G);
@@ -44,7 +45,20 @@ __global__ void __launch_bounds__(kAttrCta)
   float2 yi = make_float2(0.f, 0.f);
   if (valid) {
     yi = Ycur[i];
-    attract_row<G>(rp, col, P, Ycur, i, lane, yi, ax, ay);
+    if (rp[i + 1] - rp[i] > kHeavyDeg) {
+      if (lane == 0) {  // precomputed by k_attract_heavy; rows are sorted
+        int lo = 0, hi = heavy_count - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (heavy_rows[mid] < i) lo = mid + 1; else hi = mid;
+        }
+        const float2 f = heavy_fa[lo];
+        ax = f.x;
+        ay = f.y;
+      }
+    } else {
+      attract_row<G>(rp, col, P, Ycur, i, lane, yi, ax, ay);
+    }
     for (int c = lane; c < chunks; c += G) {
       const float2 f = frep_part[(size_t)c * n_pad + i];
       rx += f.x;
@@ -71,6 +85,47 @@ __global__ void __launch_bounds__(kAttrCta)
   gains[i] = gn;
   Ynext[i] = y;
   if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&sched->flags, kFlagNonfiniteY);
+}
+
+// Attraction of the rows with more than kHeavyDeg entries (hubs of
+// power-law graphs), one CTA per row with a fixed-order block reduction, so
+// that the 8-lane groups of k_attract never serialise on a hub row.
+__global__ void __launch_bounds__(256)
+    k_attract_heavy(const int32_t* __restrict__ rows, int count, const int64_t* __restrict__ rp,
+                    const int32_t* __restrict__ col, const float* __restrict__ P, const float2* __restrict__ Y,
+                    float2* __restrict__ fa) {
+  __shared__ float sx[256], sy[256];
+  for (int k = blockIdx.x; k < count; k += gridDim.x) {
+    const int64_t i = rows[k];
+    const float2 yi = Y[i];
+    float ax = 0.f, ay = 0.f;
+    attract_row<256>(rp, col, P, Y, i, threadIdx.x, yi, ax, ay);
+    sx[threadIdx.x] = ax;
+    sy[threadIdx.x] = ay;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        sx[threadIdx.x] += sx[threadIdx.x + o];
+        sy[threadIdx.x] += sy[threadIdx.x + o];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) fa[k] = make_float2(sx[0], sy[0]);
+    __syncthreads();
+  }
+}
+
+__global__ void k_heavy_flags(int n, const int64_t* __restrict__ rp, int32_t* __restrict__ flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    flag[i] = (rp[i + 1] - rp[i]) > kHeavyDeg ? 1 : 0;
+}
+
+__global__ void k_heavy_scatter(int n, const int32_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                                int32_t* __restrict__ rows) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    if (flag[i]) rows[pos[i]] = (int32_t)i;
 }
 
 // F^r_i = sum over the partial-force slots in slot order (fixed order, so the
@@ -172,21 +227,51 @@ tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad
 
 tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Ycur,
                                    float2* Ynext, float2* upd, float2* gains, const float2* frep_part, int chunks,
-                                   int n_pad, Sched* sched, float eta, float min_gain, cudaStream_t s) {
+                                   int n_pad, Sched* sched, float eta, float min_gain, const HeavyRows& hv,
+                                   cudaStream_t s) {
+  if (hv.count > 0) {
+    k_attract_heavy<<<hv.count < 4096 ? hv.count : 4096, 256, 0, s>>>(hv.rows, hv.count, rp, col, P, Ycur, hv.fa);
+  }
   const int grid = grid_rows((int64_t)n * kG, kAttrCta);
   k_attract<kG, false><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Ycur, Ynext, upd, gains, frep_part, chunks, n_pad,
-                                                 sched, eta, min_gain, 0.f, nullptr);
+                                                 sched, eta, min_gain, 0.f, nullptr, hv.rows, hv.count, hv.fa);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }
 
 tsgne_status launch_gradient(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
                              const float2* frep_part, int chunks, int n_pad, const Sched* sched, float alpha,
-                             float2* g, cudaStream_t s) {
+                             const HeavyRows& hv, float2* g, cudaStream_t s) {
+  if (hv.count > 0) {
+    k_attract_heavy<<<hv.count < 4096 ? hv.count : 4096, 256, 0, s>>>(hv.rows, hv.count, rp, col, P, Y, hv.fa);
+  }
   const int grid = grid_rows((int64_t)n * kG, kAttrCta);
   k_attract<kG, true><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Y, nullptr, nullptr, nullptr, frep_part, chunks,
-                                                n_pad, const_cast<Sched*>(sched), 0.f, 0.f, alpha, g);
+                                                n_pad, const_cast<Sched*>(sched), 0.f, 0.f, alpha, g, hv.rows,
+                                                hv.count, hv.fa);
   TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+tsgne_status find_heavy_rows(int n, const int64_t* rp, DevBuf<int32_t>& rows, DevBuf<float2>& fa, int* count,
+                             cudaStream_t s) {
+  DevBuf<int32_t> flag;
+  DevBuf<int64_t> pos, scr;
+  TS_TRY(flag.alloc((size_t)n));
+  TS_TRY(pos.alloc((size_t)n + 1));
+  TS_TRY(scr.alloc(scan_scratch_bytes(n) / sizeof(int64_t)));
+  const int g = grid_rows(n, 256) < 4096 ? grid_rows(n, 256) : 4096;
+  k_heavy_flags<<<g, 256, 0, s>>>(n, rp, flag.get());
+  TS_TRY(scan_i32_to_i64(flag.get(), pos.get(), n, scr.get(), s));
+  int64_t total = 0;
+  TS_CUDA(cudaMemcpyAsync(&total, pos.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TS_CUDA(cudaStreamSynchronize(s));
+  *count = (int)total;
+  TS_TRY(rows.alloc((size_t)(total > 0 ? total : 1)));
+  TS_TRY(fa.alloc((size_t)(total > 0 ? total : 1)));
+  if (total > 0) k_heavy_scatter<<<g, 256, 0, s>>>(n, flag.get(), pos.get(), rows.get());
+  TS_CUDA(cudaGetLastError());
+  TS_CUDA(cudaStreamSynchronize(s));
   return TSGNE_OK;
 }
 

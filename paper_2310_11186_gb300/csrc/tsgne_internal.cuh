@@ -134,16 +134,27 @@ tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const float2* Y, fl
                                   cudaStream_t s);
 
 // ------------------------------------------------------------ iteration
+// Rows with more than kHeavyDeg entries get their attraction from a CTA of
+// their own (k_attract_heavy); rows[] is sorted, fa[] holds their sums.
+constexpr int kHeavyDeg = 256;
+struct HeavyRows {
+  const int32_t* rows = nullptr;
+  float2* fa = nullptr;
+  int count = 0;
+};
+tsgne_status find_heavy_rows(int n, const int64_t* rp, DevBuf<int32_t>& rows, DevBuf<float2>& fa, int* count,
+                             cudaStream_t s);
 // F^r[i] = sum_k part[k * n_pad + i] for k < slots, in slot order.
 tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad, float2* out, cudaStream_t s);
 // Attraction + gradient + optimiser update: reads Ycur, writes Ynext.
 tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Ycur,
                                    float2* Ynext, float2* upd, float2* gains, const float2* frep_part, int chunks,
-                                   int n_pad, Sched* sched, float eta, float min_gain, cudaStream_t s);
+                                   int n_pad, Sched* sched, float eta, float min_gain, const HeavyRows& hv,
+                                   cudaStream_t s);
 // Gradient export g = 4 (alpha F^a - F^r / Z) without state change.
 tsgne_status launch_gradient(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
                              const float2* frep_part, int chunks, int n_pad, const Sched* sched, float alpha,
-                             float2* g, cudaStream_t s);
+                             const HeavyRows& hv, float2* g, cudaStream_t s);
 // KL terms: sched->red[0] = sum p ln(p / w), sched->red[1] = sum p.
 tsgne_status launch_kl(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
                        double* partials, int nparts, Sched* sched, cudaStream_t s);

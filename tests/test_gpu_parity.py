@@ -311,3 +311,31 @@ def test_device_layout_io():
         G = torch.empty_like(out)
         lay.gradient(1.0, out=G)
         assert np.array_equal(G.cpu().numpy(), lay.gradient(1.0)[0])
+
+
+def test_gradient_parity_with_hub_rows():
+    """Rows above the 256-entry threshold take the one-CTA-per-row path."""
+    n = 6000
+    rng = np.random.default_rng(3)
+    g = synth.random_graph(n, 5.0, seed=77)
+    hubs = {7: 3000, 4000: 800, 5999: 300}
+    src, dst = [], []
+    for h, k in hubs.items():
+        nb = rng.choice(n, size=k, replace=False)
+        nb = nb[nb != h]
+        src.append(np.full(nb.size, h))
+        dst.append(nb)
+    rows = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    rp, col = synth.csr_from_edges(n, np.concatenate([rows] + src), np.concatenate([g.col] + dst))
+    labels = (np.arange(n) % 5).astype(np.int32)
+    X = synth.block_embedding(labels, 8, seed=5)
+    orp, ocol, oP = oracle.build_P(n, rp, col, X, 3.0)
+    assert np.diff(orp).max() > 2000
+    Y = synth.spread_layout(labels, scale=15.0, seed=9)
+    for alpha in (1.0, 12.0):
+        oG, oZ = oracle.gradient(n, orp, ocol, oP, Y.astype(np.float64), alpha)
+        with pkg.Layout(perplexity=3.0) as lay:
+            lay.build_P(rp, col, X)
+            lay.init_Y(Y)
+            G, Z = lay.gradient(alpha)
+        assert rel_l2(G, oG) < 1e-4, rel_l2(G, oG)

@@ -44,6 +44,8 @@ __all__ = [
     "poisson_arrivals",
     "log_uniform_ints",
     "sbm_mixed_batch",
+    "rmat",
+    "induced_bfs_ball",
 ]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -340,3 +342,83 @@ def sbm_mixed_batch(count: int, n_lo: int, n_hi: int, deg_lo: float, deg_hi: flo
         g = sbm_zipf(n, nb, edges, zipf_s=0.0, rewire=0.10, seed=seed * 100003 + k)
         out.append((g, block_embedding(g.labels, d, seed=seed * 100003 + k)))
     return out
+
+
+S_RMAT = 99
+
+
+def rmat(scale: int, edges: int, a: float = 0.57, b: float = 0.19, c: float = 0.19, d_emb: int = 64,
+         community_bits: int = 6, seed: int = 0, chunk: int = 1 << 22):
+    """R-MAT graph (Chakrabarti, Zhan, Faloutsos 2004) with 2^scale nodes:
+    each edge descends ``scale`` levels choosing quadrant (0,0), (0,1), (1,0),
+    (1,1) with probabilities a, b, c, 1-a-b-c (one 32-bit uniform per level,
+    two per SplitMix64 draw); draws continue until ``edges`` distinct
+    undirected non-loop edges exist, keeping first occurrences in draw order.
+    Communities are the top ``community_bits`` bits of the node id (the first
+    levels of the recursion); X = community centre N(0, 4I) + N(0, I) in
+    ``d_emb`` dimensions.  Returns (Graph, X)."""
+    n = 1 << scale
+    half = (scale + 1) // 2
+    ta, tab, tabc = (np.uint64(int(x * 2 ** 32)) for x in (a, a + b, a + b + c))
+    keys_all = []
+    have = 0
+    ctr = 0
+    while True:
+        m = chunk
+        r = splitmix64(seed, S_RMAT, ctr, m * half).reshape(half, m)
+        ctr += m * half
+        src = np.zeros(m, dtype=np.int64)
+        dst = np.zeros(m, dtype=np.int64)
+        for lvl in range(scale):
+            w = r[lvl // 2]
+            u32 = (w >> np.uint64(32)) if (lvl & 1) == 0 else (w & np.uint64(0xFFFFFFFF))
+            bit_s = u32 >= tab
+            bit_d = ((u32 >= ta) & (u32 < tab)) | (u32 >= tabc)
+            src = (src << 1) | bit_s
+            dst = (dst << 1) | bit_d
+        ok = src != dst
+        keys_all.append(np.minimum(src[ok], dst[ok]) * n + np.maximum(src[ok], dst[ok]))
+        have += int(ok.sum())
+        if have < edges:
+            continue
+        allk = np.concatenate(keys_all)
+        _, first = np.unique(allk, return_index=True)
+        if first.size >= edges:
+            first.sort()
+            keys = allk[first[:edges]]
+            break
+        keys_all = [allk]
+    u_, v_ = keys // n, keys % n
+    rp, col = csr_from_edges(n, u_, v_)
+    labels = (np.arange(n) >> (scale - community_bits)).astype(np.int32)
+    return Graph(n, rp, col, labels), block_embedding(labels, d_emb, seed=seed)
+
+
+def induced_bfs_ball(g: Graph, size: int, start: int | None = None):
+    """Nodes of a BFS ball (levels in order, neighbours in ascending id) from
+    ``start`` (default: the highest-degree node), truncated at ``size``, and
+    the induced subgraph on them (ids renumbered in that order).
+    Returns (nodes int64[k], Graph)."""
+    deg = np.diff(g.row_ptr)
+    s = int(np.argmax(deg)) if start is None else int(start)
+    seen = np.zeros(g.n, dtype=bool)
+    seen[s] = True
+    order = [s]
+    head = 0
+    while head < len(order) and len(order) < size:
+        v = order[head]
+        head += 1
+        nb = g.col[g.row_ptr[v]:g.row_ptr[v + 1]]
+        for w in np.sort(nb):
+            if not seen[w]:
+                seen[w] = True
+                order.append(int(w))
+                if len(order) >= size:
+                    break
+    nodes = np.array(order, dtype=np.int64)
+    remap = np.full(g.n, -1, dtype=np.int64)
+    remap[nodes] = np.arange(nodes.size)
+    rows = np.repeat(np.arange(g.n), deg)
+    keep = (remap[rows] >= 0) & (remap[g.col] >= 0) & (rows < g.col)
+    rp, col = csr_from_edges(nodes.size, remap[rows[keep]], remap[g.col[keep]])
+    return nodes, Graph(nodes.size, rp, col, g.labels[nodes])
