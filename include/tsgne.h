@@ -268,6 +268,31 @@ tsgne_status tsgne_batch_autotune(tsgne_batch* b, int32_t trial_iters, int32_t* 
 /* Cached tile for the current membership's key, 0 if none was tuned yet. */
 tsgne_status tsgne_batch_cached_tile(tsgne_batch* b, int32_t* tile_warps);
 
+/*
+ * ------------------------------------------------- ShortestPath embedding
+ * The paper's graph embedding for t-SGNE (Sec. 2.3, Eq. 8): for d target
+ * nodes (the paper draws them at random; the caller passes them, int32[d] in
+ * [0, n), repeats allowed), X[i][t] = shortest-path length from node i to
+ * target t when it is <= l0, else l0 + 1 (also when no path exists).  l0 <= 0
+ * selects the paper's default floor(sqrt(|E|)), |E| the undirected edges after
+ * symmetrisation.  The graph is read like tsgne_build_P reads it (any CSR,
+ * symmetrised).  X_out float[n*d] row-major.  1 <= d <= 1024.  All pointers
+ * live where ptr_kind says; work runs on cuda_stream (NULL: legacy default)
+ * and the call synchronises.  Errors: INVALID_ARG (also a target outside
+ * [0, n)), BAD_CSR, OOM.
+ */
+tsgne_status tsgne_shortest_path_embedding(int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                           const int32_t* targets, int32_t d, int32_t l0, float* X_out,
+                                           int32_t ptr_kind, void* cuda_stream);
+
+/*
+ * The paper's full pipeline GD = DR o GE (Sec. 2, Eq. 1) for the context:
+ * ShortestPath embedding of the graph (as tsgne_shortest_path_embedding, X
+ * kept on the device) followed by tsgne_build_P on (G, X).
+ */
+tsgne_status tsgne_build_P_shortest_path(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                         const int32_t* targets, int32_t d, int32_t l0, int32_t ptr_kind);
+
 /* Largest n accepted by tsgne_repulsion_noalloc. */
 #define TSGNE_NOALLOC_MAX_N 65536
 

@@ -76,6 +76,8 @@ def _load():
             lib.tsgo_attraction_rows.restype = ctypes.c_int
             lib.tsgo_optimize.argtypes = [_i32, _p, _p, _p, _p, _p, _p, _i32, _i32, _dbl, _i32, _dbl, _dbl, _dbl, _dbl]
             lib.tsgo_optimize.restype = ctypes.c_int
+            lib.tsgo_shortest_path.argtypes = [_i32, _p, _p, _p, _i32, _i32, _p]
+            lib.tsgo_shortest_path.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -244,3 +246,20 @@ def optimize(n, rp, col, P, Y, n_iter, *, upd=None, gains=None, t0=0, early_exag
                                float(min_gain))
     _check(st, "optimize")
     return Yd, u, g
+
+
+def default_l0(num_edges: int) -> int:
+    """l0 = sqrt(|E|) (Sec. 2.3); distances are integers, so floor(sqrt(|E|))."""
+    import math
+
+    return int(math.isqrt(int(num_edges)))
+
+
+def shortest_path_embedding(n, rp, col, targets, l0):
+    """ShortestPath embedding (Eq. 8) on a symmetric CSR: n x d FP64."""
+    rp, col = _c(rp, np.int64), _c(col, np.int32)
+    tg = _c(targets, np.int32)
+    X = np.zeros((n, tg.size))
+    _check(_load().tsgo_shortest_path(n, _ptr(rp), _ptr(col if col.size else np.zeros(1, np.int32)), _ptr(tg),
+                                      tg.size, int(l0), _ptr(X)), "shortest_path")
+    return X

@@ -24,6 +24,8 @@
  *   tsgo_optimize       gradient descent with gains, momentum and early
  *                       exaggeration (the paper gives no schedule; the
  *                       published t-SNE defaults are used)
+ *   tsgo_shortest_path  ShortestPath graph embedding (Sec. 2.3, Eq. 8): BFS
+ *                       distances to d target nodes, capped at l0 + 1
  *
  * Readings of the paper where it is silent (also listed in the design notes):
  *   - N(i) is the set of graph neighbours (k = graph edges), union of both
@@ -368,5 +370,48 @@ int tsgo_optimize(int32_t n, const int64_t* rp, const int32_t* col, const double
     }
   }
   free(G);
+  return TSGO_OK;
+}
+
+/*
+ * ShortestPath embedding (Sec. 2.3, Eq. 8): E_it = dist(v_i, target_t) when
+ * that distance is <= l0, else l0 + 1 (also when no path exists).  One BFS
+ * per target over the undirected graph given by a symmetric CSR.  X is n x d
+ * row-major (FP64 here; the values are small integers).
+ */
+int tsgo_shortest_path(int32_t n, const int64_t* rp, const int32_t* col, const int32_t* targets, int32_t d,
+                       int32_t l0, double* X) {
+  if (n < 1 || d < 1 || l0 < 0) return TSGO_EINVAL;
+  int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!dist || !queue) {
+    free(dist); free(queue);
+    return TSGO_ENOMEM;
+  }
+  for (int32_t t = 0; t < d; ++t) {
+    int32_t s = targets[t];
+    if (s < 0 || s >= n) {
+      free(dist); free(queue);
+      return TSGO_EINVAL;
+    }
+    for (int32_t i = 0; i < n; ++i) dist[i] = -1;
+    int32_t head = 0, tail = 0;
+    dist[s] = 0;
+    queue[tail++] = s;
+    while (head < tail) {
+      int32_t v = queue[head++];
+      for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+        int32_t w = col[e];
+        if (dist[w] < 0) {
+          dist[w] = dist[v] + 1;
+          queue[tail++] = w;
+        }
+      }
+    }
+    for (int32_t i = 0; i < n; ++i)
+      X[(int64_t)i * d + t] = (dist[i] >= 0 && dist[i] <= l0) ? (double)dist[i] : (double)(l0 + 1);
+  }
+  free(dist);
+  free(queue);
   return TSGO_OK;
 }

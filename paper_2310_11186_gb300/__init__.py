@@ -47,6 +47,8 @@ __all__ = [
     "tsgne_repulsion_shape",
     "tsgne_sync",
     "tsgne_repulsion_noalloc",
+    "tsgne_shortest_path_embedding",
+    "tsgne_build_P_shortest_path",
     "NOALLOC_MAX_N",
     "Layout",
     "Batch",
@@ -141,6 +143,8 @@ EXPORTS = {
     "tsgne_batch_reset": (_st, [_p]),
     "tsgne_batch_autotune": (_st, [_p, _i32, ctypes.POINTER(_i32), _p]),
     "tsgne_batch_cached_tile": (_st, [_p, ctypes.POINTER(_i32)]),
+    "tsgne_shortest_path_embedding": (_st, [_i32, _p, _p, _p, _i32, _i32, _p, _i32, _p]),
+    "tsgne_build_P_shortest_path": (_st, [_p, _i32, _p, _p, _p, _i32, _i32, _i32]),
 }
 
 NOALLOC_MAX_N = 65536  # TSGNE_NOALLOC_MAX_N
@@ -245,6 +249,39 @@ def tsgne_build_P(ctx, n, row_ptr, col_idx, X):
     d = int(X.shape[1])
     kind = _same_kind(rp, ci, x)
     _check(ctx, lib().tsgne_build_P(ctx, int(n), rp[0], ci[0], x[0], d, kind))
+
+
+def tsgne_shortest_path_embedding(row_ptr, col_idx, targets, l0: int = 0, out=None, stream=None):
+    """ShortestPath embedding (Sec. 2.3, Eq. 8): float32 n x d BFS distances to
+    the targets, capped at l0 + 1 (l0 <= 0: floor(sqrt(|E|)))."""
+    n = len(row_ptr) - 1
+    rp = _as_buffer(row_ptr, np.int64)
+    ci = _as_buffer(col_idx, np.int32)
+    tg = _as_buffer(targets, np.int32)
+    kind = _same_kind(rp, ci, tg)
+    d = len(targets)
+    if out is None:
+        if kind == PTR_DEVICE:
+            torch = _torch()
+            out = torch.empty((n, d), dtype=torch.float32, device=row_ptr.device)
+        else:
+            out = np.zeros((n, d), np.float32)
+    ob = _as_buffer(out, np.float32)
+    if ob[1] != kind:
+        raise ValueError("out must live where the inputs live")
+    s = None if stream is None else ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+    st = lib().tsgne_shortest_path_embedding(n, rp[0], ci[0], tg[0], d, int(l0), ob[0], kind, s)
+    if st != 0:
+        raise TsgneError(st, "tsgne_shortest_path_embedding failed")
+    return out
+
+
+def tsgne_build_P_shortest_path(ctx, n, row_ptr, col_idx, targets, l0: int = 0):
+    rp = _as_buffer(row_ptr, np.int64)
+    ci = _as_buffer(col_idx, np.int32)
+    tg = _as_buffer(targets, np.int32)
+    kind = _same_kind(rp, ci, tg)
+    _check(ctx, lib().tsgne_build_P_shortest_path(ctx, int(n), rp[0], ci[0], tg[0], len(targets), int(l0), kind))
 
 
 def tsgne_set_P(ctx, n, row_ptr, col_idx, P):
@@ -426,6 +463,11 @@ class Layout:
     def build_P(self, row_ptr, col, X):
         self._order_after_torch()
         tsgne_build_P(self.ctx, len(row_ptr) - 1, row_ptr, col, X)
+
+    def build_P_shortest_path(self, row_ptr, col, targets, l0: int = 0):
+        """The paper's pipeline: ShortestPath embedding (Eq. 8) then P."""
+        self._order_after_torch()
+        tsgne_build_P_shortest_path(self.ctx, len(row_ptr) - 1, row_ptr, col, targets, l0)
 
     def set_P(self, row_ptr, col, P):
         self._order_after_torch()

@@ -483,6 +483,28 @@ tsgne_status tsgne_build_P(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, co
   return TSGNE_OK;
 }
 
+tsgne_status tsgne_build_P_shortest_path(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                         const int32_t* targets, int32_t d, int32_t l0, int32_t ptr_kind) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (n < 2 || d < 1 || d > 1024 || !row_ptr || !targets || !valid_kind(ptr_kind))
+    return fail(ctx, TSGNE_ERR_INVALID_ARG, "need n >= 2, 1 <= d <= 1024, row_ptr, targets, a valid ptr_kind");
+  int64_t first = 0, m = 0;
+  API_TRY(ctx, read_ends(row_ptr, n, ptr_kind, ctx->stream, &first, &m));
+  if (first != 0 || m < 0) return fail(ctx, TSGNE_ERR_BAD_CSR, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+  DevBuf<int64_t> rp_in;
+  DevBuf<int32_t> col_in, tg;
+  DevBuf<float> X;
+  API_TRY(ctx, to_device(row_ptr, (size_t)n + 1, ptr_kind, rp_in, ctx->stream));
+  API_TRY(ctx, to_device(col_idx, (size_t)m, ptr_kind, col_in, ctx->stream));
+  API_TRY(ctx, to_device(targets, (size_t)d, ptr_kind, tg, ctx->stream));
+  API_TRY(ctx, X.alloc((size_t)n * d));
+  const tsgne_status st = tsgne_shortest_path_embedding(n, rp_in.get(), col_in.get(), tg.get(), d, l0, X.get(),
+                                                        TSGNE_PTR_DEVICE, ctx->stream);
+  if (st != TSGNE_OK) return fail(ctx, st, last_msg().empty() ? "ShortestPath embedding failed" : last_msg());
+  return tsgne_build_P(ctx, n, rp_in.get(), col_in.get(), X.get(), d, TSGNE_PTR_DEVICE);
+}
+
 tsgne_status tsgne_set_P(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* Pv,
                          int32_t ptr_kind) {
   TS_TRY(enter(ctx));

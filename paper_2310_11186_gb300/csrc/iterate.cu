@@ -1,9 +1,10 @@
 // Per-iteration kernels other than the repulsion.
 //
 // k_attract (S3 + S5 fused): G lanes per row i gather the row's neighbours
-//   (float2 loads of Y, int32 columns, FP32 P):
+//   (float2 loads of Y, int32 columns, FP32 P) into shared memory, then one
+//   thread per row applies the update:
 //     F^a_i = sum_{j in N(i)} p_ij w_ij (y_i - y_j),  w = (1 + ||y_i-y_j||^2)^-1,
-//   add the repulsion partials of the row in a fixed chunk order, and form the
+//   add the repulsion forces of the row (chunk order), and form the
 //   gradient of Eq. 5 with P scaled by alpha (early exaggeration):
 //     g_i = 4 (alpha F^a_i - F^r_i / Z).
 //   In update mode lane 0 then applies the optimiser (the paper gives none;
@@ -30,6 +31,10 @@ namespace {
 constexpr int kAttrCta = 256;
 constexpr int kG = 8;  // lanes per row
 
+// Two phases per CTA of kAttrCta rows: (1) groups of G lanes gather the
+// attraction of the CTA's rows into shared memory; (2) one thread per row
+// reads F^r, the optimiser state and Y_i and writes the update, so the state
+// traffic is fully coalesced.
 template <int G, bool EXPORT>
 __global__ void __launch_bounds__(kAttrCta)
     k_attract(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ P,
@@ -37,43 +42,48 @@ __global__ void __launch_bounds__(kAttrCta)
               float2* __restrict__ gains, const float2* __restrict__ frep_part, int chunks, int n_pad,
               Sched* sched, float eta, float min_gain, float alpha_export, float2* __restrict__ g_out,
               const int32_t* __restrict__ heavy_rows, int heavy_count, const float2* __restrict__ heavy_fa) {
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = gt / G;
-  const int lane = (int)(gt % G);
-  const bool valid = i < n;
-  float ax = 0.f, ay = 0.f, rx = 0.f, ry = 0.f;
-  float2 yi = make_float2(0.f, 0.f);
-  if (valid) {
-    yi = Ycur[i];
-    if (rp[i + 1] - rp[i] > kHeavyDeg) {
-      if (lane == 0) {  // precomputed by k_attract_heavy; rows are sorted
-        int lo = 0, hi = heavy_count - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (heavy_rows[mid] < i) lo = mid + 1; else hi = mid;
+  constexpr int NGRP = kAttrCta / G;
+  __shared__ float2 sfa[kAttrCta];
+  const int64_t row0 = (int64_t)blockIdx.x * kAttrCta;
+  const int grp = threadIdx.x / G, lane = threadIdx.x % G;
+  for (int r = grp; r < kAttrCta; r += NGRP) {
+    const int64_t i = row0 + r;
+    float ax = 0.f, ay = 0.f;
+    if (i < n) {
+      if (rp[i + 1] - rp[i] > kHeavyDeg) {
+        if (lane == 0) {  // precomputed by k_attract_heavy; rows are sorted
+          int lo = 0, hi = heavy_count - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (heavy_rows[mid] < i) lo = mid + 1; else hi = mid;
+          }
+          const float2 f = heavy_fa[lo];
+          ax = f.x;
+          ay = f.y;
         }
-        const float2 f = heavy_fa[lo];
-        ax = f.x;
-        ay = f.y;
+      } else {
+        attract_row<G>(rp, col, P, Ycur, i, lane, Ycur[i], ax, ay);
       }
-    } else {
-      attract_row<G>(rp, col, P, Ycur, i, lane, yi, ax, ay);
     }
-    for (int c = lane; c < chunks; c += G) {
-      const float2 f = frep_part[(size_t)c * n_pad + i];
-      rx += f.x;
-      ry += f.y;
-    }
+    ax = group_sum<G>(ax);
+    ay = group_sum<G>(ay);
+    if (lane == 0) sfa[r] = make_float2(ax, ay);
   }
-  ax = group_sum<G>(ax);
-  ay = group_sum<G>(ay);
-  rx = group_sum<G>(rx);
-  ry = group_sum<G>(ry);
-  if (!valid || lane != 0) return;
+  __syncthreads();
+  const int64_t i = row0 + threadIdx.x;
+  if (i >= n) return;
+  const float2 fa = sfa[threadIdx.x];
+  const float2 yi = Ycur[i];
+  float rx = 0.f, ry = 0.f;
+  for (int c = 0; c < chunks; ++c) {
+    const float2 f = frep_part[(size_t)c * n_pad + i];
+    rx += f.x;
+    ry += f.y;
+  }
   const float invZ = (float)(1.0 / sched->Z);
   const float alpha = EXPORT ? alpha_export : sched->alpha;
-  const float gx = 4.0f * (alpha * ax - rx * invZ);
-  const float gy = 4.0f * (alpha * ay - ry * invZ);
+  const float gx = 4.0f * (alpha * fa.x - rx * invZ);
+  const float gy = 4.0f * (alpha * fa.y - ry * invZ);
   if (EXPORT) {
     g_out[i] = make_float2(gx, gy);
     return;
@@ -232,7 +242,7 @@ tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col,
   if (hv.count > 0) {
     k_attract_heavy<<<hv.count < 4096 ? hv.count : 4096, 256, 0, s>>>(hv.rows, hv.count, rp, col, P, Ycur, hv.fa);
   }
-  const int grid = grid_rows((int64_t)n * kG, kAttrCta);
+  const int grid = grid_rows(n, kAttrCta);
   k_attract<kG, false><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Ycur, Ynext, upd, gains, frep_part, chunks, n_pad,
                                                  sched, eta, min_gain, 0.f, nullptr, hv.rows, hv.count, hv.fa);
   TS_CUDA(cudaGetLastError());
@@ -245,7 +255,7 @@ tsgne_status launch_gradient(int n, const int64_t* rp, const int32_t* col, const
   if (hv.count > 0) {
     k_attract_heavy<<<hv.count < 4096 ? hv.count : 4096, 256, 0, s>>>(hv.rows, hv.count, rp, col, P, Y, hv.fa);
   }
-  const int grid = grid_rows((int64_t)n * kG, kAttrCta);
+  const int grid = grid_rows(n, kAttrCta);
   k_attract<kG, true><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Y, nullptr, nullptr, nullptr, frep_part, chunks,
                                                 n_pad, const_cast<Sched*>(sched), 0.f, 0.f, alpha, g, hv.rows,
                                                 hv.count, hv.fa);

@@ -114,6 +114,12 @@ tsgne_status build_affinities(int n, const int64_t* rp, const int32_t* col, cons
                               const float* X, int d, float perplexity, float tol, int max_iter, float* P,
                               Sched* sched, cudaStream_t s);
 
+// ------------------------------------------------------ ShortestPath GE
+// X (device, n x d float) = BFS distances to the d targets on the symmetric
+// structure (rp, col) with nnz entries, capped at l0 + 1 (l0 <= 0: floor(sqrt(nnz/2))).
+tsgne_status shortest_path_embedding(int n, const int64_t* rp, const int32_t* col, int64_t nnz,
+                                     const int32_t* targets, int d, int l0, float* X, cudaStream_t s);
+
 // ------------------------------------------------------------ repulsion
 RepShape repulsion_shape(int n, int sm_count);
 size_t repulsion_zpart_count(const RepShape& sh);

@@ -385,3 +385,31 @@ def test_optimizer_schedule_switches_at_ee_iters():
 def test_auto_learning_rate():
     assert oracle.auto_learning_rate(2000, 12.0) == 50.0
     assert oracle.auto_learning_rate(300000, 12.0) == 6250.0
+
+
+# -------------------------------------------------------- ShortestPath (Eq. 8)
+
+
+def test_shortest_path_on_a_path_graph():
+    """Path 0-1-...-9: the distance to target t is |i - t|, capped at l0 + 1."""
+    n = 10
+    rp, col = synth.csr_from_edges(n, np.arange(n - 1), np.arange(1, n))
+    X = oracle.shortest_path_embedding(n, rp, col, [0, 4, 9], l0=5)
+    i = np.arange(n)[:, None]
+    want = np.abs(i - np.array([0, 4, 9])[None, :]).astype(float)
+    want[want > 5] = 6
+    assert np.array_equal(X, want)
+
+
+def test_shortest_path_against_scipy_and_unreachable():
+    sp = pytest.importorskip("scipy.sparse.csgraph")
+    sps = pytest.importorskip("scipy.sparse")
+    g = synth.random_graph(300, 2.5, seed=4)  # sparse: several components
+    A = sps.csr_matrix((np.ones(g.col.size), g.col, g.row_ptr), shape=(g.n, g.n))
+    targets = np.array([3, 50, 120, 299], np.int32)
+    D = sp.shortest_path(A, unweighted=True, indices=targets).T
+    l0 = oracle.default_l0(g.m // 2)
+    want = np.where(np.isfinite(D) & (D <= l0), D, l0 + 1)
+    X = oracle.shortest_path_embedding(g.n, g.row_ptr, g.col, targets, l0)
+    assert np.array_equal(X, want)
+    assert (X == l0 + 1).any()  # some nodes are unreachable or farther than l0
