@@ -550,10 +550,6 @@ def bench_rmat(args, pkg, log_fn=log):
                     "embedding of 64 recursion communities, perplexity 30",
         "nnz_P": int(nnz),
         "build_ms": build_ms,
-        "shortest_path_embedding": {"ms": sp_s * 1e3, "targets": 128,
-                                    "note": "host CSR in, 300000 x 128 distances back to the host"},
-        "paper_pipeline_s": {"shortest_path_plus_tsgne": sp_s + e2e_s, "iters": e2e_iters,
-                             "paper": "under 5 min (4:57) on a 32-core Xeon Gold 6338, Table 2"},
         "repulsion_ms": rep_ms,
         "attraction_roofline": {"bound": "hbm", "kernel": "attract_update (S3+S5)", "achieved": achieved,
                                 "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
