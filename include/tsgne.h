@@ -188,8 +188,8 @@ tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update
  * Profiling (cfg.profile = 1): cumulative device time in ms and launch count
  * of each kernel class since the last reset, measured with CUDA events on
  * the context's stream.  Classes: 0 repulsion, 1 attraction+update,
- * 2 gradient export, 3 KL, 4 build, 5 repulsion slot reduction.  ms and
- * launches hold n entries (n <= 6).
+ * 2 gradient export, 3 KL, 4 build, 5 repulsion slot reduction, 6 hub-row
+ * attraction chunks.  ms and launches hold n entries (n <= 7).
  * reset != 0 clears the counters after reading.  Synchronises.
  */
 tsgne_status tsgne_kernel_times(tsgne_ctx* ctx, double* ms, int64_t* launches, int32_t n, int32_t reset);

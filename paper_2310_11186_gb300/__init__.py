@@ -59,7 +59,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_PKG, "lib", "libtsgne.so")
 
 PTR_HOST, PTR_DEVICE = 0, 1
-KERNEL_CLASSES = ("repulsion", "attract_update", "gradient", "kl", "build", "reduce_slots")
+KERNEL_CLASSES = ("repulsion", "attract_update", "gradient", "kl", "build", "reduce_slots", "attract_hubs")
 
 STATUS = {
     0: "TSGNE_OK",

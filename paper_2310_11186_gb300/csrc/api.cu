@@ -38,7 +38,7 @@ __global__ void k_cmp_i32(const int32_t* a, const int32_t* b, int64_t n, uint32_
     if (a[k] != b[k]) atomicOr(neq, 1u);
 }
 
-constexpr int kClasses = 6;  // repulsion, attraction+update, gradient, KL, build, slot reduction
+constexpr int kClasses = 7;  // repulsion, attraction+update, gradient, KL, build, slot reduction, hub rows
 
 struct ProfRec {
   int cls;
@@ -72,16 +72,8 @@ struct tsgne_ctx {
   DevBuf<float2> Y[2];
   int cur = 0;
   DevBuf<float2> upd, gains, frep, fsum, grad;
-  DevBuf<int32_t> heavy_rows;
-  DevBuf<float2> heavy_fa;
-  int heavy_count = 0;
-  HeavyRows heavy() const {
-    HeavyRows h;
-    h.rows = heavy_rows.get();
-    h.fa = heavy_fa.get();
-    h.count = heavy_count;
-    return h;
-  }
+  HeavyStore hub;
+  HeavyRows heavy() const { return hub.view(); }
   DevBuf<double> zpart, klpart;
   DevBuf<Sched> sched;
 
@@ -89,8 +81,8 @@ struct tsgne_ctx {
 
   std::vector<ProfRec> pending;
   std::vector<cudaEvent_t> spare;
-  double prof_ms[kClasses] = {0, 0, 0, 0, 0, 0};
-  int64_t prof_n[kClasses] = {0, 0, 0, 0, 0, 0};
+  double prof_ms[kClasses] = {0, 0, 0, 0, 0, 0, 0};
+  int64_t prof_n[kClasses] = {0, 0, 0, 0, 0, 0, 0};
 
   ~tsgne_ctx() {
     reset_graphs();
@@ -240,6 +232,13 @@ tsgne_status enqueue_repulsion(tsgne_ctx* ctx, int advance) {
 tsgne_status enqueue_step(tsgne_ctx* ctx) {
   TS_TRY(enqueue_repulsion(ctx, 1));
   ProfRec pr;
+  if (ctx->hub.chunks > 0) {
+    ProfRec ph;
+    TS_TRY(prof_begin(ctx, 6, &ph));
+    TS_TRY(launch_attract_heavy(ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(), ctx->heavy(),
+                                ctx->stream));
+    TS_TRY(prof_end(ctx, &ph));
+  }
   TS_TRY(prof_begin(ctx, 1, &pr));
   const int nxt = ctx->cur ^ 1;
   TS_TRY(launch_attract_update(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
@@ -325,7 +324,7 @@ tsgne_status install(tsgne_ctx* ctx, int n, int64_t nnz, DevBuf<int64_t>& rp, De
   ctx->col = std::move(col);
   ctx->P = std::move(P);
   TS_TRY(alloc_layout(ctx));
-  TS_TRY(find_heavy_rows(n, ctx->rp.get(), ctx->heavy_rows, ctx->heavy_fa, &ctx->heavy_count, ctx->stream));
+  TS_TRY(find_heavy_rows(n, ctx->rp.get(), ctx->hub, ctx->stream));
   ctx->have_P = true;
   return TSGNE_OK;
 }
@@ -690,7 +689,7 @@ tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update
 tsgne_status tsgne_kernel_times(tsgne_ctx* ctx, double* ms, int64_t* launches, int32_t n, int32_t reset) {
   TS_TRY(enter(ctx));
   DeviceGuard dg(ctx->device);
-  if (n < 0 || n > kClasses) return fail(ctx, TSGNE_ERR_INVALID_ARG, "n outside [0, 6]");
+  if (n < 0 || n > kClasses) return fail(ctx, TSGNE_ERR_INVALID_ARG, "n outside [0, 7]");
   API_TRY(ctx, prof_collect(ctx));
   for (int k = 0; k < n; ++k) {
     if (ms) ms[k] = ctx->prof_ms[k];

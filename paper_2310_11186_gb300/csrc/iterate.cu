@@ -19,6 +19,7 @@
 //   fixed-order totals; KL = first + second * ln Z on the host (Eq. 5 with
 //   q = w / Z).
 #include <cmath>
+#include <vector>
 
 #include "reduce.cuh"
 #include "row_update.cuh"
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(kAttrCta)
               const float2* __restrict__ Ycur, float2* __restrict__ Ynext, float2* __restrict__ upd,
               float2* __restrict__ gains, const float2* __restrict__ frep_part, int chunks, int n_pad,
               Sched* sched, float eta, float min_gain, float alpha_export, float2* __restrict__ g_out,
-              const int32_t* __restrict__ heavy_rows, int heavy_count, const float2* __restrict__ heavy_fa) {
+              HeavyRows hv) {
   constexpr int NGRP = kAttrCta / G;
   __shared__ float2 sfa[kAttrCta];
   const int64_t row0 = (int64_t)blockIdx.x * kAttrCta;
@@ -51,15 +52,17 @@ __global__ void __launch_bounds__(kAttrCta)
     float ax = 0.f, ay = 0.f;
     if (i < n) {
       if (rp[i + 1] - rp[i] > kHeavyDeg) {
-        if (lane == 0) {  // precomputed by k_attract_heavy; rows are sorted
-          int lo = 0, hi = heavy_count - 1;
+        if (lane == 0) {  // chunk sums from k_attract_heavy, in chunk order
+          int lo = 0, hi = hv.count - 1;
           while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (heavy_rows[mid] < i) lo = mid + 1; else hi = mid;
+            if (hv.rows[mid] < i) lo = mid + 1; else hi = mid;
           }
-          const float2 f = heavy_fa[lo];
-          ax = f.x;
-          ay = f.y;
+          for (int c = hv.chunk_off[lo]; c < hv.chunk_off[lo + 1]; ++c) {
+            const float2 f = hv.fa[c];
+            ax += f.x;
+            ay += f.y;
+          }
         }
       } else {
         attract_row<G>(rp, col, P, Ycur, i, lane, Ycur[i], ax, ay);
@@ -97,19 +100,27 @@ __global__ void __launch_bounds__(kAttrCta)
   if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&sched->flags, kFlagNonfiniteY);
 }
 
-// Attraction of the rows with more than kHeavyDeg entries (hubs of
-// power-law graphs), one CTA per row with a fixed-order block reduction, so
-// that the 8-lane groups of k_attract never serialise on a hub row.
+// Attraction of the hub rows (more than kHeavyDeg entries), in chunks of at
+// most kHeavyChunk entries: one CTA per chunk, fixed-order block reduction,
+// so no group of lanes serialises on a hub and no CTA on a whole hub.
 __global__ void __launch_bounds__(256)
-    k_attract_heavy(const int32_t* __restrict__ rows, int count, const int64_t* __restrict__ rp,
-                    const int32_t* __restrict__ col, const float* __restrict__ P, const float2* __restrict__ Y,
-                    float2* __restrict__ fa) {
+    k_attract_heavy(HeavyRows hv, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                    const float* __restrict__ P, const float2* __restrict__ Y) {
   __shared__ float sx[256], sy[256];
-  for (int k = blockIdx.x; k < count; k += gridDim.x) {
-    const int64_t i = rows[k];
+  for (int c = blockIdx.x; c < hv.chunks; c += gridDim.x) {
+    const int64_t i = hv.chunk_row[c];
     const float2 yi = Y[i];
     float ax = 0.f, ay = 0.f;
-    attract_row<256>(rp, col, P, Y, i, threadIdx.x, yi, ax, ay);
+    for (int64_t e = hv.chunk_begin[c] + threadIdx.x; e < hv.chunk_end[c]; e += 256) {
+      const int32_t j = col[e];
+      const float p = P[e];
+      const float2 yj = Y[j];
+      const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+      const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
+      const float pw = p * w;
+      ax = fmaf(pw, dx, ax);
+      ay = fmaf(pw, dy, ay);
+    }
     sx[threadIdx.x] = ax;
     sy[threadIdx.x] = ay;
     __syncthreads();
@@ -120,8 +131,16 @@ __global__ void __launch_bounds__(256)
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) fa[k] = make_float2(sx[0], sy[0]);
+    if (threadIdx.x == 0) hv.fa[c] = make_float2(sx[0], sy[0]);
     __syncthreads();
+  }
+}
+
+__global__ void k_heavy_bounds(int H, const int32_t* __restrict__ rows, const int64_t* __restrict__ rp,
+                               int64_t* __restrict__ bounds) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H; k += gridDim.x * blockDim.x) {
+    bounds[k] = rp[rows[k]];
+    bounds[H + k] = rp[rows[k] + 1];
   }
 }
 
@@ -239,12 +258,9 @@ tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col,
                                    float2* Ynext, float2* upd, float2* gains, const float2* frep_part, int chunks,
                                    int n_pad, Sched* sched, float eta, float min_gain, const HeavyRows& hv,
                                    cudaStream_t s) {
-  if (hv.count > 0) {
-    k_attract_heavy<<<hv.count < 4096 ? hv.count : 4096, 256, 0, s>>>(hv.rows, hv.count, rp, col, P, Ycur, hv.fa);
-  }
   const int grid = grid_rows(n, kAttrCta);
   k_attract<kG, false><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Ycur, Ynext, upd, gains, frep_part, chunks, n_pad,
-                                                 sched, eta, min_gain, 0.f, nullptr, hv.rows, hv.count, hv.fa);
+                                                 sched, eta, min_gain, 0.f, nullptr, hv);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }
@@ -252,19 +268,23 @@ tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col,
 tsgne_status launch_gradient(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
                              const float2* frep_part, int chunks, int n_pad, const Sched* sched, float alpha,
                              const HeavyRows& hv, float2* g, cudaStream_t s) {
-  if (hv.count > 0) {
-    k_attract_heavy<<<hv.count < 4096 ? hv.count : 4096, 256, 0, s>>>(hv.rows, hv.count, rp, col, P, Y, hv.fa);
-  }
+  TS_TRY(launch_attract_heavy(rp, col, P, Y, hv, s));
   const int grid = grid_rows(n, kAttrCta);
   k_attract<kG, true><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Y, nullptr, nullptr, nullptr, frep_part, chunks,
-                                                n_pad, const_cast<Sched*>(sched), 0.f, 0.f, alpha, g, hv.rows,
-                                                hv.count, hv.fa);
+                                                n_pad, const_cast<Sched*>(sched), 0.f, 0.f, alpha, g, hv);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }
 
-tsgne_status find_heavy_rows(int n, const int64_t* rp, DevBuf<int32_t>& rows, DevBuf<float2>& fa, int* count,
-                             cudaStream_t s) {
+tsgne_status launch_attract_heavy(const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
+                                  const HeavyRows& hv, cudaStream_t s) {
+  if (hv.chunks <= 0) return TSGNE_OK;
+  k_attract_heavy<<<hv.chunks < 8192 ? hv.chunks : 8192, 256, 0, s>>>(hv, rp, col, P, Y);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+tsgne_status find_heavy_rows(int n, const int64_t* rp, HeavyStore& hs, cudaStream_t s) {
   DevBuf<int32_t> flag;
   DevBuf<int64_t> pos, scr;
   TS_TRY(flag.alloc((size_t)n));
@@ -276,11 +296,47 @@ tsgne_status find_heavy_rows(int n, const int64_t* rp, DevBuf<int32_t>& rows, De
   int64_t total = 0;
   TS_CUDA(cudaMemcpyAsync(&total, pos.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   TS_CUDA(cudaStreamSynchronize(s));
-  *count = (int)total;
-  TS_TRY(rows.alloc((size_t)(total > 0 ? total : 1)));
-  TS_TRY(fa.alloc((size_t)(total > 0 ? total : 1)));
-  if (total > 0) k_heavy_scatter<<<g, 256, 0, s>>>(n, flag.get(), pos.get(), rows.get());
+  const int H = (int)total;
+  hs.count = H;
+  TS_TRY(hs.rows.alloc((size_t)(H > 0 ? H : 1)));
+  if (H > 0) k_heavy_scatter<<<g, 256, 0, s>>>(n, flag.get(), pos.get(), hs.rows.get());
   TS_CUDA(cudaGetLastError());
+  // chunk lists on the host (the hub rows are few)
+  std::vector<int32_t> rows(H > 0 ? H : 1);
+  std::vector<int64_t> b(H > 0 ? H : 1), e(H > 0 ? H : 1);
+  if (H > 0) {
+    DevBuf<int64_t> bounds;
+    TS_TRY(bounds.alloc(2 * (size_t)H));
+    k_heavy_bounds<<<(H + 255) / 256, 256, 0, s>>>(H, hs.rows.get(), rp, bounds.get());
+    TS_CUDA(cudaGetLastError());
+    TS_CUDA(cudaMemcpyAsync(rows.data(), hs.rows.get(), sizeof(int32_t) * H, cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaMemcpyAsync(b.data(), bounds.get(), sizeof(int64_t) * H, cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaMemcpyAsync(e.data(), bounds.get() + H, sizeof(int64_t) * H, cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaStreamSynchronize(s));
+  }
+  std::vector<int32_t> off(1, 0), crow;
+  std::vector<int64_t> cb, ce;
+  for (int k = 0; k < H; ++k) {
+    for (int64_t x = b[k]; x < e[k]; x += kHeavyChunk) {
+      crow.push_back(rows[k]);
+      cb.push_back(x);
+      ce.push_back(x + kHeavyChunk < e[k] ? x + kHeavyChunk : e[k]);
+    }
+    off.push_back((int32_t)crow.size());
+  }
+  const int C = (int)crow.size();
+  hs.chunks = C;
+  TS_TRY(hs.chunk_off.alloc(off.size()));
+  TS_TRY(hs.chunk_row.alloc((size_t)(C > 0 ? C : 1)));
+  TS_TRY(hs.chunk_begin.alloc((size_t)(C > 0 ? C : 1)));
+  TS_TRY(hs.chunk_end.alloc((size_t)(C > 0 ? C : 1)));
+  TS_TRY(hs.fa.alloc((size_t)(C > 0 ? C : 1)));
+  TS_CUDA(cudaMemcpyAsync(hs.chunk_off.get(), off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, s));
+  if (C > 0) {
+    TS_CUDA(cudaMemcpyAsync(hs.chunk_row.get(), crow.data(), sizeof(int32_t) * C, cudaMemcpyHostToDevice, s));
+    TS_CUDA(cudaMemcpyAsync(hs.chunk_begin.get(), cb.data(), sizeof(int64_t) * C, cudaMemcpyHostToDevice, s));
+    TS_CUDA(cudaMemcpyAsync(hs.chunk_end.get(), ce.data(), sizeof(int64_t) * C, cudaMemcpyHostToDevice, s));
+  }
   TS_CUDA(cudaStreamSynchronize(s));
   return TSGNE_OK;
 }

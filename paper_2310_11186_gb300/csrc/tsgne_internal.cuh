@@ -140,16 +140,44 @@ tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const float2* Y, fl
                                   cudaStream_t s);
 
 // ------------------------------------------------------------ iteration
-// Rows with more than kHeavyDeg entries get their attraction from a CTA of
-// their own (k_attract_heavy); rows[] is sorted, fa[] holds their sums.
+// Rows with more than kHeavyDeg entries get their attraction from chunks of
+// kHeavyChunk entries, one CTA per chunk (k_attract_heavy); the update adds a
+// row's chunk sums in chunk order.  rows[] is sorted; chunks of heavy row k
+// are chunk_off[k] .. chunk_off[k+1]-1.
 constexpr int kHeavyDeg = 256;
+constexpr int kHeavyChunk = 2048;
 struct HeavyRows {
-  const int32_t* rows = nullptr;
-  float2* fa = nullptr;
+  const int32_t* rows = nullptr;       // [count] sorted row ids
+  const int32_t* chunk_off = nullptr;  // [count + 1]
+  const int32_t* chunk_row = nullptr;  // [chunks]
+  const int64_t* chunk_begin = nullptr;  // [chunks] first entry
+  const int64_t* chunk_end = nullptr;    // [chunks] one past the last entry
+  float2* fa = nullptr;                // [chunks] partial sums
   int count = 0;
+  int chunks = 0;
 };
-tsgne_status find_heavy_rows(int n, const int64_t* rp, DevBuf<int32_t>& rows, DevBuf<float2>& fa, int* count,
-                             cudaStream_t s);
+struct HeavyStore {
+  DevBuf<int32_t> rows, chunk_off, chunk_row;
+  DevBuf<int64_t> chunk_begin, chunk_end;
+  DevBuf<float2> fa;
+  int count = 0, chunks = 0;
+  HeavyRows view() const {
+    HeavyRows h;
+    h.rows = rows.get();
+    h.chunk_off = chunk_off.get();
+    h.chunk_row = chunk_row.get();
+    h.chunk_begin = chunk_begin.get();
+    h.chunk_end = chunk_end.get();
+    h.fa = fa.get();
+    h.count = count;
+    h.chunks = chunks;
+    return h;
+  }
+};
+tsgne_status find_heavy_rows(int n, const int64_t* rp, HeavyStore& hs, cudaStream_t s);
+// The hub-row chunks alone (the update kernel then reads their sums).
+tsgne_status launch_attract_heavy(const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
+                                  const HeavyRows& hv, cudaStream_t s);
 // F^r[i] = sum_k part[k * n_pad + i] for k < slots, in slot order.
 tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad, float2* out, cudaStream_t s);
 // Attraction + gradient + optimiser update: reads Ycur, writes Ynext.
