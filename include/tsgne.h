@@ -67,7 +67,9 @@ typedef enum { TSGNE_PTR_HOST = 0, TSGNE_PTR_DEVICE = 1 } tsgne_ptr_kind;
  */
 typedef struct {
   float perplexity;        /* target Perp(P_i) = 2^{H(P_i)} (Sec. 2.1); > 1 */
-  int32_t k_nn;            /* 0: neighbours = graph edges (the only value accepted) */
+  int32_t k_nn;            /* 0: neighbours = graph edges; 1..256: the first k_nn nodes in
+                              breadth-first order from each node (Eq. 7), ties by ascending
+                              id, symmetrised by union */
   float early_exag;        /* alpha multiplying P in the gradient while t < ee_iters */
   int32_t ee_iters;        /* length of the early-exaggeration phase */
   float momentum0;         /* momentum while t < ee_iters */
@@ -104,9 +106,11 @@ const char* tsgne_status_string(tsgne_status s);
 /*
  * Builds the joint affinities P from a graph and its high-dimensional
  * embedding (the t-SGNE input pair (G, X), Sec. 2.2):
- *   1. neighbour structure N(i) = { j != i : (i,j) or (j,i) in G } (Eq. 7
- *      with the graph's edges as neighbours): symmetric, sorted, unique,
- *      no self loops;
+ *   1. neighbour structure (Eq. 7): with cfg.k_nn = 0, N(i) = { j != i :
+ *      (i,j) or (j,i) in G }; with k_nn = k > 0, the first k nodes of the
+ *      breadth-first order from i on that graph (levels in order, each node's
+ *      neighbours by ascending id), symmetrised by union; either way
+ *      symmetric, sorted, unique, no self loops;
  *   2. p_{j|i} = exp(-beta_i ||x_i-x_j||^2) / sum_{k in N(i)} exp(...) (Eq. 2
  *      over N(i)), beta_i by bisection until |H_i - ln perplexity| <=
  *      bisect_tol (Sec. 2.1); rows with |N(i)| <= perplexity are uniform;

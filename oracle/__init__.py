@@ -78,6 +78,8 @@ def _load():
             lib.tsgo_optimize.restype = ctypes.c_int
             lib.tsgo_shortest_path.argtypes = [_i32, _p, _p, _p, _i32, _i32, _p]
             lib.tsgo_shortest_path.restype = ctypes.c_int
+            lib.tsgo_bfs_knn.argtypes = [_i32, _p, _p, _i32, _p, _p]
+            lib.tsgo_bfs_knn.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -263,3 +265,25 @@ def shortest_path_embedding(n, rp, col, targets, l0):
     _check(_load().tsgo_shortest_path(n, _ptr(rp), _ptr(col if col.size else np.zeros(1, np.int32)), _ptr(tg),
                                       tg.size, int(l0), _ptr(X)), "shortest_path")
     return X
+
+
+def bfs_knn(n, rp, col, k):
+    """BFS k-nearest lists (Eq. 7) on a sorted structure: (out n x k, cnt n)."""
+    rp, col = _c(rp, np.int64), _c(col, np.int32)
+    out = np.full((n, k), -1, np.int32)
+    cnt = np.zeros(n, np.int32)
+    _check(_load().tsgo_bfs_knn(n, _ptr(rp), _ptr(col if col.size else np.zeros(1, np.int32)), int(k), _ptr(out),
+                                _ptr(cnt)), "bfs_knn")
+    return out, cnt
+
+
+def knn_structure(n, row_ptr, col, k):
+    """Neighbour structure with k_nn = k: BFS lists of the graph's structure,
+    symmetrised by union (Eq. 7 read with k nodes per list)."""
+    srp, scol = structure(n, row_ptr, col)
+    out, cnt = bfs_knn(n, srp, scol, k)
+    rows = np.repeat(np.arange(n), cnt)
+    lists = np.concatenate([out[i, :cnt[i]] for i in range(n)]) if n else np.zeros(0, np.int32)
+    krp = np.zeros(n + 1, np.int64)
+    krp[1:] = np.cumsum(cnt)
+    return structure(n, krp, lists.astype(np.int32))

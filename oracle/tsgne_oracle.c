@@ -26,6 +26,8 @@
  *                       published t-SNE defaults are used)
  *   tsgo_shortest_path  ShortestPath graph embedding (Sec. 2.3, Eq. 8): BFS
  *                       distances to d target nodes, capped at l0 + 1
+ *   tsgo_bfs_knn        the k-nearest neighbours of Eq. 7 "by a breadth-first
+ *                       search of k steps" (Sec. 2.2), before symmetrisation
  *
  * Readings of the paper where it is silent (also listed in the design notes):
  *   - N(i) is the set of graph neighbours (k = graph edges), union of both
@@ -412,6 +414,44 @@ int tsgo_shortest_path(int32_t n, const int64_t* rp, const int32_t* col, const i
       X[(int64_t)i * d + t] = (dist[i] >= 0 && dist[i] <= l0) ? (double)dist[i] : (double)(l0 + 1);
   }
   free(dist);
+  free(queue);
+  return TSGO_OK;
+}
+
+/*
+ * k nearest neighbours of every node by breadth-first search on G (Eq. 7,
+ * Sec. 2.2): the first k nodes other than i in BFS order from i, levels in
+ * order, and within a level in order of discovery, each node's neighbours
+ * scanned in ascending id (rows of rp/col must be sorted); fewer when i's
+ * component is smaller.  out is n x k (row i: its list in BFS order), cnt[i]
+ * its length.  The caller symmetrises the lists by union.
+ */
+int tsgo_bfs_knn(int32_t n, const int64_t* rp, const int32_t* col, int32_t k, int32_t* out, int32_t* cnt) {
+  if (n < 1 || k < 1) return TSGO_EINVAL;
+  char* seen = (char*)calloc((size_t)n, 1);
+  int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!seen || !queue) {
+    free(seen); free(queue);
+    return TSGO_ENOMEM;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t head = 0, tail = 0, found = 0;
+    queue[tail++] = i;
+    seen[i] = 1;
+    while (head < tail && found < k) {
+      int32_t v = queue[head++];
+      for (int64_t e = rp[v]; e < rp[v + 1] && found < k; ++e) {
+        int32_t w = col[e];
+        if (seen[w]) continue;
+        seen[w] = 1;
+        queue[tail++] = w;
+        out[(int64_t)i * k + found++] = w;
+      }
+    }
+    cnt[i] = found;
+    for (int32_t t = 0; t < tail; ++t) seen[queue[t]] = 0;
+  }
+  free(seen);
   free(queue);
   return TSGO_OK;
 }

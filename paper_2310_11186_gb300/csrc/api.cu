@@ -393,10 +393,10 @@ tsgne_status tsgne_create(tsgne_ctx** out, const tsgne_config* cfg, void* cuda_s
   *out = nullptr;
   tsgne_config c;
   if (cfg) c = *cfg; else tsgne_config_default(&c);
-  if (!(c.perplexity > 1.f) || c.k_nn != 0 || c.precision != 0 || c.ee_iters < 0 || !(c.min_gain >= 0.f) ||
+  if (!(c.perplexity > 1.f) || c.k_nn < 0 || c.k_nn > 256 || c.precision != 0 || c.ee_iters < 0 || !(c.min_gain >= 0.f) ||
       !(c.bisect_tol > 0.f) || c.bisect_max_iter < 1 || !std::isfinite(c.early_exag) || !std::isfinite(c.momentum0) ||
       !std::isfinite(c.momentum1)) {
-    last_msg() = "invalid configuration (perplexity must exceed 1; k_nn and precision must be 0)";
+    last_msg() = "invalid configuration (perplexity must exceed 1; k_nn in [0, 256]; precision 0)";
     return TSGNE_ERR_INVALID_ARG;
   }
   tsgne_ctx* ctx = new (std::nothrow) tsgne_ctx();
@@ -468,7 +468,7 @@ tsgne_status tsgne_build_P(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, co
   DevBuf<int32_t> col;
   DevBuf<float> P;
   int64_t nnz = 0;
-  API_TRY(ctx, build_structure(n, rp_d, col_d, m, rp, col, tslot, &nnz, ctx->sched.get(), ctx->stream));
+  API_TRY(ctx, build_neighbor_structure(n, rp_d, col_d, m, ctx->cfg.k_nn, rp, col, tslot, &nnz, ctx->stream));
   API_TRY(ctx, P.alloc((size_t)nnz));
   API_CUDA(ctx, cudaMemsetAsync(ctx->sched.get(), 0, sizeof(Sched), ctx->stream));
   API_TRY(ctx, build_affinities(n, rp.get(), col.get(), tslot.get(), nnz, X_d, d, ctx->cfg.perplexity,

@@ -418,7 +418,7 @@ tsgne_status tsgne_batch_create(tsgne_batch** out, const tsgne_config* cfg, int3
   *out = nullptr;
   tsgne_config c;
   if (cfg) c = *cfg; else tsgne_config_default(&c);
-  if (!(c.perplexity > 1.f) || c.k_nn != 0 || c.precision != 0 || c.ee_iters < 0)
+  if (!(c.perplexity > 1.f) || c.k_nn < 0 || c.k_nn > 256 || c.precision != 0 || c.ee_iters < 0)
     return TSGNE_ERR_INVALID_ARG;
   if (!(tile_warps == 0 || tile_warps == 1 || tile_warps == 2 || tile_warps == 4 || tile_warps == 8))
     return TSGNE_ERR_INVALID_ARG;
@@ -490,7 +490,8 @@ tsgne_status tsgne_batch_add(tsgne_batch* b, int32_t n, const int64_t* row_ptr, 
   B_CUDA(b, cudaMemcpyAsync(X_in.get(), X, sizeof(float) * (size_t)n * d, kin, b->stream));
   B_TRY(b, mb.sched.alloc(1));
   B_CUDA(b, cudaMemsetAsync(mb.sched.get(), 0, sizeof(Sched), b->stream));
-  B_TRY(b, build_structure(n, rp_in.get(), col_in.get(), m, mb.rp, mb.col, tslot, &mb.nnz, mb.sched.get(), b->stream));
+  B_TRY(b, build_neighbor_structure(n, rp_in.get(), col_in.get(), m, b->cfg.k_nn, mb.rp, mb.col, tslot, &mb.nnz,
+                                    b->stream));
   B_TRY(b, mb.P.alloc((size_t)mb.nnz));
   B_TRY(b, build_affinities(n, mb.rp.get(), mb.col.get(), tslot.get(), mb.nnz, X_in.get(), d, b->cfg.perplexity,
                             b->cfg.bisect_tol, b->cfg.bisect_max_iter, mb.P.get(), mb.sched.get(), b->stream));

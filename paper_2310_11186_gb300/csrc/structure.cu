@@ -285,6 +285,51 @@ __global__ void k_tslot(int n, const int64_t* __restrict__ rp, const int32_t* __
   }
 }
 
+// k nearest neighbours by breadth-first search on the structure (Eq. 7 with
+// k nodes per list, Sec. 2.2): one warp per source i; its list in shared
+// memory doubles as the BFS queue.  Levels come in order because the queue is
+// processed in order; each node's sorted neighbours are taken 32 at a time,
+// lanes test their candidate against the list (and i), and the fresh ones are
+// appended in lane (= ascending id) order until k are found.
+constexpr int kKnnMax = 256;
+constexpr int kKnnWarps = 8;
+
+__global__ void __launch_bounds__(32 * kKnnWarps)
+    k_bfs_knn(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int k,
+              int32_t* __restrict__ out, int32_t* __restrict__ cnt) {
+  __shared__ int32_t lists[kKnnWarps][kKnnMax];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* L = lists[wid];
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += warps) {
+    int c = 0;
+    for (int head = -1; head < c && c < k; ++head) {
+      const int64_t u = head < 0 ? s : L[head];
+      const int64_t b = rp[u + 1];
+      for (int64_t e0 = rp[u]; e0 < b && c < k; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const int32_t v = e < b ? col[e] : -1;
+        bool fresh = v >= 0 && v != (int32_t)s;
+        for (int t = 0; fresh && t < c; ++t)
+          if (L[t] == v) fresh = false;
+        const unsigned mask = __ballot_sync(0xffffffffu, fresh);
+        const int pos = c + __popc(mask & ((1u << lane) - 1u));
+        if (fresh && pos < k) L[pos] = v;
+        c = min(k, c + __popc(mask));
+        __syncwarp();
+      }
+    }
+    for (int t = lane; t < c; t += 32) out[s * k + t] = L[t];
+    if (lane == 0) cnt[s] = c;
+    __syncwarp();
+  }
+}
+
+__global__ void k_iota_stride(int n, int64_t stride_k, int64_t* __restrict__ off) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+    off[i] = i * stride_k;
+}
+
 int grid_for(int64_t work, int per_cta, int cap) {
   int64_t g = (work + per_cta - 1) / per_cta;
   if (g < 1) g = 1;
@@ -387,6 +432,46 @@ tsgne_status build_structure(int n, const int64_t* rp_in, const int32_t* col_in,
   }
   *nnz_out = nnz;
   return TSGNE_OK;
+}
+
+}  // namespace tsgne
+
+namespace tsgne {
+
+tsgne_status build_neighbor_structure(int n, const int64_t* rp_in, const int32_t* col_in, int64_t m, int k_nn,
+                                      DevBuf<int64_t>& rp_out, DevBuf<int32_t>& col_out, DevBuf<int64_t>& tslot_out,
+                                      int64_t* nnz_out, cudaStream_t s) {
+  if (k_nn <= 0) return build_structure(n, rp_in, col_in, m, rp_out, col_out, tslot_out, nnz_out, nullptr, s);
+  if (k_nn > kKnnMax) {
+    last_msg() = "k_nn above 256";
+    return TSGNE_ERR_INVALID_ARG;
+  }
+  DevBuf<int64_t> rp1, tslot1, off, krp, scr;
+  DevBuf<int32_t> col1, lists, cnt, kcol;
+  int64_t nnz1 = 0;
+  TS_TRY(build_structure(n, rp_in, col_in, m, rp1, col1, tslot1, &nnz1, nullptr, s));
+  tslot1.reset();
+  int dev = 0, sms = 1;
+  TS_CUDA(cudaGetDevice(&dev));
+  TS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  TS_TRY(lists.alloc((size_t)n * k_nn));
+  TS_TRY(cnt.alloc((size_t)n));
+  const int g = grid_for((int64_t)n * 32, 32 * kKnnWarps, sms * 32);
+  k_bfs_knn<<<g, 32 * kKnnWarps, 0, s>>>(n, rp1.get(), col1.get(), k_nn, lists.get(), cnt.get());
+  TS_CUDA(cudaGetLastError());
+  TS_TRY(krp.alloc((size_t)n + 1));
+  TS_TRY(scr.alloc(scan_scratch_bytes(n) / sizeof(int64_t)));
+  TS_TRY(scan_i32_to_i64(cnt.get(), krp.get(), n, scr.get(), s));
+  int64_t total = 0;
+  TS_CUDA(cudaMemcpyAsync(&total, krp.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TS_CUDA(cudaStreamSynchronize(s));
+  TS_TRY(kcol.alloc((size_t)(total > 0 ? total : 1)));
+  TS_TRY(off.alloc((size_t)n + 1));
+  k_iota_stride<<<grid_for((int64_t)n + 1, 256, sms * 8), 256, 0, s>>>(n, k_nn, off.get());
+  k_compact<<<grid_for((int64_t)n * 32, 256, sms * 32), 256, 0, s>>>(n, off.get(), lists.get(), krp.get(), kcol.get());
+  TS_CUDA(cudaGetLastError());
+  lists.reset();
+  return build_structure(n, krp.get(), kcol.get(), total, rp_out, col_out, tslot_out, nnz_out, nullptr, s);
 }
 
 }  // namespace tsgne

@@ -107,6 +107,13 @@ tsgne_status build_structure(int n, const int64_t* rp_in, const int32_t* col_in,
                              DevBuf<int32_t>& col_out, DevBuf<int64_t>& tslot_out, int64_t* nnz_out,
                              Sched* sched, cudaStream_t s);
 
+// Neighbour structure for k_nn: 0 = the graph's edges (build_structure);
+// k > 0 = the first k nodes of each node's BFS order (ties by ascending id),
+// symmetrised by union (Eq. 7 with k nodes per list).  1 <= k <= 256.
+tsgne_status build_neighbor_structure(int n, const int64_t* rp_in, const int32_t* col_in, int64_t m, int k_nn,
+                                      DevBuf<int64_t>& rp_out, DevBuf<int32_t>& col_out, DevBuf<int64_t>& tslot_out,
+                                      int64_t* nnz_out, cudaStream_t s);
+
 // ------------------------------------------------------------- affinity
 // p_{j|i} per entry (Eq. 2 over N(i), bisection of Sec. 2.1) then the joint
 // P of Eq. 3 normalised by the total.  Sets kFlagNonfiniteP on NaN / Inf.

@@ -339,3 +339,24 @@ def test_gradient_parity_with_hub_rows():
             lay.init_Y(Y)
             G, Z = lay.gradient(alpha)
         assert rel_l2(G, oG) < 1e-4, rel_l2(G, oG)
+
+
+@pytest.mark.parametrize("wl,k,perp", [("rand3000", 1, 2.0), ("rand3000", 5, 3.0), ("rand3000", 91, 30.0),
+                                       ("sbm2k", 91, 30.0), ("sbm2k", 256, 30.0)])
+def test_knn_neighbours_match_oracle(wl, k, perp):
+    """k_nn > 0: BFS-k lists (Eq. 7) symmetrised by union; structure bit-exact,
+    P within 1e-5 (at k = 91, perplexity 30 every row bisects)."""
+    if wl == "sbm2k":
+        g, X = synth.workload("sbm2k")
+    else:
+        g = synth.random_graph(3000, 6.0, seed=k)
+        X = np.random.default_rng(k).normal(size=(3000, 12)).astype(np.float32)
+    with pkg.Layout(perplexity=perp, k_nn=k) as lay:
+        lay.build_P(g.row_ptr, g.col, X)
+        rp, col, P = lay.get_P()
+    orp, ocol = oracle.knn_structure(g.n, g.row_ptr, g.col, k)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    pc, _, _ = oracle.cond_affinity(g.n, orp, ocol, X, perp)
+    oP, _ = oracle.joint_P(g.n, orp, ocol, pc)
+    tol = 1e-5 * oP + 1e-9 * oP.max()
+    assert not (np.abs(P - oP) > tol).any()

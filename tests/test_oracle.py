@@ -413,3 +413,58 @@ def test_shortest_path_against_scipy_and_unreachable():
     X = oracle.shortest_path_embedding(g.n, g.row_ptr, g.col, targets, l0)
     assert np.array_equal(X, want)
     assert (X == l0 + 1).any()  # some nodes are unreachable or farther than l0
+
+
+# ----------------------------------------------------- BFS-k neighbours (Eq. 7)
+
+
+def _py_bfs_lists(n, rp, col, k):
+    """Independent brute force: deque BFS with sorted neighbour scans."""
+    from collections import deque
+
+    lists = []
+    for s in range(n):
+        seen = {s}
+        q = deque([s])
+        found = []
+        while q and len(found) < k:
+            v = q.popleft()
+            for w in sorted(col[rp[v]:rp[v + 1]].tolist()):
+                if w not in seen:
+                    seen.add(w)
+                    q.append(w)
+                    found.append(w)
+                    if len(found) == k:
+                        break
+        lists.append(found)
+    return lists
+
+
+@pytest.mark.parametrize("n,deg,k", [(30, 3.0, 4), (80, 2.0, 10), (60, 8.0, 25)])
+def test_bfs_knn_brute_force(n, deg, k):
+    g = synth.random_graph(n, deg, seed=n + k)
+    rp, col = oracle.structure(n, g.row_ptr, g.col)
+    out, cnt = oracle.bfs_knn(n, rp, col, k)
+    want = _py_bfs_lists(n, rp, col, k)
+    for i in range(n):
+        assert out[i, :cnt[i]].tolist() == want[i]
+
+
+def test_bfs_knn_closed_forms():
+    # path 0-1-...-9, k = 2: interior nodes get (i-1, i+1); ends get the next two
+    n = 10
+    rp, col = synth.csr_from_edges(n, np.arange(n - 1), np.arange(1, n))
+    out, cnt = oracle.bfs_knn(n, rp, col, 2)
+    assert out[0].tolist() == [1, 2] and out[9].tolist() == [8, 7] and out[4].tolist() == [3, 5]
+    # star with centre 0 and 6 leaves, k = 3: centre -> 3 smallest leaves,
+    # leaf -> centre then the 2 smallest other leaves
+    rp, col = synth.csr_from_edges(7, np.zeros(6, np.int64), np.arange(1, 7))
+    out, cnt = oracle.bfs_knn(7, rp, col, 3)
+    assert out[0].tolist() == [1, 2, 3] and out[5].tolist() == [0, 1, 2]
+    # a component smaller than k: the whole component
+    rp, col = synth.csr_from_edges(5, np.array([0, 3]), np.array([1, 4]))
+    out, cnt = oracle.bfs_knn(5, rp, col, 4)
+    assert cnt.tolist() == [1, 1, 0, 1, 1]
+    # symmetrised structure = union of the lists: 2 is in the lists of 0, 1, 3
+    krp, kcol = oracle.knn_structure(10, *synth.csr_from_edges(10, np.arange(9), np.arange(1, 10)), 2)
+    assert kcol[krp[0]:krp[1]].tolist() == [1, 2] and kcol[krp[2]:krp[3]].tolist() == [0, 1, 3]
