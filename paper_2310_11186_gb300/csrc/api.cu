@@ -232,14 +232,18 @@ tsgne_status enqueue_repulsion(tsgne_ctx* ctx, int advance) {
 tsgne_status enqueue_step(tsgne_ctx* ctx) {
   TS_TRY(enqueue_repulsion(ctx, 1));
   ProfRec pr;
+  // the layout is pulled into L2 before the gathers (hub chunks, then rows)
   if (ctx->hub.chunks > 0) {
     ProfRec ph;
     TS_TRY(prof_begin(ctx, 6, &ph));
+    TS_TRY(launch_prefetch_l2(ctx->Y[ctx->cur].get(), (int64_t)ctx->n * 8, ctx->stream));
     TS_TRY(launch_attract_heavy(ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(), ctx->heavy(),
                                 ctx->stream));
     TS_TRY(prof_end(ctx, &ph));
   }
   TS_TRY(prof_begin(ctx, 1, &pr));
+  if (ctx->hub.chunks == 0)
+    TS_TRY(launch_prefetch_l2(ctx->Y[ctx->cur].get(), (int64_t)ctx->n * 8, ctx->stream));
   const int nxt = ctx->cur ^ 1;
   TS_TRY(launch_attract_update(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
                                ctx->Y[nxt].get(), ctx->upd.get(), ctx->gains.get(), ctx->fsum.get(), 1,

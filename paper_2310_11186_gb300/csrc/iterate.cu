@@ -165,12 +165,20 @@ __global__ void __launch_bounds__(kAttrCta)
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     float fx = 0.f, fy = 0.f;
     for (int k = 0; k < slots; ++k) {
-      const float2 f = part[(size_t)k * n_pad + i];
+      const float2 f = __ldcs(part + (size_t)k * n_pad + i);  // streamed: keep Y resident in L2
       fx += f.x;
       fy += f.y;
     }
     out[i] = make_float2(fx, fy);
   }
+}
+
+// Pulls the layout into L2 (one sequential read) so that the neighbour
+// gathers of the attraction hit L2 rather than DRAM sectors.
+__global__ void k_prefetch_l2(const char* __restrict__ p, int64_t bytes) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 128;
+  for (int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 128; o < bytes; o += stride)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + o));
 }
 
 __global__ void __launch_bounds__(kAttrCta)
@@ -268,10 +276,20 @@ tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col,
 tsgne_status launch_gradient(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
                              const float2* frep_part, int chunks, int n_pad, const Sched* sched, float alpha,
                              const HeavyRows& hv, float2* g, cudaStream_t s) {
+  TS_TRY(launch_prefetch_l2(Y, (int64_t)n * 8, s));
   TS_TRY(launch_attract_heavy(rp, col, P, Y, hv, s));
   const int grid = grid_rows(n, kAttrCta);
   k_attract<kG, true><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Y, nullptr, nullptr, nullptr, frep_part, chunks,
                                                 n_pad, const_cast<Sched*>(sched), 0.f, 0.f, alpha, g, hv);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+tsgne_status launch_prefetch_l2(const void* p, int64_t bytes, cudaStream_t s) {
+  if (bytes < (1 << 20)) return TSGNE_OK;  // small layouts stay in L2 anyway
+  const int64_t lines = (bytes + 127) / 128;
+  const int g = (int)((lines + 255) / 256 < 2048 ? (lines + 255) / 256 : 2048);
+  k_prefetch_l2<<<g, 256, 0, s>>>(static_cast<const char*>(p), bytes);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }

@@ -182,6 +182,8 @@ struct HeavyStore {
   }
 };
 tsgne_status find_heavy_rows(int n, const int64_t* rp, HeavyStore& hs, cudaStream_t s);
+// L2 prefetch of a buffer (no-op below 1 MB).
+tsgne_status launch_prefetch_l2(const void* p, int64_t bytes, cudaStream_t s);
 // The hub-row chunks alone (the update kernel then reads their sums).
 tsgne_status launch_attract_heavy(const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
                                   const HeavyRows& hv, cudaStream_t s);
