@@ -45,13 +45,16 @@ __global__ void __launch_bounds__(kAttrCta)
               HeavyRows hv) {
   constexpr int NGRP = kAttrCta / G;
   __shared__ float2 sfa[kAttrCta];
+  __shared__ int64_t srp[kAttrCta + 1];
   const int64_t row0 = (int64_t)blockIdx.x * kAttrCta;
   const int grp = threadIdx.x / G, lane = threadIdx.x % G;
+  for (int t = threadIdx.x; t <= kAttrCta; t += kAttrCta) srp[t] = row0 + t <= n ? rp[row0 + t] : 0;
+  __syncthreads();
   for (int r = grp; r < kAttrCta; r += NGRP) {
     const int64_t i = row0 + r;
     float ax = 0.f, ay = 0.f;
     if (i < n) {
-      if (rp[i + 1] - rp[i] > kHeavyDeg) {
+      if (srp[r + 1] - srp[r] > kHeavyDeg) {
         if (lane == 0) {  // chunk sums from k_attract_heavy, in chunk order
           int lo = 0, hi = hv.count - 1;
           while (lo < hi) {
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(kAttrCta)
           }
         }
       } else {
-        attract_row<G>(rp, col, P, Ycur, i, lane, Ycur[i], ax, ay);
+        attract_entries<G>(srp[r], srp[r + 1], col, P, Ycur, i, lane, Ycur[i], ax, ay);
       }
     }
     ax = group_sum<G>(ax);
@@ -111,16 +114,7 @@ __global__ void __launch_bounds__(256)
     const int64_t i = hv.chunk_row[c];
     const float2 yi = Y[i];
     float ax = 0.f, ay = 0.f;
-    for (int64_t e = hv.chunk_begin[c] + threadIdx.x; e < hv.chunk_end[c]; e += 256) {
-      const int32_t j = col[e];
-      const float p = P[e];
-      const float2 yj = Y[j];
-      const float dx = yi.x - yj.x, dy = yi.y - yj.y;
-      const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
-      const float pw = p * w;
-      ax = fmaf(pw, dx, ax);
-      ay = fmaf(pw, dy, ay);
-    }
+    attract_entries<256>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Y, i, threadIdx.x, yi, ax, ay);
     sx[threadIdx.x] = ax;
     sy[threadIdx.x] = ay;
     __syncthreads();

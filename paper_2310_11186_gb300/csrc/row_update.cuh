@@ -10,21 +10,45 @@ namespace tsgne {
 
 // This lane's share of F^a_i = sum_{j in N(i)} p_ij w_ij (y_i - y_j),
 // w = (1 + ||y_i - y_j||^2)^-1, over entries rp[i] + lane, + G, ...
+// Entries [a, b) of the row; 4 entries per lane are in flight at once (their
+// column / P loads, then their gathers), accumulated in entry order, so the
+// result is the same as one entry at a time.
+template <int G>
+__device__ __forceinline__ void attract_entries(int64_t a, int64_t b, const int32_t* __restrict__ col,
+                                                const float* __restrict__ P, const float2* __restrict__ Y,
+                                                int64_t i, int lane, float2 yi, float& ax, float& ay) {
+  constexpr int U = 4;
+  for (int64_t e0 = a + lane; e0 < b; e0 += U * G) {
+    int32_t j[U];
+    float p[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = e0 + (int64_t)u * G;
+      const bool ok = e < b;
+      j[u] = ok ? col[e] : (int32_t)i;
+      p[u] = ok ? P[e] : 0.f;
+    }
+    float2 yj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) yj[u] = Y[j[u]];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (e0 + (int64_t)u * G < b) {
+        const float dx = yi.x - yj[u].x, dy = yi.y - yj[u].y;
+        const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
+        const float pw = p[u] * w;
+        ax = fmaf(pw, dx, ax);
+        ay = fmaf(pw, dy, ay);
+      }
+    }
+  }
+}
+
 template <int G>
 __device__ __forceinline__ void attract_row(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                             const float* __restrict__ P, const float2* __restrict__ Y, int64_t i,
                                             int lane, float2 yi, float& ax, float& ay) {
-  const int64_t b = rp[i + 1];
-  for (int64_t e = rp[i] + lane; e < b; e += G) {
-    const int32_t j = col[e];
-    const float p = P[e];
-    const float2 yj = Y[j];
-    const float dx = yi.x - yj.x, dy = yi.y - yj.y;
-    const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
-    const float pw = p * w;
-    ax = fmaf(pw, dx, ax);
-    ay = fmaf(pw, dy, ay);
-  }
+  attract_entries<G>(rp[i], rp[i + 1], col, P, Y, i, lane, yi, ax, ay);
 }
 
 // Sum over the G lanes of a row group (xor butterfly: every lane gets the
