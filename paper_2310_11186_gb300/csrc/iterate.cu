@@ -103,30 +103,22 @@ __global__ void __launch_bounds__(kAttrCta)
   if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&sched->flags, kFlagNonfiniteY);
 }
 
-// Attraction of the hub rows (more than kHeavyDeg entries), in chunks of at
-// most kHeavyChunk entries: one CTA per chunk, fixed-order block reduction,
-// so no group of lanes serialises on a hub and no CTA on a whole hub.
+// Attraction of the long rows (more than kHeavyDeg entries), in chunks of at
+// most kHeavyChunk entries: one warp per chunk, xor-butterfly reduction
+// (fixed order), so no group of lanes serialises on a hub row.
 __global__ void __launch_bounds__(256)
     k_attract_heavy(HeavyRows hv, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                     const float* __restrict__ P, const float2* __restrict__ Y) {
-  __shared__ float sx[256], sy[256];
-  for (int c = blockIdx.x; c < hv.chunks; c += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < hv.chunks; c += warps) {
     const int64_t i = hv.chunk_row[c];
     const float2 yi = Y[i];
     float ax = 0.f, ay = 0.f;
-    attract_entries<256>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Y, i, threadIdx.x, yi, ax, ay);
-    sx[threadIdx.x] = ax;
-    sy[threadIdx.x] = ay;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (threadIdx.x < o) {
-        sx[threadIdx.x] += sx[threadIdx.x + o];
-        sy[threadIdx.x] += sy[threadIdx.x + o];
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) hv.fa[c] = make_float2(sx[0], sy[0]);
-    __syncthreads();
+    attract_entries<32>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Y, i, lane, yi, ax, ay);
+    ax = group_sum<32>(ax);
+    ay = group_sum<32>(ay);
+    if (lane == 0) hv.fa[c] = make_float2(ax, ay);
   }
 }
 
@@ -291,7 +283,8 @@ tsgne_status launch_prefetch_l2(const void* p, int64_t bytes, cudaStream_t s) {
 tsgne_status launch_attract_heavy(const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
                                   const HeavyRows& hv, cudaStream_t s) {
   if (hv.chunks <= 0) return TSGNE_OK;
-  k_attract_heavy<<<hv.chunks < 8192 ? hv.chunks : 8192, 256, 0, s>>>(hv, rp, col, P, Y);
+  const int g = (hv.chunks + 7) / 8 < 16384 ? (hv.chunks + 7) / 8 : 16384;
+  k_attract_heavy<<<g, 256, 0, s>>>(hv, rp, col, P, Y);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }

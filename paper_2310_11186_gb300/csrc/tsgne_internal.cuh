@@ -148,11 +148,12 @@ tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const float2* Y, fl
 
 // ------------------------------------------------------------ iteration
 // Rows with more than kHeavyDeg entries get their attraction from chunks of
-// kHeavyChunk entries, one CTA per chunk (k_attract_heavy); the update adds a
+// kHeavyChunk entries, one warp per chunk (k_attract_heavy); the update adds a
 // row's chunk sums in chunk order.  rows[] is sorted; chunks of heavy row k
-// are chunk_off[k] .. chunk_off[k+1]-1.
-constexpr int kHeavyDeg = 256;
-constexpr int kHeavyChunk = 2048;
+// are chunk_off[k] .. chunk_off[k+1]-1.  Rows up to kHeavyDeg entries are
+// one 4-entry batch per lane of an 8-lane group, so no group waits on another.
+constexpr int kHeavyDeg = 32;
+constexpr int kHeavyChunk = 1024;
 struct HeavyRows {
   const int32_t* rows = nullptr;       // [count] sorted row ids
   const int32_t* chunk_off = nullptr;  // [count + 1]
