@@ -502,7 +502,8 @@ def bench_rmat(args, pkg, log_fn=log):
     import oracle
 
     t0 = time.perf_counter()
-    g, X = synth.rmat(21, 1 << 24, seed=args.seed)
+    scale = args.rmat_scale
+    g, X = synth.rmat(scale, 1 << (scale + 3), seed=args.seed)
     log_fn(f"[bench] rmat: n={g.n} edges={g.m // 2} max degree {int(np.diff(g.row_ptr).max())} "
            f"({time.perf_counter() - t0:.1f}s)")
     lay = pkg.Layout(profile=1)
@@ -547,8 +548,8 @@ def bench_rmat(args, pkg, log_fn=log):
         G, Z = l2.gradient(1.0)
         kl = l2.kl()
     return {
-        "workload": "R-MAT scale 21 (2,097,152 nodes), 2^24 distinct undirected edges, a=0.57 b=c=0.19, 64-d "
-                    "embedding of 64 recursion communities, perplexity 30",
+        "workload": f"R-MAT scale {scale} ({1 << scale} nodes), 2^{scale + 3} distinct undirected edges, a=0.57 "
+                    f"b=c=0.19, 64-d embedding of 64 recursion communities, perplexity 30",
         "nnz_P": int(nnz),
         "build_ms": build_ms,
         "repulsion_ms": rep_ms,
@@ -583,6 +584,8 @@ def main():
     ap.add_argument("--serve-iters", type=int, default=500)
     ap.add_argument("--rmat", action="store_true", help="also run the R-MAT 2^21 workload (about a minute)")
     ap.add_argument("--rmat-steps", type=int, default=5)
+    ap.add_argument("--rmat-scale", type=int, default=21)
+    ap.add_argument("--only-rmat", action="store_true", help="run only the R-MAT section (profiling)")
     ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOAD,
                     help="zipf300k is the benchmark; the others are smaller cases for profiling")
     args = ap.parse_args()
@@ -590,6 +593,16 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_rmat:
+        import torch
+
+        from paper_2310_11186_gb300 import build as pbuild
+        import paper_2310_11186_gb300 as pkg
+
+        torch.cuda.set_device(0)
+        pbuild.build()
+        print(json.dumps({"rmat": bench_rmat(args, pkg)}), flush=True)
+        return 0
     return run_ours(args)
 
 
