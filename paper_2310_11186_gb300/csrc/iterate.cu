@@ -50,49 +50,30 @@ __global__ void __launch_bounds__(kAttrCta)
   const int grp = threadIdx.x / G, lane = threadIdx.x % G;
   for (int t = threadIdx.x; t <= kAttrCta; t += kAttrCta) srp[t] = row0 + t <= n ? rp[row0 + t] : 0;
   __syncthreads();
-  static_assert(4 * G >= kHeavyDeg, "short rows must fit one 4-entry batch per lane");
-  // rows r and r + NGRP together: their loads overlap
-  for (int r = grp; r < kAttrCta; r += 2 * NGRP) {
-    const int r1 = r + NGRP;
-    const int64_t i0 = row0 + r, i1 = row0 + r1;
-    float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
-    // long rows (and rows past n) take no entries here; an empty range skips loads
-    const bool v0 = i0 < n, v1 = r1 < kAttrCta && i1 < n;
-    const bool h0 = v0 && srp[r + 1] - srp[r] > kHeavyDeg;
-    const bool h1 = v1 && srp[r1 + 1] - srp[r1] > kHeavyDeg;
-    const int64_t a0 = (v0 && !h0) ? srp[r] : 0, b0 = (v0 && !h0) ? srp[r + 1] : 0;
-    const int64_t a1 = (v1 && !h1) ? srp[r1] : 0, b1 = (v1 && !h1) ? srp[r1 + 1] : 0;
-    const float2 y0 = v0 ? Ycur[i0] : make_float2(0.f, 0.f);
-    const float2 y1 = v1 ? Ycur[i1] : make_float2(0.f, 0.f);
-    attract_two_short_rows<G>(a0, b0, v0 ? i0 : 0, a1, b1, v1 ? i1 : 0, col, P, Ycur, lane, y0, y1, ax0, ay0, ax1,
-                              ay1);
-    if (lane == 0) {  // long rows: chunk sums from k_attract_heavy, in chunk order
-      for (int q = 0; q < 2; ++q) {
-        const bool hq = q == 0 ? h0 : h1;
-        if (!hq) continue;
-        const int64_t iq = q == 0 ? i0 : i1;
-        int lo = 0, hi = hv.count - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (hv.rows[mid] < iq) lo = mid + 1; else hi = mid;
+  for (int r = grp; r < kAttrCta; r += NGRP) {
+    const int64_t i = row0 + r;
+    float ax = 0.f, ay = 0.f;
+    if (i < n) {
+      if (srp[r + 1] - srp[r] > kHeavyDeg) {
+        if (lane == 0) {  // chunk sums from k_attract_heavy, in chunk order
+          int lo = 0, hi = hv.count - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (hv.rows[mid] < i) lo = mid + 1; else hi = mid;
+          }
+          for (int c = hv.chunk_off[lo]; c < hv.chunk_off[lo + 1]; ++c) {
+            const float2 f = hv.fa[c];
+            ax += f.x;
+            ay += f.y;
+          }
         }
-        float sx = 0.f, sy = 0.f;
-        for (int c = hv.chunk_off[lo]; c < hv.chunk_off[lo + 1]; ++c) {
-          const float2 f = hv.fa[c];
-          sx += f.x;
-          sy += f.y;
-        }
-        if (q == 0) { ax0 = sx; ay0 = sy; } else { ax1 = sx; ay1 = sy; }
+      } else {
+        attract_entries<G>(srp[r], srp[r + 1], col, P, Ycur, i, lane, Ycur[i], ax, ay);
       }
     }
-    ax0 = group_sum<G>(ax0);
-    ay0 = group_sum<G>(ay0);
-    ax1 = group_sum<G>(ax1);
-    ay1 = group_sum<G>(ay1);
-    if (lane == 0) {
-      sfa[r] = make_float2(ax0, ay0);
-      if (r1 < kAttrCta) sfa[r1] = make_float2(ax1, ay1);
-    }
+    ax = group_sum<G>(ax);
+    ay = group_sum<G>(ay);
+    if (lane == 0) sfa[r] = make_float2(ax, ay);
   }
   __syncthreads();
   const int64_t i = row0 + threadIdx.x;
@@ -134,7 +115,7 @@ __global__ void __launch_bounds__(256)
     const int64_t i = hv.chunk_row[c];
     const float2 yi = Y[i];
     float ax = 0.f, ay = 0.f;
-    attract_entries<32, 8>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Y, i, lane, yi, ax, ay);
+    attract_entries<32>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Y, i, lane, yi, ax, ay);
     ax = group_sum<32>(ax);
     ay = group_sum<32>(ay);
     if (lane == 0) hv.fa[c] = make_float2(ax, ay);

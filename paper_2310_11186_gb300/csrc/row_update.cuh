@@ -10,13 +10,14 @@ namespace tsgne {
 
 // This lane's share of F^a_i = sum_{j in N(i)} p_ij w_ij (y_i - y_j),
 // w = (1 + ||y_i - y_j||^2)^-1, over entries rp[i] + lane, + G, ...
-// Entries [a, b) of the row; U entries per lane are in flight at once (their
+// Entries [a, b) of the row; 4 entries per lane are in flight at once (their
 // column / P loads, then their gathers), accumulated in entry order, so the
 // result is the same as one entry at a time.
-template <int G, int U = 4>
+template <int G>
 __device__ __forceinline__ void attract_entries(int64_t a, int64_t b, const int32_t* __restrict__ col,
                                                 const float* __restrict__ P, const float2* __restrict__ Y,
                                                 int64_t i, int lane, float2 yi, float& ax, float& ay) {
+  constexpr int U = 4;
   for (int64_t e0 = a + lane; e0 < b; e0 += U * G) {
     int32_t j[U];
     float p[U];
@@ -47,7 +48,7 @@ template <int G>
 __device__ __forceinline__ void attract_row(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                             const float* __restrict__ P, const float2* __restrict__ Y, int64_t i,
                                             int lane, float2 yi, float& ax, float& ay) {
-  attract_entries<G, 4>(rp[i], rp[i + 1], col, P, Y, i, lane, yi, ax, ay);
+  attract_entries<G>(rp[i], rp[i + 1], col, P, Y, i, lane, yi, ax, ay);
 }
 
 // Sum over the G lanes of a row group (xor butterfly: every lane gets the
@@ -72,56 +73,6 @@ __device__ __forceinline__ float2 optimizer_step(float gx, float gy, float2& u, 
   u.x = mu * u.x - eta * gn.x * gx;
   u.y = mu * u.y - eta * gn.y * gy;
   return make_float2(yi.x + u.x, yi.y + u.y);
-}
-
-}  // namespace tsgne
-
-namespace tsgne {
-
-// Two short rows (at most 4 * G entries each) of a G-lane group at once:
-// all their column / P loads, then all their gathers, then the arithmetic of
-// each row in entry order (the same order as attract_entries).
-template <int G>
-__device__ __forceinline__ void attract_two_short_rows(int64_t a0, int64_t b0, int64_t i0, int64_t a1, int64_t b1,
-                                                       int64_t i1, const int32_t* __restrict__ col,
-                                                       const float* __restrict__ P, const float2* __restrict__ Y,
-                                                       int lane, float2 y0, float2 y1, float& ax0, float& ay0,
-                                                       float& ax1, float& ay1) {
-  constexpr int U = 4;
-  int32_t j[2 * U];
-  float p[2 * U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int64_t e0 = a0 + lane + (int64_t)u * G, e1 = a1 + lane + (int64_t)u * G;
-    const bool k0 = e0 < b0, k1 = e1 < b1;
-    j[u] = k0 ? col[e0] : (int32_t)i0;
-    p[u] = k0 ? P[e0] : 0.f;
-    j[U + u] = k1 ? col[e1] : (int32_t)i1;
-    p[U + u] = k1 ? P[e1] : 0.f;
-  }
-  float2 yj[2 * U];
-#pragma unroll
-  for (int u = 0; u < 2 * U; ++u) yj[u] = Y[j[u]];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    if (a0 + lane + (int64_t)u * G < b0) {
-      const float dx = y0.x - yj[u].x, dy = y0.y - yj[u].y;
-      const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
-      const float pw = p[u] * w;
-      ax0 = fmaf(pw, dx, ax0);
-      ay0 = fmaf(pw, dy, ay0);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    if (a1 + lane + (int64_t)u * G < b1) {
-      const float dx = y1.x - yj[U + u].x, dy = y1.y - yj[U + u].y;
-      const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
-      const float pw = p[U + u] * w;
-      ax1 = fmaf(pw, dx, ax1);
-      ay1 = fmaf(pw, dy, ay1);
-    }
-  }
 }
 
 }  // namespace tsgne
