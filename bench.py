@@ -168,6 +168,23 @@ def oracle_sample(Y, n, target_s: float):
         rows = min(n, int(rows * max(2.0, min(16.0, 1.2 * target_s / max(dt, 1e-4)))))
 
 
+def aggregate_ranks(local_seconds: float, units_per_rank: float):
+    """Whole-job throughput of N replicas: every rank's units over the slowest
+    rank's time (max over ranks; no collective when running alone).
+    Returns (max_seconds, units_per_second)."""
+    import torch
+    import torch.distributed as dist
+
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = local_seconds
+    if ws > 1:
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        tt = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, ws * units_per_rank / t
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -279,12 +296,7 @@ def run_ours(args):
     nnz_P = lay.sizes()[1]
     lay.close()
 
-    # max over ranks
-    if ws > 1:
-        tt = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(tt.item())
-    value = ws * args.steps / total_s
+    total_s, value = aggregate_ranks(total_s, args.steps)
 
     # ---- end to end: whole layout from pinned host buffers through the C ABI
     e2e_iters = args.e2e_iters
@@ -302,11 +314,7 @@ def run_ours(args):
     lay2.init_Y(Y0_h)
     lay2.run(e2e_iters)
     lay2.get_Y(Y_out)
-    e2e_s = time.perf_counter() - te
-    if ws > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s, _ = aggregate_ranks(time.perf_counter() - te, e2e_iters)
     kl_final = lay2.kl()
     lay2.close()
     # the paper's embedding step: ShortestPath to 128 random targets (Sec. 2.3)
