@@ -80,6 +80,8 @@ def _load():
             lib.tsgo_shortest_path.restype = ctypes.c_int
             lib.tsgo_bfs_knn.argtypes = [_i32, _p, _p, _i32, _p, _p]
             lib.tsgo_bfs_knn.restype = ctypes.c_int
+            lib.tsgo_repulsion_tree.argtypes = [_i32, _p, _dbl, _i32, _p, _p, _p]
+            lib.tsgo_repulsion_tree.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -194,6 +196,20 @@ def repulsion_rows(Y, i0, i1):
     zr = np.zeros(max(1, i1 - i0))
     _check(_load().tsgo_repulsion_rows(n, _ptr(Yd), i0, i1, _ptr(F), _ptr(zr)), "repulsion_rows")
     return F[: i1 - i0], zr[: i1 - i0]
+
+
+def repulsion_tree(Y, theta, bucket=16):
+    """Tree-code approximation of the repulsive sums (steps in the C source):
+    returns (F_rep n x 2, zrow n, Z) in the input order.  theta = 0 gives the
+    exact sums of repulsion_rows."""
+    Yd = _c(Y, np.float64)
+    n = Yd.shape[0]
+    F = np.zeros((n, 2))
+    zr = np.zeros(n)
+    z = ctypes.c_double(0.0)
+    _check(_load().tsgo_repulsion_tree(n, _ptr(Yd), float(theta), int(bucket), _ptr(F), _ptr(zr), ctypes.byref(z)),
+           "repulsion_tree")
+    return F, zr, z.value
 
 
 def repulsion_all(Y, threads=None):

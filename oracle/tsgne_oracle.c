@@ -26,8 +26,11 @@
  *                       published t-SNE defaults are used)
  *   tsgo_shortest_path  ShortestPath graph embedding (Sec. 2.3, Eq. 8): BFS
  *                       distances to d target nodes, capped at l0 + 1
- *   tsgo_bfs_knn        the k-nearest neighbours of Eq. 7 "by a breadth-first
- *                       search of k steps" (Sec. 2.2), before symmetrisation
+ *   tsgo_bfs_knn        the k nearest neighbours of Eq. 7, found by a k-step
+ *                       breadth-first search (Sec. 2.2), before symmetrisation
+ *   tsgo_repulsion_tree tree-code approximation of the repulsive sums and Z
+ *                       (an extension; the paper sums Eq. 4 exactly); its
+ *                       steps are listed above the function
  *
  * Readings of the paper where it is silent (also listed in the design notes):
  *   - N(i) is the set of graph neighbours (k = graph edges), union of both
@@ -453,5 +456,247 @@ int tsgo_bfs_knn(int32_t n, const int64_t* rp, const int32_t* col, int32_t k, in
   }
   free(seen);
   free(queue);
+  return TSGO_OK;
+}
+
+/*
+ * ---------------------------------------------------------------------------
+ * Tree-code approximation of the repulsive sums (an extension: the paper
+ * evaluates the O(|V|^2) sum of Eq. 4 exactly, Sec. 2.1 "Time complexity").
+ * The approximation is defined by the steps below; decisions that pick
+ * interactions (cell codes, tree shape, acceptance) are taken in FP32, as the
+ * GPU takes them, and the sums are then accumulated in FP64.
+ *
+ *  1. Bounding square: lo = (min x, min y), side = max(max x - min x,
+ *     max y - min y) floored at 1e-30; scale = 65536 / side.
+ *  2. Cell of a point: c = (v - lo) * scale per axis, truncated to an integer
+ *     and clamped to [0, 65535] (NaN -> 0); key = Morton interleave of the
+ *     two 16-bit cells, x in the even bits, y in the odd bits.
+ *  3. Order: points sorted by (key, index).  Position k of the sorted order
+ *     gets the 64-bit augmented key (key << 32) | k, unique per point.
+ *  4. Tree: the binary radix tree of the augmented keys.  A node covers
+ *     sorted positions [f, l]; if f < l it splits at the highest bit in which
+ *     the augmented keys of f and l differ: the left child holds the
+ *     positions whose bit is 0.  A single position is a leaf.
+ *  5. Node summaries (FP32): count; coordinate sums, left + right; bounding
+ *     box; centre = sums / count; r2 = (longest box side)^2.
+ *  6. Groups: runs of 32 consecutive sorted positions (the last may be
+ *     shorter), with the bounding box of their points.
+ *  7. Walk, per group, from the root, left child before right:
+ *     - a leaf is an exact interaction with its point;
+ *     - otherwise d2 = squared distance from the node's centre to the group
+ *       box (0 inside); if r2 < theta^2 * d2 the node is one interaction of
+ *       weight count at its centre;
+ *     - otherwise, if count <= bucket, exact interactions with each of its
+ *       points; else both children are walked.
+ *     An exact interaction of point i with point j != i adds w = 1/(1 + |y_i
+ *     - y_j|^2) to zrow_i and w^2 (y_i - y_j) to F_i; a node interaction
+ *     adds count * w and count * w^2 (y_i - c) with w taken at the centre c.
+ *     A point never interacts with itself exactly.
+ *  Z = sum_i zrow_i.  theta = 0 accepts no node and reduces to the exact sums
+ *  of tsgo_repulsion_rows.
+ * ---------------------------------------------------------------------------
+ */
+typedef struct {
+  int32_t first, last, left, right; /* left/right: node ids, -1 for a leaf */
+  float sx, sy, x0, y0, x1, y1, cx, cy, r2;
+} tsgo_tnode;
+
+typedef struct {
+  uint32_t key;
+  int32_t idx;
+} tsgo_keyed;
+
+static int cmp_keyed(const void* a, const void* b) {
+  const tsgo_keyed* x = (const tsgo_keyed*)a;
+  const tsgo_keyed* y = (const tsgo_keyed*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+static uint32_t spread_bits16(uint32_t v) {
+  uint32_t r = 0;
+  for (int b = 0; b < 16; ++b) r |= ((v >> b) & 1u) << (2 * b);
+  return r;
+}
+
+static uint32_t cell16(float v, float lo, float scale) {
+  float c = (v - lo) * scale;
+  if (!(c >= 0.0f)) return 0u;
+  if (c >= 65535.0f) return 65535u;
+  return (uint32_t)c;
+}
+
+/* Builds the subtree over sorted positions [f, l]; returns its node id. */
+static int32_t tree_build(const uint64_t* aug, const float* xs, const float* ys, int32_t f, int32_t l,
+                          tsgo_tnode* nodes, int32_t* count) {
+  int32_t id = (*count)++;
+  tsgo_tnode* t = &nodes[id];
+  t->first = f;
+  t->last = l;
+  if (f == l) {
+    t->left = t->right = -1;
+    t->sx = t->x0 = t->x1 = t->cx = xs[f];
+    t->sy = t->y0 = t->y1 = t->cy = ys[f];
+    t->r2 = 0.0f;
+    return id;
+  }
+  int bit = 63;
+  uint64_t diff = aug[f] ^ aug[l];
+  while (!((diff >> bit) & 1u)) --bit;
+  int32_t g = f;
+  while (g + 1 <= l && !((aug[g + 1] >> bit) & 1u)) ++g;
+  int32_t L = tree_build(aug, xs, ys, f, g, nodes, count);
+  int32_t R = tree_build(aug, xs, ys, g + 1, l, nodes, count);
+  t = &nodes[id];
+  const tsgo_tnode* a = &nodes[L];
+  const tsgo_tnode* b = &nodes[R];
+  t->left = L;
+  t->right = R;
+  t->sx = a->sx + b->sx;
+  t->sy = a->sy + b->sy;
+  t->x0 = fminf(a->x0, b->x0);
+  t->y0 = fminf(a->y0, b->y0);
+  t->x1 = fmaxf(a->x1, b->x1);
+  t->y1 = fmaxf(a->y1, b->y1);
+  float cnt = (float)(l - f + 1);
+  t->cx = t->sx / cnt;
+  t->cy = t->sy / cnt;
+  float r = fmaxf(t->x1 - t->x0, t->y1 - t->y0);
+  t->r2 = r * r;
+  return id;
+}
+
+typedef struct {
+  const tsgo_tnode* nodes;
+  const float* xs;
+  const float* ys;
+  int32_t g0, g1; /* group's sorted positions [g0, g1) */
+  float bx0, by0, bx1, by1, theta2;
+  int32_t bucket;
+  double* F;    /* per sorted position */
+  double* zrow; /* per sorted position */
+} tsgo_walk;
+
+static void exact_pairs(const tsgo_walk* w, int32_t j) {
+  for (int32_t i = w->g0; i < w->g1; ++i) {
+    if (i == j) continue;
+    double dx = (double)w->xs[i] - (double)w->xs[j];
+    double dy = (double)w->ys[i] - (double)w->ys[j];
+    double k = 1.0 / (1.0 + dx * dx + dy * dy);
+    w->zrow[i] += k;
+    w->F[2 * i] += k * k * dx;
+    w->F[2 * i + 1] += k * k * dy;
+  }
+}
+
+static void tree_walk(const tsgo_walk* w, int32_t id) {
+  const tsgo_tnode* t = &w->nodes[id];
+  if (t->left < 0) {
+    exact_pairs(w, t->first);
+    return;
+  }
+  float dx = fmaxf(fmaxf(w->bx0 - t->cx, t->cx - w->bx1), 0.0f);
+  float dy = fmaxf(fmaxf(w->by0 - t->cy, t->cy - w->by1), 0.0f);
+  float d2 = dx * dx + dy * dy;
+  if (t->r2 < w->theta2 * d2) {
+    double c = (double)(t->last - t->first + 1);
+    for (int32_t i = w->g0; i < w->g1; ++i) {
+      double ex = (double)w->xs[i] - (double)t->cx;
+      double ey = (double)w->ys[i] - (double)t->cy;
+      double k = 1.0 / (1.0 + ex * ex + ey * ey);
+      w->zrow[i] += c * k;
+      w->F[2 * i] += c * k * k * ex;
+      w->F[2 * i + 1] += c * k * k * ey;
+    }
+    return;
+  }
+  if (t->last - t->first + 1 <= w->bucket) {
+    for (int32_t j = t->first; j <= t->last; ++j) exact_pairs(w, j);
+    return;
+  }
+  tree_walk(w, t->left);
+  tree_walk(w, t->right);
+}
+
+/*
+ * Y: n x 2 layout (FP32 values carried in doubles); theta >= 0; bucket >= 1.
+ * Frep (n x 2) and zrow (n) come back in the input order; returns Z through
+ * *Z_out.
+ */
+int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket, double* Frep, double* zrow,
+                        double* Z_out) {
+  if (n < 1 || !(theta >= 0.0) || bucket < 1) return TSGO_EINVAL;
+  float* xs = (float*)malloc(sizeof(float) * (size_t)n);
+  float* ys = (float*)malloc(sizeof(float) * (size_t)n);
+  tsgo_keyed* kv = (tsgo_keyed*)malloc(sizeof(tsgo_keyed) * (size_t)n);
+  uint64_t* aug = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
+  tsgo_tnode* nodes = (tsgo_tnode*)malloc(sizeof(tsgo_tnode) * (size_t)(2 * n - 1));
+  double* F = (double*)calloc(2 * (size_t)n, sizeof(double));
+  double* zr = (double*)calloc((size_t)n, sizeof(double));
+  if (!xs || !ys || !kv || !aug || !nodes || !F || !zr) {
+    free(xs); free(ys); free(kv); free(aug); free(nodes); free(F); free(zr);
+    return TSGO_ENOMEM;
+  }
+  /* 1-2: bounding square and keys */
+  float lx = (float)Y[0], ly = (float)Y[1], hx = lx, hy = ly;
+  for (int32_t i = 1; i < n; ++i) {
+    float x = (float)Y[2 * i], y = (float)Y[2 * i + 1];
+    lx = fminf(lx, x);
+    hx = fmaxf(hx, x);
+    ly = fminf(ly, y);
+    hy = fmaxf(hy, y);
+  }
+  float side = fmaxf(fmaxf(hx - lx, hy - ly), 1e-30f);
+  float scale = 65536.0f / side;
+  for (int32_t i = 0; i < n; ++i) {
+    uint32_t cx = cell16((float)Y[2 * i], lx, scale), cy = cell16((float)Y[2 * i + 1], ly, scale);
+    kv[i].key = spread_bits16(cx) | (spread_bits16(cy) << 1);
+    kv[i].idx = i;
+  }
+  /* 3: order */
+  qsort(kv, (size_t)n, sizeof(tsgo_keyed), cmp_keyed);
+  for (int32_t k = 0; k < n; ++k) {
+    xs[k] = (float)Y[2 * kv[k].idx];
+    ys[k] = (float)Y[2 * kv[k].idx + 1];
+    aug[k] = ((uint64_t)kv[k].key << 32) | (uint32_t)k;
+  }
+  /* 4-5: tree */
+  int32_t count = 0;
+  int32_t root = tree_build(aug, xs, ys, 0, n - 1, nodes, &count);
+  /* 6-7: groups and walks */
+  float th = (float)theta;
+  tsgo_walk w;
+  w.nodes = nodes;
+  w.xs = xs;
+  w.ys = ys;
+  w.theta2 = th * th;
+  w.bucket = bucket;
+  w.F = F;
+  w.zrow = zr;
+  for (int32_t g0 = 0; g0 < n; g0 += 32) {
+    int32_t g1 = g0 + 32 < n ? g0 + 32 : n;
+    w.g0 = g0;
+    w.g1 = g1;
+    w.bx0 = w.bx1 = xs[g0];
+    w.by0 = w.by1 = ys[g0];
+    for (int32_t i = g0 + 1; i < g1; ++i) {
+      w.bx0 = fminf(w.bx0, xs[i]);
+      w.bx1 = fmaxf(w.bx1, xs[i]);
+      w.by0 = fminf(w.by0, ys[i]);
+      w.by1 = fmaxf(w.by1, ys[i]);
+    }
+    tree_walk(&w, root);
+  }
+  double Z = 0.0;
+  for (int32_t k = 0; k < n; ++k) {
+    int32_t i = kv[k].idx;
+    Frep[2 * i] = F[2 * k];
+    Frep[2 * i + 1] = F[2 * k + 1];
+    if (zrow) zrow[i] = zr[k];
+    Z += zr[k];
+  }
+  if (Z_out) *Z_out = Z;
+  free(xs); free(ys); free(kv); free(aug); free(nodes); free(F); free(zr);
   return TSGO_OK;
 }

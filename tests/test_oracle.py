@@ -468,3 +468,78 @@ def test_bfs_knn_closed_forms():
     # symmetrised structure = union of the lists: 2 is in the lists of 0, 1, 3
     krp, kcol = oracle.knn_structure(10, *synth.csr_from_edges(10, np.arange(9), np.arange(1, 10)), 2)
     assert kcol[krp[0]:krp[1]].tolist() == [1, 2] and kcol[krp[2]:krp[3]].tolist() == [0, 1, 3]
+
+
+# ------------------------------------------------ tree-code repulsion (extension)
+
+
+def _exact_rep(Y):
+    F, zr = oracle.repulsion_rows(Y, 0, Y.shape[0])
+    return F, zr
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 1000])
+def test_tree_theta0_equals_exact_sums(n):
+    """theta = 0 accepts no node: every pair is summed exactly."""
+    Y = np.random.default_rng(n).normal(size=(n, 2)).astype(np.float32)
+    F, zr, Z = oracle.repulsion_tree(Y, 0.0)
+    Fe, ze = _exact_rep(Y)
+    # same terms in another order: FP64 rounding only
+    assert np.abs(F - Fe).max() <= 1e-12 * max(np.abs(Fe).max(), 1e-300)
+    assert np.allclose(zr, ze, rtol=1e-12)
+    assert Z == pytest.approx(ze.sum(), rel=1e-12, abs=0.0)
+
+
+def test_tree_far_cluster_is_one_monopole():
+    """Two 32-point clusters 100 apart on the x axis: the root splits them
+    (x's top cell bit differs), each is one group, and each sees the other
+    as a single node of weight 32 at its centre of mass."""
+    rng = np.random.default_rng(7)
+    A = rng.uniform(-0.5, 0.5, size=(32, 2))
+    B = rng.uniform(-0.5, 0.5, size=(32, 2)) + [100.0, 0.0]
+    Y = np.concatenate([B, A]).astype(np.float32)  # input order does not matter
+    Yd = Y.astype(np.float64)
+    F, zr, Z = oracle.repulsion_tree(Y, 0.5)
+    for own, other in ((slice(32, 64), slice(0, 32)), (slice(0, 32), slice(32, 64))):
+        c = Yd[other].mean(0)
+        for i in range(own.start, own.stop):
+            d = Yd[own] - Yd[i]
+            w = 1.0 / (1.0 + (d ** 2).sum(1))
+            m = np.arange(own.start, own.stop) != i
+            e = Yd[i] - Yd[own][m]
+            f_in = ((w[m] ** 2)[:, None] * e).sum(0)
+            wc = 1.0 / (1.0 + ((Yd[i] - c) ** 2).sum())
+            f = f_in + 32 * wc ** 2 * (Yd[i] - c)
+            z = w[m].sum() + 32 * wc
+            assert np.allclose(F[i], f, rtol=1e-6, atol=1e-12), (i, F[i], f)
+            assert zr[i] == pytest.approx(z, rel=1e-9)
+    # and the monopole differs from the exact far-field sum (it is an approximation)
+    Fe, _ = _exact_rep(Y)
+    assert not np.allclose(F, Fe, rtol=1e-9, atol=0)
+
+
+def test_tree_error_shrinks_with_theta():
+    n = 5000
+    lab = (np.arange(n) % 7).astype(np.int32)
+    Y = synth.spread_layout(lab, scale=20.0, seed=1).astype(np.float32)
+    Fe, ze = _exact_rep(Y)
+    errs, zerr = [], []
+    for th in (0.1, 0.25, 0.5, 1.0):
+        F, _, Z = oracle.repulsion_tree(Y, th)
+        errs.append(np.linalg.norm(F - Fe) / np.linalg.norm(Fe))
+        zerr.append(abs(Z - ze.sum()) / ze.sum())
+    assert all(a < b for a, b in zip(errs, errs[1:])), errs
+    assert errs[0] < 1e-4 and errs[2] < 1e-2 and zerr[2] < 5e-3, (errs, zerr)
+
+
+def test_tree_coincident_points():
+    """200 points on one spot: their nodes have r = 0, so accepting them is
+    exact; duplicates are split by position, not by coordinates."""
+    rng = np.random.default_rng(3)
+    Y = np.concatenate([np.full((200, 2), 1.0), rng.normal(scale=5.0, size=(300, 2))]).astype(np.float32)
+    Fe, ze = _exact_rep(Y)
+    for th in (0.0, 0.5):
+        F, zr, Z = oracle.repulsion_tree(Y, th)
+        assert np.all(np.isfinite(F))
+        assert np.linalg.norm(F - Fe) / np.linalg.norm(Fe) < (1e-12 if th == 0 else 1e-2)
+        assert abs(Z - ze.sum()) / ze.sum() < (1e-12 if th == 0 else 5e-3)
