@@ -503,9 +503,11 @@ def hbm_peak():
 
 
 def bench_rmat(args, pkg, log_fn=log):
-    """R-MAT 2^21 nodes / 2^24 edges: the attraction+update kernel against the
-    HBM roofline, and FP32 accuracy against the FP64 oracle on a 20K-node
-    induced subgraph (BFS ball from the highest-degree node)."""
+    """R-MAT 2^21 nodes / 2^24 edges in both storage precisions (FP32; BF16
+    P and Y reads with FP32 arithmetic and FP64 Z): the attraction+update
+    kernel against the HBM roofline, and each arm's gradient / KL error
+    against the FP64 oracle on a 20K-node induced subgraph (BFS ball from the
+    highest-degree node)."""
     import torch
     import oracle
 
@@ -514,62 +516,72 @@ def bench_rmat(args, pkg, log_fn=log):
     g, X = synth.rmat(scale, 1 << (scale + 3), seed=args.seed)
     log_fn(f"[bench] rmat: n={g.n} edges={g.m // 2} max degree {int(np.diff(g.row_ptr).max())} "
            f"({time.perf_counter() - t0:.1f}s)")
-    lay = pkg.Layout(profile=1)
-    tb = time.perf_counter()
-    lay.build_P(g.row_ptr, g.col, X)
-    build_ms = (time.perf_counter() - tb) * 1e3
-    n, nnz = lay.sizes()
-    lay.init_Y(synth.y_init(n, seed=args.seed))
-    for _ in range(2):
-        lay.step()
-    lay.sync()
-    lay.kernel_times(reset=True)
-    flush = torch.empty(320 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
-    steps = args.rmat_steps
-    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        for k in range(steps):
-            with torch.cuda.stream(lay.stream):
-                flush.fill_(float(k))
-            lay.step()
-        lay.sync()
-    kt = lay.kernel_times(reset=True)
-    lay.close()
-    att_ms = kt["attract_update"][0] / kt["attract_update"][1]
-    hub_ms = kt["attract_hubs"][0] / max(kt["attract_hubs"][1], 1)
-    rep_ms = kt["repulsion"][0] / kt["repulsion"][1]
-    # algorithmic bytes of one attraction+update launch: row_ptr, col and P
-    # once, Y_i, F^r, update and gains read, Y_next, update and gains written
-    # (neighbour gathers of Y hit L2: Y is 16.8 MB)
-    att_bytes = 8 * (n + 1) + 8 * nnz + 7 * 8 * n
     peak, src = hbm_peak()
-    achieved = att_bytes / ((att_ms + hub_ms) * 1e-3) / 1e9
-    # accuracy on an induced 20K-node subgraph (FP32 GPU vs FP64 oracle)
+    flush = torch.empty(320 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
     nodes, sub = synth.induced_bfs_ball(g, 20_000)
     Xs = X[nodes]
     Ys = synth.spread_layout(sub.labels, scale=25.0, seed=args.seed)
     orp, ocol, oP = oracle.build_P(sub.n, sub.row_ptr, sub.col, Xs, 30.0)
     oG, oZ = oracle.gradient(sub.n, orp, ocol, oP, Ys.astype(np.float64), 1.0)
     okl, _ = oracle.kl(sub.n, orp, ocol, oP, Ys.astype(np.float64))
-    with pkg.Layout() as l2:
-        l2.build_P(sub.row_ptr, sub.col, Xs)
-        l2.init_Y(Ys)
-        G, Z = l2.gradient(1.0)
-        kl = l2.kl()
-    return {
+    out = {
         "workload": f"R-MAT scale {scale} ({1 << scale} nodes), 2^{scale + 3} distinct undirected edges, a=0.57 "
                     f"b=c=0.19, 64-d embedding of 64 recursion communities, perplexity 30",
-        "nnz_P": int(nnz),
-        "build_ms": build_ms,
-        "repulsion_ms": rep_ms,
-        "attraction_roofline": {"bound": "hbm", "kernel": "attract_update (S3+S5)", "achieved": achieved,
-                                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
-                                "bytes_per_launch": att_bytes, "ms_per_launch": att_ms + hub_ms,
-                                "ms_split": {"rows_up_to_256_entries_and_update": att_ms, "hub_row_chunks": hub_ms},
-                                "l2": "flushed (320 MB write) before every step"},
-        "clocks": clk.summary(),
-        "fp32_vs_oracle_20k": {"nodes": int(sub.n), "grad_rel_l2": float(np.linalg.norm(G - oG) / np.linalg.norm(oG)),
-                               "kl_rel": abs(kl - okl) / okl, "Z_rel": abs(Z - oZ) / oZ},
+        "l2": "flushed (320 MB write) before every step",
+        "oracle_subgraph_nodes": int(sub.n),
     }
+    for prec, name in ((0, "fp32"), (1, "bf16")):
+        lay = pkg.Layout(profile=1, precision=prec)
+        tb = time.perf_counter()
+        lay.build_P(g.row_ptr, g.col, X)
+        build_ms = (time.perf_counter() - tb) * 1e3
+        n, nnz = lay.sizes()
+        lay.init_Y(synth.y_init(n, seed=args.seed))
+        for _ in range(2):
+            lay.step()
+        lay.sync()
+        lay.kernel_times(reset=True)
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            for k in range(args.rmat_steps):
+                with torch.cuda.stream(lay.stream):
+                    flush.fill_(float(k))
+                lay.step()
+            lay.sync()
+        kt = lay.kernel_times(reset=True)
+        lay.close()
+        att_ms = kt["attract_update"][0] / kt["attract_update"][1]
+        hub_ms = kt["attract_hubs"][0] / max(kt["attract_hubs"][1], 1)
+        rep_ms = kt["repulsion"][0] / kt["repulsion"][1]
+        # algorithmic bytes of one attraction+update launch: row_ptr, col and
+        # P once; per point F^r, update and gains read, Y_next, update and
+        # gains written, and Y_i read (FP32: 8 B; BF16: the 4-B shadow for
+        # the forces plus the 8-B master for the update, and a 4-B shadow
+        # write).  Neighbour gathers of Y hit L2 (16.8 MB FP32, 8.4 MB BF16).
+        if prec == 0:
+            att_bytes = 8 * (n + 1) + 8 * nnz + 7 * 8 * n
+        else:
+            att_bytes = 8 * (n + 1) + 6 * nnz + 8 * 8 * n
+        achieved = att_bytes / ((att_ms + hub_ms) * 1e-3) / 1e9
+        with pkg.Layout(precision=prec) as l2:
+            l2.build_P(sub.row_ptr, sub.col, Xs)
+            l2.init_Y(Ys)
+            G, Z = l2.gradient(1.0)
+            kl = l2.kl()
+        out[name] = {
+            "nnz_P": int(nnz),
+            "build_ms": build_ms,
+            "repulsion_ms": rep_ms,
+            "attraction_roofline": {"bound": "hbm", "kernel": "attract_update (S3+S5)", "achieved": achieved,
+                                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
+                                    "bytes_per_launch": att_bytes, "ms_per_launch": att_ms + hub_ms,
+                                    "ms_split": {"rows_and_update": att_ms, "hub_row_chunks": hub_ms}},
+            "clocks": clk.summary(),
+            "vs_fp64_oracle_20k": {"grad_rel_l2": float(np.linalg.norm(G - oG) / np.linalg.norm(oG)),
+                                   "kl_rel": abs(kl - okl) / okl, "Z_rel": abs(Z - oZ) / oZ},
+        }
+        log_fn(f"[bench] rmat {name}: attraction {att_ms + hub_ms:.3f} ms ({achieved:.0f} GB/s), "
+               f"repulsion {rep_ms:.1f} ms, grad err {out[name]['vs_fp64_oracle_20k']['grad_rel_l2']:.2e}")
+    return out
 
 
 def main():

@@ -79,9 +79,23 @@ typedef struct {
   float bisect_tol;        /* |H_i - ln perp| tolerance of the bisection, nats */
   int32_t bisect_max_iter; /* max entropy evaluations per row */
   uint64_t seed;           /* seed of tsgne_init_Y(ctx, NULL, ...) */
-  int32_t precision;       /* 0: FP32 storage of Y and P (the only value accepted) */
+  int32_t precision;       /* storage read by the force kernels (arithmetic is FP32, Z and KL
+                              FP64 in both): 0 = FP32 P and Y; 1 = BF16 copies of P and of
+                              the layout, rounded to nearest even from the FP32 values, which
+                              stay the optimiser's master copy and what every getter returns.
+                              Not an option of the paper; the batch API accepts 0 only. */
   int32_t profile;         /* 1: time every kernel with CUDA events (see tsgne_kernel_times) */
   int64_t spin_budget_cycles; /* bound on device-side waits (reserved; > 0) */
+  int32_t repulsion;       /* 0: exact all-pairs sums of Eq. 4 (default); 1: tree code, an
+                              approximation the paper does not use: points sorted along a
+                              Morton curve, binary radix tree, per group of 32 consecutive
+                              points a walk that takes a node with box side r and centre at
+                              distance d from the group's box as one interaction when
+                              r < theta * d; opened nodes of <= 16 points are summed exactly.
+                              Z and the forces are both approximated; the batch API accepts
+                              0 only */
+  float theta;             /* opening angle of the tree code, [0, 1] (default 0.5; 0 sums
+                              every pair exactly through the tree) */
 } tsgne_config;
 
 /* Fills *cfg with the defaults listed above (perplexity 30). */
@@ -191,9 +205,11 @@ tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update
 /*
  * Profiling (cfg.profile = 1): cumulative device time in ms and launch count
  * of each kernel class since the last reset, measured with CUDA events on
- * the context's stream.  Classes: 0 repulsion, 1 attraction+update,
- * 2 gradient export, 3 KL, 4 build, 5 repulsion slot reduction, 6 hub-row
- * attraction chunks.  ms and launches hold n entries (n <= 7).
+ * the context's stream.  Classes: 0 repulsion (the tree walk when
+ * cfg.repulsion = 1), 1 attraction+update, 2 gradient export, 3 KL, 4 build,
+ * 5 repulsion slot reduction, 6 hub-row attraction chunks, 7 tree build
+ * (bounding box, keys, sort, tree, summaries).  ms and launches hold n
+ * entries (n <= 8).
  * reset != 0 clears the counters after reading.  Synchronises.
  */
 tsgne_status tsgne_kernel_times(tsgne_ctx* ctx, double* ms, int64_t* launches, int32_t n, int32_t reset);

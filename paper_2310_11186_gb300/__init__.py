@@ -59,7 +59,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_PKG, "lib", "libtsgne.so")
 
 PTR_HOST, PTR_DEVICE = 0, 1
-KERNEL_CLASSES = ("repulsion", "attract_update", "gradient", "kl", "build", "reduce_slots", "attract_hubs")
+KERNEL_CLASSES = ("repulsion", "attract_update", "gradient", "kl", "build", "reduce_slots", "attract_hubs",
+                  "tree_build")
 
 STATUS = {
     0: "TSGNE_OK",
@@ -99,6 +100,8 @@ class Config(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("profile", ctypes.c_int32),
         ("spin_budget_cycles", ctypes.c_int64),
+        ("repulsion", ctypes.c_int32),
+        ("theta", ctypes.c_float),
     ]
 
 

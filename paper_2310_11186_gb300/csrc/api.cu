@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "storage.cuh"
 #include "tsgne_internal.cuh"
 
 namespace tsgne {
@@ -38,7 +39,7 @@ __global__ void k_cmp_i32(const int32_t* a, const int32_t* b, int64_t n, uint32_
     if (a[k] != b[k]) atomicOr(neq, 1u);
 }
 
-constexpr int kClasses = 7;  // repulsion, attraction+update, gradient, KL, build, slot reduction, hub rows
+constexpr int kClasses = 8;  // repulsion, attraction+update, gradient, KL, build, slot reduction, hub rows, tree build
 
 struct ProfRec {
   int cls;
@@ -72,6 +73,16 @@ struct tsgne_ctx {
   DevBuf<float2> Y[2];
   int cur = 0;
   DevBuf<float2> upd, gains, frep, fsum, grad;
+  // BF16 storage (cfg.precision = 1): P and a shadow of the layout, read by
+  // every force kernel; the FP32 master layout is what the update advances
+  bool bf16 = false;
+  DevBuf<tsgne::bf16> P16;
+  DevBuf<tsgne::bf162> Y16[2];
+  const void* Pread() const { return bf16 ? (const void*)P16.get() : (const void*)P.get(); }
+  const void* Yread(int k) const { return bf16 ? (const void*)Y16[k].get() : (const void*)Y[k].get(); }
+  // tree-code repulsion (cfg.repulsion = 1): reads the FP32 master layout
+  bool use_tree = false;
+  TreeBufs tree;
   HeavyStore hub;
   HeavyRows heavy() const { return hub.view(); }
   DevBuf<double> zpart, klpart;
@@ -81,8 +92,8 @@ struct tsgne_ctx {
 
   std::vector<ProfRec> pending;
   std::vector<cudaEvent_t> spare;
-  double prof_ms[kClasses] = {0, 0, 0, 0, 0, 0, 0};
-  int64_t prof_n[kClasses] = {0, 0, 0, 0, 0, 0, 0};
+  double prof_ms[kClasses] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t prof_n[kClasses] = {0, 0, 0, 0, 0, 0, 0, 0};
 
   ~tsgne_ctx() {
     reset_graphs();
@@ -217,10 +228,20 @@ tsgne_status prof_end(tsgne_ctx* ctx, ProfRec* rec) {
 tsgne_status enqueue_repulsion(tsgne_ctx* ctx, int advance) {
   const tsgne_config& c = ctx->cfg;
   ProfRec pr;
+  if (ctx->use_tree) {
+    ProfRec pb;
+    TS_TRY(prof_begin(ctx, 7, &pb));
+    TS_TRY(launch_tree_build(ctx->tree, ctx->Y[ctx->cur].get(), ctx->stream));
+    TS_TRY(prof_end(ctx, &pb));
+    TS_TRY(prof_begin(ctx, 0, &pr));
+    TS_TRY(launch_tree_walk(ctx->tree, c.theta, ctx->fsum.get(), ctx->sched.get(), advance, c.early_exag,
+                            c.ee_iters, c.momentum0, c.momentum1, ctx->stream));
+    return prof_end(ctx, &pr);
+  }
   TS_TRY(prof_begin(ctx, 0, &pr));
-  TS_TRY(launch_repulsion_sym(ctx->shape, ctx->n, ctx->Y[ctx->cur].get(), ctx->frep.get(), ctx->zpart.get(),
-                              ctx->sched.get(), advance, c.early_exag, c.ee_iters, c.momentum0, c.momentum1,
-                              ctx->stream));
+  TS_TRY(launch_repulsion_sym(ctx->shape, ctx->n, ctx->Yread(ctx->cur), ctx->bf16 ? 1 : 0, ctx->frep.get(),
+                              ctx->zpart.get(), ctx->sched.get(), advance, c.early_exag, c.ee_iters, c.momentum0,
+                              c.momentum1, ctx->stream));
   TS_TRY(prof_end(ctx, &pr));
   ProfRec pr2;
   TS_TRY(prof_begin(ctx, 5, &pr2));
@@ -229,26 +250,55 @@ tsgne_status enqueue_repulsion(tsgne_ctx* ctx, int advance) {
   return prof_end(ctx, &pr2);
 }
 
+// Reads of the current layout / P for the force kernels of the context.
+AttractArgs attract_args(tsgne_ctx* ctx) {
+  AttractArgs a;
+  a.n = ctx->n;
+  a.rp = ctx->rp.get();
+  a.col = ctx->col.get();
+  a.P = ctx->Pread();
+  a.p_bf16 = ctx->bf16 ? 1 : 0;
+  a.Yr = ctx->Yread(ctx->cur);
+  a.y_bf16 = ctx->bf16 ? 1 : 0;
+  a.Ym = ctx->Y[ctx->cur].get();
+  a.frep = ctx->fsum.get();
+  a.chunks = 1;
+  a.n_pad = ctx->shape.n_pad;
+  a.sched = ctx->sched.get();
+  a.hv = ctx->heavy();
+  return a;
+}
+
+// Refreshes the BF16 shadow of Y[k] (all n_pad points, sentinels included).
+tsgne_status sync_shadow(tsgne_ctx* ctx, int k) {
+  if (!ctx->bf16) return TSGNE_OK;
+  return launch_to_bf16(reinterpret_cast<const float*>(ctx->Y[k].get()), ctx->Y16[k].get(),
+                        2 * (int64_t)ctx->shape.n_pad, ctx->stream);
+}
+
 tsgne_status enqueue_step(tsgne_ctx* ctx) {
   TS_TRY(enqueue_repulsion(ctx, 1));
   ProfRec pr;
   // the layout is pulled into L2 before the gathers (hub chunks, then rows)
+  const int nxt = ctx->cur ^ 1;
+  AttractArgs a = attract_args(ctx);
+  a.Ynext = ctx->Y[nxt].get();
+  a.Ynext16 = ctx->bf16 ? (void*)ctx->Y16[nxt].get() : nullptr;
+  a.upd = ctx->upd.get();
+  a.gains = ctx->gains.get();
+  a.eta = ctx->eta;
+  a.min_gain = ctx->cfg.min_gain;
+  const int64_t ybytes = (int64_t)ctx->n * (ctx->bf16 ? 4 : 8);
   if (ctx->hub.chunks > 0) {
     ProfRec ph;
     TS_TRY(prof_begin(ctx, 6, &ph));
-    TS_TRY(launch_prefetch_l2(ctx->Y[ctx->cur].get(), (int64_t)ctx->n * 8, ctx->stream));
-    TS_TRY(launch_attract_heavy(ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(), ctx->heavy(),
-                                ctx->stream));
+    TS_TRY(launch_prefetch_l2(a.Yr, ybytes, ctx->stream));
+    TS_TRY(launch_attract_heavy(a, ctx->stream));
     TS_TRY(prof_end(ctx, &ph));
   }
   TS_TRY(prof_begin(ctx, 1, &pr));
-  if (ctx->hub.chunks == 0)
-    TS_TRY(launch_prefetch_l2(ctx->Y[ctx->cur].get(), (int64_t)ctx->n * 8, ctx->stream));
-  const int nxt = ctx->cur ^ 1;
-  TS_TRY(launch_attract_update(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
-                               ctx->Y[nxt].get(), ctx->upd.get(), ctx->gains.get(), ctx->fsum.get(), 1,
-                               ctx->shape.n_pad, ctx->sched.get(), ctx->eta, ctx->cfg.min_gain, ctx->heavy(),
-                               ctx->stream));
+  if (ctx->hub.chunks == 0) TS_TRY(launch_prefetch_l2(a.Yr, ybytes, ctx->stream));
+  TS_TRY(launch_attract_update(a, ctx->stream));
   TS_TRY(prof_end(ctx, &pr));
   ctx->cur = nxt;
   return TSGNE_OK;
@@ -266,6 +316,10 @@ tsgne_status check_flags(tsgne_ctx* ctx) {
   if (h.flags & kFlagNonfiniteY) {
     last_msg() = "the layout became non-finite";
     return TSGNE_ERR_NONFINITE;
+  }
+  if (h.flags & kFlagTreeOverflow) {
+    last_msg() = "tree walk stack overflow (results of the pass are incomplete)";
+    return TSGNE_ERR_CUDA;
   }
   return TSGNE_OK;
 }
@@ -307,11 +361,29 @@ tsgne_status alloc_layout(tsgne_ctx* ctx) {
   TS_TRY(ctx->gains.alloc(np));
   TS_TRY(ctx->grad.alloc(np));
   TS_TRY(ctx->fsum.alloc(np));
-  TS_TRY(ctx->frep.alloc(np * (size_t)ctx->shape.chunks));
-  TS_TRY(ctx->zpart.alloc((size_t)ctx->shape.units));
+  ctx->use_tree = ctx->cfg.repulsion == 1;
+  if (ctx->use_tree) {
+    ctx->frep = DevBuf<float2>();
+    ctx->zpart = DevBuf<double>();
+    TS_TRY(ctx->tree.alloc(ctx->n, ctx->sms));
+  } else {
+    ctx->tree = TreeBufs();
+    TS_TRY(ctx->frep.alloc(np * (size_t)ctx->shape.chunks));
+    TS_TRY(ctx->zpart.alloc((size_t)ctx->shape.units));
+  }
   TS_TRY(ctx->klpart.alloc(2 * (size_t)kl_partial_count(ctx->sms)));
   TS_TRY(launch_fill_sentinel(ctx->Y[0].get(), 0, (int)np, ctx->stream));
   TS_TRY(launch_fill_sentinel(ctx->Y[1].get(), 0, (int)np, ctx->stream));
+  ctx->bf16 = ctx->cfg.precision == 1;
+  if (ctx->bf16) {
+    TS_TRY(ctx->Y16[0].alloc(np));
+    TS_TRY(ctx->Y16[1].alloc(np));
+    TS_TRY(sync_shadow(ctx, 0));
+    TS_TRY(sync_shadow(ctx, 1));
+  } else {
+    ctx->Y16[0] = DevBuf<tsgne::bf162>();
+    ctx->Y16[1] = DevBuf<tsgne::bf162>();
+  }
   const float ee = ctx->cfg.early_exag > 0.f ? ctx->cfg.early_exag : 1.f;
   ctx->eta = ctx->cfg.learning_rate > 0.f ? ctx->cfg.learning_rate : std::fmax((float)ctx->n / ee / 4.0f, 50.0f);
   return TSGNE_OK;
@@ -328,6 +400,12 @@ tsgne_status install(tsgne_ctx* ctx, int n, int64_t nnz, DevBuf<int64_t>& rp, De
   ctx->col = std::move(col);
   ctx->P = std::move(P);
   TS_TRY(alloc_layout(ctx));
+  if (ctx->bf16) {
+    TS_TRY(ctx->P16.alloc((size_t)nnz));
+    TS_TRY(launch_to_bf16(ctx->P.get(), ctx->P16.get(), nnz, ctx->stream));
+  } else {
+    ctx->P16 = DevBuf<tsgne::bf16>();
+  }
   TS_TRY(find_heavy_rows(n, ctx->rp.get(), ctx->hub, ctx->stream));
   ctx->have_P = true;
   return TSGNE_OK;
@@ -375,6 +453,8 @@ void tsgne_config_default(tsgne_config* cfg) {
   cfg->precision = 0;
   cfg->profile = 0;
   cfg->spin_budget_cycles = 2000000000LL;
+  cfg->repulsion = 0;
+  cfg->theta = 0.5f;
 }
 
 const char* tsgne_status_string(tsgne_status s) {
@@ -397,10 +477,13 @@ tsgne_status tsgne_create(tsgne_ctx** out, const tsgne_config* cfg, void* cuda_s
   *out = nullptr;
   tsgne_config c;
   if (cfg) c = *cfg; else tsgne_config_default(&c);
-  if (!(c.perplexity > 1.f) || c.k_nn < 0 || c.k_nn > 256 || c.precision != 0 || c.ee_iters < 0 || !(c.min_gain >= 0.f) ||
-      !(c.bisect_tol > 0.f) || c.bisect_max_iter < 1 || !std::isfinite(c.early_exag) || !std::isfinite(c.momentum0) ||
-      !std::isfinite(c.momentum1)) {
-    last_msg() = "invalid configuration (perplexity must exceed 1; k_nn in [0, 256]; precision 0)";
+  if (!(c.perplexity > 1.f) || c.k_nn < 0 || c.k_nn > 256 || (c.precision != 0 && c.precision != 1) ||
+      c.ee_iters < 0 || !(c.min_gain >= 0.f) || !(c.bisect_tol > 0.f) || c.bisect_max_iter < 1 ||
+      !std::isfinite(c.early_exag) || !std::isfinite(c.momentum0) || !std::isfinite(c.momentum1) ||
+      (c.repulsion != 0 && c.repulsion != 1) || !(c.theta >= 0.f && c.theta <= 1.f)) {
+    last_msg() =
+        "invalid configuration (perplexity must exceed 1; k_nn in [0, 256]; precision 0 or 1; repulsion 0 or 1; "
+        "theta in [0, 1])";
     return TSGNE_ERR_INVALID_ARG;
   }
   tsgne_ctx* ctx = new (std::nothrow) tsgne_ctx();
@@ -573,6 +656,7 @@ tsgne_status tsgne_init_Y(tsgne_ctx* ctx, const float* Y0, int32_t ptr_kind) {
   } else {
     API_TRY(ctx, launch_init_Y(ctx->n, ctx->cfg.seed, 1e-4f, ctx->Y[0].get(), ctx->stream));
   }
+  API_TRY(ctx, sync_shadow(ctx, 0));
   API_TRY(ctx, reset_optimizer(ctx, 0));
   API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->have_Y = true;
@@ -619,8 +703,9 @@ tsgne_status tsgne_kl(tsgne_ctx* ctx, double* kl_out) {
   API_TRY(ctx, enqueue_repulsion(ctx, 0));
   ProfRec pr;
   API_TRY(ctx, prof_begin(ctx, 3, &pr));
-  API_TRY(ctx, launch_kl(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
-                         ctx->klpart.get(), kl_partial_count(ctx->sms), ctx->sched.get(), ctx->stream));
+  API_TRY(ctx, launch_kl(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->Pread(), ctx->bf16 ? 1 : 0,
+                         ctx->Yread(ctx->cur), ctx->bf16 ? 1 : 0, ctx->klpart.get(), kl_partial_count(ctx->sms),
+                         ctx->sched.get(), ctx->stream));
   API_TRY(ctx, prof_end(ctx, &pr));
   Sched h;
   API_TRY(ctx, read_sched(ctx, &h));
@@ -637,9 +722,7 @@ tsgne_status tsgne_gradient(tsgne_ctx* ctx, float alpha, float* g_out, double* z
   API_TRY(ctx, enqueue_repulsion(ctx, 0));
   ProfRec pr;
   API_TRY(ctx, prof_begin(ctx, 2, &pr));
-  API_TRY(ctx, launch_gradient(ctx->n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->Y[ctx->cur].get(),
-                               ctx->fsum.get(), 1, ctx->shape.n_pad, ctx->sched.get(), alpha, ctx->heavy(),
-                               ctx->grad.get(), ctx->stream));
+  API_TRY(ctx, launch_gradient(attract_args(ctx), alpha, ctx->grad.get(), ctx->stream));
   API_TRY(ctx, prof_end(ctx, &pr));
   API_TRY(ctx, copy_out(g_out, ctx->grad.get(), sizeof(float2) * (size_t)ctx->n, ptr_kind, ctx->stream));
   Sched h;
@@ -683,6 +766,7 @@ tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update
   ctx->cur = 0;
   API_TRY(ctx, reset_optimizer(ctx, iter));
   API_TRY(ctx, copy_in(ctx->Y[0].get(), Y, bytes, ptr_kind, ctx->stream));
+  API_TRY(ctx, sync_shadow(ctx, 0));
   if (update) API_TRY(ctx, copy_in(ctx->upd.get(), update, bytes, ptr_kind, ctx->stream));
   if (gains) API_TRY(ctx, copy_in(ctx->gains.get(), gains, bytes, ptr_kind, ctx->stream));
   API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -693,7 +777,7 @@ tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update
 tsgne_status tsgne_kernel_times(tsgne_ctx* ctx, double* ms, int64_t* launches, int32_t n, int32_t reset) {
   TS_TRY(enter(ctx));
   DeviceGuard dg(ctx->device);
-  if (n < 0 || n > kClasses) return fail(ctx, TSGNE_ERR_INVALID_ARG, "n outside [0, 7]");
+  if (n < 0 || n > kClasses) return fail(ctx, TSGNE_ERR_INVALID_ARG, "n outside [0, 8]");
   API_TRY(ctx, prof_collect(ctx));
   for (int k = 0; k < n; ++k) {
     if (ms) ms[k] = ctx->prof_ms[k];

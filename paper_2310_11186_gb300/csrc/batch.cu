@@ -418,7 +418,7 @@ tsgne_status tsgne_batch_create(tsgne_batch** out, const tsgne_config* cfg, int3
   *out = nullptr;
   tsgne_config c;
   if (cfg) c = *cfg; else tsgne_config_default(&c);
-  if (!(c.perplexity > 1.f) || c.k_nn < 0 || c.k_nn > 256 || c.precision != 0 || c.ee_iters < 0)
+  if (!(c.perplexity > 1.f) || c.k_nn < 0 || c.k_nn > 256 || c.precision != 0 || c.repulsion != 0 || c.ee_iters < 0)
     return TSGNE_ERR_INVALID_ARG;
   if (!(tile_warps == 0 || tile_warps == 1 || tile_warps == 2 || tile_warps == 4 || tile_warps == 8))
     return TSGNE_ERR_INVALID_ARG;

@@ -23,6 +23,7 @@
 
 #include "reduce.cuh"
 #include "row_update.cuh"
+#include "storage.cuh"
 #include "tsgne_internal.cuh"
 
 namespace tsgne {
@@ -36,13 +37,13 @@ constexpr int kG = 8;  // lanes per row
 // attraction of the CTA's rows into shared memory; (2) one thread per row
 // reads F^r, the optimiser state and Y_i and writes the update, so the state
 // traffic is fully coalesced.
-template <int G, bool EXPORT>
+template <int G, bool EXPORT, class PT, class YT>
 __global__ void __launch_bounds__(kAttrCta)
-    k_attract(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ P,
-              const float2* __restrict__ Ycur, float2* __restrict__ Ynext, float2* __restrict__ upd,
-              float2* __restrict__ gains, const float2* __restrict__ frep_part, int chunks, int n_pad,
-              Sched* sched, float eta, float min_gain, float alpha_export, float2* __restrict__ g_out,
-              HeavyRows hv) {
+    k_attract(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const PT* __restrict__ P,
+              const YT* __restrict__ Ycur, const float2* __restrict__ Ym, float2* __restrict__ Ynext,
+              bf162* __restrict__ Ynext16, float2* __restrict__ upd, float2* __restrict__ gains,
+              const float2* __restrict__ frep_part, int chunks, int n_pad, Sched* sched, float eta, float min_gain,
+              float alpha_export, float2* __restrict__ g_out, HeavyRows hv) {
   constexpr int NGRP = kAttrCta / G;
   __shared__ float2 sfa[kAttrCta];
   __shared__ int64_t srp[kAttrCta + 1];
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kAttrCta)
           }
         }
       } else {
-        attract_entries<G>(srp[r], srp[r + 1], col, P, Ycur, i, lane, Ycur[i], ax, ay);
+        attract_entries<G, PT, YT>(srp[r], srp[r + 1], col, P, Ycur, i, lane, ld_y(Ycur, i), ax, ay);
       }
     }
     ax = group_sum<G>(ax);
@@ -79,7 +80,6 @@ __global__ void __launch_bounds__(kAttrCta)
   const int64_t i = row0 + threadIdx.x;
   if (i >= n) return;
   const float2 fa = sfa[threadIdx.x];
-  const float2 yi = Ycur[i];
   float rx = 0.f, ry = 0.f;
   for (int c = 0; c < chunks; ++c) {
     const float2 f = frep_part[(size_t)c * n_pad + i];
@@ -96,26 +96,28 @@ __global__ void __launch_bounds__(kAttrCta)
   }
   const float mu = sched->mu;
   float2 u = upd[i], gn = gains[i];
-  const float2 y = optimizer_step(gx, gy, u, gn, mu, eta, min_gain, yi);
+  const float2 y = optimizer_step(gx, gy, u, gn, mu, eta, min_gain, Ym[i]);
   upd[i] = u;
   gains[i] = gn;
   Ynext[i] = y;
+  if (Ynext16) Ynext16[i] = __float22bfloat162_rn(y);
   if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&sched->flags, kFlagNonfiniteY);
 }
 
 // Attraction of the long rows (more than kHeavyDeg entries), in chunks of at
 // most kHeavyChunk entries: one warp per chunk, xor-butterfly reduction
 // (fixed order), so no group of lanes serialises on a hub row.
+template <class PT, class YT>
 __global__ void __launch_bounds__(256)
     k_attract_heavy(HeavyRows hv, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                    const float* __restrict__ P, const float2* __restrict__ Y) {
+                    const PT* __restrict__ P, const YT* __restrict__ Y) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < hv.chunks; c += warps) {
     const int64_t i = hv.chunk_row[c];
-    const float2 yi = Y[i];
+    const float2 yi = ld_y(Y, i);
     float ax = 0.f, ay = 0.f;
-    attract_entries<32>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Y, i, lane, yi, ax, ay);
+    attract_entries<32, PT, YT>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Y, i, lane, yi, ax, ay);
     ax = group_sum<32>(ax);
     ay = group_sum<32>(ay);
     if (lane == 0) hv.fa[c] = make_float2(ax, ay);
@@ -167,18 +169,19 @@ __global__ void k_prefetch_l2(const char* __restrict__ p, int64_t bytes) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p + o));
 }
 
+template <class PT, class YT>
 __global__ void __launch_bounds__(kAttrCta)
-    k_kl(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ P,
-         const float2* __restrict__ Y, double* __restrict__ parts, Sched* sched) {
+    k_kl(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const PT* __restrict__ P,
+         const YT* __restrict__ Y, double* __restrict__ parts, Sched* sched) {
   double s1 = 0.0, s2 = 0.0;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
-    const float2 yi = Y[i];
+    const float2 yi = ld_y(Y, i);
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) {
-      const float p = P[e];
+      const float p = ld_p(P, e);
       if (!(p > 0.f)) continue;
-      const float2 yj = Y[col[e]];
+      const float2 yj = ld_y(Y, col[e]);
       const float dx = yi.x - yj.x, dy = yi.y - yj.y;
       // ln(p / w) = ln p + ln(1 + d^2)
       s1 += (double)p * ((double)logf(p) + (double)log1pf(fmaf(dy, dy, dx * dx)));
@@ -232,6 +235,12 @@ __global__ void k_fill2(float2* a, int64_t lo, int64_t hi, float v) {
   for (int64_t k = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < hi; k += stride) a[k] = make_float2(v, v);
 }
 
+__global__ void k_to_bf16(const float* __restrict__ in, bf16* __restrict__ out, int64_t count) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride)
+    out[k] = __float2bfloat16_rn(in[k]);
+}
+
 int grid_rows(int64_t n, int per_cta) {
   int64_t g = (n + per_cta - 1) / per_cta;
   return (int)(g < 1 ? 1 : g);
@@ -248,43 +257,11 @@ tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad
   return TSGNE_OK;
 }
 
-tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Ycur,
-                                   float2* Ynext, float2* upd, float2* gains, const float2* frep_part, int chunks,
-                                   int n_pad, Sched* sched, float eta, float min_gain, const HeavyRows& hv,
-                                   cudaStream_t s) {
-  const int grid = grid_rows(n, kAttrCta);
-  k_attract<kG, false><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Ycur, Ynext, upd, gains, frep_part, chunks, n_pad,
-                                                 sched, eta, min_gain, 0.f, nullptr, hv);
-  TS_CUDA(cudaGetLastError());
-  return TSGNE_OK;
-}
-
-tsgne_status launch_gradient(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
-                             const float2* frep_part, int chunks, int n_pad, const Sched* sched, float alpha,
-                             const HeavyRows& hv, float2* g, cudaStream_t s) {
-  TS_TRY(launch_prefetch_l2(Y, (int64_t)n * 8, s));
-  TS_TRY(launch_attract_heavy(rp, col, P, Y, hv, s));
-  const int grid = grid_rows(n, kAttrCta);
-  k_attract<kG, true><<<grid, kAttrCta, 0, s>>>(n, rp, col, P, Y, nullptr, nullptr, nullptr, frep_part, chunks,
-                                                n_pad, const_cast<Sched*>(sched), 0.f, 0.f, alpha, g, hv);
-  TS_CUDA(cudaGetLastError());
-  return TSGNE_OK;
-}
-
 tsgne_status launch_prefetch_l2(const void* p, int64_t bytes, cudaStream_t s) {
   if (bytes < (1 << 20)) return TSGNE_OK;  // small layouts stay in L2 anyway
   const int64_t lines = (bytes + 127) / 128;
   const int g = (int)((lines + 255) / 256 < 2048 ? (lines + 255) / 256 : 2048);
   k_prefetch_l2<<<g, 256, 0, s>>>(static_cast<const char*>(p), bytes);
-  TS_CUDA(cudaGetLastError());
-  return TSGNE_OK;
-}
-
-tsgne_status launch_attract_heavy(const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
-                                  const HeavyRows& hv, cudaStream_t s) {
-  if (hv.chunks <= 0) return TSGNE_OK;
-  const int g = (hv.chunks + 7) / 8 < 16384 ? (hv.chunks + 7) / 8 : 16384;
-  k_attract_heavy<<<g, 256, 0, s>>>(hv, rp, col, P, Y);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }
@@ -346,9 +323,74 @@ tsgne_status find_heavy_rows(int n, const int64_t* rp, HeavyStore& hs, cudaStrea
   return TSGNE_OK;
 }
 
-tsgne_status launch_kl(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
-                       double* partials, int nparts, Sched* sched, cudaStream_t s) {
-  k_kl<<<nparts, kAttrCta, 0, s>>>(n, rp, col, P, Y, partials, sched);
+tsgne_status launch_kl(int n, const int64_t* rp, const int32_t* col, const void* P, int p_bf16, const void* Y,
+                       int y_bf16, double* partials, int nparts, Sched* sched, cudaStream_t s) {
+  if (p_bf16 && y_bf16)
+    k_kl<bf16, bf162><<<nparts, kAttrCta, 0, s>>>(n, rp, col, static_cast<const bf16*>(P),
+                                                  static_cast<const bf162*>(Y), partials, sched);
+  else if (!p_bf16 && !y_bf16)
+    k_kl<float, float2><<<nparts, kAttrCta, 0, s>>>(n, rp, col, static_cast<const float*>(P),
+                                                    static_cast<const float2*>(Y), partials, sched);
+  else {
+    last_msg() = "KL needs P and Y in the same storage precision";
+    return TSGNE_ERR_INVALID_ARG;
+  }
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+namespace {
+
+template <bool EXPORT, class PT, class YT>
+tsgne_status attract_t(const AttractArgs& a, float alpha, float2* g, cudaStream_t s) {
+  const int grid = grid_rows(a.n, kAttrCta);
+  k_attract<kG, EXPORT, PT, YT><<<grid, kAttrCta, 0, s>>>(
+      a.n, a.rp, a.col, static_cast<const PT*>(a.P), static_cast<const YT*>(a.Yr), a.Ym, a.Ynext,
+      static_cast<bf162*>(a.Ynext16), a.upd, a.gains, a.frep, a.chunks, a.n_pad, a.sched, a.eta, a.min_gain, alpha,
+      g, a.hv);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+template <bool EXPORT>
+tsgne_status attract_dispatch(const AttractArgs& a, float alpha, float2* g, cudaStream_t s) {
+  if (a.p_bf16 && a.y_bf16) return attract_t<EXPORT, bf16, bf162>(a, alpha, g, s);
+  if (!a.p_bf16 && !a.y_bf16) return attract_t<EXPORT, float, float2>(a, alpha, g, s);
+  last_msg() = "P and Y must share a storage precision";
+  return TSGNE_ERR_INVALID_ARG;
+}
+
+template <class PT, class YT>
+tsgne_status heavy_t(const AttractArgs& a, cudaStream_t s) {
+  const int g = (a.hv.chunks + 7) / 8 < 16384 ? (a.hv.chunks + 7) / 8 : 16384;
+  k_attract_heavy<PT, YT><<<g, 256, 0, s>>>(a.hv, a.rp, a.col, static_cast<const PT*>(a.P),
+                                            static_cast<const YT*>(a.Yr));
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
+
+}  // namespace
+
+tsgne_status launch_attract_update(const AttractArgs& a, cudaStream_t s) { return attract_dispatch<false>(a, 0.f, nullptr, s); }
+
+tsgne_status launch_attract_heavy(const AttractArgs& a, cudaStream_t s) {
+  if (a.hv.chunks <= 0) return TSGNE_OK;
+  if (a.p_bf16 && a.y_bf16) return heavy_t<bf16, bf162>(a, s);
+  if (!a.p_bf16 && !a.y_bf16) return heavy_t<float, float2>(a, s);
+  last_msg() = "P and Y must share a storage precision";
+  return TSGNE_ERR_INVALID_ARG;
+}
+
+tsgne_status launch_gradient(const AttractArgs& a, float alpha, float2* g, cudaStream_t s) {
+  TS_TRY(launch_prefetch_l2(a.Yr, (int64_t)a.n * (a.y_bf16 ? 4 : 8), s));
+  TS_TRY(launch_attract_heavy(a, s));
+  return attract_dispatch<true>(a, alpha, g, s);
+}
+
+tsgne_status launch_to_bf16(const float* in, void* out, int64_t count, cudaStream_t s) {
+  if (count <= 0) return TSGNE_OK;
+  const int g = grid_rows(count, 256) < 8192 ? grid_rows(count, 256) : 8192;
+  k_to_bf16<<<g, 256, 0, s>>>(in, static_cast<bf16*>(out), count);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }

@@ -39,9 +39,9 @@ namespace tsgne {
 
 namespace {
 
-template <int W>
+template <int W, class YT>
 __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
-    k_repulsion_sym(const float2* __restrict__ Y, int n, int nt, int n_pad, float2* __restrict__ part,
+    k_repulsion_sym(const YT* __restrict__ Y, int n, int nt, int n_pad, float2* __restrict__ part,
                     double* __restrict__ zunit, Sched* sched, int advance, float ee, int ee_iters, float mom0,
                     float mom1) {
   constexpr int T = W * 32 * kRI;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
     __syncthreads();
     const int u = s_unit, a = s_a, b = s_b;
     if (u >= units) break;
-    const double zt = sym_unit<W>(Y, n, n_pad, part, a, b, sj, sacc);
+    const double zt = sym_unit<W, YT>(Y, n, n_pad, part, a, b, sj, sacc);
     const double zb = block_sum_d(zt);
     if (tid == 0) zunit[u] = zb;
     __syncthreads();  // shared tiles are rewritten by the next unit
@@ -91,16 +91,23 @@ size_t smem_bytes() {
 
 template <int W>
 tsgne_status prepare() {
-  TS_CUDA(cudaFuncSetAttribute(k_repulsion_sym<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TS_CUDA(cudaFuncSetAttribute(k_repulsion_sym<W, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_bytes<W>()));
+  TS_CUDA(cudaFuncSetAttribute(k_repulsion_sym<W, bf162>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_bytes<W>()));
   return TSGNE_OK;
 }
 
 template <int W>
-tsgne_status launch(const RepShape& sh, int n, const float2* Y, float2* part, double* zunit, Sched* sched,
+tsgne_status launch(const RepShape& sh, int n, const void* Y, int y_bf16, float2* part, double* zunit, Sched* sched,
                     int advance, float ee, int ee_iters, float mom0, float mom1, cudaStream_t s) {
-  k_repulsion_sym<W><<<sh.grid, W * 32, sh.smem, s>>>(Y, n, sh.chunks, sh.n_pad, part, zunit, sched, advance, ee,
-                                                      ee_iters, mom0, mom1);
+  if (y_bf16)
+    k_repulsion_sym<W, bf162><<<sh.grid, W * 32, sh.smem, s>>>(static_cast<const bf162*>(Y), n, sh.chunks, sh.n_pad,
+                                                               part, zunit, sched, advance, ee, ee_iters, mom0, mom1);
+  else
+    k_repulsion_sym<W, float2><<<sh.grid, W * 32, sh.smem, s>>>(static_cast<const float2*>(Y), n, sh.chunks,
+                                                                sh.n_pad, part, zunit, sched, advance, ee, ee_iters,
+                                                                mom0, mom1);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }
@@ -149,14 +156,14 @@ tsgne_status repulsion_sym_prepare(const RepShape& sh) {
   }
 }
 
-tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const float2* Y, float2* frep_part, double* zpart,
-                                  Sched* sched, int advance, float ee, int ee_iters, float mom0, float mom1,
-                                  cudaStream_t s) {
+tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, float2* frep_part,
+                                  double* zpart, Sched* sched, int advance, float ee, int ee_iters, float mom0,
+                                  float mom1, cudaStream_t s) {
   switch (sh.warps) {
-    case 8: return launch<8>(sh, n, Y, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
-    case 4: return launch<4>(sh, n, Y, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
-    case 2: return launch<2>(sh, n, Y, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
-    default: return launch<1>(sh, n, Y, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+    case 8: return launch<8>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+    case 4: return launch<4>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+    case 2: return launch<2>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+    default: return launch<1>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
   }
 }
 

@@ -6,6 +6,8 @@
 
 #include <cstdint>
 
+#include "storage.cuh"
+
 namespace tsgne {
 
 // This lane's share of F^a_i = sum_{j in N(i)} p_ij w_ij (y_i - y_j),
@@ -13,9 +15,9 @@ namespace tsgne {
 // Entries [a, b) of the row; 4 entries per lane are in flight at once (their
 // column / P loads, then their gathers), accumulated in entry order, so the
 // result is the same as one entry at a time.
-template <int G>
+template <int G, class PT = float, class YT = float2>
 __device__ __forceinline__ void attract_entries(int64_t a, int64_t b, const int32_t* __restrict__ col,
-                                                const float* __restrict__ P, const float2* __restrict__ Y,
+                                                const PT* __restrict__ P, const YT* __restrict__ Y,
                                                 int64_t i, int lane, float2 yi, float& ax, float& ay) {
   constexpr int U = 4;
   for (int64_t e0 = a + lane; e0 < b; e0 += U * G) {
@@ -26,11 +28,11 @@ __device__ __forceinline__ void attract_entries(int64_t a, int64_t b, const int3
       const int64_t e = e0 + (int64_t)u * G;
       const bool ok = e < b;
       j[u] = ok ? col[e] : (int32_t)i;
-      p[u] = ok ? P[e] : 0.f;
+      p[u] = ok ? ld_p(P, e) : 0.f;
     }
     float2 yj[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) yj[u] = Y[j[u]];
+    for (int u = 0; u < U; ++u) yj[u] = ld_y(Y, j[u]);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (e0 + (int64_t)u * G < b) {

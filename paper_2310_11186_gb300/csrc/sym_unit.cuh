@@ -4,6 +4,7 @@
 #pragma once
 
 #include "f32x2.cuh"
+#include "storage.cuh"
 #include "tsgne_internal.cuh"
 
 namespace tsgne {
@@ -52,8 +53,8 @@ __device__ __forceinline__ void ring_pair(const float4 q, float& accx, float& ac
 // the unit's Z (ordered pairs; the diagonal unit includes the w_ii = 1 terms
 // of its real points).  Every thread of the CTA must call it; it ends with the
 // shared tiles free for reuse only after a __syncthreads by the caller.
-template <int W>
-__device__ __forceinline__ double sym_unit(const float2* __restrict__ Y, int n, int n_pad, float2* __restrict__ part,
+template <int W, class YT = float2>
+__device__ __forceinline__ double sym_unit(const YT* __restrict__ Y, int n, int n_pad, float2* __restrict__ part,
                                            int a, int b, float4* sj, float2* sacc) {
   constexpr int T = W * 32 * kRI;
   constexpr int G = T / kGroup;  // = 4W groups
@@ -62,7 +63,7 @@ __device__ __forceinline__ double sym_unit(const float2* __restrict__ Y, int n, 
 
   // j tile b into shared memory
   for (int k = tid; k < T; k += W * 32) {
-    const float2 p = Y[(size_t)b * T + k];
+    const float2 p = ld_y(Y, (size_t)b * T + k);
     sj[k] = make_float4(-p.x, -p.x, -p.y, -p.y);
     sacc[k] = make_float2(0.f, 0.f);
   }
@@ -71,8 +72,8 @@ __device__ __forceinline__ double sym_unit(const float2* __restrict__ Y, int n, 
   u64 X2[kH], Y2[kH], FX[kH], FY[kH], Z2[kH];
 #pragma unroll
   for (int h = 0; h < kH; ++h) {
-    const float2 p0 = Y[ibase + (2 * h) * 32];
-    const float2 p1 = Y[ibase + (2 * h + 1) * 32];
+    const float2 p0 = ld_y(Y, ibase + (2 * h) * 32);
+    const float2 p1 = ld_y(Y, ibase + (2 * h + 1) * 32);
     X2[h] = pk(p0.x, p1.x);
     Y2[h] = pk(p0.y, p1.y);
     FX[h] = FY[h] = Z2[h] = 0ull;

@@ -30,6 +30,7 @@ struct Sched {
 
 constexpr uint32_t kFlagNonfiniteY = 1u;
 constexpr uint32_t kFlagNonfiniteP = 2u;
+constexpr uint32_t kFlagTreeOverflow = 4u;
 
 // Geometry of one repulsion pass (see repulsion.cu and repulsion_sym.cu).
 struct RepShape {
@@ -142,9 +143,10 @@ tsgne_status launch_repulsion(const RepShape& sh, int n, const float2* Y, float2
 // outside stream capture, once per shape).
 RepShape repulsion_shape_sym(int n, int sm_count);
 tsgne_status repulsion_sym_prepare(const RepShape& sh);
-tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const float2* Y, float2* frep_part, double* zpart,
-                                  Sched* sched, int advance, float ee, int ee_iters, float mom0, float mom1,
-                                  cudaStream_t s);
+// Y is float2[n_pad] (y_bf16 = 0) or __nv_bfloat162[n_pad] (y_bf16 = 1).
+tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, float2* frep_part,
+                                  double* zpart, Sched* sched, int advance, float ee, int ee_iters, float mom0,
+                                  float mom1, cudaStream_t s);
 
 // ------------------------------------------------------------ iteration
 // Rows with more than kHeavyDeg entries get their attraction from chunks of
@@ -185,26 +187,84 @@ struct HeavyStore {
 tsgne_status find_heavy_rows(int n, const int64_t* rp, HeavyStore& hs, cudaStream_t s);
 // L2 prefetch of a buffer (no-op below 1 MB).
 tsgne_status launch_prefetch_l2(const void* p, int64_t bytes, cudaStream_t s);
-// The hub-row chunks alone (the update kernel then reads their sums).
-tsgne_status launch_attract_heavy(const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
-                                  const HeavyRows& hv, cudaStream_t s);
+
 // F^r[i] = sum_k part[k * n_pad + i] for k < slots, in slot order.
 tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad, float2* out, cudaStream_t s);
 // Attraction + gradient + optimiser update: reads Ycur, writes Ynext.
-tsgne_status launch_attract_update(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Ycur,
-                                   float2* Ynext, float2* upd, float2* gains, const float2* frep_part, int chunks,
-                                   int n_pad, Sched* sched, float eta, float min_gain, const HeavyRows& hv,
-                                   cudaStream_t s);
+// Arguments of the attraction / update pass.  P is float[nnz] (p_bf16 = 0)
+// or bf16[nnz]; Yr is the layout the forces read: float2 (y_bf16 = 0) or the
+// bf16x2 shadow; Ym is the FP32 master layout the update advances into Ynext
+// (and, if not NULL, its bf16x2 shadow Ynext16).
+struct AttractArgs {
+  int n = 0;
+  const int64_t* rp = nullptr;
+  const int32_t* col = nullptr;
+  const void* P = nullptr;
+  int p_bf16 = 0;
+  const void* Yr = nullptr;
+  int y_bf16 = 0;
+  const float2* Ym = nullptr;
+  float2* Ynext = nullptr;
+  void* Ynext16 = nullptr;
+  float2* upd = nullptr;
+  float2* gains = nullptr;
+  const float2* frep = nullptr;
+  int chunks = 1;
+  int n_pad = 0;
+  Sched* sched = nullptr;
+  float eta = 0.f;
+  float min_gain = 0.f;
+  HeavyRows hv;
+};
+tsgne_status launch_attract_update(const AttractArgs& a, cudaStream_t s);
 // Gradient export g = 4 (alpha F^a - F^r / Z) without state change.
-tsgne_status launch_gradient(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
-                             const float2* frep_part, int chunks, int n_pad, const Sched* sched, float alpha,
-                             const HeavyRows& hv, float2* g, cudaStream_t s);
+tsgne_status launch_gradient(const AttractArgs& a, float alpha, float2* g, cudaStream_t s);
+// Hub-row chunks for the layout a reads (the update then adds their sums).
+tsgne_status launch_attract_heavy(const AttractArgs& a, cudaStream_t s);
 // KL terms: sched->red[0] = sum p ln(p / w), sched->red[1] = sum p.
-tsgne_status launch_kl(int n, const int64_t* rp, const int32_t* col, const float* P, const float2* Y,
-                       double* partials, int nparts, Sched* sched, cudaStream_t s);
+tsgne_status launch_kl(int n, const int64_t* rp, const int32_t* col, const void* P, int p_bf16, const void* Y,
+                       int y_bf16, double* partials, int nparts, Sched* sched, cudaStream_t s);
+// FP32 -> BF16 copies (round to nearest even); count scalars.
+tsgne_status launch_to_bf16(const float* in, void* out, int64_t count, cudaStream_t s);
 int kl_partial_count(int sm_count);
 // Y0 ~ N(0, sigma^2) from a seed (SplitMix64 counter mode + Box-Muller).
 tsgne_status launch_init_Y(int n, uint64_t seed, float sigma, float2* Y, cudaStream_t s);
+// ------------------------------------------------- tree-code repulsion
+// (repulsion_tree.cu): an opened node of at most this many points is summed
+// exactly over its points.
+constexpr int kTreeBucket = 16;
+
+struct TreeState {
+  float lo_x, lo_y, scale, pad;  // bounding square of the last pass
+  uint32_t box_done, walk_done;  // last-CTA counters
+};
+
+// Device buffers of the tree code for n points.
+struct TreeBufs {
+  int n = 0, nchunks = 0, ngroups = 0, box_blocks = 0;
+  DevBuf<uint32_t> keys[2];
+  DevBuf<int32_t> vals[2];    // vals[0] after a build: sorted position -> point
+  DevBuf<float2> ys;          // layout in sorted order
+  DevBuf<int32_t> counts;     // radix counts, digit-major
+  DevBuf<int64_t> offs, scan_scr;
+  DevBuf<float4> nodeA;       // internal node: centre x, y, r2, count
+  DevBuf<int4> nodeB;         // internal node: left, right, first, last
+  DevBuf<float4> box;         // internal node: x0, y0, x1, y1
+  DevBuf<float2> sum;         // internal node: coordinate sums
+  DevBuf<uint32_t> flags;     // bottom-up arrival counters (kept at zero between passes)
+  DevBuf<int32_t> parent;     // internal nodes [0, n - 1), leaves after
+  DevBuf<float4> boxpart;
+  DevBuf<double> zgroup;      // FP64 Z partial per group of 32 sorted points
+  DevBuf<TreeState> state;
+  tsgne_status alloc(int n_points, int sm_count);
+};
+// Bounding square, keys, sort, tree and summaries of the layout Y[0..n).
+tsgne_status launch_tree_build(TreeBufs& tb, const float2* Y, cudaStream_t s);
+// Walk with opening angle theta: frep[i] (input order) and sched->Z, then the
+// schedule of iteration sched->t as launch_repulsion does.
+tsgne_status launch_tree_walk(TreeBufs& tb, float theta, float2* frep, Sched* sched, int advance, float ee,
+                              int ee_iters, float mom0, float mom1, cudaStream_t s);
+
 // Fill y[lo..hi) with the sentinel point.
 tsgne_status launch_fill_sentinel(float2* Y, int lo, int hi, cudaStream_t s);
 // Set every element of a float2 array to (v, v).

@@ -314,7 +314,8 @@ def test_device_layout_io():
 
 
 def test_gradient_parity_with_hub_rows():
-    """Rows above the 256-entry threshold take the one-CTA-per-row path."""
+    """Rows above 32 entries take the chunked path (one warp per 1,024-entry
+    chunk, chunk sums added by the row's update thread)."""
     n = 6000
     rng = np.random.default_rng(3)
     g = synth.random_graph(n, 5.0, seed=77)
