@@ -82,6 +82,8 @@ def _load():
             lib.tsgo_bfs_knn.restype = ctypes.c_int
             lib.tsgo_repulsion_tree.argtypes = [_i32, _p, _dbl, _i32, _p, _p, _p]
             lib.tsgo_repulsion_tree.restype = ctypes.c_int
+            lib.tsgo_gradient_tree.argtypes = [_i32, _p, _p, _p, _p, _dbl, _dbl, _i32, _p, _p]
+            lib.tsgo_gradient_tree.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -210,6 +212,18 @@ def repulsion_tree(Y, theta, bucket=16):
     _check(_load().tsgo_repulsion_tree(n, _ptr(Yd), float(theta), int(bucket), _ptr(F), _ptr(zr), ctypes.byref(z)),
            "repulsion_tree")
     return F, zr, z.value
+
+
+def gradient_tree(n, rp, col, P, Y, alpha=1.0, theta=0.5, bucket=16):
+    """Gradient of Eq. 5 with the tree code's repulsive sums and Z; returns (G, Z)."""
+    rp, col, P, Yd = _c(rp, np.int64), _c(col, np.int32), _c(P, np.float64), _c(Y, np.float64)
+    G = np.zeros((n, 2))
+    z = ctypes.c_double(0.0)
+    st = _load().tsgo_gradient_tree(n, _ptr(rp), _ptr(col if col.size else np.zeros(1, np.int32)),
+                                    _ptr(P if P.size else np.zeros(1)), _ptr(Yd), float(alpha), float(theta),
+                                    int(bucket), _ptr(G), ctypes.byref(z))
+    _check(st, "gradient_tree")
+    return G, z.value
 
 
 def repulsion_all(Y, threads=None):

@@ -31,6 +31,7 @@
  *   tsgo_repulsion_tree tree-code approximation of the repulsive sums and Z
  *                       (an extension; the paper sums Eq. 4 exactly); its
  *                       steps are listed above the function
+ *   tsgo_gradient_tree  tsgo_gradient with the tree code's F^r and Z
  *
  * Readings of the paper where it is silent (also listed in the design notes):
  *   - N(i) is the set of graph neighbours (k = graph edges), union of both
@@ -698,5 +699,35 @@ int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket
   }
   if (Z_out) *Z_out = Z;
   free(xs); free(ys); free(kv); free(aug); free(nodes); free(F); free(zr);
+  return TSGO_OK;
+}
+
+/*
+ * Gradient of Eq. 5 (as tsgo_gradient) with the repulsive sums and Z taken
+ * from the tree code: g_i = 4 (alpha F^a_i - F^r_i / Z).
+ */
+int tsgo_gradient_tree(int32_t n, const int64_t* rp, const int32_t* col, const double* P, const double* Y,
+                       double alpha, double theta, int32_t bucket, double* G, double* Z_out) {
+  double* Fr = (double*)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+  if (!Fr) return TSGO_ENOMEM;
+  double Z = 0.0;
+  int st = tsgo_repulsion_tree(n, Y, theta, bucket, Fr, NULL, &Z);
+  if (st != TSGO_OK) {
+    free(Fr);
+    return st;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    double ax = 0.0, ay = 0.0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int64_t j = col[e];
+      double w = kernel_w(Y, i, j);
+      ax += P[e] * w * (Y[2 * i] - Y[2 * j]);
+      ay += P[e] * w * (Y[2 * i + 1] - Y[2 * j + 1]);
+    }
+    G[2 * i] = 4.0 * (alpha * ax - Fr[2 * i] / Z);
+    G[2 * i + 1] = 4.0 * (alpha * ay - Fr[2 * i + 1] / Z);
+  }
+  free(Fr);
+  if (Z_out) *Z_out = Z;
   return TSGO_OK;
 }

@@ -365,7 +365,7 @@ tsgne_status alloc_layout(tsgne_ctx* ctx) {
   if (ctx->use_tree) {
     ctx->frep = DevBuf<float2>();
     ctx->zpart = DevBuf<double>();
-    TS_TRY(ctx->tree.alloc(ctx->n, ctx->sms));
+    TS_TRY(ctx->tree.alloc(ctx->n, ctx->sms, ctx->stream));
   } else {
     ctx->tree = TreeBufs();
     TS_TRY(ctx->frep.alloc(np * (size_t)ctx->shape.chunks));

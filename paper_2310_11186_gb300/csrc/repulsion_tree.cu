@@ -391,7 +391,7 @@ int grid_for(int64_t items, int per_block, int cap) {
 
 }  // namespace
 
-tsgne_status TreeBufs::alloc(int n_points, int sm_count) {
+tsgne_status TreeBufs::alloc(int n_points, int sm_count, cudaStream_t s) {
   n = n_points;
   nchunks = (n + kRadixChunk - 1) / kRadixChunk;
   ngroups = (n + 31) / 32;
@@ -414,8 +414,8 @@ tsgne_status TreeBufs::alloc(int n_points, int sm_count) {
   TS_TRY(boxpart.alloc((size_t)box_blocks));
   TS_TRY(zgroup.alloc((size_t)ngroups));
   TS_TRY(state.alloc(1));
-  TS_CUDA(cudaMemset(flags.get(), 0, sizeof(uint32_t) * nn));
-  TS_CUDA(cudaMemset(state.get(), 0, sizeof(TreeState)));
+  TS_CUDA(cudaMemsetAsync(flags.get(), 0, sizeof(uint32_t) * nn, s));
+  TS_CUDA(cudaMemsetAsync(state.get(), 0, sizeof(TreeState), s));
   return TSGNE_OK;
 }
 

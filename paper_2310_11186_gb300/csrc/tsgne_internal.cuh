@@ -256,7 +256,7 @@ struct TreeBufs {
   DevBuf<float4> boxpart;
   DevBuf<double> zgroup;      // FP64 Z partial per group of 32 sorted points
   DevBuf<TreeState> state;
-  tsgne_status alloc(int n_points, int sm_count);
+  tsgne_status alloc(int n_points, int sm_count, cudaStream_t s);
 };
 // Bounding square, keys, sort, tree and summaries of the layout Y[0..n).
 tsgne_status launch_tree_build(TreeBufs& tb, const float2* Y, cudaStream_t s);

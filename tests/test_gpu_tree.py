@@ -1,0 +1,186 @@
+"""Tree-code repulsion (cfg.repulsion = 1) against the oracle's tree code.
+
+Both sides take the same FP32 decisions (keys, tree shape, acceptance), so
+they sum the same interactions; the GPU accumulates them in FP32 with FP64
+Z, the oracle in FP64.  Tolerances are those of the exact path: gradient
+1e-4 relative L2, Z 1e-5 relative.  At theta = 0 the tree code sums every
+pair exactly, which ties it to the exact oracle as well.  The distance of
+the approximation from the exact sums is a property of theta: it is
+recorded, and bounded loosely.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2310_11186_gb300 as pkg  # noqa: E402
+import tsgne_synth as synth  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2310_11186_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+    yield
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def grad_err(G, oG):
+    """Relative L2 error; a gradient that vanishes (a 2-node graph has p = q)
+    is compared in absolute terms instead."""
+    nb = np.linalg.norm(oG)
+    if nb < 1e-12:
+        return float(np.abs(np.asarray(G, np.float64) - oG).max())
+    return rel_l2(G, oG)
+
+
+def _case(n, deg, seed, perp=3.0):
+    g = synth.random_graph(n, deg, seed=seed)
+    labels = (np.arange(n) % 7).astype(np.int32)
+    X = synth.block_embedding(labels, 16, seed=seed)
+    rp, col, P = oracle.build_P(n, g.row_ptr, g.col, X, perp)
+    return labels, rp, col, P
+
+
+def _layout(kind, labels, seed):
+    n = labels.size
+    if kind == "spread":
+        return synth.spread_layout(labels, scale=20.0, seed=seed)
+    if kind == "tiny":
+        return synth.y_init(n, sigma=1e-4, seed=seed)
+    if kind == "coincident":
+        Y = synth.spread_layout(labels, scale=5.0, seed=seed)
+        Y[: n // 3] = Y[0]  # a third of the points on one spot
+        return Y
+    raise ValueError(kind)
+
+
+def _gpu_gradient(rp, col, P, Y, alpha, theta):
+    with pkg.Layout(repulsion=1, theta=theta) as lay:
+        lay.set_P(rp, col, P.astype(np.float32))
+        lay.init_Y(Y)
+        return lay.gradient(alpha)
+
+
+@pytest.mark.parametrize("n,theta,kind", [
+    (2, 0.5, "spread"), (33, 0.5, "spread"), (1000, 0.0, "spread"), (1000, 0.5, "spread"),
+    (5003, 0.3, "spread"), (5003, 0.5, "tiny"), (5003, 1.0, "spread"), (9000, 0.5, "coincident"),
+    (20000, 0.5, "spread"),
+])
+def test_tree_gradient_matches_oracle_tree(n, theta, kind, record_property):
+    labels, rp, col, P = _case(n, 6.0, seed=n)
+    Y = _layout(kind, labels, seed=n)
+    alpha = 12.0 if kind == "tiny" else 1.0
+    oG, oZ = oracle.gradient_tree(n, rp, col, P, Y, alpha, theta=theta)
+    G, Z = _gpu_gradient(rp, col, P, Y, alpha, theta)
+    assert abs(Z - oZ) / oZ < 1e-5, (Z, oZ)
+    assert grad_err(G, oG) < 1e-4, grad_err(G, oG)
+    if n <= 5003 and n > 2:
+        eG, eZ = oracle.gradient(n, rp, col, P, Y.astype(np.float64), alpha)
+        record_property("grad_rel_l2_vs_exact", rel_l2(G, eG))
+        record_property("Z_rel_vs_exact", abs(Z - eZ) / eZ)
+        if theta == 0.0:
+            assert rel_l2(G, eG) < 1e-4 and abs(Z - eZ) / eZ < 1e-5
+        else:
+            assert rel_l2(G, eG) < 5e-2
+
+
+def test_tree_far_clusters_monopole():
+    """Two 32-point clusters 100 apart: each is one node for the other."""
+    rng = np.random.default_rng(7)
+    Y = np.concatenate([rng.uniform(-0.5, 0.5, size=(32, 2)),
+                        rng.uniform(-0.5, 0.5, size=(32, 2)) + [100.0, 0.0]]).astype(np.float32)
+    rp = np.zeros(65, np.int64)
+    col = np.zeros(0, np.int32)
+    P = np.zeros(0, np.float32)
+    oG, oZ = oracle.gradient_tree(64, rp, col, P, Y, 1.0, theta=0.5)
+    G, Z = _gpu_gradient(rp, col, P, Y, 1.0, 0.5)
+    assert abs(Z - oZ) / oZ < 1e-6 and rel_l2(G, oG) < 1e-5
+
+
+def test_tree_is_deterministic_and_iterates():
+    """Bit-identical gradients, layouts and checkpoints from run to run."""
+    g, X = synth.workload("sbm2k")
+    Y0 = synth.y_init(g.n, seed=1)
+
+    def run(k):
+        lay = pkg.Layout(repulsion=1, theta=0.5)
+        lay.build_P(g.row_ptr, g.col, X)
+        lay.init_Y(Y0)
+        lay.run(k)
+        return lay
+
+    a, b = run(300), run(300)
+    with a, b:
+        assert np.array_equal(a.get_Y(), b.get_Y())
+        Ga, Za = a.gradient(1.0)
+        Gb, Zb = b.gradient(1.0)
+        assert np.array_equal(Ga, Gb) and Za == Zb
+        c = run(120)
+        Y, U, Gn, it = c.get_state()
+        c.close()
+        with pkg.Layout(repulsion=1, theta=0.5) as d:
+            d.build_P(g.row_ptr, g.col, X)
+            d.set_state(Y, U, Gn, it)
+            d.run(180)
+            assert np.array_equal(d.get_Y(), a.get_Y())
+
+
+def test_tree_layout_quality(record_property):
+    """1,000 iterations on the 2,000-node SBM: the final layouts of the exact
+    path and of the tree code, both scored by the exact KL, differ by < 5%."""
+    g, X = synth.workload("sbm2k")
+    Y0 = synth.y_init(g.n, seed=0)
+    finals = []
+    for rep in (0, 1):
+        with pkg.Layout(repulsion=rep, theta=0.5) as lay:
+            lay.build_P(g.row_ptr, g.col, X)
+            lay.init_Y(Y0)
+            lay.run(1000)
+            finals.append(lay.get_Y())
+    assert all(np.all(np.isfinite(Yf)) for Yf in finals)
+    kls = []
+    with pkg.Layout() as ex:
+        ex.build_P(g.row_ptr, g.col, X)
+        for Yf in finals:
+            ex.init_Y(Yf)
+            kls.append(ex.kl())
+    record_property("kl_exact", kls[0])
+    record_property("kl_tree", kls[1])
+    assert abs(kls[1] - kls[0]) / kls[0] < 5e-2, kls
+
+
+def test_tree_full_size_zipf300k(record_property):
+    """The benchmark's 300K-node workload at theta = 0.5 against the oracle's
+    tree code on the same layout (all 300K rows)."""
+    g, X = synth.workload("zipf300k")
+    labels = g.labels
+    Y = synth.spread_layout(labels, scale=30.0, seed=3)
+    with pkg.Layout(repulsion=1, theta=0.5) as lay:
+        lay.build_P(g.row_ptr, g.col, X)
+        rp, col, P = lay.get_P()
+        lay.init_Y(Y)
+        G, Z = lay.gradient(1.0)
+    oG, oZ = oracle.gradient_tree(g.n, rp, col, P.astype(np.float64), Y, 1.0, theta=0.5)
+    record_property("grad_rel_l2", rel_l2(G, oG))
+    assert abs(Z - oZ) / oZ < 1e-5, (Z, oZ)
+    assert rel_l2(G, oG) < 1e-4, rel_l2(G, oG)
+
+
+def test_tree_config_values():
+    for bad in (dict(repulsion=2), dict(repulsion=1, theta=-0.1), dict(repulsion=1, theta=1.5)):
+        with pytest.raises(pkg.TsgneError):
+            pkg.Layout(**bad)
+    with pytest.raises(pkg.TsgneError):
+        pkg.Batch(repulsion=1)

@@ -543,3 +543,20 @@ def test_tree_coincident_points():
         assert np.all(np.isfinite(F))
         assert np.linalg.norm(F - Fe) / np.linalg.norm(Fe) < (1e-12 if th == 0 else 1e-2)
         assert abs(Z - ze.sum()) / ze.sum() < (1e-12 if th == 0 else 5e-3)
+
+
+def test_tree_gradient_reduces_to_exact_at_theta0():
+    g = synth.random_graph(300, 5.0, seed=2)
+    X = synth.block_embedding((np.arange(300) % 4).astype(np.int32), 8, seed=2)
+    rp, col, P = oracle.build_P(300, g.row_ptr, g.col, X, 5.0)
+    Y = synth.spread_layout((np.arange(300) % 4).astype(np.int32), scale=10.0, seed=2).astype(np.float32)
+    for alpha in (1.0, 12.0):
+        Gt, Zt = oracle.gradient_tree(300, rp, col, P, Y, alpha, theta=0.0)
+        Ge, Ze = oracle.gradient(300, rp, col, P, Y.astype(np.float64), alpha)
+        assert np.abs(Gt - Ge).max() <= 1e-12 * np.abs(Ge).max()
+        assert Zt == pytest.approx(Ze, rel=1e-12)
+    # theta > 0 moves the repulsive part only: alpha-scaled attraction is shared
+    G1, Z1 = oracle.gradient_tree(300, rp, col, P, Y, 1.0, theta=0.8)
+    G2, Z2 = oracle.gradient_tree(300, rp, col, P, Y, 2.0, theta=0.8)
+    Fa = oracle.attraction_rows(300, rp, col, P, Y.astype(np.float64), np.arange(300))
+    assert Z1 == Z2 and np.allclose(G2 - G1, 4 * Fa, rtol=1e-10, atol=1e-15)
