@@ -346,6 +346,7 @@ def run_ours(args):
     if rank == 0 and not args.no_serving:
         serving = bench_serving(args, pkg)
     rmat_res = bench_rmat(args, pkg) if (rank == 0 and args.rmat) else None
+    tree_res = bench_tree(args, pkg, g, X, Y0, Yt) if (rank == 0 and not args.no_tree) else None
 
     if rank != 0:
         return 0
@@ -403,12 +404,82 @@ def run_ours(args):
         "serving": serving,
         "batched": batched,
         "rmat": rmat_res,
+        "tree": tree_res,
         "paper_context": "300K nodes / 1M edges in under 5 min (ShortestPath + t-SGNE, 32-core Xeon Gold 6338)",
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_tree(args, pkg, g, X, Y0, Yt, log_fn=log):
+    """The tree-code repulsion (an approximation beyond the paper's exact sum)
+    on the same workload: device-timed steps, a whole 1,000-iteration layout,
+    and its distance from the exact path (gradient at the timed layout, KL of
+    the final layouts both scored exactly)."""
+    import torch
+
+    theta = args.tree_theta
+    lay = pkg.Layout(profile=1, repulsion=1, theta=theta)
+    lay.build_P(g.row_ptr, g.col, X)
+    lay.init_Y(Y0)
+    for _ in range(args.warmup):
+        lay.step()
+    lay.sync()
+    lay.kernel_times(reset=True)
+    flush = torch.empty(320 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ms = 0.0
+    for k in range(args.steps):
+        with torch.cuda.stream(lay.stream):
+            flush.fill_(float(k))
+        ev[0].record(lay.stream)
+        lay.step()
+        ev[1].record(lay.stream)
+        ev[1].synchronize()
+        ms += ev[0].elapsed_time(ev[1])
+    kt = lay.kernel_times(reset=True)
+    # gradient at the exact path's timed layout, tree vs exact
+    lay.set_state(Yt)
+    Gt, Zt = lay.gradient(1.0)
+    lay.close()
+    with pkg.Layout() as ex:
+        ex.build_P(g.row_ptr, g.col, X)
+        ex.set_state(Yt)
+        Ge, Ze = ex.gradient(1.0)
+        # whole layout with the tree code, then scored by the exact KL
+        with pkg.Layout(repulsion=1, theta=theta) as lt:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lt.build_P(g.row_ptr, g.col, X)
+            lt.init_Y(Y0)
+            lt.run(args.e2e_iters)
+            Yf = lt.get_Y()
+            wall = time.perf_counter() - t0
+        ex.init_Y(Yf)
+        kl_tree = ex.kl()
+
+    def per(name):
+        return kt[name][0] / max(kt[name][1], 1)
+
+    out = {
+        "theta": theta,
+        "iters_per_s": args.steps / (ms / 1e3),
+        "ms_per_step": ms / args.steps,
+        "kernels_ms_per_step": {"tree_build": per("tree_build"), "tree_walk": per("repulsion"),
+                                "attract_update": per("attract_update")},
+        "grad_rel_l2_vs_exact": float(np.linalg.norm(Gt - Ge) / np.linalg.norm(Ge)),
+        "Z_rel_vs_exact": abs(Zt - Ze) / Ze,
+        "layout_s": wall,
+        "layout_iters": args.e2e_iters,
+        "kl_exact_of_tree_layout": kl_tree,
+        "note": "approximate repulsion (not the paper's exact Eq. 4 sum); parity is against the oracle's tree code",
+    }
+    log_fn(f"[bench] tree theta={theta}: {out['iters_per_s']:.1f} it/s, build {out['kernels_ms_per_step']['tree_build']:.3f} ms, "
+           f"walk {out['kernels_ms_per_step']['tree_walk']:.3f} ms, grad err {out['grad_rel_l2_vs_exact']:.2e}")
+    return out
 
 
 def bench_batched(args, pkg, log_fn=log):
@@ -504,10 +575,10 @@ def hbm_peak():
 
 def bench_rmat(args, pkg, log_fn=log):
     """R-MAT 2^21 nodes / 2^24 edges in both storage precisions (FP32; BF16
-    P and Y reads with FP32 arithmetic and FP64 Z): the attraction+update
-    kernel against the HBM roofline, and each arm's gradient / KL error
-    against the FP64 oracle on a 20K-node induced subgraph (BFS ball from the
-    highest-degree node)."""
+    P and Y reads with FP32 arithmetic and FP64 Z) and with the tree-code
+    repulsion: the attraction+update kernel against the HBM roofline, and
+    each arm's gradient / KL error against the exact FP64 oracle on a
+    20K-node induced subgraph (BFS ball from the highest-degree node)."""
     import torch
     import oracle
 
@@ -530,8 +601,9 @@ def bench_rmat(args, pkg, log_fn=log):
         "l2": "flushed (320 MB write) before every step",
         "oracle_subgraph_nodes": int(sub.n),
     }
-    for prec, name in ((0, "fp32"), (1, "bf16")):
-        lay = pkg.Layout(profile=1, precision=prec)
+    arms = ((0, 0, "fp32"), (1, 0, "bf16"), (0, 1, "fp32_tree"))
+    for prec, rep, name in arms:
+        lay = pkg.Layout(profile=1, precision=prec, repulsion=rep, theta=args.tree_theta)
         tb = time.perf_counter()
         lay.build_P(g.row_ptr, g.col, X)
         build_ms = (time.perf_counter() - tb) * 1e3
@@ -552,6 +624,8 @@ def bench_rmat(args, pkg, log_fn=log):
         att_ms = kt["attract_update"][0] / kt["attract_update"][1]
         hub_ms = kt["attract_hubs"][0] / max(kt["attract_hubs"][1], 1)
         rep_ms = kt["repulsion"][0] / kt["repulsion"][1]
+        if rep:
+            rep_ms += kt["tree_build"][0] / kt["tree_build"][1]
         # algorithmic bytes of one attraction+update launch: row_ptr, col and
         # P once; per point F^r, update and gains read, Y_next, update and
         # gains written, and Y_i read (FP32: 8 B; BF16: the 4-B shadow for
@@ -562,7 +636,7 @@ def bench_rmat(args, pkg, log_fn=log):
         else:
             att_bytes = 8 * (n + 1) + 6 * nnz + 8 * 8 * n
         achieved = att_bytes / ((att_ms + hub_ms) * 1e-3) / 1e9
-        with pkg.Layout(precision=prec) as l2:
+        with pkg.Layout(precision=prec, repulsion=rep, theta=args.tree_theta) as l2:
             l2.build_P(sub.row_ptr, sub.col, Xs)
             l2.init_Y(Ys)
             G, Z = l2.gradient(1.0)
@@ -571,6 +645,7 @@ def bench_rmat(args, pkg, log_fn=log):
             "nnz_P": int(nnz),
             "build_ms": build_ms,
             "repulsion_ms": rep_ms,
+            "repulsion": f"tree code, theta {args.tree_theta} (build + walk)" if rep else "exact all pairs",
             "attraction_roofline": {"bound": "hbm", "kernel": "attract_update (S3+S5)", "achieved": achieved,
                                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
                                     "bytes_per_launch": att_bytes, "ms_per_launch": att_ms + hub_ms,
@@ -602,6 +677,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-iters", type=int, default=500)
+    ap.add_argument("--no-tree", action="store_true", help="skip the tree-code repulsion section")
+    ap.add_argument("--tree-theta", type=float, default=0.5)
     ap.add_argument("--rmat", action="store_true", help="also run the R-MAT 2^21 workload (about a minute)")
     ap.add_argument("--rmat-steps", type=int, default=5)
     ap.add_argument("--rmat-scale", type=int, default=21)

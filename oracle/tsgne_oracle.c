@@ -468,21 +468,25 @@ int tsgo_bfs_knn(int32_t n, const int64_t* rp, const int32_t* col, int32_t k, in
  * interactions (cell codes, tree shape, acceptance) are taken in FP32, as the
  * GPU takes them, and the sums are then accumulated in FP64.
  *
- *  1. Bounding square: lo = (min x, min y), side = max(max x - min x,
- *     max y - min y) floored at 1e-30; scale = 65536 / side.
- *  2. Cell of a point: c = (v - lo) * scale per axis, truncated to an integer
- *     and clamped to [0, 65535] (NaN -> 0); key = Morton interleave of the
- *     two 16-bit cells, x in the even bits, y in the odd bits.
+ *  1. Bounding square (FP32): lo = (min x, min y), side = max(max x - min x,
+ *     max y - min y) floored at 1e-30; scale = 2^32 / side in FP64.
+ *  2. Cell of a point per axis, in FP64: c = (v - lo) * scale, truncated to
+ *     an integer and clamped to [0, 2^32 - 1] (NaN -> 0); key = 64-bit
+ *     Morton interleave of the two cells, x in the even bits.  32 bits per
+ *     axis keep points apart even when a few outliers stretch the square
+ *     to thousands of times the bulk's size.
  *  3. Order: points sorted by (key, index).  Position k of the sorted order
- *     gets the 64-bit augmented key (key << 32) | k, unique per point.
+ *     gets the 96-bit augmented key (key, k), unique per point.
  *  4. Tree: the binary radix tree of the augmented keys.  A node covers
  *     sorted positions [f, l]; if f < l it splits at the highest bit in which
  *     the augmented keys of f and l differ: the left child holds the
  *     positions whose bit is 0.  A single position is a leaf.
  *  5. Node summaries (FP32): count; coordinate sums, left + right; bounding
  *     box; centre = sums / count; r2 = (longest box side)^2.
- *  6. Groups: runs of 32 consecutive sorted positions (the last may be
- *     shorter), with the bounding box of their points.
+ *  6. Groups: the maximal subtrees of at most 32 points (nodes of <= 32
+ *     points whose parent has more; the root if n <= 32), in sorted order.
+ *     They partition the sorted positions into runs, each a Morton cell;
+ *     a group's box is the bounding box of its points.
  *  7. Walk, per group, from the root, left child before right:
  *     - a leaf is an exact interaction with its point;
  *     - otherwise d2 = squared distance from the node's centre to the group
@@ -504,7 +508,7 @@ typedef struct {
 } tsgo_tnode;
 
 typedef struct {
-  uint32_t key;
+  uint64_t key;
   int32_t idx;
 } tsgo_keyed;
 
@@ -515,21 +519,27 @@ static int cmp_keyed(const void* a, const void* b) {
   return (x->idx > y->idx) - (x->idx < y->idx);
 }
 
-static uint32_t spread_bits16(uint32_t v) {
-  uint32_t r = 0;
-  for (int b = 0; b < 16; ++b) r |= ((v >> b) & 1u) << (2 * b);
+static uint64_t spread_bits32(uint32_t v) {
+  uint64_t r = 0;
+  for (int b = 0; b < 32; ++b) r |= (uint64_t)((v >> b) & 1u) << (2 * b);
   return r;
 }
 
-static uint32_t cell16(float v, float lo, float scale) {
-  float c = (v - lo) * scale;
-  if (!(c >= 0.0f)) return 0u;
-  if (c >= 65535.0f) return 65535u;
+static uint32_t cell32(float v, double lo, double scale) {
+  double c = ((double)v - lo) * scale;
+  if (!(c >= 0.0)) return 0u;
+  if (c >= 4294967295.0) return 4294967295u;
   return (uint32_t)c;
 }
 
+/* Bit b of the augmented key (key, pos): b in [32, 96) is key bit b - 32,
+ * b in [0, 32) is position bit b. */
+static int aug_bit(uint64_t key, uint32_t pos, int b) {
+  return b >= 32 ? (int)((key >> (b - 32)) & 1u) : (int)((pos >> b) & 1u);
+}
+
 /* Builds the subtree over sorted positions [f, l]; returns its node id. */
-static int32_t tree_build(const uint64_t* aug, const float* xs, const float* ys, int32_t f, int32_t l,
+static int32_t tree_build(const uint64_t* keys, const float* xs, const float* ys, int32_t f, int32_t l,
                           tsgo_tnode* nodes, int32_t* count) {
   int32_t id = (*count)++;
   tsgo_tnode* t = &nodes[id];
@@ -542,13 +552,12 @@ static int32_t tree_build(const uint64_t* aug, const float* xs, const float* ys,
     t->r2 = 0.0f;
     return id;
   }
-  int bit = 63;
-  uint64_t diff = aug[f] ^ aug[l];
-  while (!((diff >> bit) & 1u)) --bit;
+  int bit = 95;
+  while (aug_bit(keys[f], (uint32_t)f, bit) == aug_bit(keys[l], (uint32_t)l, bit)) --bit;
   int32_t g = f;
-  while (g + 1 <= l && !((aug[g + 1] >> bit) & 1u)) ++g;
-  int32_t L = tree_build(aug, xs, ys, f, g, nodes, count);
-  int32_t R = tree_build(aug, xs, ys, g + 1, l, nodes, count);
+  while (g + 1 <= l && aug_bit(keys[g + 1], (uint32_t)(g + 1), bit) == 0) ++g;
+  int32_t L = tree_build(keys, xs, ys, f, g, nodes, count);
+  int32_t R = tree_build(keys, xs, ys, g + 1, l, nodes, count);
   t = &nodes[id];
   const tsgo_tnode* a = &nodes[L];
   const tsgo_tnode* b = &nodes[R];
@@ -620,6 +629,19 @@ static void tree_walk(const tsgo_walk* w, int32_t id) {
   tree_walk(w, t->right);
 }
 
+/* Appends the groups under node id (maximal subtrees of <= 32 points). */
+static void collect_groups(const tsgo_tnode* nodes, int32_t id, int32_t* gfirst, int32_t* glast, int32_t* ng) {
+  const tsgo_tnode* t = &nodes[id];
+  if (t->last - t->first + 1 <= 32) {
+    gfirst[*ng] = t->first;
+    glast[*ng] = t->last;
+    ++*ng;
+    return;
+  }
+  collect_groups(nodes, t->left, gfirst, glast, ng);
+  collect_groups(nodes, t->right, gfirst, glast, ng);
+}
+
 /*
  * Y: n x 2 layout (FP32 values carried in doubles); theta >= 0; bucket >= 1.
  * Frep (n x 2) and zrow (n) come back in the input order; returns Z through
@@ -631,12 +653,14 @@ int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket
   float* xs = (float*)malloc(sizeof(float) * (size_t)n);
   float* ys = (float*)malloc(sizeof(float) * (size_t)n);
   tsgo_keyed* kv = (tsgo_keyed*)malloc(sizeof(tsgo_keyed) * (size_t)n);
-  uint64_t* aug = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
+  uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
   tsgo_tnode* nodes = (tsgo_tnode*)malloc(sizeof(tsgo_tnode) * (size_t)(2 * n - 1));
   double* F = (double*)calloc(2 * (size_t)n, sizeof(double));
   double* zr = (double*)calloc((size_t)n, sizeof(double));
-  if (!xs || !ys || !kv || !aug || !nodes || !F || !zr) {
-    free(xs); free(ys); free(kv); free(aug); free(nodes); free(F); free(zr);
+  int32_t* gfirst = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* glast = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!xs || !ys || !kv || !keys || !nodes || !F || !zr || !gfirst || !glast) {
+    free(xs); free(ys); free(kv); free(keys); free(nodes); free(F); free(zr); free(gfirst); free(glast);
     return TSGO_ENOMEM;
   }
   /* 1-2: bounding square and keys */
@@ -649,10 +673,10 @@ int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket
     hy = fmaxf(hy, y);
   }
   float side = fmaxf(fmaxf(hx - lx, hy - ly), 1e-30f);
-  float scale = 65536.0f / side;
+  double scale = 4294967296.0 / (double)side;
   for (int32_t i = 0; i < n; ++i) {
-    uint32_t cx = cell16((float)Y[2 * i], lx, scale), cy = cell16((float)Y[2 * i + 1], ly, scale);
-    kv[i].key = spread_bits16(cx) | (spread_bits16(cy) << 1);
+    uint32_t cx = cell32((float)Y[2 * i], (double)lx, scale), cy = cell32((float)Y[2 * i + 1], (double)ly, scale);
+    kv[i].key = spread_bits32(cx) | (spread_bits32(cy) << 1);
     kv[i].idx = i;
   }
   /* 3: order */
@@ -660,11 +684,11 @@ int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket
   for (int32_t k = 0; k < n; ++k) {
     xs[k] = (float)Y[2 * kv[k].idx];
     ys[k] = (float)Y[2 * kv[k].idx + 1];
-    aug[k] = ((uint64_t)kv[k].key << 32) | (uint32_t)k;
+    keys[k] = kv[k].key;
   }
   /* 4-5: tree */
   int32_t count = 0;
-  int32_t root = tree_build(aug, xs, ys, 0, n - 1, nodes, &count);
+  int32_t root = tree_build(keys, xs, ys, 0, n - 1, nodes, &count);
   /* 6-7: groups and walks */
   float th = (float)theta;
   tsgo_walk w;
@@ -675,8 +699,10 @@ int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket
   w.bucket = bucket;
   w.F = F;
   w.zrow = zr;
-  for (int32_t g0 = 0; g0 < n; g0 += 32) {
-    int32_t g1 = g0 + 32 < n ? g0 + 32 : n;
+  int32_t ng = 0;
+  collect_groups(nodes, root, gfirst, glast, &ng);
+  for (int32_t g = 0; g < ng; ++g) {
+    int32_t g0 = gfirst[g], g1 = glast[g] + 1;
     w.g0 = g0;
     w.g1 = g1;
     w.bx0 = w.bx1 = xs[g0];
@@ -698,7 +724,7 @@ int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket
     Z += zr[k];
   }
   if (Z_out) *Z_out = Z;
-  free(xs); free(ys); free(kv); free(aug); free(nodes); free(F); free(zr);
+  free(xs); free(ys); free(kv); free(keys); free(nodes); free(F); free(zr); free(gfirst); free(glast);
   return TSGO_OK;
 }
 

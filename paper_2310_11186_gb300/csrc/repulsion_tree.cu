@@ -2,37 +2,44 @@
 // paper sums Eq. 4 exactly, at O(|V|^2) cost, Sec. 2.1 "Time complexity").
 //
 // Definition (the oracle restates the same steps in plain C):
-//  1. bounding square of the layout: lo = (min x, min y), side = the longer
-//     extent (floored at 1e-30), scale = 65536 / side;
-//  2. cell of a point per axis = trunc((v - lo) * scale) clamped to
-//     [0, 65535]; key = Morton interleave (x in the even bits);
-//  3. points sorted by (key, index); sorted position k has the augmented key
-//     (key << 32) | k;
+//  1. bounding square of the layout (FP32): lo = (min x, min y), side = the
+//     longer extent (floored at 1e-30); scale = 2^32 / side in FP64;
+//  2. cell of a point per axis = trunc((v - lo) * scale) in FP64, clamped
+//     to [0, 2^32 - 1]; key = 64-bit Morton interleave (x in the even bits).
+//     32 bits per axis keep the bulk resolved when a few outliers stretch
+//     the square to thousands of times its size;
+//  3. points sorted by (key, index); sorted position k has the 96-bit
+//     augmented key (key, k);
 //  4. the binary radix tree of the augmented keys (a node over positions
 //     [f, l] splits at the highest bit in which keys f and l differ);
 //  5. node summaries in FP32: coordinate sums (left + right), box, centre =
 //     sums / count, r2 = (longer box side)^2;
-//  6. groups of 32 consecutive sorted positions, with their bounding box;
+//  6. groups: the maximal subtrees of at most 32 points (nodes of <= 32
+//     points whose parent has more), in sorted order -- compact Morton
+//     cells, so no group box straddles a jump of the curve;
 //  7. per group, a depth-first walk from the root, left child first: a leaf
 //     is an exact interaction; a node whose r2 < theta^2 d2 (d = distance
 //     from its centre to the group box) is one interaction of weight count
 //     at its centre; an opened node of at most kTreeBucket points is
 //     summed exactly over its points; other nodes are opened.
-// Every decision (keys, tree shape, acceptance) is taken with IEEE FP32
-// operations written as _rn intrinsics, so no FMA contraction changes it and
-// the CPU reference takes the same decisions.
+// Every decision (keys, tree shape, acceptance) is taken with IEEE FP32 /
+// FP64 operations written as _rn intrinsics, so no FMA contraction changes
+// it and the CPU reference takes the same decisions.
 //
-// GPU mapping.  Keys: one thread per point.  Sort: LSD radix sort, 8 bits per
-// pass, stable: a warp owns a chunk of 512 keys; per-(digit, chunk) counts
+// GPU mapping.  Keys: one thread per point.  Sort: LSD radix sort, 8 passes
+// of 8 bits, stable: a warp owns a chunk of 512 keys; per-(digit, chunk) counts
 // are scanned digit-major, and the scatter ranks equal digits within a round
 // of 32 keys with __match_any_sync, so equal keys keep their input order.
 // The last pass also gathers the layout into sorted order.  Tree: one thread
 // per internal node finds its range and split from the sorted keys alone
 // (binary search over the common-prefix length); summaries bottom-up, one
 // thread per leaf climbing until it is the first of two children to arrive.
-// Walk: one warp per group, lane = point; the stack of node ids is in shared
-// memory and every lane takes the same branch, so the traversal is free of
-// divergence and every node load is a broadcast.  Z: FP32 partial sums
+// Groups: one thread per leaf climbs while the parent holds <= 32 points and
+// marks whether it starts its group; a scan numbers the groups in sorted
+// order.  Walk: a persistent grid takes groups from a queue, one warp per
+// group, lane = point; the stack of node ids is in shared memory and every
+// lane takes the same branch, so the traversal is free of divergence and
+// every node load is a broadcast.  Z: FP32 partial sums
 // flushed into FP64 every 64 interactions, a fixed xor butterfly per warp,
 // one FP64 partial per group, and the group partials added in group order by
 // the last CTA -- bit-reproducible from run to run.
@@ -51,7 +58,7 @@ constexpr int kRadixChunk = 32 * kRadixItems;  // keys per warp chunk
 constexpr int kRadixWarps = 8;
 constexpr int kRadixBins = 256;
 constexpr int kWalkWarps = 8;
-constexpr int kStack = 72;  // a root-to-leaf path has at most 64 splits (one per key bit)
+constexpr int kStack = 100;  // a root-to-leaf path has at most 96 splits (one per augmented-key bit)
 constexpr int kZFlush = 64;
 
 __device__ __forceinline__ float warp_min(float v) {
@@ -108,35 +115,36 @@ __global__ void __launch_bounds__(256) k_tree_box(const float2* __restrict__ Y, 
       const float side = fmaxf(fmaxf(__fsub_rn(b.z, b.x), __fsub_rn(b.w, b.y)), 1e-30f);
       st->lo_x = b.x;
       st->lo_y = b.y;
-      st->scale = __fdiv_rn(65536.0f, side);
+      st->scale = __ddiv_rn(4294967296.0, (double)side);
     }
   }
 }
 
 // ---------------------------------------------------------------- 2. keys
 
-__device__ __forceinline__ uint32_t spread16(uint32_t v) {
-  v &= 0xffffu;
-  v = (v | (v << 8)) & 0x00ff00ffu;
-  v = (v | (v << 4)) & 0x0f0f0f0fu;
-  v = (v | (v << 2)) & 0x33333333u;
-  v = (v | (v << 1)) & 0x55555555u;
-  return v;
+__device__ __forceinline__ uint64_t spread32(uint32_t v) {
+  uint64_t x = v;
+  x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+  x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
 }
 
-__device__ __forceinline__ uint32_t cell16(float v, float lo, float scale) {
-  const float c = __fmul_rn(__fsub_rn(v, lo), scale);
-  if (!(c >= 0.0f)) return 0u;
-  if (c >= 65535.0f) return 65535u;
+__device__ __forceinline__ uint32_t cell32(float v, double lo, double scale) {
+  const double c = __dmul_rn(__dsub_rn((double)v, lo), scale);
+  if (!(c >= 0.0)) return 0u;
+  if (c >= 4294967295.0) return 0xffffffffu;
   return (uint32_t)c;
 }
 
 __global__ void k_tree_keys(const float2* __restrict__ Y, int n, const TreeState* __restrict__ st,
-                            uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
-  const float lx = st->lo_x, ly = st->lo_y, sc = st->scale;
+                            uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+  const double lx = st->lo_x, ly = st->lo_y, sc = st->scale;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float2 p = Y[i];
-    keys[i] = spread16(cell16(p.x, lx, sc)) | (spread16(cell16(p.y, ly, sc)) << 1);
+    keys[i] = spread32(cell32(p.x, lx, sc)) | (spread32(cell32(p.y, ly, sc)) << 1);
     vals[i] = i;
   }
 }
@@ -144,7 +152,7 @@ __global__ void k_tree_keys(const float2* __restrict__ Y, int n, const TreeState
 // ---------------------------------------------------------------- 3. sort
 
 __global__ void __launch_bounds__(32 * kRadixWarps)
-    k_radix_hist(const uint32_t* __restrict__ keys, int n, int shift, int nchunks, int32_t* __restrict__ counts) {
+    k_radix_hist(const uint64_t* __restrict__ keys, int n, int shift, int nchunks, int32_t* __restrict__ counts) {
   __shared__ uint32_t h[kRadixWarps][kRadixBins];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * kRadixWarps + w;
@@ -152,15 +160,15 @@ __global__ void __launch_bounds__(32 * kRadixWarps)
   __syncwarp();
   if (c >= nchunks) return;
   const int64_t base = (int64_t)c * kRadixChunk + lane;
-  uint32_t kk[kRadixItems];
+  uint32_t dd[kRadixItems];
 #pragma unroll
   for (int r = 0; r < kRadixItems; ++r) {
     const int64_t k = base + 32 * r;
-    kk[r] = k < n ? keys[k] : 0u;
+    dd[r] = k < n ? (uint32_t)(keys[k] >> shift) & 255u : 0u;
   }
 #pragma unroll
   for (int r = 0; r < kRadixItems; ++r)
-    if (base + 32 * r < n) atomicAdd(&h[w][(kk[r] >> shift) & 255u], 1u);
+    if (base + 32 * r < n) atomicAdd(&h[w][dd[r]], 1u);
   __syncwarp();
   for (int d = lane; d < kRadixBins; d += 32) counts[(int64_t)d * nchunks + c] = (int32_t)h[w][d];
 }
@@ -168,8 +176,8 @@ __global__ void __launch_bounds__(32 * kRadixWarps)
 // Stable scatter of one pass.  offs = exclusive scan of counts (digit-major).
 // With Y != NULL the layout is gathered into sorted order (ys[pos] = Y[val]).
 __global__ void __launch_bounds__(32 * kRadixWarps)
-    k_radix_scatter(const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, int n, int shift, int nchunks,
-                    const int64_t* __restrict__ offs, uint32_t* __restrict__ kout, int32_t* __restrict__ vout,
+    k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin, int n, int shift, int nchunks,
+                    const int64_t* __restrict__ offs, uint64_t* __restrict__ kout, int32_t* __restrict__ vout,
                     const float2* __restrict__ Y, float2* __restrict__ ys) {
   __shared__ int32_t base[kRadixWarps][kRadixBins];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -182,9 +190,9 @@ __global__ void __launch_bounds__(32 * kRadixWarps)
   for (int r = 0; r < kRadixItems; ++r) {
     const int64_t k = k0 + 32 * r;
     const bool valid = k < n;
-    const uint32_t key = valid ? kin[k] : 0u;
+    const uint64_t key = valid ? kin[k] : 0ull;
     const int32_t val = valid ? vin[k] : 0;
-    const uint32_t d = valid ? (key >> shift) & 255u : 256u + (uint32_t)lane;  // invalid lanes match only themselves
+    const uint32_t d = valid ? (uint32_t)(key >> shift) & 255u : 256u + (uint32_t)lane;  // invalid lanes match only themselves
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(peers & lt);
     int pos = 0;
@@ -204,16 +212,16 @@ __global__ void __launch_bounds__(32 * kRadixWarps)
 
 // Common-prefix length of the augmented keys of sorted positions i and j
 // (-1 when j is outside [0, n)).
-__device__ __forceinline__ int tree_delta(const uint32_t* __restrict__ keys, int n, int i, int64_t j) {
+__device__ __forceinline__ int tree_delta(const uint64_t* __restrict__ keys, int n, int i, int64_t j) {
   if (j < 0 || j >= n) return -1;
-  const uint32_t a = keys[i], b = keys[j];
-  return a != b ? __clz(a ^ b) : 32 + __clz((uint32_t)i ^ (uint32_t)j);
+  const uint64_t a = keys[i], b = keys[j];
+  return a != b ? __clzll((long long)(a ^ b)) : 64 + __clz((uint32_t)i ^ (uint32_t)j);
 }
 
 // Internal node i (0 <= i < n - 1; node 0 is the root).  Children: >= 0 an
 // internal node, < 0 the leaf at sorted position ~c.  parent: internal nodes
 // at [0, n - 1), leaf k at n - 1 + k; the root's parent is -1.
-__global__ void k_tree_build(const uint32_t* __restrict__ keys, int n, int4* __restrict__ nodeB,
+__global__ void k_tree_build(const uint64_t* __restrict__ keys, int n, int4* __restrict__ nodeB,
                              int32_t* __restrict__ parent) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
@@ -284,6 +292,39 @@ __global__ void k_tree_up(int n, const int4* __restrict__ nodeB, const int32_t* 
   }
 }
 
+// --------------------------------------------------------------- 6. groups
+
+constexpr int kGroupMax = 32;
+
+// is_start[k] = 1 if sorted position k begins its group.
+__global__ void k_tree_group_starts(int n, const int4* __restrict__ nodeB, const int32_t* __restrict__ parent,
+                                    int32_t* __restrict__ is_start) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  if (n == 1) {
+    is_start[0] = 1;
+    return;
+  }
+  int first = k;
+  int p = parent[n - 1 + k];
+  while (p >= 0) {  // at most kGroupMax steps: every step up adds a point
+    const int4 b = nodeB[p];
+    if (b.w - b.z + 1 > kGroupMax) break;
+    first = b.z;
+    p = parent[p];
+  }
+  is_start[k] = first == k ? 1 : 0;
+}
+
+// gstart[g] = first position of group g; gstart[ngroups] = n.
+__global__ void k_tree_group_list(int n, const int32_t* __restrict__ is_start, const int64_t* __restrict__ gscan,
+                                  int32_t* __restrict__ gstart) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  if (is_start[k]) gstart[gscan[k]] = k;
+  if (k == 0) gstart[gscan[n]] = n;
+}
+
 // ---------------------------------------------------------------- 7. walk
 
 // One interaction of weight c at q (c = 0 for the lane's own point and for
@@ -298,17 +339,49 @@ __device__ __forceinline__ void interact(float2 p, float qx, float qy, float c, 
   fy = fmaf(cw2, dy, fy);
 }
 
+// Stack entry of the walk: a node's record (centre x, y, r2, count) and
+// (left, right, first, last).  A leaf at sorted position j is the record
+// (y_j, 0, 1) with (-1, -1, j, j): accepting it is the exact interaction with
+// its point (count 1 at the point itself), and it is never accepted by the
+// lanes of its own group (its distance to their box is 0), which take the
+// exact path with the self term removed.
+struct WalkEntry {
+  float4 a;
+  int4 b;
+};
+
+__device__ __forceinline__ WalkEntry node_entry(int c, const float2* __restrict__ ys,
+                                                const float4* __restrict__ nodeA, const int4* __restrict__ nodeB) {
+  WalkEntry e;
+  if (c < 0) {
+    const float2 q = ys[~c];
+    e.a = make_float4(q.x, q.y, 0.f, 1.f);
+    e.b = make_int4(-1, -1, ~c, ~c);
+  } else {
+    e.a = nodeA[c];
+    e.b = nodeB[c];
+  }
+  return e;
+}
+
 __global__ void __launch_bounds__(32 * kWalkWarps)
     k_tree_walk(int n, const float2* __restrict__ ys, const int32_t* __restrict__ perm,
-                const float4* __restrict__ nodeA, const int4* __restrict__ nodeB, float theta2,
-                float2* __restrict__ frep, double* __restrict__ zgroup, int ngroups, Sched* sched, TreeState* st,
-                int advance, float ee, int ee_iters, float mom0, float mom1) {
-  __shared__ int stk[kWalkWarps][kStack];
+                const float4* __restrict__ nodeA, const int4* __restrict__ nodeB, const int32_t* __restrict__ gstart,
+                const int64_t* __restrict__ gscan, float theta2, float2* __restrict__ frep,
+                double* __restrict__ zgroup, Sched* sched, TreeState* st, int advance, float ee, int ee_iters,
+                float mom0, float mom1) {
+  __shared__ WalkEntry stk[kWalkWarps][kStack];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = blockIdx.x * kWalkWarps + w;
-  if (g < ngroups) {
-    const int k0 = 32 * g, k = k0 + lane;
-    const bool act = k < n;
+  const int ngroups = (int)gscan[n];
+  const WalkEntry root = node_entry(n > 1 ? 0 : ~0, ys, nodeA, nodeB);
+  for (;;) {
+    int g = 0;
+    if (lane == 0) g = (int)atomicAdd(&st->next_group, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= ngroups) break;
+    const int k0 = gstart[g], k1 = gstart[g + 1];
+    const int k = k0 + lane;
+    const bool act = k < k1;
     const float2 p = ys[act ? k : k0];
     const float gx0 = warp_min(p.x), gy0 = warp_min(p.y), gx1 = warp_max(p.x), gy1 = warp_max(p.y);
     const float self = act ? 1.0f : 0.0f;
@@ -316,49 +389,48 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
     double zd = 0.0;
     int nacc = 0;
     bool overflow = false;
-    if (lane == 0) stk[w][0] = n > 1 ? 0 : ~0;
-    int sp = 1;
-    __syncwarp();
-    while (sp > 0) {
-      const int v = stk[w][--sp];
-      __syncwarp();
-      if (v < 0) {
-        const int j = ~v;
-        const float2 q = ys[j];
-        interact(p, q.x, q.y, j == k ? 0.f : self, fx, fy, zf);
+    WalkEntry e = root;
+    int sp = 0;  // entries on the stack besides e
+    for (;;) {
+      const float dx = fmaxf(fmaxf(__fsub_rn(gx0, e.a.x), __fsub_rn(e.a.x, gx1)), 0.0f);
+      const float dy = fmaxf(fmaxf(__fsub_rn(gy0, e.a.y), __fsub_rn(e.a.y, gy1)), 0.0f);
+      const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+      bool pop = true;
+      if (e.a.z < __fmul_rn(theta2, d2)) {
+        interact(p, e.a.x, e.a.y, act ? e.a.w : 0.f, fx, fy, zf);
         ++nacc;
-      } else {
-        const float4 A = nodeA[v];
-        const float dx = fmaxf(fmaxf(__fsub_rn(gx0, A.x), __fsub_rn(A.x, gx1)), 0.0f);
-        const float dy = fmaxf(fmaxf(__fsub_rn(gy0, A.y), __fsub_rn(A.y, gy1)), 0.0f);
-        const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-        if (A.z < __fmul_rn(theta2, d2)) {
-          interact(p, A.x, A.y, act ? A.w : 0.f, fx, fy, zf);
-          ++nacc;
-        } else {
-          const int4 B = nodeB[v];
-          if (B.w - B.z + 1 <= kTreeBucket) {
-            for (int j = B.z; j <= B.w; ++j) {
-              const float2 q = ys[j];
-              interact(p, q.x, q.y, j == k ? 0.f : self, fx, fy, zf);
-            }
-            nacc += B.w - B.z + 1;
-          } else if (sp + 2 <= kStack) {
-            if (lane == 0) {
-              stk[w][sp] = B.y;
-              stk[w][sp + 1] = B.x;
-            }
-            sp += 2;
-            __syncwarp();
-          } else {
-            overflow = true;  // cannot happen for a radix tree of 64-bit keys; recorded, never indexed past
-          }
+      } else if (e.b.w - e.b.z + 1 <= kTreeBucket) {
+        const int last = e.b.w;
+        for (int j = e.b.z; j <= last; j += 4) {
+          float2 q[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) q[u] = ys[min(j + u, last)];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            interact(p, q[u].x, q[u].y, (j + u <= last && j + u != k) ? self : 0.f, fx, fy, zf);
         }
+        nacc += last - e.b.z + 1;
+      } else if (sp + 1 < kStack) {
+        // open: continue with the left child, park the right one
+        const WalkEntry l = node_entry(e.b.x, ys, nodeA, nodeB);
+        const WalkEntry r = node_entry(e.b.y, ys, nodeA, nodeB);
+        if (lane == 0) stk[w][sp] = r;
+        ++sp;
+        e = l;
+        pop = false;
+      } else {
+        overflow = true;  // cannot happen for a radix tree of 96-bit keys; recorded, never indexed past
       }
       if (nacc >= kZFlush) {
         zd += (double)zf;
         zf = 0.f;
         nacc = 0;
+      }
+      if (pop) {
+        if (sp == 0) break;
+        __syncwarp();
+        e = stk[w][--sp];
+        __syncwarp();
       }
     }
     zd += (double)zf;
@@ -373,6 +445,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
   if (arrive_last(&st->walk_done)) {
     const double total = sum_partials(zgroup, ngroups);
     if (threadIdx.x == 0) {
+      st->next_group = 0u;
       sched->Z = total;
       const int t = sched->t;
       sched->alpha = t < ee_iters ? ee : 1.0f;
@@ -394,8 +467,10 @@ int grid_for(int64_t items, int per_block, int cap) {
 tsgne_status TreeBufs::alloc(int n_points, int sm_count, cudaStream_t s) {
   n = n_points;
   nchunks = (n + kRadixChunk - 1) / kRadixChunk;
-  ngroups = (n + 31) / 32;
   box_blocks = grid_for(n, 256, 2 * sm_count);
+  int per_sm = 0;
+  TS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree_walk, 32 * kWalkWarps, 0));
+  walk_blocks = sm_count * (per_sm > 0 ? per_sm : 1);
   const size_t nn = (size_t)(n > 1 ? n - 1 : 1);
   TS_TRY(keys[0].alloc((size_t)n));
   TS_TRY(keys[1].alloc((size_t)n));
@@ -404,7 +479,11 @@ tsgne_status TreeBufs::alloc(int n_points, int sm_count, cudaStream_t s) {
   TS_TRY(ys.alloc((size_t)n));
   TS_TRY(counts.alloc((size_t)kRadixBins * nchunks));
   TS_TRY(offs.alloc((size_t)kRadixBins * nchunks + 1));
-  TS_TRY(scan_scr.alloc(scan_scratch_bytes((int64_t)kRadixBins * nchunks) / sizeof(int64_t)));
+  const int64_t scan_len = (int64_t)kRadixBins * nchunks > n ? (int64_t)kRadixBins * nchunks : n;
+  TS_TRY(scan_scr.alloc(scan_scratch_bytes(scan_len) / sizeof(int64_t)));
+  TS_TRY(is_start.alloc((size_t)n));
+  TS_TRY(gscan.alloc((size_t)n + 1));
+  TS_TRY(gstart.alloc((size_t)n + 1));
   TS_TRY(nodeA.alloc(nn));
   TS_TRY(nodeB.alloc(nn));
   TS_TRY(box.alloc(nn));
@@ -412,7 +491,7 @@ tsgne_status TreeBufs::alloc(int n_points, int sm_count, cudaStream_t s) {
   TS_TRY(flags.alloc(nn));
   TS_TRY(parent.alloc(2 * (size_t)n));
   TS_TRY(boxpart.alloc((size_t)box_blocks));
-  TS_TRY(zgroup.alloc((size_t)ngroups));
+  TS_TRY(zgroup.alloc((size_t)n));
   TS_TRY(state.alloc(1));
   TS_CUDA(cudaMemsetAsync(flags.get(), 0, sizeof(uint32_t) * nn, s));
   TS_CUDA(cudaMemsetAsync(state.get(), 0, sizeof(TreeState), s));
@@ -426,19 +505,19 @@ tsgne_status launch_tree_build(TreeBufs& tb, const float2* Y, cudaStream_t s) {
   TS_CUDA(cudaGetLastError());
   const int rblocks = (tb.nchunks + kRadixWarps - 1) / kRadixWarps;
   const int64_t ncount = (int64_t)kRadixBins * tb.nchunks;
-  for (int pass = 0; pass < 4; ++pass) {
+  for (int pass = 0; pass < 8; ++pass) {
     const int in = pass & 1, out = in ^ 1;
     k_radix_hist<<<rblocks, 32 * kRadixWarps, 0, s>>>(tb.keys[in].get(), n, 8 * pass, tb.nchunks, tb.counts.get());
     TS_CUDA(cudaGetLastError());
     TS_TRY(scan_i32_to_i64(tb.counts.get(), tb.offs.get(), ncount, tb.scan_scr.get(), s));
-    const bool last = pass == 3;
+    const bool last = pass == 7;
     k_radix_scatter<<<rblocks, 32 * kRadixWarps, 0, s>>>(tb.keys[in].get(), tb.vals[in].get(), n, 8 * pass,
                                                          tb.nchunks, tb.offs.get(), tb.keys[out].get(),
                                                          tb.vals[out].get(), last ? Y : nullptr,
                                                          last ? tb.ys.get() : nullptr);
     TS_CUDA(cudaGetLastError());
   }
-  // four passes: sorted keys / permutation are back in slot 0
+  // eight passes: sorted keys / permutation are back in slot 0
   if (n > 1) {
     k_tree_build<<<grid_for(n - 1, 256, 1 << 30), 256, 0, s>>>(tb.keys[0].get(), n, tb.nodeB.get(),
                                                                tb.parent.get());
@@ -446,16 +525,23 @@ tsgne_status launch_tree_build(TreeBufs& tb, const float2* Y, cudaStream_t s) {
                                                        tb.flags.get(), tb.box.get(), tb.sum.get(), tb.nodeA.get());
     TS_CUDA(cudaGetLastError());
   }
+  k_tree_group_starts<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, tb.nodeB.get(), tb.parent.get(),
+                                                                 tb.is_start.get());
+  TS_CUDA(cudaGetLastError());
+  TS_TRY(scan_i32_to_i64(tb.is_start.get(), tb.gscan.get(), n, tb.scan_scr.get(), s));
+  k_tree_group_list<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, tb.is_start.get(), tb.gscan.get(),
+                                                               tb.gstart.get());
+  TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }
 
 tsgne_status launch_tree_walk(TreeBufs& tb, float theta, float2* frep, Sched* sched, int advance, float ee,
                               int ee_iters, float mom0, float mom1, cudaStream_t s) {
   const float theta2 = theta * theta;
-  const int blocks = (tb.ngroups + kWalkWarps - 1) / kWalkWarps;
-  k_tree_walk<<<blocks, 32 * kWalkWarps, 0, s>>>(tb.n, tb.ys.get(), tb.vals[0].get(), tb.nodeA.get(),
-                                                 tb.nodeB.get(), theta2, frep, tb.zgroup.get(), tb.ngroups, sched,
-                                                 tb.state.get(), advance, ee, ee_iters, mom0, mom1);
+  k_tree_walk<<<tb.walk_blocks, 32 * kWalkWarps, 0, s>>>(tb.n, tb.ys.get(), tb.vals[0].get(), tb.nodeA.get(),
+                                                         tb.nodeB.get(), tb.gstart.get(), tb.gscan.get(), theta2,
+                                                         frep, tb.zgroup.get(), sched, tb.state.get(), advance, ee,
+                                                         ee_iters, mom0, mom1);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }

@@ -235,14 +235,16 @@ tsgne_status launch_init_Y(int n, uint64_t seed, float sigma, float2* Y, cudaStr
 constexpr int kTreeBucket = 16;
 
 struct TreeState {
-  float lo_x, lo_y, scale, pad;  // bounding square of the last pass
+  double scale;                  // 2^32 / side of the bounding square of the last pass
+  float lo_x, lo_y;              // its low corner
   uint32_t box_done, walk_done;  // last-CTA counters
+  uint32_t next_group, pad2;     // work-queue head of the walk
 };
 
 // Device buffers of the tree code for n points.
 struct TreeBufs {
-  int n = 0, nchunks = 0, ngroups = 0, box_blocks = 0;
-  DevBuf<uint32_t> keys[2];
+  int n = 0, nchunks = 0, box_blocks = 0, walk_blocks = 0;
+  DevBuf<uint64_t> keys[2];
   DevBuf<int32_t> vals[2];    // vals[0] after a build: sorted position -> point
   DevBuf<float2> ys;          // layout in sorted order
   DevBuf<int32_t> counts;     // radix counts, digit-major
@@ -254,7 +256,10 @@ struct TreeBufs {
   DevBuf<uint32_t> flags;     // bottom-up arrival counters (kept at zero between passes)
   DevBuf<int32_t> parent;     // internal nodes [0, n - 1), leaves after
   DevBuf<float4> boxpart;
-  DevBuf<double> zgroup;      // FP64 Z partial per group of 32 sorted points
+  DevBuf<int32_t> is_start;   // 1 where a group begins (sorted positions)
+  DevBuf<int64_t> gscan;      // exclusive scan of is_start; gscan[n] = number of groups
+  DevBuf<int32_t> gstart;     // first sorted position of each group, then n
+  DevBuf<double> zgroup;      // FP64 Z partial per group
   DevBuf<TreeState> state;
   tsgne_status alloc(int n_points, int sm_count, cudaStream_t s);
 };

@@ -560,3 +560,17 @@ def test_tree_gradient_reduces_to_exact_at_theta0():
     G2, Z2 = oracle.gradient_tree(300, rp, col, P, Y, 2.0, theta=0.8)
     Fa = oracle.attraction_rows(300, rp, col, P, Y.astype(np.float64), np.arange(300))
     assert Z1 == Z2 and np.allclose(G2 - G1, 4 * Fa, rtol=1e-10, atol=1e-15)
+
+
+def test_tree_outliers_keep_resolution():
+    """A few points 400x farther out than the bulk stretch the bounding
+    square; 32-bit cells per axis still separate the bulk, so the error at
+    theta = 0.5 stays that of an unstretched layout."""
+    n = 4000
+    lab = (np.arange(n) % 5).astype(np.int32)
+    Y = synth.spread_layout(lab, scale=10.0, seed=4).astype(np.float32)
+    Y[:4] = [[4000.0, 0.0], [-3000.0, 10.0], [0.0, 3500.0], [20.0, -3900.0]]
+    Fe, ze = _exact_rep(Y)
+    F, _, Z = oracle.repulsion_tree(Y, 0.5)
+    assert np.linalg.norm(F - Fe) / np.linalg.norm(Fe) < 1e-2
+    assert abs(Z - ze.sum()) / ze.sum() < 5e-3
