@@ -96,6 +96,17 @@ typedef struct {
                               0 only */
   float theta;             /* opening angle of the tree code, [0, 1] (default 0.5; 0 sums
                               every pair exactly through the tree) */
+  int32_t p_walks;         /* 0: p_{j|i} by the perplexity bisection of Eq. 2 (default);
+                              1..512: the random-walk estimate of Eq. 6 instead: p_walks
+                              walks of p_walk_length steps from every node over the
+                              neighbour graph, a step from u to v in N(u) with probability
+                              proportional to exp(-||x_u - x_v||^2); p_{j|i} = (walks from
+                              i ending at j) / p_walks, j != i; P then follows Eq. 3 on the
+                              symmetrised set of walk pairs (tsgne_get_P returns that
+                              structure).  Draws come from SplitMix64 seeded with
+                              seed ^ 0xD1B54A32D192ED03, output 1 + (i p_walks + r)
+                              p_walk_length + s for step s of walk r from node i. */
+  int32_t p_walk_length;   /* steps per walk, 1..64 (default 3) */
 } tsgne_config;
 
 /* Fills *cfg with the defaults listed above (perplexity 30). */
@@ -130,6 +141,9 @@ const char* tsgne_status_string(tsgne_status s);
  *      bisect_tol (Sec. 2.1); rows with |N(i)| <= perplexity are uniform;
  *   3. p_ij = (p_{j|i} + p_{i|j}) / T, T the sum of all numerators (Eq. 3;
  *      T = 2n when no node is isolated), so sum P = 1.
+ * With cfg.p_walks > 0 step 2 is the random-walk estimate of Eq. 6 over the
+ * structure of step 1 (see tsgne_config.p_walks), and step 3 runs on the
+ * symmetrised set of walk pairs, which becomes the structure of P.
  * n >= 2 nodes; row_ptr int64[n+1] with row_ptr[0] = 0, non-decreasing;
  * col_idx int32[row_ptr[n]] in [0, n) (any order, duplicates and self loops
  * allowed, either direction suffices); X float[n*d] row-major, d >= 1.

@@ -84,6 +84,12 @@ def _load():
             lib.tsgo_repulsion_tree.restype = ctypes.c_int
             lib.tsgo_gradient_tree.argtypes = [_i32, _p, _p, _p, _p, _dbl, _dbl, _i32, _p, _p]
             lib.tsgo_gradient_tree.restype = ctypes.c_int
+            lib.tsgo_random_walk_counts.argtypes = [_i32, _p, _p, _p, _i32, _i32, _i32, ctypes.c_uint64, _p, _p, _p]
+            lib.tsgo_random_walk_counts.restype = ctypes.c_int
+            lib.tsgo_random_walk_pcond.argtypes = [_i32, _p, _p, _p, _i32, _p, _p, _p]
+            lib.tsgo_random_walk_pcond.restype = ctypes.c_int
+            lib.tsgo_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            lib.tsgo_splitmix64.restype = ctypes.c_uint64
             _lib = lib
     return _lib
 
@@ -224,6 +230,44 @@ def gradient_tree(n, rp, col, P, Y, alpha=1.0, theta=0.5, bucket=16):
                                     int(bucket), _ptr(G), ctypes.byref(z))
     _check(st, "gradient_tree")
     return G, z.value
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """Output number k >= 1 of the SplitMix64 sequence seeded with seed."""
+    return int(_load().tsgo_splitmix64(seed & (2 ** 64 - 1), k))
+
+
+def random_walk_counts(n, rp, col, X, walks, length, seed=0):
+    """Eq. 6 walk counts: (wrp, wcol, wcnt), per node the distinct end points
+    j != i of its walks (increasing) and how many walks ended there."""
+    rp, col, Xd = _c(rp, np.int64), _c(col, np.int32), _c(X, np.float64)
+    d = Xd.shape[1]
+    cap = max(1, n * int(walks))
+    wrp = np.zeros(n + 1, np.int64)
+    wcol = np.zeros(cap, np.int32)
+    wcnt = np.zeros(cap, np.int32)
+    st = _load().tsgo_random_walk_counts(n, _ptr(rp), _ptr(col if col.size else np.zeros(1, np.int32)), _ptr(Xd), d,
+                                         int(walks), int(length), seed & (2 ** 64 - 1), _ptr(wrp), _ptr(wcol),
+                                         _ptr(wcnt))
+    _check(st, "random_walk_counts")
+    m = int(wrp[n])
+    return wrp, wcol[:m].copy(), wcnt[:m].copy()
+
+
+def random_walk_P(n, row_ptr, col, X, walks, length, seed=0):
+    """Joint P (Eq. 3) from the random-walk conditionals (Eq. 6) on the
+    graph's neighbour structure; returns (rp, col, P) on the symmetrised
+    structure of the walk pairs."""
+    rp, cl = structure(n, row_ptr, col)
+    wrp, wcol, wcnt = random_walk_counts(n, rp, cl, X, walks, length, seed)
+    srp, scol = structure(n, wrp, wcol)
+    pcond = np.zeros(max(1, scol.size))
+    _check(_load().tsgo_random_walk_pcond(n, _ptr(wrp), _ptr(wcol if wcol.size else np.zeros(1, np.int32)),
+                                          _ptr(wcnt if wcnt.size else np.zeros(1, np.int32)), int(walks), _ptr(srp),
+                                          _ptr(scol if scol.size else np.zeros(1, np.int32)), _ptr(pcond)),
+           "random_walk_pcond")
+    P, _ = joint_P(n, srp, scol, pcond[: scol.size])
+    return srp, scol, P
 
 
 def repulsion_all(Y, threads=None):

@@ -757,3 +757,118 @@ int tsgo_gradient_tree(int32_t n, const int64_t* rp, const int32_t* col, const d
   if (Z_out) *Z_out = Z;
   return TSGO_OK;
 }
+
+/*
+ * ---------------------------------------------------------------------------
+ * Random-walk estimate of p_{j|i} (Sec. 2.1, Eq. 6), on the neighbour graph
+ * N of Eq. 7 (the symmetric structure rp, col).
+ *
+ *  - Transition from u: to v in N(u) with probability proportional to
+ *    exp(-||x_u - x_v||^2) (the exponent's sign is read as negative; the
+ *    squared distances are shifted by the row minimum before exp, which does
+ *    not change the normalised probabilities).  Distances in FP64, summed
+ *    over dimensions in index order; the walk takes the first neighbour whose
+ *    running sum of weights exceeds U * (total weight), U uniform in [0, 1).
+ *    A node without neighbours keeps the walk where it is.
+ *  - R walks of L steps start at every node i.  Reading of Eq. 6: a walk
+ *    goes "from i to j" when it ends at j; walks ending at i are dropped
+ *    (p_ii = 0), so p_{j|i} = count_ij / R.  With L = 1 the expectation of
+ *    p_{j|i} is the transition probability itself, i.e. Eq. 2 with
+ *    2 sigma^2 = 1.
+ *  - U for step s of walk r from node i is the SplitMix64 output number
+ *    k = 1 + (i R + r) L + s of the sequence seeded with
+ *    seed ^ 0xD1B54A32D192ED03: state = that seed + k * 0x9E3779B97F4A7C15,
+ *    mixed as published (xor-shift 30, * 0xBF58476D1CE4E5B9, xor-shift 27,
+ *    * 0x94D049BB133111EB, xor-shift 31); U = (output >> 11) * 2^-53.
+ *
+ * Output: per node i the distinct end points j != i in increasing order with
+ * their counts: wrp[0..n], wcol / wcnt of length wrp[n] <= n R.
+ * ---------------------------------------------------------------------------
+ */
+static uint64_t sm64_output(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + k * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static double sq_dist(const double* X, int32_t d, int64_t u, int64_t v) {
+  double s = 0.0;
+  for (int32_t k = 0; k < d; ++k) {
+    double t = X[u * d + k] - X[v * d + k];
+    s += t * t;
+  }
+  return s;
+}
+
+static int32_t walk_step(const int64_t* rp, const int32_t* col, const double* X, int32_t d, int32_t u, double U) {
+  int64_t a = rp[u], b = rp[u + 1];
+  if (a == b) return u;
+  double dmin = INFINITY;
+  for (int64_t e = a; e < b; ++e) {
+    double s = sq_dist(X, d, u, col[e]);
+    if (s < dmin) dmin = s;
+  }
+  double total = 0.0;
+  for (int64_t e = a; e < b; ++e) total += exp(-(sq_dist(X, d, u, col[e]) - dmin));
+  double target = U * total, run = 0.0;
+  for (int64_t e = a; e < b; ++e) {
+    run += exp(-(sq_dist(X, d, u, col[e]) - dmin));
+    if (run > target) return col[e];
+  }
+  return col[b - 1];
+}
+
+int tsgo_random_walk_counts(int32_t n, const int64_t* rp, const int32_t* col, const double* X, int32_t d,
+                            int32_t R, int32_t L, uint64_t seed, int64_t* wrp, int32_t* wcol, int32_t* wcnt) {
+  if (n < 1 || R < 1 || L < 1 || d < 1) return TSGO_EINVAL;
+  int st = tsgo_check_csr(n, rp, col);
+  if (st != TSGO_OK) return st;
+  const uint64_t s0 = seed ^ 0xD1B54A32D192ED03ull;
+  int32_t* ends = (int32_t*)malloc(sizeof(int32_t) * (size_t)R);
+  if (!ends) return TSGO_ENOMEM;
+  int64_t m = 0;
+  wrp[0] = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t ne = 0;
+    for (int32_t r = 0; r < R; ++r) {
+      int32_t u = i;
+      for (int32_t s = 0; s < L; ++s) {
+        uint64_t k = 1u + ((uint64_t)i * (uint64_t)R + (uint64_t)r) * (uint64_t)L + (uint64_t)s;
+        double U = (double)(sm64_output(s0, k) >> 11) * (1.0 / 9007199254740992.0);
+        u = walk_step(rp, col, X, d, u, U);
+      }
+      if (u != i) ends[ne++] = u;
+    }
+    qsort(ends, (size_t)ne, sizeof(int32_t), cmp_i32);
+    for (int32_t t = 0; t < ne;) {
+      int32_t u = t;
+      while (u < ne && ends[u] == ends[t]) ++u;
+      wcol[m] = ends[t];
+      wcnt[m] = u - t;
+      ++m;
+      t = u;
+    }
+    wrp[i + 1] = m;
+  }
+  free(ends);
+  return TSGO_OK;
+}
+
+/*
+ * p_{j|i} = count_ij / R on a structure (rp, col) that contains every walk
+ * pair (i, j) (e.g. its symmetrisation); 0 where no walk from i ended at j.
+ */
+int tsgo_random_walk_pcond(int32_t n, const int64_t* wrp, const int32_t* wcol, const int32_t* wcnt, int32_t R,
+                           const int64_t* rp, const int32_t* col, double* pcond) {
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      pcond[e] = 0.0;
+      for (int64_t t = wrp[i]; t < wrp[i + 1]; ++t)
+        if (wcol[t] == col[e]) pcond[e] = (double)wcnt[t] / (double)R;
+    }
+  return TSGO_OK;
+}
+
+/* Output number k (k >= 1) of the SplitMix64 sequence seeded with seed. */
+uint64_t tsgo_splitmix64(uint64_t seed, uint64_t k) { return sm64_output(seed, k); }

@@ -102,6 +102,8 @@ class Config(ctypes.Structure):
         ("spin_budget_cycles", ctypes.c_int64),
         ("repulsion", ctypes.c_int32),
         ("theta", ctypes.c_float),
+        ("p_walks", ctypes.c_int32),
+        ("p_walk_length", ctypes.c_int32),
     ]
 
 

@@ -172,11 +172,20 @@ tsgne_status build_affinities(int n, const int64_t* rp, const int32_t* col, cons
     k_cond_affinity<false><<<grid, kAffCta, 0, s>>>(n, rp, col, X, d, perplexity, Hstar, tol, max_iter, dist.get(),
                                                     pcond.get());
   TS_CUDA(cudaGetLastError());
+  TS_TRY(joint_affinities(nnz, pcond.get(), tslot, P, sched, s));
+  return TSGNE_OK;
+}
+
+tsgne_status joint_affinities(int64_t nnz, const float* pcond, const int64_t* tslot, float* P, Sched* sched,
+                              cudaStream_t s) {
+  int dev = 0, sms = 1;
+  TS_CUDA(cudaGetDevice(&dev));
+  TS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int egrid = sms * 4;
   DevBuf<double> parts;
   TS_TRY(parts.alloc(egrid));
-  k_joint_total<<<egrid, kAffCta, 0, s>>>(nnz, pcond.get(), tslot, parts.get(), sched);
-  k_joint_scale<<<egrid, kAffCta, 0, s>>>(nnz, pcond.get(), tslot, P, sched);
+  k_joint_total<<<egrid, kAffCta, 0, s>>>(nnz, pcond, tslot, parts.get(), sched);
+  k_joint_scale<<<egrid, kAffCta, 0, s>>>(nnz, pcond, tslot, P, sched);
   TS_CUDA(cudaGetLastError());
   TS_CUDA(cudaStreamSynchronize(s));  // temporaries are freed on return
   return TSGNE_OK;

@@ -455,6 +455,8 @@ void tsgne_config_default(tsgne_config* cfg) {
   cfg->spin_budget_cycles = 2000000000LL;
   cfg->repulsion = 0;
   cfg->theta = 0.5f;
+  cfg->p_walks = 0;
+  cfg->p_walk_length = 3;
 }
 
 const char* tsgne_status_string(tsgne_status s) {
@@ -480,10 +482,11 @@ tsgne_status tsgne_create(tsgne_ctx** out, const tsgne_config* cfg, void* cuda_s
   if (!(c.perplexity > 1.f) || c.k_nn < 0 || c.k_nn > 256 || (c.precision != 0 && c.precision != 1) ||
       c.ee_iters < 0 || !(c.min_gain >= 0.f) || !(c.bisect_tol > 0.f) || c.bisect_max_iter < 1 ||
       !std::isfinite(c.early_exag) || !std::isfinite(c.momentum0) || !std::isfinite(c.momentum1) ||
-      (c.repulsion != 0 && c.repulsion != 1) || !(c.theta >= 0.f && c.theta <= 1.f)) {
+      (c.repulsion != 0 && c.repulsion != 1) || !(c.theta >= 0.f && c.theta <= 1.f) || c.p_walks < 0 ||
+      c.p_walks > 512 || c.p_walk_length < 1 || c.p_walk_length > 64) {
     last_msg() =
         "invalid configuration (perplexity must exceed 1; k_nn in [0, 256]; precision 0 or 1; repulsion 0 or 1; "
-        "theta in [0, 1])";
+        "theta in [0, 1]; p_walks in [0, 512]; p_walk_length in [1, 64])";
     return TSGNE_ERR_INVALID_ARG;
   }
   tsgne_ctx* ctx = new (std::nothrow) tsgne_ctx();
@@ -556,10 +559,23 @@ tsgne_status tsgne_build_P(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, co
   DevBuf<float> P;
   int64_t nnz = 0;
   API_TRY(ctx, build_neighbor_structure(n, rp_d, col_d, m, ctx->cfg.k_nn, rp, col, tslot, &nnz, ctx->stream));
-  API_TRY(ctx, P.alloc((size_t)nnz));
   API_CUDA(ctx, cudaMemsetAsync(ctx->sched.get(), 0, sizeof(Sched), ctx->stream));
-  API_TRY(ctx, build_affinities(n, rp.get(), col.get(), tslot.get(), nnz, X_d, d, ctx->cfg.perplexity,
-                                ctx->cfg.bisect_tol, ctx->cfg.bisect_max_iter, P.get(), ctx->sched.get(), ctx->stream));
+  if (ctx->cfg.p_walks > 0) {  // Eq. 6: the structure becomes that of the walk pairs
+    DevBuf<int64_t> wrp;
+    DevBuf<int32_t> wcol;
+    int64_t wnnz = 0;
+    API_TRY(ctx, random_walk_affinities(n, rp.get(), col.get(), nnz, X_d, d, ctx->cfg.p_walks,
+                                        ctx->cfg.p_walk_length, ctx->cfg.seed, wrp, wcol, P, &wnnz, ctx->sched.get(),
+                                        ctx->stream));
+    rp = std::move(wrp);
+    col = std::move(wcol);
+    nnz = wnnz;
+  } else {
+    API_TRY(ctx, P.alloc((size_t)nnz));
+    API_TRY(ctx, build_affinities(n, rp.get(), col.get(), tslot.get(), nnz, X_d, d, ctx->cfg.perplexity,
+                                  ctx->cfg.bisect_tol, ctx->cfg.bisect_max_iter, P.get(), ctx->sched.get(),
+                                  ctx->stream));
+  }
   API_TRY(ctx, prof_end(ctx, &pr));
   Sched h;
   API_TRY(ctx, read_sched(ctx, &h));

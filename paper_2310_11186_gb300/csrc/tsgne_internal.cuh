@@ -122,6 +122,19 @@ tsgne_status build_affinities(int n, const int64_t* rp, const int32_t* col, cons
                               const float* X, int d, float perplexity, float tol, int max_iter, float* P,
                               Sched* sched, cudaStream_t s);
 
+// Eq. 3 from conditional affinities pcond on a symmetric structure with
+// transpose slots: P = (pcond + pcond^T) / total, total into sched->red[0].
+// Synchronises the stream.
+tsgne_status joint_affinities(int64_t nnz, const float* pcond, const int64_t* tslot, float* P, Sched* sched,
+                              cudaStream_t s);
+
+// Random-walk estimate (Eq. 6, random_walk.cu): R walks of L steps from
+// every node over the structure (rp, col); allocates the symmetrised
+// structure of the walk pairs and its joint P.  Synchronises the stream.
+tsgne_status random_walk_affinities(int n, const int64_t* rp, const int32_t* col, int64_t nnz, const float* X, int d,
+                                    int R, int L, uint64_t seed, DevBuf<int64_t>& rp_out, DevBuf<int32_t>& col_out,
+                                    DevBuf<float>& P_out, int64_t* nnz_out, Sched* sched, cudaStream_t s);
+
 // ------------------------------------------------------ ShortestPath GE
 // X (device, n x d float) = BFS distances to the d targets on the symmetric
 // structure (rp, col) with nnz entries, capped at l0 + 1 (l0 <= 0: floor(sqrt(nnz/2))).

@@ -574,3 +574,90 @@ def test_tree_outliers_keep_resolution():
     F, _, Z = oracle.repulsion_tree(Y, 0.5)
     assert np.linalg.norm(F - Fe) / np.linalg.norm(Fe) < 1e-2
     assert abs(Z - ze.sum()) / ze.sum() < 5e-3
+
+
+# -------------------------------------------- random-walk estimator (Eq. 6)
+
+import os  # noqa: E402
+
+_GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_splitmix64_published_vector():
+    vals = [int(l) for l in open(os.path.join(_GOLDEN, "splitmix64_seed1234567.txt")) if l.strip()[:1].isdigit()]
+    assert [oracle.splitmix64(1234567, k) for k in range(1, 6)] == vals
+
+
+def _transition_matrix(n, rp, col, X):
+    """T[u, v] = exp(-|x_u - x_v|^2) / sum over N(u); a node without
+    neighbours stays (T[u, u] = 1)."""
+    T = np.zeros((n, n))
+    for u in range(n):
+        nb = col[rp[u]:rp[u + 1]]
+        if nb.size == 0:
+            T[u, u] = 1.0
+            continue
+        d2 = ((X[nb] - X[u]) ** 2).sum(1)
+        w = np.exp(-(d2 - d2.min()))
+        T[u, nb] = w / w.sum()
+    return T
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_random_walk_counts_follow_the_markov_chain(L):
+    """Walk counts / R estimate the L-step transition probabilities (T^L) of
+    the chain with T from exp(-||x_u - x_v||^2): each count within 5 binomial
+    standard deviations, and the self-returns dropped."""
+    n, R = 12, 20000
+    g = synth.random_graph(n, 3.0, seed=5)
+    rp, col = oracle.structure(n, g.row_ptr, g.col)
+    X = synth.normal(9, synth.S_MISC, 0, n * 3).reshape(n, 3) * 0.7
+    wrp, wcol, wcnt = oracle.random_walk_counts(n, rp, col, X, R, L, seed=11)
+    TL = np.linalg.matrix_power(_transition_matrix(n, rp, col, X), L)
+    for i in range(n):
+        got = np.zeros(n)
+        got[wcol[wrp[i]:wrp[i + 1]]] = wcnt[wrp[i]:wrp[i + 1]]
+        assert got[i] == 0
+        for j in range(n):
+            if j == i:
+                continue
+            p = TL[i, j]
+            sd = np.sqrt(R * p * (1 - p)) + 1e-9
+            assert abs(got[j] - R * p) <= 5 * sd + 1, (i, j, got[j], R * p)
+
+
+def test_random_walk_deterministic_cases():
+    # path 0-1-2-3, L = 1: the ends have one neighbour each
+    n = 4
+    rp, col = synth.csr_from_edges(n, np.arange(3), np.arange(1, 4))
+    X = np.zeros((n, 2))
+    wrp, wcol, wcnt = oracle.random_walk_counts(n, rp, col, X, 64, 1, seed=3)
+    assert wcol[wrp[0]:wrp[1]].tolist() == [1] and wcnt[wrp[0]:wrp[1]].tolist() == [64]
+    assert wcol[wrp[3]:wrp[4]].tolist() == [2] and wcnt[wrp[3]:wrp[4]].tolist() == [64]
+    # L = 2 from an end: every walk goes 0 -> 1 -> {0, 2}; returns to 0 are dropped
+    wrp, wcol, wcnt = oracle.random_walk_counts(n, rp, col, X, 64, 2, seed=3)
+    assert wcol[wrp[0]:wrp[1]].tolist() == [2] and 0 < wcnt[wrp[0]] < 64
+    # an isolated node keeps its walks at home: no pairs
+    rp1 = np.zeros(4, np.int64)
+    wrp, wcol, wcnt = oracle.random_walk_counts(3, rp1, np.zeros(0, np.int32), np.zeros((3, 2)), 8, 3)
+    assert wrp.tolist() == [0, 0, 0, 0]
+    # seeds: same seed same counts, another seed other counts
+    g = synth.random_graph(50, 4.0, seed=1)
+    r2, c2 = oracle.structure(50, g.row_ptr, g.col)
+    X = synth.normal(2, synth.S_MISC, 0, 100).reshape(50, 2)
+    a = oracle.random_walk_counts(50, r2, c2, X, 16, 3, seed=1)
+    b = oracle.random_walk_counts(50, r2, c2, X, 16, 3, seed=1)
+    c = oracle.random_walk_counts(50, r2, c2, X, 16, 3, seed=2)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert not (np.array_equal(a[1], c[1]) and np.array_equal(a[2], c[2]))
+
+
+def test_random_walk_P_is_a_symmetric_distribution():
+    n = 300
+    g = synth.random_graph(n, 5.0, seed=8)
+    X = synth.block_embedding((np.arange(n) % 3).astype(np.int32), 8, seed=8) * 0.3
+    rp, col, P = oracle.random_walk_P(n, g.row_ptr, g.col, X, 32, 2, seed=4)
+    assert P.sum() == pytest.approx(1.0, rel=1e-12)
+    assert np.all(P > 0)
+    t = oracle.transpose_slots(n, rp, col)
+    assert np.allclose(P, P[t], rtol=0, atol=0)
