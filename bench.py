@@ -683,6 +683,7 @@ def main():
     ap.add_argument("--rmat-steps", type=int, default=5)
     ap.add_argument("--rmat-scale", type=int, default=21)
     ap.add_argument("--only-rmat", action="store_true", help="run only the R-MAT section (profiling)")
+    ap.add_argument("--only-tree", action="store_true", help="run only the tree-code section (profiling)")
     ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOAD,
                     help="zipf300k is the benchmark; the others are smaller cases for profiling")
     args = ap.parse_args()
@@ -699,6 +700,19 @@ def main():
         torch.cuda.set_device(0)
         pbuild.build()
         print(json.dumps({"rmat": bench_rmat(args, pkg)}), flush=True)
+        return 0
+    if args.only_tree:
+        import torch
+
+        from paper_2310_11186_gb300 import build as pbuild
+        import paper_2310_11186_gb300 as pkg
+
+        torch.cuda.set_device(0)
+        pbuild.build()
+        g, X = synth.workload(args.workload, seed=args.seed)
+        Y0 = synth.y_init(g.n, seed=args.seed)
+        Yt = synth.spread_layout(g.labels, scale=30.0, seed=args.seed)
+        print(json.dumps({"tree": bench_tree(args, pkg, g, X, Y0, Yt)}), flush=True)
         return 0
     return run_ours(args)
 
