@@ -347,6 +347,7 @@ def run_ours(args):
         serving = bench_serving(args, pkg)
     rmat_res = bench_rmat(args, pkg) if (rank == 0 and args.rmat) else None
     tree_res = bench_tree(args, pkg, g, X, Y0, Yt) if (rank == 0 and not args.no_tree) else None
+    rw_res = bench_random_walk(args, pkg, g, X) if (rank == 0 and not args.no_tree) else None
 
     if rank != 0:
         return 0
@@ -405,6 +406,7 @@ def run_ours(args):
         "batched": batched,
         "rmat": rmat_res,
         "tree": tree_res,
+        "random_walk_P": rw_res,
         "paper_context": "300K nodes / 1M edges in under 5 min (ShortestPath + t-SGNE, 32-core Xeon Gold 6338)",
     }
     print(json.dumps(line), flush=True)
@@ -479,6 +481,26 @@ def bench_tree(args, pkg, g, X, Y0, Yt, log_fn=log):
     }
     log_fn(f"[bench] tree theta={theta}: {out['iters_per_s']:.1f} it/s, build {out['kernels_ms_per_step']['tree_build']:.3f} ms, "
            f"walk {out['kernels_ms_per_step']['tree_walk']:.3f} ms, grad err {out['grad_rel_l2_vs_exact']:.2e}")
+    return out
+
+
+def bench_random_walk(args, pkg, g, X, log_fn=log):
+    """One-time cost of the random-walk estimate of P (Eq. 6) on the same
+    graph, next to the perplexity bisection's, and the size of the P it
+    produces (walk pairs reach beyond the graph's edges)."""
+    import torch
+
+    out = {"walks": args.rw_walks, "length": args.rw_length}
+    for name, cfg in (("bisection", {}), ("random_walk", {"p_walks": args.rw_walks,
+                                                          "p_walk_length": args.rw_length})):
+        with pkg.Layout(**cfg) as lay:
+            lay.build_P(g.row_ptr, g.col, X)  # warm (allocations, module load)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lay.build_P(g.row_ptr, g.col, X)
+            out[name] = {"build_ms": (time.perf_counter() - t0) * 1e3, "nnz_P": int(lay.sizes()[1])}
+    log_fn(f"[bench] P build: bisection {out['bisection']['build_ms']:.1f} ms, random walks "
+           f"{out['random_walk']['build_ms']:.1f} ms (nnz {out['random_walk']['nnz_P']})")
     return out
 
 
@@ -679,6 +701,8 @@ def main():
     ap.add_argument("--serve-iters", type=int, default=500)
     ap.add_argument("--no-tree", action="store_true", help="skip the tree-code repulsion section")
     ap.add_argument("--tree-theta", type=float, default=0.5)
+    ap.add_argument("--rw-walks", type=int, default=64)
+    ap.add_argument("--rw-length", type=int, default=3)
     ap.add_argument("--rmat", action="store_true", help="also run the R-MAT 2^21 workload (about a minute)")
     ap.add_argument("--rmat-steps", type=int, default=5)
     ap.add_argument("--rmat-scale", type=int, default=21)

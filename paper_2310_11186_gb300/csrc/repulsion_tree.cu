@@ -37,10 +37,10 @@
 // Groups: one thread per leaf climbs while the parent holds <= 32 points and
 // marks whether it starts its group; a scan numbers the groups in sorted
 // order.  Walk: a persistent grid takes groups from a queue, one warp per
-// group, lane = point; the stack of node ids is in shared memory and every
-// lane takes the same branch, so the traversal is free of divergence and
-// every node load is a broadcast.  Z: FP32 partial sums
-// flushed into FP64 every 64 interactions, a fixed xor butterfly per warp,
+// group, lane = point; per round the lanes decide up to 32 stack entries at
+// once and then all apply the round's accepted nodes and exact points, so
+// the dependent node loads along the tree are issued 32 at a time.  Z: FP32
+// partial sums flushed into FP64 every round, a fixed xor butterfly per warp,
 // one FP64 partial per group, and the group partials added in group order by
 // the last CTA -- bit-reproducible from run to run.
 #include <cmath>
@@ -58,8 +58,6 @@ constexpr int kRadixChunk = 32 * kRadixItems;  // keys per warp chunk
 constexpr int kRadixWarps = 8;
 constexpr int kRadixBins = 256;
 constexpr int kWalkWarps = 8;
-constexpr int kStack = 100;  // a root-to-leaf path has at most 96 splits (one per augmented-key bit)
-constexpr int kZFlush = 64;
 
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
@@ -339,30 +337,22 @@ __device__ __forceinline__ void interact(float2 p, float qx, float qy, float c, 
   fy = fmaf(cw2, dy, fy);
 }
 
-// Stack entry of the walk: a node's record (centre x, y, r2, count) and
-// (left, right, first, last).  A leaf at sorted position j is the record
-// (y_j, 0, 1) with (-1, -1, j, j): accepting it is the exact interaction with
-// its point (count 1 at the point itself), and it is never accepted by the
-// lanes of its own group (its distance to their box is 0), which take the
-// exact path with the self term removed.
-struct WalkEntry {
-  float4 a;
-  int4 b;
-};
-
-__device__ __forceinline__ WalkEntry node_entry(int c, const float2* __restrict__ ys,
-                                                const float4* __restrict__ nodeA, const int4* __restrict__ nodeB) {
-  WalkEntry e;
-  if (c < 0) {
-    const float2 q = ys[~c];
-    e.a = make_float4(q.x, q.y, 0.f, 1.f);
-    e.b = make_int4(-1, -1, ~c, ~c);
-  } else {
-    e.a = nodeA[c];
-    e.b = nodeB[c];
-  }
-  return e;
-}
+// Walk of one group, 32 stack entries per round: each lane takes one entry
+// (the top of the stack), loads its node record and decides: accept (r2 <
+// theta^2 d2: one interaction of weight count at the centre), sum exactly
+// (at most kTreeBucket points) or open (push both children).  Ballots
+// compact the three outcomes into shared-memory lists in lane order; then
+// every lane applies all accepted nodes and all exact points of the round
+// to its own point.  A leaf (sorted position j) is the record (y_j, r2 = 0,
+// count 1): accepting it is the exact interaction with its point, and it is
+// never accepted by its own group (distance 0 to the box), which takes the
+// exact path with the self term removed.  The set of interactions is the
+// definition's; only the order of the sums differs from a depth-first walk.
+// Stack bound: a round pops up to 32 entries and pushes up to 64; above
+// kWalkStack - 200 entries rounds pop one entry (a depth-first walk, which
+// adds at most one entry per tree level, i.e. < 100), so kWalkStack is never
+// passed.
+constexpr int kWalkStack = 1024;
 
 __global__ void __launch_bounds__(32 * kWalkWarps)
     k_tree_walk(int n, const float2* __restrict__ ys, const int32_t* __restrict__ perm,
@@ -370,10 +360,12 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                 const int64_t* __restrict__ gscan, float theta2, float2* __restrict__ frep,
                 double* __restrict__ zgroup, Sched* sched, TreeState* st, int advance, float ee, int ee_iters,
                 float mom0, float mom1) {
-  __shared__ WalkEntry stk[kWalkWarps][kStack];
+  __shared__ int stk[kWalkWarps][kWalkStack];
+  __shared__ float4 acc_list[kWalkWarps][32];
+  __shared__ int2 exact_list[kWalkWarps][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   const int ngroups = (int)gscan[n];
-  const WalkEntry root = node_entry(n > 1 ? 0 : ~0, ys, nodeA, nodeB);
   for (;;) {
     int g = 0;
     if (lane == 0) g = (int)atomicAdd(&st->next_group, 1u);
@@ -385,55 +377,72 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
     const float2 p = ys[act ? k : k0];
     const float gx0 = warp_min(p.x), gy0 = warp_min(p.y), gx1 = warp_max(p.x), gy1 = warp_max(p.y);
     const float self = act ? 1.0f : 0.0f;
-    float fx = 0.f, fy = 0.f, zf = 0.f;
+    float fx = 0.f, fy = 0.f;
     double zd = 0.0;
-    int nacc = 0;
     bool overflow = false;
-    WalkEntry e = root;
-    int sp = 0;  // entries on the stack besides e
-    for (;;) {
-      const float dx = fmaxf(fmaxf(__fsub_rn(gx0, e.a.x), __fsub_rn(e.a.x, gx1)), 0.0f);
-      const float dy = fmaxf(fmaxf(__fsub_rn(gy0, e.a.y), __fsub_rn(e.a.y, gy1)), 0.0f);
-      const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-      bool pop = true;
-      if (e.a.z < __fmul_rn(theta2, d2)) {
-        interact(p, e.a.x, e.a.y, act ? e.a.w : 0.f, fx, fy, zf);
-        ++nacc;
-      } else if (e.b.w - e.b.z + 1 <= kTreeBucket) {
-        const int last = e.b.w;
-        for (int j = e.b.z; j <= last; j += 4) {
+    if (lane == 0) stk[w][0] = n > 1 ? 0 : ~0;
+    int sp = 1;
+    while (sp > 0) {
+      __syncwarp();
+      const int take = sp > kWalkStack - 200 ? 1 : (sp < 32 ? sp : 32);
+      const bool has = lane < take;
+      const int v = has ? stk[w][sp - take + lane] : 0;
+      sp -= take;
+      int kind = 0;  // 1 accept, 2 exact, 3 open
+      float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
+      int4 B = make_int4(0, 0, 0, 0);
+      if (has) {
+        if (v < 0) {
+          const float2 q = ys[~v];
+          A = make_float4(q.x, q.y, 0.f, 1.f);
+          B = make_int4(-1, -1, ~v, ~v);
+        } else {
+          A = nodeA[v];
+          B = nodeB[v];
+        }
+        const float dx = fmaxf(fmaxf(__fsub_rn(gx0, A.x), __fsub_rn(A.x, gx1)), 0.0f);
+        const float dy = fmaxf(fmaxf(__fsub_rn(gy0, A.y), __fsub_rn(A.y, gy1)), 0.0f);
+        const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        kind = A.z < __fmul_rn(theta2, d2) ? 1 : (B.w - B.z + 1 <= kTreeBucket ? 2 : 3);
+      }
+      const uint32_t ma = __ballot_sync(0xffffffffu, kind == 1);
+      const uint32_t mb = __ballot_sync(0xffffffffu, kind == 2);
+      const uint32_t mo = __ballot_sync(0xffffffffu, kind == 3);
+      __syncwarp();  // every lane has read its entry before the pushes reuse the slots
+      if (kind == 1) acc_list[w][__popc(ma & lt)] = A;
+      if (kind == 2) exact_list[w][__popc(mb & lt)] = make_int2(B.z, B.w);
+      const int npush = 2 * __popc(mo);
+      if (sp + npush <= kWalkStack) {
+        if (kind == 3) {
+          const int slot = sp + 2 * __popc(mo & lt);
+          stk[w][slot] = B.y;  // right below, left on top
+          stk[w][slot + 1] = B.x;
+        }
+        sp += npush;
+      } else {
+        overflow = true;  // excluded by the bound above; recorded, never written past
+      }
+      __syncwarp();
+      float zf = 0.f;
+      const int na = __popc(ma);
+      for (int t = 0; t < na; ++t) {
+        const float4 e = acc_list[w][t];
+        interact(p, e.x, e.y, act ? e.w : 0.f, fx, fy, zf);
+      }
+      const int nb = __popc(mb);
+      for (int t = 0; t < nb; ++t) {
+        const int2 r = exact_list[w][t];
+        for (int j = r.x; j <= r.y; j += 4) {
           float2 q[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) q[u] = ys[min(j + u, last)];
+          for (int u = 0; u < 4; ++u) q[u] = ys[min(j + u, r.y)];
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            interact(p, q[u].x, q[u].y, (j + u <= last && j + u != k) ? self : 0.f, fx, fy, zf);
+            interact(p, q[u].x, q[u].y, (j + u <= r.y && j + u != k) ? self : 0.f, fx, fy, zf);
         }
-        nacc += last - e.b.z + 1;
-      } else if (sp + 1 < kStack) {
-        // open: continue with the left child, park the right one
-        const WalkEntry l = node_entry(e.b.x, ys, nodeA, nodeB);
-        const WalkEntry r = node_entry(e.b.y, ys, nodeA, nodeB);
-        if (lane == 0) stk[w][sp] = r;
-        ++sp;
-        e = l;
-        pop = false;
-      } else {
-        overflow = true;  // cannot happen for a radix tree of 96-bit keys; recorded, never indexed past
       }
-      if (nacc >= kZFlush) {
-        zd += (double)zf;
-        zf = 0.f;
-        nacc = 0;
-      }
-      if (pop) {
-        if (sp == 0) break;
-        __syncwarp();
-        e = stk[w][--sp];
-        __syncwarp();
-      }
+      zd += (double)zf;
     }
-    zd += (double)zf;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) zd += __shfl_xor_sync(0xffffffffu, zd, o);
     if (lane == 0) {
