@@ -27,7 +27,7 @@
 // it and the CPU reference takes the same decisions.
 //
 // GPU mapping.  Keys: one thread per point.  Sort: LSD radix sort, 8 passes
-// of 8 bits, stable: a warp owns a chunk of 512 keys; per-(digit, chunk) counts
+// of 8 bits, stable: a warp owns a chunk of 256 keys; per-(digit, chunk) counts
 // are scanned digit-major, and the scatter ranks equal digits within a round
 // of 32 keys with __match_any_sync, so equal keys keep their input order.
 // The last pass also gathers the layout into sorted order.  Tree: one thread
@@ -53,7 +53,7 @@ namespace tsgne {
 
 namespace {
 
-constexpr int kRadixItems = 16;                // keys per lane of a warp chunk
+constexpr int kRadixItems = 8;                 // keys per lane of a warp chunk
 constexpr int kRadixChunk = 32 * kRadixItems;  // keys per warp chunk
 constexpr int kRadixWarps = 8;
 constexpr int kRadixBins = 256;
@@ -72,6 +72,27 @@ __device__ __forceinline__ float warp_max(float v) {
 
 // ---------------------------------------------------------- 1. bounding box
 
+// Min / max over a 256-thread CTA (exact in any order); valid in thread 0.
+__device__ __forceinline__ float4 block_box(float lx, float ly, float hx, float hy, float4* ws) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  lx = warp_min(lx);
+  ly = warp_min(ly);
+  hx = warp_max(hx);
+  hy = warp_max(hy);
+  if (lane == 0) ws[w] = make_float4(lx, ly, hx, hy);
+  __syncthreads();
+  float4 b = ws[0];
+  if (threadIdx.x == 0)
+    for (int k = 1; k < 8; ++k) {
+      b.x = fminf(b.x, ws[k].x);
+      b.y = fminf(b.y, ws[k].y);
+      b.z = fmaxf(b.z, ws[k].z);
+      b.w = fmaxf(b.w, ws[k].w);
+    }
+  __syncthreads();
+  return b;
+}
+
 __global__ void __launch_bounds__(256) k_tree_box(const float2* __restrict__ Y, int n, float4* __restrict__ part,
                                                   TreeState* st) {
   __shared__ float4 ws[8];
@@ -83,33 +104,20 @@ __global__ void __launch_bounds__(256) k_tree_box(const float2* __restrict__ Y, 
     hx = fmaxf(hx, p.x);
     hy = fmaxf(hy, p.y);
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  lx = warp_min(lx);
-  ly = warp_min(ly);
-  hx = warp_max(hx);
-  hy = warp_max(hy);
-  if (lane == 0) ws[w] = make_float4(lx, ly, hx, hy);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float4 b = ws[0];
-    for (int k = 1; k < 8; ++k) {
-      b.x = fminf(b.x, ws[k].x);
-      b.y = fminf(b.y, ws[k].y);
-      b.z = fmaxf(b.z, ws[k].z);
-      b.w = fmaxf(b.w, ws[k].w);
-    }
-    part[blockIdx.x] = b;
-  }
+  float4 b = block_box(lx, ly, hx, hy, ws);
+  if (threadIdx.x == 0) part[blockIdx.x] = b;
   if (arrive_last(&st->box_done)) {
+    lx = ly = INFINITY;
+    hx = hy = -INFINITY;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+      const float4 q = __ldcg(part + k);
+      lx = fminf(lx, q.x);
+      ly = fminf(ly, q.y);
+      hx = fmaxf(hx, q.z);
+      hy = fmaxf(hy, q.w);
+    }
+    b = block_box(lx, ly, hx, hy, ws);
     if (threadIdx.x == 0) {
-      float4 b = __ldcg(part);
-      for (unsigned k = 1; k < gridDim.x; ++k) {
-        const float4 q = __ldcg(part + k);
-        b.x = fminf(b.x, q.x);
-        b.y = fminf(b.y, q.y);
-        b.z = fmaxf(b.z, q.z);
-        b.w = fmaxf(b.w, q.w);
-      }
       const float side = fmaxf(fmaxf(__fsub_rn(b.z, b.x), __fsub_rn(b.w, b.y)), 1e-30f);
       st->lo_x = b.x;
       st->lo_y = b.y;
@@ -182,15 +190,21 @@ __global__ void __launch_bounds__(32 * kRadixWarps)
   const int c = blockIdx.x * kRadixWarps + w;
   if (c >= nchunks) return;
   for (int d = lane; d < kRadixBins; d += 32) base[w][d] = (int32_t)offs[(int64_t)d * nchunks + c];
-  __syncwarp();
   const uint32_t lt = (1u << lane) - 1u;
   const int64_t k0 = (int64_t)c * kRadixChunk + lane;
-  for (int r = 0; r < kRadixItems; ++r) {
+  uint64_t key[kRadixItems];
+  int32_t val[kRadixItems];
+#pragma unroll
+  for (int r = 0; r < kRadixItems; ++r) {  // all loads of the chunk in flight at once
     const int64_t k = k0 + 32 * r;
-    const bool valid = k < n;
-    const uint64_t key = valid ? kin[k] : 0ull;
-    const int32_t val = valid ? vin[k] : 0;
-    const uint32_t d = valid ? (uint32_t)(key >> shift) & 255u : 256u + (uint32_t)lane;  // invalid lanes match only themselves
+    key[r] = k < n ? kin[k] : 0ull;
+    val[r] = k < n ? vin[k] : 0;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < kRadixItems; ++r) {
+    const bool valid = k0 + 32 * r < n;
+    const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 255u : 256u + (uint32_t)lane;  // invalid lanes match only themselves
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(peers & lt);
     int pos = 0;
@@ -199,9 +213,9 @@ __global__ void __launch_bounds__(32 * kRadixWarps)
     if (valid && rank == 0) base[w][d] += __popc(peers);
     __syncwarp();
     if (valid) {
-      kout[pos] = key;
-      vout[pos] = val;
-      if (ys) ys[pos] = Y[val];
+      kout[pos] = key[r];
+      vout[pos] = val[r];
+      if (ys) ys[pos] = Y[val[r]];
     }
   }
 }
@@ -516,10 +530,11 @@ tsgne_status launch_tree_build(TreeBufs& tb, const float2* Y, cudaStream_t s) {
   const int64_t ncount = (int64_t)kRadixBins * tb.nchunks;
   for (int pass = 0; pass < 8; ++pass) {
     const int in = pass & 1, out = in ^ 1;
-    k_radix_hist<<<rblocks, 32 * kRadixWarps, 0, s>>>(tb.keys[in].get(), n, 8 * pass, tb.nchunks, tb.counts.get());
+    const bool last = pass == 7;
+    k_radix_hist<<<rblocks, 32 * kRadixWarps, 0, s>>>(tb.keys[in].get(), n, 8 * pass, tb.nchunks,
+                                                      tb.counts.get());
     TS_CUDA(cudaGetLastError());
     TS_TRY(scan_i32_to_i64(tb.counts.get(), tb.offs.get(), ncount, tb.scan_scr.get(), s));
-    const bool last = pass == 7;
     k_radix_scatter<<<rblocks, 32 * kRadixWarps, 0, s>>>(tb.keys[in].get(), tb.vals[in].get(), n, 8 * pass,
                                                          tb.nchunks, tb.offs.get(), tb.keys[out].get(),
                                                          tb.vals[out].get(), last ? Y : nullptr,

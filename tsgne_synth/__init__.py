@@ -297,6 +297,8 @@ def workload(name: str, seed: int = 0):
     rewiring, 10 % rewired, 128-d X.
     ``zipf100k``: the same recipe at 100,000 nodes and 333,333 edges (a
     smaller case of the same kernels, for profiling).
+    ``zipf3m``: the same recipe at the scale of the paper's largest LFR graph
+    (3,000,000 nodes, 4,937,941 edges: mean degree 3.3), 200 blocks, 64-d X.
     """
     if name == "sbm2k":
         g = sbm_equal(2000, 10, 0.05, 0.0005, seed=seed)
@@ -307,6 +309,9 @@ def workload(name: str, seed: int = 0):
     if name == "zipf100k":
         g = sbm_zipf(100_000, 50, 333_333, 1.2, 0.10, seed=seed)
         return g, block_embedding(g.labels, 128, seed=seed)
+    if name == "zipf3m":
+        g = sbm_zipf(3_000_000, 200, 4_937_941, 1.2, 0.10, seed=seed)
+        return g, block_embedding(g.labels, 64, seed=seed)
     raise KeyError(name)
 
 
