@@ -270,23 +270,25 @@ def random_walk_P(n, row_ptr, col, X, walks, length, seed=0):
     return srp, scol, P
 
 
-def repulsion_all(Y, threads=None):
-    """All rows of repulsion_rows, split over threads (ctypes drops the GIL).
+def repulsion_all(Y, threads=None, i0=0, i1=None):
+    """Rows [i0, i1) (default all) of repulsion_rows, split over threads
+    (ctypes drops the GIL).
 
     The split only partitions rows; each row is still the plain loop.
-    Returns (F_rep n x 2, zrow n).
+    Returns (F_rep, zrow) for those rows.
     """
     Yd = _c(Y, np.float64)
     n = Yd.shape[0]
+    i1 = n if i1 is None else i1
     threads = threads or os.cpu_count() or 1
-    bounds = np.linspace(0, n, 4 * threads + 1).astype(int)
-    F = np.zeros((n, 2))
-    zr = np.zeros(n)
+    bounds = np.linspace(i0, i1, 4 * threads + 1).astype(int)
+    F = np.zeros((i1 - i0, 2))
+    zr = np.zeros(i1 - i0)
 
     def work(k):
         a, b = int(bounds[k]), int(bounds[k + 1])
         if b > a:
-            F[a:b], zr[a:b] = repulsion_rows(Yd, a, b)
+            F[a - i0:b - i0], zr[a - i0:b - i0] = repulsion_rows(Yd, a, b)
 
     with ThreadPoolExecutor(threads) as ex:
         list(ex.map(work, range(len(bounds) - 1)))
