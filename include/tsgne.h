@@ -331,6 +331,82 @@ tsgne_status tsgne_build_P_shortest_path(tsgne_ctx* ctx, int32_t n, const int64_
 #define TSGNE_NOALLOC_MAX_N 65536
 
 /*
+ * ---------------------------------------------------------------- serving
+ * Continuous-batching server over one batch (the paper has no serving
+ * layer).  Requests wait in a FIFO queue; each tsgne_server_tick
+ *   1. admits queued requests in order while the estimated device bytes of
+ *      the resident layouts (tsgne_server_estimate_bytes) stay within
+ *      budget_bytes and below the free device memory -- the first request is
+ *      admitted whatever its size when nothing is resident;
+ *   2. selects the resident layouts to advance: all (policy 0) or, policy 1,
+ *      those with the least remaining iterations x n^2, in that order, until
+ *      their pairs per iteration reach fill_pairs;
+ *   3. runs tick_iters iterations of the selected layouts (tsgne_batch_run);
+ *   4. retires the layouts that reached iters: the layout is copied to
+ *      server-owned host memory and the member's device memory freed.
+ * A request's layout equals the one it gets alone (members are independent,
+ * see tsgne_batch_*).  Cancelling frees a queued or resident request; its
+ * result then reports TSGNE_ERR_CANCELLED.  Not thread-safe.
+ */
+typedef struct tsgne_server tsgne_server;
+
+typedef struct {
+  int64_t budget_bytes; /* admission budget of the resident layouts (default 80 GiB) */
+  int32_t iters;        /* iterations per request (default 500; a multiple of tick_iters) */
+  int32_t tick_iters;   /* iterations per tick (default 10) */
+  int32_t max_members;  /* resident layouts at most (default 256) */
+  int32_t tile_warps;   /* repulsion tile of the batch: 1, 2, 4 or 8 warps (default 2) */
+  int32_t policy;       /* 0: advance every resident layout; 1: shortest remaining work first (default) */
+  double fill_pairs;    /* policy 1: pairs per iteration that fill the GPU (default 4e9) */
+} tsgne_server_config;
+
+void tsgne_server_config_default(tsgne_server_config* cfg);
+
+/* Device bytes a resident layout of n points and nnz affinities holds in a
+ * batch with the given tile (P, layout, optimiser state, initial layout,
+ * per-tile repulsion slots, Z partials); -1 for invalid arguments.  Host
+ * arithmetic only (no GPU needed). */
+int64_t tsgne_server_estimate_bytes(int32_t n, int64_t nnz, int32_t tile_warps);
+
+/* cfg (may be NULL: defaults) configures every layout; cuda_stream as for
+ * tsgne_batch_create.  Errors: INVALID_ARG (iters not a multiple of
+ * tick_iters, policy not 0/1, ...), OOM, CUDA. */
+tsgne_status tsgne_server_create(tsgne_server** out, const tsgne_server_config* scfg, const tsgne_config* cfg,
+                                 void* cuda_stream);
+void tsgne_server_destroy(tsgne_server* s);
+const char* tsgne_server_last_error(const tsgne_server* s);
+
+/* Queues a request (host arrays, copied): the graph's CSR (as for
+ * tsgne_build_P), X float[n*d], Y0 float[n*2] or NULL (N(0, 1e-4^2) from the
+ * seed).  *request_id receives its id (> 0).  Errors: INVALID_ARG, BAD_CSR,
+ * OOM (host). */
+tsgne_status tsgne_server_submit(tsgne_server* s, int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                 const float* X, int32_t d, const float* Y0, int64_t* request_id);
+
+/* One scheduling round (admit, select, run, retire; see above).  Outputs
+ * (may be NULL): resident layouts and queued requests after the round, and
+ * how many were retired by it.  Synchronises. */
+tsgne_status tsgne_server_tick(tsgne_server* s, int32_t* resident, int32_t* queued, int32_t* retired);
+
+/* Pops up to capacity ids of requests retired since the last call, oldest first. */
+tsgne_status tsgne_server_finished(tsgne_server* s, int64_t* ids, int32_t capacity, int32_t* count);
+
+/* State of a request: 0 queued, 1 resident, 2 done, 3 cancelled; and its iterations. */
+tsgne_status tsgne_server_status(tsgne_server* s, int64_t request_id, int32_t* state, int32_t* iterations);
+
+/* Copies a finished layout into Y_out (host float[n*2]) and forgets the
+ * request.  NOT_BUILT if it has not finished; CANCELLED (and forgets it) if
+ * it was cancelled; INVALID_ARG for an unknown id. */
+tsgne_status tsgne_server_result(tsgne_server* s, int64_t request_id, float* Y_out);
+
+/* Cancels a queued or resident request (its device memory is freed at
+ * once).  INVALID_ARG if it is unknown, finished or already cancelled. */
+tsgne_status tsgne_server_cancel(tsgne_server* s, int64_t request_id);
+
+/* Estimated device bytes held, resident layouts, queued requests. */
+tsgne_status tsgne_server_usage(tsgne_server* s, int64_t* used_bytes, int32_t* resident, int32_t* queued);
+
+/*
  * Repulsion pass that allocates no device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc, e.g. code running inside a framework or plugin host that owns

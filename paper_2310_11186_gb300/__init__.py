@@ -52,6 +52,9 @@ __all__ = [
     "NOALLOC_MAX_N",
     "Layout",
     "Batch",
+    "ServerConfig",
+    "Server",
+    "server_estimate_bytes",
     "KERNEL_CLASSES",
 ]
 
@@ -150,6 +153,18 @@ EXPORTS = {
     "tsgne_batch_cached_tile": (_st, [_p, ctypes.POINTER(_i32)]),
     "tsgne_shortest_path_embedding": (_st, [_i32, _p, _p, _p, _i32, _i32, _p, _i32, _p]),
     "tsgne_build_P_shortest_path": (_st, [_p, _i32, _p, _p, _p, _i32, _i32, _i32]),
+    "tsgne_server_config_default": (None, [_p]),
+    "tsgne_server_estimate_bytes": (_i64, [_i32, _i64, _i32]),
+    "tsgne_server_create": (_st, [ctypes.POINTER(_p), _p, _p, _p]),
+    "tsgne_server_destroy": (None, [_p]),
+    "tsgne_server_last_error": (ctypes.c_char_p, [_p]),
+    "tsgne_server_submit": (_st, [_p, _i32, _p, _p, _p, _i32, _p, ctypes.POINTER(_i64)]),
+    "tsgne_server_tick": (_st, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "tsgne_server_finished": (_st, [_p, _p, _i32, ctypes.POINTER(_i32)]),
+    "tsgne_server_status": (_st, [_p, _i64, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "tsgne_server_result": (_st, [_p, _i64, _p]),
+    "tsgne_server_cancel": (_st, [_p, _i64]),
+    "tsgne_server_usage": (_st, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
 }
 
 NOALLOC_MAX_N = 65536  # TSGNE_NOALLOC_MAX_N
@@ -640,4 +655,124 @@ class Batch:
         try:
             self.close()
         except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- serving
+
+class ServerConfig(ctypes.Structure):
+    """Mirror of ``tsgne_server_config``."""
+
+    _fields_ = [
+        ("budget_bytes", ctypes.c_int64),
+        ("iters", ctypes.c_int32),
+        ("tick_iters", ctypes.c_int32),
+        ("max_members", ctypes.c_int32),
+        ("tile_warps", ctypes.c_int32),
+        ("policy", ctypes.c_int32),
+        ("fill_pairs", ctypes.c_double),
+    ]
+
+
+def server_estimate_bytes(n: int, nnz: int, tile_warps: int) -> int:
+    """tsgne_server_estimate_bytes (host arithmetic; no GPU needed)."""
+    return int(lib().tsgne_server_estimate_bytes(int(n), int(nnz), int(tile_warps)))
+
+
+class Server:
+    """The ``tsgne_server_*`` C calls: queue, admission by device-memory
+    budget, shortest-remaining-work scheduling and retirement all run in the
+    library; this class only marshals.
+
+    >>> srv = Server(iters=500)
+    >>> rid = srv.submit(g.row_ptr, g.col, X)
+    >>> while srv.tick()[0] or srv.tick()[1]: ...
+    >>> Y = srv.result(rid)
+    """
+
+    STATES = ("queued", "resident", "done", "cancelled")
+
+    def __init__(self, config: Config | None = None, stream=None, **server_fields):
+        sc = ServerConfig()
+        lib().tsgne_server_config_default(ctypes.byref(sc))
+        for k, v in server_fields.items():
+            setattr(sc, k, v)
+        self.server_config = sc
+        self.config = config if config is not None else tsgne_config_default()
+        self._stream = stream
+        if stream is None:
+            torch = _torch()
+            if torch is not None and torch.cuda.is_available():
+                self._stream = torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(getattr(self._stream, "cuda_stream", self._stream)) if self._stream is not None else None
+        st = lib().tsgne_server_create(ctypes.byref(h), ctypes.byref(sc), ctypes.byref(self.config), s)
+        if st != 0:
+            raise TsgneError(st, "tsgne_server_create failed")
+        self.h = h
+        self.sizes = {}
+
+    def _check(self, st):
+        if st != 0:
+            raise TsgneError(st, lib().tsgne_server_last_error(self.h).decode())
+
+    def submit(self, row_ptr, col, X, Y0=None) -> int:
+        rp = np.ascontiguousarray(row_ptr, np.int64)
+        ci = np.ascontiguousarray(col, np.int32)
+        x = np.ascontiguousarray(X, np.float32)
+        y = None if Y0 is None else np.ascontiguousarray(Y0, np.float32)
+        rid = _i64()
+        n = rp.size - 1
+        self._check(lib().tsgne_server_submit(self.h, n, rp.ctypes.data_as(_p), ci.ctypes.data_as(_p) if ci.size else None,
+                                              x.ctypes.data_as(_p), int(x.shape[1]),
+                                              None if y is None else y.ctypes.data_as(_p), ctypes.byref(rid)))
+        self.sizes[rid.value] = n
+        return rid.value
+
+    def tick(self):
+        """One scheduling round; returns (resident, queued, retired)."""
+        r, q, d = _i32(), _i32(), _i32()
+        self._check(lib().tsgne_server_tick(self.h, ctypes.byref(r), ctypes.byref(q), ctypes.byref(d)))
+        return r.value, q.value, d.value
+
+    def finished(self, capacity: int = 1024):
+        ids = np.zeros(max(1, capacity), np.int64)
+        k = _i32()
+        self._check(lib().tsgne_server_finished(self.h, ids.ctypes.data_as(_p), int(capacity), ctypes.byref(k)))
+        return ids[: k.value].tolist()
+
+    def status(self, rid: int):
+        st, it = _i32(), _i32()
+        self._check(lib().tsgne_server_status(self.h, int(rid), ctypes.byref(st), ctypes.byref(it)))
+        return self.STATES[st.value], it.value
+
+    def result(self, rid: int):
+        out = np.empty((self.sizes[rid], 2), np.float32)
+        self._check(lib().tsgne_server_result(self.h, int(rid), out.ctypes.data_as(_p)))
+        self.sizes.pop(rid, None)
+        return out
+
+    def cancel(self, rid: int):
+        self._check(lib().tsgne_server_cancel(self.h, int(rid)))
+
+    def usage(self):
+        u, r, q = _i64(), _i32(), _i32()
+        self._check(lib().tsgne_server_usage(self.h, ctypes.byref(u), ctypes.byref(r), ctypes.byref(q)))
+        return {"used_bytes": u.value, "resident": r.value, "queued": q.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tsgne_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover
             pass

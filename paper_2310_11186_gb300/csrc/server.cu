@@ -1,0 +1,318 @@
+// Continuous-batching layout server (host scheduler over the batch engine).
+//
+// A request is a graph (CSR + embedding, optional Y0) to lay out for a fixed
+// number of iterations.  Submitted requests wait in a FIFO queue; every tick
+//   1. admits queued requests in order while the estimated device bytes of
+//      all resident layouts stay within the budget and below the free device
+//      memory (the first request is admitted whatever its size when nothing
+//      is resident, so no request starves);
+//   2. selects the resident layouts to advance: all of them (policy 0), or
+//      (policy 1, shortest remaining work first) those with the least
+//      remaining iterations x n^2 until their pairs per iteration reach
+//      fill_pairs, enough tile pairs to keep every SM busy;
+//   3. runs tick_iters iterations of the selected layouts in one batched call;
+//   4. retires the layouts that reached their iterations: the layout is
+//      copied to server-owned host memory and the member's device memory is
+//      freed.
+// Every member's arithmetic is independent of the others (batch.cu), so a
+// request's layout is the same whatever else is resident.  Cancelling a
+// queued or resident request frees it at once; its result reports
+// TSGNE_ERR_CANCELLED.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tsgne.h"
+
+namespace {
+
+enum ReqState : int32_t { kQueued = 0, kResident = 1, kDone = 2, kCancelled = 3 };
+
+struct Req {
+  int64_t id = 0;
+  int32_t n = 0, d = 0;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> col;
+  std::vector<float> X, Y0, Y;
+  int32_t state = kQueued;
+  int32_t iters = 0;
+  int32_t member = -1;
+  int64_t bytes = 0;
+};
+
+}  // namespace
+
+struct tsgne_server {
+  tsgne_server_config cfg{};
+  tsgne_batch* batch = nullptr;
+  std::map<int64_t, Req> reqs;
+  std::deque<int64_t> queue;
+  std::vector<int64_t> finished;  // retired since the last tsgne_server_finished
+  int64_t next_id = 1;
+  int64_t used = 0;
+  std::string msg;
+};
+
+namespace {
+
+tsgne_status sfail(tsgne_server* s, tsgne_status st, const std::string& m) {
+  s->msg = m;
+  return st;
+}
+
+tsgne_status batch_fail(tsgne_server* s, tsgne_status st) {
+  s->msg = tsgne_batch_last_error(s->batch);
+  return st;
+}
+
+int64_t free_device_bytes(int64_t fallback) {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fallback;
+  return (int64_t)fr;
+}
+
+tsgne_status admit(tsgne_server* s) {
+  int32_t members = 0;
+  for (const auto& kv : s->reqs) members += kv.second.state == kResident;
+  while (!s->queue.empty()) {
+    Req& r = s->reqs[s->queue.front()];
+    const int64_t need = tsgne_server_estimate_bytes(r.n, 2 * r.rp[r.n], s->cfg.tile_warps);
+    if (members > 0 && (members >= s->cfg.max_members || s->used + need > s->cfg.budget_bytes ||
+                        need > free_device_bytes(s->cfg.budget_bytes)))
+      break;
+    int32_t mid = -1;
+    const tsgne_status st = tsgne_batch_add(s->batch, r.n, r.rp.data(), r.col.empty() ? nullptr : r.col.data(),
+                                            r.X.data(), r.d, r.Y0.empty() ? nullptr : r.Y0.data(), TSGNE_PTR_HOST,
+                                            &mid);
+    if (st != TSGNE_OK) return batch_fail(s, st);
+    r.member = mid;
+    r.state = kResident;
+    r.bytes = need;
+    s->used += need;
+    ++members;
+    s->queue.pop_front();
+    std::vector<int64_t>().swap(r.rp);  // the batch holds its own copy now
+    std::vector<int32_t>().swap(r.col);
+    std::vector<float>().swap(r.X);
+    std::vector<float>().swap(r.Y0);
+  }
+  return TSGNE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tsgne_server_config_default(tsgne_server_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->budget_bytes = (int64_t)80 << 30;
+  c->iters = 500;
+  c->tick_iters = 10;
+  c->max_members = 256;
+  c->tile_warps = 2;
+  c->policy = 1;
+  c->fill_pairs = 4e9;
+}
+
+int64_t tsgne_server_estimate_bytes(int32_t n, int64_t nnz, int32_t tile_warps) {
+  if (n < 1 || nnz < 0 || tile_warps < 1) return -1;
+  const int64_t T = 256 * (int64_t)tile_warps;
+  const int64_t n_pad_max = (n + 2047) / 2048 * 2048;
+  const int64_t nt = (n + T - 1) / T;
+  const int64_t n_pad = nt * T;
+  const int64_t units = nt * (nt + 1) / 2;
+  return 8 * ((int64_t)n + 1) + 8 * nnz + 5 * 8 * n_pad_max + 8 * (int64_t)n + 8 * nt * n_pad + 8 * units + 256;
+}
+
+tsgne_status tsgne_server_create(tsgne_server** out, const tsgne_server_config* scfg, const tsgne_config* cfg,
+                                 void* cuda_stream) {
+  if (!out) return TSGNE_ERR_INVALID_ARG;
+  *out = nullptr;
+  tsgne_server_config c;
+  if (scfg) c = *scfg; else tsgne_server_config_default(&c);
+  if (c.iters < 1 || c.tick_iters < 1 || c.iters % c.tick_iters != 0 || c.max_members < 1 || c.budget_bytes < 1 ||
+      !(c.policy == 0 || c.policy == 1) || !(c.fill_pairs > 0.0))
+    return TSGNE_ERR_INVALID_ARG;
+  tsgne_server* s = new (std::nothrow) tsgne_server();
+  if (!s) return TSGNE_ERR_OOM;
+  s->cfg = c;
+  const tsgne_status st = tsgne_batch_create(&s->batch, cfg, c.tile_warps, cuda_stream);
+  if (st != TSGNE_OK) {
+    delete s;
+    return st;
+  }
+  *out = s;
+  return TSGNE_OK;
+}
+
+void tsgne_server_destroy(tsgne_server* s) {
+  if (!s) return;
+  tsgne_batch_destroy(s->batch);
+  delete s;
+}
+
+const char* tsgne_server_last_error(const tsgne_server* s) { return s ? s->msg.c_str() : ""; }
+
+tsgne_status tsgne_server_submit(tsgne_server* s, int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                 const float* X, int32_t d, const float* Y0, int64_t* request_id) {
+  if (!s) return TSGNE_ERR_INVALID_ARG;
+  if (n < 2 || d < 1 || !row_ptr || !X || !request_id)
+    return sfail(s, TSGNE_ERR_INVALID_ARG, "need n >= 2, d >= 1, row_ptr, X and request_id");
+  const int64_t m = row_ptr[n];
+  if (row_ptr[0] != 0 || m < 0) return sfail(s, TSGNE_ERR_BAD_CSR, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+  for (int32_t i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return sfail(s, TSGNE_ERR_BAD_CSR, "row_ptr decreases");
+  if (m > 0 && !col_idx) return sfail(s, TSGNE_ERR_INVALID_ARG, "col_idx is NULL");
+  for (int64_t e = 0; e < m; ++e)
+    if (col_idx[e] < 0 || col_idx[e] >= n) return sfail(s, TSGNE_ERR_BAD_CSR, "column outside [0, n)");
+  Req r;
+  r.id = s->next_id++;
+  r.n = n;
+  r.d = d;
+  try {
+    r.rp.assign(row_ptr, row_ptr + n + 1);
+    if (m > 0) r.col.assign(col_idx, col_idx + m);
+    r.X.assign(X, X + (size_t)n * d);
+    if (Y0) r.Y0.assign(Y0, Y0 + 2 * (size_t)n);
+    s->queue.push_back(r.id);
+    s->reqs.emplace(r.id, std::move(r));
+  } catch (const std::bad_alloc&) {
+    return sfail(s, TSGNE_ERR_OOM, "host memory for the request");
+  }
+  *request_id = s->next_id - 1;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_server_tick(tsgne_server* s, int32_t* resident, int32_t* queued, int32_t* retired) {
+  if (!s) return TSGNE_ERR_INVALID_ARG;
+  {
+    const tsgne_status st = admit(s);
+    if (st != TSGNE_OK) return st;
+  }
+  std::vector<std::pair<double, int64_t>> res;  // (remaining work, id)
+  for (const auto& kv : s->reqs)
+    if (kv.second.state == kResident)
+      res.emplace_back((double)(s->cfg.iters - kv.second.iters) * (double)kv.second.n * (double)kv.second.n,
+                       kv.first);
+  int32_t done_now = 0;
+  if (!res.empty()) {
+    std::sort(res.begin(), res.end());
+    std::vector<int64_t> chosen;
+    double pairs = 0.0;
+    for (const auto& w : res) {
+      chosen.push_back(w.second);
+      pairs += 0.5 * (double)s->reqs[w.second].n * (double)s->reqs[w.second].n;
+      if (s->cfg.policy == 1 && pairs >= s->cfg.fill_pairs) break;
+    }
+    for (const auto& w : res) {
+      const bool want = std::find(chosen.begin(), chosen.end(), w.second) != chosen.end();
+      const tsgne_status st = tsgne_batch_set_active(s->batch, s->reqs[w.second].member, want ? 1 : 0);
+      if (st != TSGNE_OK) return batch_fail(s, st);
+    }
+    tsgne_status st = tsgne_batch_run(s->batch, s->cfg.tick_iters);
+    if (st != TSGNE_OK) return batch_fail(s, st);
+    for (int64_t id : chosen) {
+      Req& r = s->reqs[id];
+      r.iters += s->cfg.tick_iters;
+      if (r.iters < s->cfg.iters) continue;
+      try {
+        r.Y.resize(2 * (size_t)r.n);
+      } catch (const std::bad_alloc&) {
+        return sfail(s, TSGNE_ERR_OOM, "host memory for a result");
+      }
+      int32_t it = 0;
+      st = tsgne_batch_get_Y(s->batch, r.member, r.Y.data(), &it, TSGNE_PTR_HOST);
+      if (st != TSGNE_OK) return batch_fail(s, st);
+      r.iters = it;  // the member's own device counter
+      st = tsgne_batch_remove(s->batch, r.member);
+      if (st != TSGNE_OK) return batch_fail(s, st);
+      r.state = kDone;
+      r.member = -1;
+      s->used -= r.bytes;
+      s->finished.push_back(id);
+      ++done_now;
+    }
+  }
+  int32_t nres = 0;
+  for (const auto& kv : s->reqs) nres += kv.second.state == kResident;
+  if (resident) *resident = nres;
+  if (queued) *queued = (int32_t)s->queue.size();
+  if (retired) *retired = done_now;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_server_finished(tsgne_server* s, int64_t* ids, int32_t capacity, int32_t* count) {
+  if (!s || !count || capacity < 0 || (capacity > 0 && !ids)) return TSGNE_ERR_INVALID_ARG;
+  const int32_t k = std::min<int32_t>(capacity, (int32_t)s->finished.size());
+  for (int32_t i = 0; i < k; ++i) ids[i] = s->finished[i];
+  s->finished.erase(s->finished.begin(), s->finished.begin() + k);
+  *count = k;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_server_status(tsgne_server* s, int64_t request_id, int32_t* state, int32_t* iterations) {
+  if (!s) return TSGNE_ERR_INVALID_ARG;
+  auto it = s->reqs.find(request_id);
+  if (it == s->reqs.end()) return sfail(s, TSGNE_ERR_INVALID_ARG, "unknown request id");
+  if (state) *state = it->second.state;
+  if (iterations) *iterations = it->second.iters;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_server_result(tsgne_server* s, int64_t request_id, float* Y_out) {
+  if (!s) return TSGNE_ERR_INVALID_ARG;
+  auto it = s->reqs.find(request_id);
+  if (it == s->reqs.end()) return sfail(s, TSGNE_ERR_INVALID_ARG, "unknown request id");
+  Req& r = it->second;
+  if (r.state == kCancelled) {
+    s->reqs.erase(it);
+    return sfail(s, TSGNE_ERR_CANCELLED, "the request was cancelled");
+  }
+  if (r.state != kDone) return sfail(s, TSGNE_ERR_NOT_BUILT, "the request has not finished");
+  if (!Y_out) return sfail(s, TSGNE_ERR_INVALID_ARG, "Y_out is NULL");
+  std::memcpy(Y_out, r.Y.data(), sizeof(float) * r.Y.size());
+  s->reqs.erase(it);
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_server_cancel(tsgne_server* s, int64_t request_id) {
+  if (!s) return TSGNE_ERR_INVALID_ARG;
+  auto it = s->reqs.find(request_id);
+  if (it == s->reqs.end()) return sfail(s, TSGNE_ERR_INVALID_ARG, "unknown request id");
+  Req& r = it->second;
+  if (r.state == kQueued) {
+    s->queue.erase(std::find(s->queue.begin(), s->queue.end(), request_id));
+  } else if (r.state == kResident) {
+    const tsgne_status st = tsgne_batch_remove(s->batch, r.member);
+    if (st != TSGNE_OK) return batch_fail(s, st);
+    s->used -= r.bytes;
+    r.member = -1;
+  } else {
+    return sfail(s, TSGNE_ERR_INVALID_ARG, "the request has already finished or been cancelled");
+  }
+  r.state = kCancelled;
+  std::vector<int64_t>().swap(r.rp);
+  std::vector<int32_t>().swap(r.col);
+  std::vector<float>().swap(r.X);
+  std::vector<float>().swap(r.Y0);
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_server_usage(tsgne_server* s, int64_t* used_bytes, int32_t* resident, int32_t* queued) {
+  if (!s) return TSGNE_ERR_INVALID_ARG;
+  int32_t nres = 0;
+  for (const auto& kv : s->reqs) nres += kv.second.state == kResident;
+  if (used_bytes) *used_bytes = s->used;
+  if (resident) *resident = nres;
+  if (queued) *queued = (int32_t)s->queue.size();
+  return TSGNE_OK;
+}
+
+}  // extern "C"

@@ -165,3 +165,39 @@ def test_srpt_runs_short_jobs_first_and_results_stay_exact():
     assert reqs[1].finished < reqs[0].finished and reqs[2].finished < reqs[0].finished
     for r, (g, X, Y0) in zip(reqs, gs):
         assert np.array_equal(r.Y, _alone(g, X, Y0, 2, 30))
+
+
+def test_server_cancel_and_bookkeeping():
+    """Cancelling a resident and a queued request frees them at once and their
+    results report CANCELLED; the others finish exactly as alone, and the
+    server's memory account returns to zero."""
+    gs = _graphs([1500, 1200, 900, 700], seed=90)
+    one = serve.estimate_bytes(1500, int(gs[0][0].row_ptr[-1]) * 2, 2)
+    with pkg.Server(iters=30, tick_iters=10, tile_warps=2, policy=0, budget_bytes=int(2.5 * one)) as srv:
+        ids = [srv.submit(g.row_ptr, g.col, X, Y0) for g, X, Y0 in gs]
+        assert all(srv.status(i) == ("queued", 0) for i in ids)
+        resident, queued, retired = srv.tick()
+        assert resident == 2 and queued == 2 and retired == 0  # the budget holds two
+        assert srv.status(ids[0]) == ("resident", 10)
+        before = srv.usage()["used_bytes"]
+        srv.cancel(ids[1])  # resident
+        srv.cancel(ids[3])  # queued
+        assert srv.usage()["used_bytes"] < before and srv.usage()["queued"] == 1
+        with pytest.raises(pkg.TsgneError) as e:
+            srv.cancel(ids[1])
+        assert e.value.status == 1
+        with pytest.raises(pkg.TsgneError) as e:
+            srv.result(ids[0])  # not finished
+        assert e.value.status == 5
+        while srv.usage()["resident"] or srv.usage()["queued"]:
+            srv.tick()
+        assert sorted(srv.finished()) == [ids[0], ids[2]]
+        for k in (0, 2):
+            g, X, Y0 = gs[k]
+            assert srv.status(ids[k]) == ("done", 30)
+            assert np.array_equal(srv.result(ids[k]), _alone(g, X, Y0, 2, 30))
+        for k in (1, 3):
+            with pytest.raises(pkg.TsgneError) as e:
+                srv.result(ids[k])
+            assert e.value.status == 8
+        assert srv.usage() == {"used_bytes": 0, "resident": 0, "queued": 0}
