@@ -625,6 +625,11 @@ def bench_serving(args, pkg, log_fn=log):
         "p50_s": served["p50_s"],
         "p99_s": served["p99_s"],
         "wall_s": served["wall_s"],
+        "offered_per_s": args.serve_rate,
+        # an offered rate above what the GPU completes keeps the queue busy for
+        # the whole trace, so the completion rate is then the sustainable rate
+        "max_sustainable_per_s": (served["layouts_per_s"] if served["layouts_per_s"] < 0.9 * args.serve_rate
+                                  else None),
         "serial_one_at_a_time": serial,
     }
 

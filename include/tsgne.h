@@ -228,6 +228,20 @@ tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update
  */
 tsgne_status tsgne_kernel_times(tsgne_ctx* ctx, double* ms, int64_t* launches, int32_t n, int32_t reset);
 
+/*
+ * Process-wide limit on the device bytes the library holds (contexts,
+ * batches and servers together, the no-allocation entry point's static array
+ * excepted); bytes <= 0 removes it.  An allocation that would pass the limit
+ * fails with TSGNE_ERR_OOM before cudaMalloc is called; the object that
+ * asked stays usable (a later call may retry).  The paper has no
+ * counterpart: the limit serves hosts that share a GPU among tenants, and
+ * tests of the out-of-memory paths.
+ */
+void tsgne_set_device_memory_limit(int64_t bytes);
+
+/* Device bytes the library holds at the moment (same account). */
+int64_t tsgne_device_memory_in_use(void);
+
 /* Launch geometry of the repulsion pass: grid CTAs, threads per CTA, i per
  * thread, j-tile, j-chunks, pad length.  Any pointer may be NULL. */
 tsgne_status tsgne_repulsion_shape(tsgne_ctx* ctx, int32_t* grid, int32_t* block, int32_t* i_per_thread,

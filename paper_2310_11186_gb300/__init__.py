@@ -55,6 +55,8 @@ __all__ = [
     "ServerConfig",
     "Server",
     "server_estimate_bytes",
+    "set_device_memory_limit",
+    "device_memory_in_use",
     "KERNEL_CLASSES",
 ]
 
@@ -153,6 +155,8 @@ EXPORTS = {
     "tsgne_batch_cached_tile": (_st, [_p, ctypes.POINTER(_i32)]),
     "tsgne_shortest_path_embedding": (_st, [_i32, _p, _p, _p, _i32, _i32, _p, _i32, _p]),
     "tsgne_build_P_shortest_path": (_st, [_p, _i32, _p, _p, _p, _i32, _i32, _i32]),
+    "tsgne_set_device_memory_limit": (None, [_i64]),
+    "tsgne_device_memory_in_use": (_i64, []),
     "tsgne_server_config_default": (None, [_p]),
     "tsgne_server_estimate_bytes": (_i64, [_i32, _i64, _i32]),
     "tsgne_server_create": (_st, [ctypes.POINTER(_p), _p, _p, _p]),
@@ -672,6 +676,16 @@ class ServerConfig(ctypes.Structure):
         ("policy", ctypes.c_int32),
         ("fill_pairs", ctypes.c_double),
     ]
+
+
+def set_device_memory_limit(nbytes: int):
+    """tsgne_set_device_memory_limit: cap on the library's device bytes (<= 0: none)."""
+    lib().tsgne_set_device_memory_limit(int(nbytes))
+
+
+def device_memory_in_use() -> int:
+    """tsgne_device_memory_in_use."""
+    return int(lib().tsgne_device_memory_in_use())
 
 
 def server_estimate_bytes(n: int, nnz: int, tile_warps: int) -> int:

@@ -2,6 +2,7 @@
 // argument validation, host/device copies, CUDA-graph replay of iterations
 // and per-kernel CUDA-event profiling.  All arithmetic runs in the kernels of
 // structure.cu, affinity.cu, repulsion.cu and iterate.cu.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -17,6 +18,23 @@ std::string& last_msg() {
   thread_local std::string m;
   return m;
 }
+
+namespace {
+std::atomic<int64_t> g_dev_bytes{0};
+std::atomic<int64_t> g_dev_limit{0};  // 0: no limit
+}  // namespace
+
+bool device_bytes_reserve(size_t bytes) {
+  const int64_t b = (int64_t)bytes;
+  const int64_t lim = g_dev_limit.load();
+  int64_t cur = g_dev_bytes.load();
+  do {
+    if (lim > 0 && cur + b > lim) return false;
+  } while (!g_dev_bytes.compare_exchange_weak(cur, cur + b));
+  return true;
+}
+
+void device_bytes_release(size_t bytes) { g_dev_bytes.fetch_sub((int64_t)bytes); }
 
 tsgne_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
   std::string s = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" + std::to_string(line) + ")";
@@ -806,6 +824,10 @@ tsgne_status tsgne_kernel_times(tsgne_ctx* ctx, double* ms, int64_t* launches, i
     }
   return TSGNE_OK;
 }
+
+void tsgne_set_device_memory_limit(int64_t bytes) { tsgne::g_dev_limit.store(bytes > 0 ? bytes : 0); }
+
+int64_t tsgne_device_memory_in_use(void) { return tsgne::g_dev_bytes.load(); }
 
 tsgne_status tsgne_repulsion_shape(tsgne_ctx* ctx, int32_t* grid, int32_t* block, int32_t* i_per_thread,
                                    int32_t* j_tile, int32_t* j_chunks, int32_t* n_pad) {

@@ -179,17 +179,21 @@ __global__ void __launch_bounds__(32 * kRadixWarps)
   for (int d = lane; d < kRadixBins; d += 32) counts[(int64_t)d * nchunks + c] = (int32_t)h[w][d];
 }
 
-// Stable scatter of one pass.  offs = exclusive scan of counts (digit-major).
+// Stable scatter of one pass.  The exclusive scan of counts (digit-major)
+// at index k is offs[k] + boffs[k / kScanBlock] (scan_i32_to_i64_blocks).
 // With Y != NULL the layout is gathered into sorted order (ys[pos] = Y[val]).
 __global__ void __launch_bounds__(32 * kRadixWarps)
     k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin, int n, int shift, int nchunks,
-                    const int64_t* __restrict__ offs, uint64_t* __restrict__ kout, int32_t* __restrict__ vout,
-                    const float2* __restrict__ Y, float2* __restrict__ ys) {
+                    const int64_t* __restrict__ offs, const int64_t* __restrict__ boffs, uint64_t* __restrict__ kout,
+                    int32_t* __restrict__ vout, const float2* __restrict__ Y, float2* __restrict__ ys) {
   __shared__ int32_t base[kRadixWarps][kRadixBins];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * kRadixWarps + w;
   if (c >= nchunks) return;
-  for (int d = lane; d < kRadixBins; d += 32) base[w][d] = (int32_t)offs[(int64_t)d * nchunks + c];
+  for (int d = lane; d < kRadixBins; d += 32) {
+    const int64_t k = (int64_t)d * nchunks + c;
+    base[w][d] = (int32_t)(offs[k] + boffs[k / kScanBlock]);
+  }
   const uint32_t lt = (1u << lane) - 1u;
   const int64_t k0 = (int64_t)c * kRadixChunk + lane;
   uint64_t key[kRadixItems];
@@ -284,11 +288,12 @@ __global__ void k_tree_up(int n, const int4* __restrict__ nodeB, const int32_t* 
   if (k >= n) return;
   int p = parent[n - 1 + k];
   while (p >= 0) {
+    const int4 b = nodeB[p];  // written by an earlier launch: safe before the arrival
+    const int pp = parent[p];
     __threadfence();
     if (atomicAdd(&flags[p], 1u) == 0u) return;
     __threadfence();
     flags[p] = 0u;
-    const int4 b = nodeB[p];
     float4 bl, br;
     float2 sl, sr;
     child_summary(b.x, ys, box, sum, bl, sl);
@@ -300,7 +305,7 @@ __global__ void k_tree_up(int n, const int4* __restrict__ nodeB, const int32_t* 
     const float cnt = (float)(b.w - b.z + 1);
     const float r = fmaxf(__fsub_rn(bp.z, bp.x), __fsub_rn(bp.w, bp.y));
     nodeA[p] = make_float4(__fdiv_rn(sp.x, cnt), __fdiv_rn(sp.y, cnt), __fmul_rn(r, r), cnt);
-    p = parent[p];
+    p = pp;
   }
 }
 
@@ -534,11 +539,11 @@ tsgne_status launch_tree_build(TreeBufs& tb, const float2* Y, cudaStream_t s) {
     k_radix_hist<<<rblocks, 32 * kRadixWarps, 0, s>>>(tb.keys[in].get(), n, 8 * pass, tb.nchunks,
                                                       tb.counts.get());
     TS_CUDA(cudaGetLastError());
-    TS_TRY(scan_i32_to_i64(tb.counts.get(), tb.offs.get(), ncount, tb.scan_scr.get(), s));
+    TS_TRY(scan_i32_to_i64_blocks(tb.counts.get(), tb.offs.get(), ncount, tb.scan_scr.get(), s));
     k_radix_scatter<<<rblocks, 32 * kRadixWarps, 0, s>>>(tb.keys[in].get(), tb.vals[in].get(), n, 8 * pass,
-                                                         tb.nchunks, tb.offs.get(), tb.keys[out].get(),
-                                                         tb.vals[out].get(), last ? Y : nullptr,
-                                                         last ? tb.ys.get() : nullptr);
+                                                         tb.nchunks, tb.offs.get(), tb.scan_scr.get(),
+                                                         tb.keys[out].get(), tb.vals[out].get(),
+                                                         last ? Y : nullptr, last ? tb.ys.get() : nullptr);
     TS_CUDA(cudaGetLastError());
   }
   // eight passes: sorted keys / permutation are back in slot 0

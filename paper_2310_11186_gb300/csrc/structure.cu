@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kScanThreads = 1024;
 constexpr int kScanPerBlock = 2 * kScanThreads;
+static_assert(kScanPerBlock == kScanBlock, "block size of scan_i32_to_i64_blocks");
 constexpr int kMidCap = 4096;  // longest row sorted in shared memory
 
 // Exclusive block-wide scan of one value per thread; *total gets the block sum.
@@ -343,6 +344,16 @@ size_t scan_scratch_bytes(int64_t n) {
   int64_t nb = (n + kScanPerBlock - 1) / kScanPerBlock;
   if (nb < 1) nb = 1;
   return sizeof(int64_t) * (size_t)(nb + 1);
+}
+
+tsgne_status scan_i32_to_i64_blocks(const int32_t* in, int64_t* out, int64_t n, void* scratch, cudaStream_t s) {
+  int64_t nb = (n + kScanPerBlock - 1) / kScanPerBlock;
+  if (nb < 1) nb = 1;
+  int64_t* bsum = static_cast<int64_t*>(scratch);
+  k_scan_local<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, bsum);
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(bsum, (int)nb);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
 }
 
 tsgne_status scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* scratch, cudaStream_t s) {

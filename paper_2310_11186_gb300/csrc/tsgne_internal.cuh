@@ -65,6 +65,12 @@ tsgne_status cuda_fail(cudaError_t e, const char* what, const char* file, int li
     if (s_ != TSGNE_OK) return s_;          \
   } while (0)
 
+// Process-wide account of the device bytes held by DevBufs, checked against
+// an optional limit (tsgne_set_device_memory_limit).  reserve() returns false
+// when the allocation would pass the limit; release() gives bytes back.
+bool device_bytes_reserve(size_t bytes);
+void device_bytes_release(size_t bytes);
+
 // Owning device buffer released with cudaFree.
 template <class T>
 struct DevBuf {
@@ -80,15 +86,26 @@ struct DevBuf {
   }
   ~DevBuf() { reset(); }
   void reset() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      device_bytes_release(n * sizeof(T));
+    }
     p = nullptr;
     n = 0;
   }
   tsgne_status alloc(size_t count) {
     reset();
     if (count == 0) count = 1;
+    if (!device_bytes_reserve(count * sizeof(T))) {
+      last_msg() = "device memory limit reached (tsgne_set_device_memory_limit)";
+      return TSGNE_ERR_OOM;
+    }
     cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-    if (e != cudaSuccess) { p = nullptr; return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__); }
+    if (e != cudaSuccess) {
+      p = nullptr;
+      device_bytes_release(count * sizeof(T));
+      return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+    }
     n = count;
     return TSGNE_OK;
   }
@@ -99,6 +116,11 @@ struct DevBuf {
 // Exclusive prefix sum of in[0..n) into out[0..n], out[n] = total.
 size_t scan_scratch_bytes(int64_t n);
 tsgne_status scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* scratch, cudaStream_t s);
+// The first two phases only: out[k] = exclusive scan of k's block of
+// kScanBlock entries, scratch[b] = exclusive scan of the block totals; the
+// full exclusive scan at k is out[k] + scratch[k / kScanBlock].
+constexpr int64_t kScanBlock = 2048;
+tsgne_status scan_i32_to_i64_blocks(const int32_t* in, int64_t* out, int64_t n, void* scratch, cudaStream_t s);
 
 // ------------------------------------------------------------ structure
 // Symmetric, sorted, unique, loop-free structure of a validated CSR (device

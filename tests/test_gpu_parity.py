@@ -361,3 +361,30 @@ def test_knn_neighbours_match_oracle(wl, k, perp):
     oP, _ = oracle.joint_P(g.n, orp, ocol, pc)
     tol = 1e-5 * oP + 1e-9 * oP.max()
     assert not (np.abs(P - oP) > tol).any()
+
+
+def test_device_memory_limit_gives_oom_and_recovers():
+    """An allocation past the process-wide limit fails with OOM before any
+    cudaMalloc; the context stays usable and, with the limit lifted, builds
+    and computes exactly what a fresh context does."""
+    g, X = synth.workload("sbm2k")
+    Y0 = synth.y_init(g.n, seed=4)
+    with pkg.Layout() as ref:
+        ref.build_P(g.row_ptr, g.col, X)
+        ref.init_Y(Y0)
+        G0, Z0 = ref.gradient(1.0)
+    base = pkg.device_memory_in_use()
+    try:
+        with pkg.Layout() as lay:
+            pkg.set_device_memory_limit(pkg.device_memory_in_use() + 4096)
+            with pytest.raises(pkg.TsgneError) as e:
+                lay.build_P(g.row_ptr, g.col, X)
+            assert e.value.status == 3
+            pkg.set_device_memory_limit(0)
+            lay.build_P(g.row_ptr, g.col, X)
+            lay.init_Y(Y0)
+            G, Z = lay.gradient(1.0)
+            assert np.array_equal(G, G0) and Z == Z0
+    finally:
+        pkg.set_device_memory_limit(0)
+    assert pkg.device_memory_in_use() == base
