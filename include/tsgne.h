@@ -220,8 +220,9 @@ tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update
  * Profiling (cfg.profile = 1): cumulative device time in ms and launch count
  * of each kernel class since the last reset, measured with CUDA events on
  * the context's stream.  Classes: 0 repulsion (the tree walk when
- * cfg.repulsion = 1), 1 attraction+update, 2 gradient export, 3 KL, 4 build,
- * 5 repulsion slot reduction, 6 hub-row attraction chunks, 7 tree build
+ * cfg.repulsion = 1), 1 attraction+update (hub-row chunks included), 2
+ * gradient export, 3 KL, 4 build, 5 repulsion slot reduction, 6 hub-row
+ * attraction chunks of the gradient export, 7 tree build
  * (bounding box, keys, sort, tree, summaries).  ms and launches hold n
  * entries (n <= 8).
  * reset != 0 clears the counters after reading.  Synchronises.

@@ -297,7 +297,7 @@ tsgne_status sync_shadow(tsgne_ctx* ctx, int k) {
 tsgne_status enqueue_step(tsgne_ctx* ctx) {
   TS_TRY(enqueue_repulsion(ctx, 1));
   ProfRec pr;
-  // the layout is pulled into L2 before the gathers (hub chunks, then rows)
+  // the layout is pulled into L2 before the gathers
   const int nxt = ctx->cur ^ 1;
   AttractArgs a = attract_args(ctx);
   a.Ynext = ctx->Y[nxt].get();
@@ -307,16 +307,9 @@ tsgne_status enqueue_step(tsgne_ctx* ctx) {
   a.eta = ctx->eta;
   a.min_gain = ctx->cfg.min_gain;
   const int64_t ybytes = (int64_t)ctx->n * (ctx->bf16 ? 4 : 8);
-  if (ctx->hub.chunks > 0) {
-    ProfRec ph;
-    TS_TRY(prof_begin(ctx, 6, &ph));
-    TS_TRY(launch_prefetch_l2(a.Yr, ybytes, ctx->stream));
-    TS_TRY(launch_attract_heavy(a, ctx->stream));
-    TS_TRY(prof_end(ctx, &ph));
-  }
   TS_TRY(prof_begin(ctx, 1, &pr));
-  if (ctx->hub.chunks == 0) TS_TRY(launch_prefetch_l2(a.Yr, ybytes, ctx->stream));
-  TS_TRY(launch_attract_update(a, ctx->stream));
+  TS_TRY(launch_prefetch_l2(a.Yr, ybytes, ctx->stream));
+  TS_TRY(launch_attract_update(a, ctx->stream));  // hub-row chunks included (one launch)
   TS_TRY(prof_end(ctx, &pr));
   ctx->cur = nxt;
   return TSGNE_OK;

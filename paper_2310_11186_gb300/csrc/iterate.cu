@@ -33,53 +33,14 @@ namespace {
 constexpr int kAttrCta = 256;
 constexpr int kG = 8;  // lanes per row
 
-// Two phases per CTA of kAttrCta rows: (1) groups of G lanes gather the
-// attraction of the CTA's rows into shared memory; (2) one thread per row
-// reads F^r, the optimiser state and Y_i and writes the update, so the state
-// traffic is fully coalesced.
-template <int G, bool EXPORT, class PT, class YT>
-__global__ void __launch_bounds__(kAttrCta)
-    k_attract(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const PT* __restrict__ P,
-              const YT* __restrict__ Ycur, const float2* __restrict__ Ym, float2* __restrict__ Ynext,
-              bf162* __restrict__ Ynext16, float2* __restrict__ upd, float2* __restrict__ gains,
-              const float2* __restrict__ frep_part, int chunks, int n_pad, Sched* sched, float eta, float min_gain,
-              float alpha_export, float2* __restrict__ g_out, HeavyRows hv) {
-  constexpr int NGRP = kAttrCta / G;
-  __shared__ float2 sfa[kAttrCta];
-  __shared__ int64_t srp[kAttrCta + 1];
-  const int64_t row0 = (int64_t)blockIdx.x * kAttrCta;
-  const int grp = threadIdx.x / G, lane = threadIdx.x % G;
-  for (int t = threadIdx.x; t <= kAttrCta; t += kAttrCta) srp[t] = row0 + t <= n ? rp[row0 + t] : 0;
-  __syncthreads();
-  for (int r = grp; r < kAttrCta; r += NGRP) {
-    const int64_t i = row0 + r;
-    float ax = 0.f, ay = 0.f;
-    if (i < n) {
-      if (srp[r + 1] - srp[r] > kHeavyDeg) {
-        if (lane == 0) {  // chunk sums from k_attract_heavy, in chunk order
-          int lo = 0, hi = hv.count - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (hv.rows[mid] < i) lo = mid + 1; else hi = mid;
-          }
-          for (int c = hv.chunk_off[lo]; c < hv.chunk_off[lo + 1]; ++c) {
-            const float2 f = hv.fa[c];
-            ax += f.x;
-            ay += f.y;
-          }
-        }
-      } else {
-        attract_entries<G, PT, YT>(srp[r], srp[r + 1], col, P, Ycur, i, lane, ld_y(Ycur, i), ax, ay);
-      }
-    }
-    ax = group_sum<G>(ax);
-    ay = group_sum<G>(ay);
-    if (lane == 0) sfa[r] = make_float2(ax, ay);
-  }
-  __syncthreads();
-  const int64_t i = row0 + threadIdx.x;
-  if (i >= n) return;
-  const float2 fa = sfa[threadIdx.x];
+// Gradient of row i from its attraction sum fa, then (EXPORT) the gradient
+// export or the optimiser step into the next layout.
+template <bool EXPORT>
+__device__ __forceinline__ void finish_row(int64_t i, float2 fa, const float2* __restrict__ frep_part, int chunks,
+                                           int n_pad, Sched* sched, float alpha_export, float2* __restrict__ g_out,
+                                           const float2* __restrict__ Ym, float2* __restrict__ Ynext,
+                                           bf162* __restrict__ Ynext16, float2* __restrict__ upd,
+                                           float2* __restrict__ gains, float eta, float min_gain) {
   float rx = 0.f, ry = 0.f;
   for (int c = 0; c < chunks; ++c) {
     const float2 f = frep_part[(size_t)c * n_pad + i];
@@ -102,6 +63,96 @@ __global__ void __launch_bounds__(kAttrCta)
   Ynext[i] = y;
   if (Ynext16) Ynext16[i] = __float22bfloat162_rn(y);
   if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&sched->flags, kFlagNonfiniteY);
+}
+
+// Two phases per CTA of kAttrCta rows: (1) groups of G lanes gather the
+// attraction of the CTA's rows into shared memory; (2) one thread per row
+// reads F^r, the optimiser state and Y_i and writes the update, so the state
+// traffic is fully coalesced.
+//
+// FUSED (update only): the first heavy_blocks CTAs instead take the chunks
+// of the long rows (more than kHeavyDeg entries), one warp per chunk; the
+// warp that completes a row's last chunk adds the row's chunk sums in chunk
+// order and applies that row's update, and the row CTAs skip long rows.  The
+// hub rows' gathers then overlap with the short rows' in one launch, and the
+// results are bit-identical to the two-launch form (k_attract_heavy, then
+// chunk sums added in the row CTA).
+template <int G, bool EXPORT, class PT, class YT, bool FUSED = false>
+__global__ void __launch_bounds__(kAttrCta, 6)
+    k_attract(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const PT* __restrict__ P,
+              const YT* __restrict__ Ycur, const float2* __restrict__ Ym, float2* __restrict__ Ynext,
+              bf162* __restrict__ Ynext16, float2* __restrict__ upd, float2* __restrict__ gains,
+              const float2* __restrict__ frep_part, int chunks, int n_pad, Sched* sched, float eta, float min_gain,
+              float alpha_export, float2* __restrict__ g_out, HeavyRows hv, int heavy_blocks) {
+  constexpr int NGRP = kAttrCta / G;
+  __shared__ float2 sfa[kAttrCta];
+  __shared__ int64_t srp[kAttrCta + 1];
+  if (FUSED && (int)blockIdx.x < heavy_blocks) {
+    const int lane = threadIdx.x & 31;
+    const int stride = heavy_blocks * (kAttrCta / 32);
+    for (int c = blockIdx.x * (kAttrCta / 32) + (threadIdx.x >> 5); c < hv.chunks; c += stride) {
+      const int64_t i = hv.chunk_row[c];
+      float ax = 0.f, ay = 0.f;
+      attract_entries<32, PT, YT>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Ycur, i, lane, ld_y(Ycur, i), ax,
+                                  ay);
+      ax = group_sum<32>(ax);
+      ay = group_sum<32>(ay);
+      if (lane == 0) {
+        hv.fa[c] = make_float2(ax, ay);
+        const int h = hv.chunk_heavy[c];
+        const int c0 = hv.chunk_off[h], c1 = hv.chunk_off[h + 1];
+        __threadfence();
+        if (atomicAdd(&hv.arrivals[h], 1u) == (unsigned)(c1 - c0 - 1)) {  // last chunk of the row
+          __threadfence();
+          hv.arrivals[h] = 0u;
+          float sx = 0.f, sy = 0.f;
+          for (int q = c0; q < c1; ++q) {
+            const float2 f = __ldcg(hv.fa + q);
+            sx += f.x;
+            sy += f.y;
+          }
+          finish_row<false>(i, make_float2(sx, sy), frep_part, chunks, n_pad, sched, 0.f, nullptr, Ym, Ynext,
+                            Ynext16, upd, gains, eta, min_gain);
+        }
+      }
+    }
+    return;
+  }
+  const int64_t row0 = (int64_t)(blockIdx.x - (FUSED ? heavy_blocks : 0)) * kAttrCta;
+  const int grp = threadIdx.x / G, lane = threadIdx.x % G;
+  for (int t = threadIdx.x; t <= kAttrCta; t += kAttrCta) srp[t] = row0 + t <= n ? rp[row0 + t] : 0;
+  __syncthreads();
+  for (int r = grp; r < kAttrCta; r += NGRP) {
+    const int64_t i = row0 + r;
+    float ax = 0.f, ay = 0.f;
+    if (i < n) {
+      if (srp[r + 1] - srp[r] > kHeavyDeg) {
+        if (!FUSED && lane == 0) {  // chunk sums from k_attract_heavy, in chunk order
+          int lo = 0, hi = hv.count - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (hv.rows[mid] < i) lo = mid + 1; else hi = mid;
+          }
+          for (int c = hv.chunk_off[lo]; c < hv.chunk_off[lo + 1]; ++c) {
+            const float2 f = hv.fa[c];
+            ax += f.x;
+            ay += f.y;
+          }
+        }
+      } else {
+        attract_entries<G, PT, YT>(srp[r], srp[r + 1], col, P, Ycur, i, lane, ld_y(Ycur, i), ax, ay);
+      }
+    }
+    ax = group_sum<G>(ax);
+    ay = group_sum<G>(ay);
+    if (lane == 0) sfa[r] = make_float2(ax, ay);
+  }
+  __syncthreads();
+  const int64_t i = row0 + threadIdx.x;
+  if (i >= n) return;
+  if (FUSED && srp[threadIdx.x + 1] - srp[threadIdx.x] > kHeavyDeg) return;  // updated by its last chunk
+  finish_row<EXPORT>(i, sfa[threadIdx.x], frep_part, chunks, n_pad, sched, alpha_export, g_out, Ym, Ynext, Ynext16,
+                     upd, gains, eta, min_gain);
 }
 
 // Attraction of the long rows (more than kHeavyDeg entries), in chunks of at
@@ -296,11 +347,12 @@ tsgne_status find_heavy_rows(int n, const int64_t* rp, HeavyStore& hs, cudaStrea
     TS_CUDA(cudaMemcpyAsync(e.data(), bounds.get() + H, sizeof(int64_t) * H, cudaMemcpyDeviceToHost, s));
     TS_CUDA(cudaStreamSynchronize(s));
   }
-  std::vector<int32_t> off(1, 0), crow;
+  std::vector<int32_t> off(1, 0), crow, cheavy;
   std::vector<int64_t> cb, ce;
   for (int k = 0; k < H; ++k) {
     for (int64_t x = b[k]; x < e[k]; x += kHeavyChunk) {
       crow.push_back(rows[k]);
+      cheavy.push_back(k);
       cb.push_back(x);
       ce.push_back(x + kHeavyChunk < e[k] ? x + kHeavyChunk : e[k]);
     }
@@ -313,8 +365,12 @@ tsgne_status find_heavy_rows(int n, const int64_t* rp, HeavyStore& hs, cudaStrea
   TS_TRY(hs.chunk_begin.alloc((size_t)(C > 0 ? C : 1)));
   TS_TRY(hs.chunk_end.alloc((size_t)(C > 0 ? C : 1)));
   TS_TRY(hs.fa.alloc((size_t)(C > 0 ? C : 1)));
+  TS_TRY(hs.chunk_heavy.alloc((size_t)(C > 0 ? C : 1)));
+  TS_TRY(hs.arrivals.alloc((size_t)(H > 0 ? H : 1)));
+  TS_CUDA(cudaMemsetAsync(hs.arrivals.get(), 0, sizeof(uint32_t) * (size_t)(H > 0 ? H : 1), s));
   TS_CUDA(cudaMemcpyAsync(hs.chunk_off.get(), off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, s));
   if (C > 0) {
+    TS_CUDA(cudaMemcpyAsync(hs.chunk_heavy.get(), cheavy.data(), sizeof(int32_t) * C, cudaMemcpyHostToDevice, s));
     TS_CUDA(cudaMemcpyAsync(hs.chunk_row.get(), crow.data(), sizeof(int32_t) * C, cudaMemcpyHostToDevice, s));
     TS_CUDA(cudaMemcpyAsync(hs.chunk_begin.get(), cb.data(), sizeof(int64_t) * C, cudaMemcpyHostToDevice, s));
     TS_CUDA(cudaMemcpyAsync(hs.chunk_end.get(), ce.data(), sizeof(int64_t) * C, cudaMemcpyHostToDevice, s));
@@ -344,10 +400,19 @@ namespace {
 template <bool EXPORT, class PT, class YT>
 tsgne_status attract_t(const AttractArgs& a, float alpha, float2* g, cudaStream_t s) {
   const int grid = grid_rows(a.n, kAttrCta);
-  k_attract<kG, EXPORT, PT, YT><<<grid, kAttrCta, 0, s>>>(
-      a.n, a.rp, a.col, static_cast<const PT*>(a.P), static_cast<const YT*>(a.Yr), a.Ym, a.Ynext,
-      static_cast<bf162*>(a.Ynext16), a.upd, a.gains, a.frep, a.chunks, a.n_pad, a.sched, a.eta, a.min_gain, alpha,
-      g, a.hv);
+  if (!EXPORT && a.hv.chunks > 0) {  // hub chunks and short rows in one launch
+    int heavy = (a.hv.chunks + kAttrCta / 32 - 1) / (kAttrCta / 32);
+    if (heavy > 4096) heavy = 4096;
+    k_attract<kG, false, PT, YT, true><<<heavy + grid, kAttrCta, 0, s>>>(
+        a.n, a.rp, a.col, static_cast<const PT*>(a.P), static_cast<const YT*>(a.Yr), a.Ym, a.Ynext,
+        static_cast<bf162*>(a.Ynext16), a.upd, a.gains, a.frep, a.chunks, a.n_pad, a.sched, a.eta, a.min_gain, alpha,
+        g, a.hv, heavy);
+  } else {
+    k_attract<kG, EXPORT, PT, YT><<<grid, kAttrCta, 0, s>>>(
+        a.n, a.rp, a.col, static_cast<const PT*>(a.P), static_cast<const YT*>(a.Yr), a.Ym, a.Ynext,
+        static_cast<bf162*>(a.Ynext16), a.upd, a.gains, a.frep, a.chunks, a.n_pad, a.sched, a.eta, a.min_gain, alpha,
+        g, a.hv, 0);
+  }
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }

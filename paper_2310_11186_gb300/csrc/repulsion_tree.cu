@@ -344,18 +344,6 @@ __global__ void k_tree_group_list(int n, const int32_t* __restrict__ is_start, c
 
 // ---------------------------------------------------------------- 7. walk
 
-// One interaction of weight c at q (c = 0 for the lane's own point and for
-// lanes past the end of the layout).
-__device__ __forceinline__ void interact(float2 p, float qx, float qy, float c, float& fx, float& fy, float& zf) {
-  const float dx = p.x - qx, dy = p.y - qy;
-  const float w = rcp_approx(fmaf(dy, dy, fmaf(dx, dx, 1.0f)));
-  const float cw = c * w;
-  zf += cw;
-  const float cw2 = cw * w;
-  fx = fmaf(cw2, dx, fx);
-  fy = fmaf(cw2, dy, fy);
-}
-
 // Walk of one group, 32 stack entries per round: each lane takes one entry
 // (the top of the stack), loads its node record and decides: accept (r2 <
 // theta^2 d2: one interaction of weight count at the centre), sum exactly
@@ -372,6 +360,24 @@ __device__ __forceinline__ void interact(float2 p, float qx, float qy, float c, 
 // adds at most one entry per tree level, i.e. < 100), so kWalkStack is never
 // passed.
 constexpr int kWalkStack = 1024;
+
+// Two interactions at once on FP32x2 pairs: (qx0, qy0) weight c0 and
+// (qx1, qy1) weight c1 against p; FX, FY, Z hold two partial sums each.
+__device__ __forceinline__ void interact2(u64 PX, u64 PY, float qx0, float qy0, float c0, float qx1, float qy1,
+                                          float c1, u64& FX, u64& FY, u64& Z) {
+  const u64 dx = add2(PX, pk(-qx0, -qx1));
+  const u64 dy = add2(PY, pk(-qy0, -qy1));
+  u64 q = fma2(dx, dx, pk(1.0f, 1.0f));
+  q = fma2(dy, dy, q);
+  float q0, q1;
+  upk(q, q0, q1);
+  const u64 w = pk(rcp_approx(q0), rcp_approx(q1));
+  const u64 cw = mul2(pk(c0, c1), w);
+  Z = add2(Z, cw);
+  const u64 cw2 = mul2(cw, w);
+  FX = fma2(cw2, dx, FX);
+  FY = fma2(cw2, dy, FY);
+}
 
 __global__ void __launch_bounds__(32 * kWalkWarps)
     k_tree_walk(int n, const float2* __restrict__ ys, const int32_t* __restrict__ perm,
@@ -396,7 +402,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
     const float2 p = ys[act ? k : k0];
     const float gx0 = warp_min(p.x), gy0 = warp_min(p.y), gx1 = warp_max(p.x), gy1 = warp_max(p.y);
     const float self = act ? 1.0f : 0.0f;
-    float fx = 0.f, fy = 0.f;
+    const u64 PX = pk(p.x, p.x), PY = pk(p.y, p.y);
+    u64 FX = 0ull, FY = 0ull;
     double zd = 0.0;
     bool overflow = false;
     if (lane == 0) stk[w][0] = n > 1 ? 0 : ~0;
@@ -442,11 +449,12 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
         overflow = true;  // excluded by the bound above; recorded, never written past
       }
       __syncwarp();
-      float zf = 0.f;
+      u64 Z = 0ull;
       const int na = __popc(ma);
-      for (int t = 0; t < na; ++t) {
-        const float4 e = acc_list[w][t];
-        interact(p, e.x, e.y, act ? e.w : 0.f, fx, fy, zf);
+      for (int t = 0; t < na; t += 2) {
+        const float4 e0 = acc_list[w][t];
+        const float4 e1 = acc_list[w][t + 1 < na ? t + 1 : t];
+        interact2(PX, PY, e0.x, e0.y, act ? e0.w : 0.f, e1.x, e1.y, (act && t + 1 < na) ? e1.w : 0.f, FX, FY, Z);
       }
       const int nb = __popc(mb);
       for (int t = 0; t < nb; ++t) {
@@ -456,11 +464,14 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
 #pragma unroll
           for (int u = 0; u < 4; ++u) q[u] = ys[min(j + u, r.y)];
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            interact(p, q[u].x, q[u].y, (j + u <= r.y && j + u != k) ? self : 0.f, fx, fy, zf);
+          for (int u = 0; u < 4; u += 2)
+            interact2(PX, PY, q[u].x, q[u].y, (j + u <= r.y && j + u != k) ? self : 0.f, q[u + 1].x, q[u + 1].y,
+                      (j + u + 1 <= r.y && j + u + 1 != k) ? self : 0.f, FX, FY, Z);
         }
       }
-      zd += (double)zf;
+      float z0, z1;
+      upk(Z, z0, z1);
+      zd += (double)z0 + (double)z1;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) zd += __shfl_xor_sync(0xffffffffu, zd, o);
@@ -468,7 +479,12 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
       zgroup[g] = zd;
       if (overflow) atomicOr(&sched->flags, kFlagTreeOverflow);
     }
-    if (act) frep[perm[k]] = make_float2(fx, fy);
+    if (act) {
+      float fx0, fx1, fy0, fy1;
+      upk(FX, fx0, fx1);
+      upk(FY, fy0, fy1);
+      frep[perm[k]] = make_float2(fx0 + fx1, fy0 + fy1);
+    }
   }
   if (arrive_last(&st->walk_done)) {
     const double total = sum_partials(zgroup, ngroups);

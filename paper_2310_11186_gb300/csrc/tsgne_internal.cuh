@@ -198,13 +198,16 @@ struct HeavyRows {
   const int64_t* chunk_begin = nullptr;  // [chunks] first entry
   const int64_t* chunk_end = nullptr;    // [chunks] one past the last entry
   float2* fa = nullptr;                // [chunks] partial sums
+  const int32_t* chunk_heavy = nullptr;  // [chunks] index of the chunk's row in rows
+  uint32_t* arrivals = nullptr;        // [count] chunks done this pass (zero between passes)
   int count = 0;
   int chunks = 0;
 };
 struct HeavyStore {
-  DevBuf<int32_t> rows, chunk_off, chunk_row;
+  DevBuf<int32_t> rows, chunk_off, chunk_row, chunk_heavy;
   DevBuf<int64_t> chunk_begin, chunk_end;
   DevBuf<float2> fa;
+  DevBuf<uint32_t> arrivals;
   int count = 0, chunks = 0;
   HeavyRows view() const {
     HeavyRows h;
@@ -212,6 +215,8 @@ struct HeavyStore {
     h.chunk_off = chunk_off.get();
     h.chunk_row = chunk_row.get();
     h.chunk_begin = chunk_begin.get();
+    h.chunk_heavy = chunk_heavy.get();
+    h.arrivals = arrivals.get();
     h.chunk_end = chunk_end.get();
     h.fa = fa.get();
     h.count = count;

@@ -388,3 +388,34 @@ def test_device_memory_limit_gives_oom_and_recovers():
     finally:
         pkg.set_device_memory_limit(0)
     assert pkg.device_memory_in_use() == base
+
+
+def test_layout_after_10_iterations_with_hub_rows():
+    """The update path with rows above 32 entries (hub chunks and short rows
+    in one launch, the hub rows updated by their last chunk) against the
+    oracle's optimiser; also bit-identical from run to run."""
+    n = 6000
+    rng = np.random.default_rng(3)
+    g = synth.random_graph(n, 5.0, seed=77)
+    src, dst = [], []
+    for h, k in {7: 3000, 4000: 800, 5999: 300, 100: 40}.items():
+        nb = rng.choice(n, size=k, replace=False)
+        nb = nb[nb != h]
+        src.append(np.full(nb.size, h))
+        dst.append(nb)
+    rows = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    rp, col = synth.csr_from_edges(n, np.concatenate([rows] + src), np.concatenate([g.col] + dst))
+    labels = (np.arange(n) % 5).astype(np.int32)
+    X = synth.block_embedding(labels, 8, seed=5)
+    orp, ocol, oP = oracle.build_P(n, rp, col, X, 3.0)
+    Y0 = synth.y_init(n, seed=9)
+    oY, _, _ = oracle.optimize(n, orp, ocol, oP, Y0, 10)
+    out = []
+    for _ in range(2):
+        with pkg.Layout(perplexity=3.0) as lay:
+            lay.set_P(orp, ocol, oP.astype(np.float32))
+            lay.init_Y(Y0)
+            lay.run(10)
+            out.append(lay.get_Y())
+    assert np.array_equal(out[0], out[1])
+    assert rel_l2(out[0], oY) < 1e-4, rel_l2(out[0], oY)
