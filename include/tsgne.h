@@ -243,8 +243,10 @@ void tsgne_set_device_memory_limit(int64_t bytes);
 /* Device bytes the library holds at the moment (same account). */
 int64_t tsgne_device_memory_in_use(void);
 
-/* Launch geometry of the repulsion pass: grid CTAs, threads per CTA, i per
- * thread, j-tile, j-chunks, pad length.  Any pointer may be NULL. */
+/* Launch geometry of the exact repulsion pass (cfg.repulsion = 0; with the
+ * tree code the layout buffers still use this padding): grid CTAs, threads
+ * per CTA, i per thread, j-tile, j-chunks, pad length.  Any pointer may be
+ * NULL. */
 tsgne_status tsgne_repulsion_shape(tsgne_ctx* ctx, int32_t* grid, int32_t* block, int32_t* i_per_thread,
                                    int32_t* j_tile, int32_t* j_chunks, int32_t* n_pad);
 

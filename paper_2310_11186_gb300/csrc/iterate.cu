@@ -19,6 +19,7 @@
 //   fixed-order totals; KL = first + second * ln Z on the host (Eq. 5 with
 //   q = w / Z).
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "reduce.cuh"
@@ -400,7 +401,12 @@ namespace {
 template <bool EXPORT, class PT, class YT>
 tsgne_status attract_t(const AttractArgs& a, float alpha, float2* g, cudaStream_t s) {
   const int grid = grid_rows(a.n, kAttrCta);
-  if (!EXPORT && a.hv.chunks > 0) {  // hub chunks and short rows in one launch
+  // FP32 storage: hub chunks and short rows in one launch.  The BF16 variant
+  // of the fused kernel spills under the 6-CTA register cap and runs slower
+  // than two launches, so BF16 keeps k_attract_heavy first.
+  constexpr bool kFuse = std::is_same<PT, float>::value;
+  if (!EXPORT && !kFuse && a.hv.chunks > 0) TS_TRY(launch_attract_heavy(a, s));
+  if (!EXPORT && kFuse && a.hv.chunks > 0) {
     int heavy = (a.hv.chunks + kAttrCta / 32 - 1) / (kAttrCta / 32);
     if (heavy > 4096) heavy = 4096;
     k_attract<kG, false, PT, YT, true><<<heavy + grid, kAttrCta, 0, s>>>(

@@ -168,3 +168,24 @@ def test_precision_values():
         pkg.Layout(precision=2)
     with pytest.raises(pkg.TsgneError):
         pkg.Batch(precision=1)
+
+
+def test_bf16_with_tree_code():
+    """BF16 storage with the tree-code repulsion: the tree reads the FP32
+    master layout (its keys and decisions are the FP32 tree's), the
+    attraction reads the BF16 copies; deterministic, finite, and its
+    gradient within the BF16 format error of the FP32 tree code's."""
+    g, X = synth.workload("sbm2k")
+    rp, col, P = oracle.build_P(g.n, g.row_ptr, g.col, X, 30.0)
+    Y = synth.spread_layout(g.labels, scale=15.0)
+    out = {}
+    for prec in (0, 1):
+        with pkg.Layout(precision=prec, repulsion=1, theta=0.5) as lay:
+            lay.set_P(rp, col, P.astype(np.float32))
+            lay.init_Y(Y)
+            out[prec] = lay.gradient(1.0)
+            lay.run(50)
+            assert np.all(np.isfinite(lay.get_Y()))
+    (G0, Z0), (G1, Z1) = out[0], out[1]
+    assert Z1 == Z0  # the repulsion (and Z) come from the FP32 layout in both arms
+    assert rel_l2(G1, G0.astype(np.float64)) < 0.5
