@@ -91,7 +91,7 @@ typedef struct {
                               Morton curve, binary radix tree, per group of 32 consecutive
                               points a walk that takes a node with box side r and centre at
                               distance d from the group's box as one interaction when
-                              r < theta * d; opened nodes of <= 16 points are summed exactly.
+                              r < theta * d; opened nodes of <= 4 points are summed exactly.
                               Z and the forces are both approximated; the batch API accepts
                               0 only */
   float theta;             /* opening angle of the tree code, [0, 1] (default 0.5; 0 sums

@@ -206,7 +206,7 @@ def repulsion_rows(Y, i0, i1):
     return F[: i1 - i0], zr[: i1 - i0]
 
 
-def repulsion_tree(Y, theta, bucket=16):
+def repulsion_tree(Y, theta, bucket=4):
     """Tree-code approximation of the repulsive sums (steps in the C source):
     returns (F_rep n x 2, zrow n, Z) in the input order.  theta = 0 gives the
     exact sums of repulsion_rows."""
@@ -220,7 +220,7 @@ def repulsion_tree(Y, theta, bucket=16):
     return F, zr, z.value
 
 
-def gradient_tree(n, rp, col, P, Y, alpha=1.0, theta=0.5, bucket=16):
+def gradient_tree(n, rp, col, P, Y, alpha=1.0, theta=0.5, bucket=4):
     """Gradient of Eq. 5 with the tree code's repulsive sums and Z; returns (G, Z)."""
     rp, col, P, Yd = _c(rp, np.int64), _c(col, np.int32), _c(P, np.float64), _c(Y, np.float64)
     G = np.zeros((n, 2))

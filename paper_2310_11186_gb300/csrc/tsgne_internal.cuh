@@ -272,7 +272,7 @@ tsgne_status launch_init_Y(int n, uint64_t seed, float sigma, float2* Y, cudaStr
 // ------------------------------------------------- tree-code repulsion
 // (repulsion_tree.cu): an opened node of at most this many points is summed
 // exactly over its points.
-constexpr int kTreeBucket = 16;
+constexpr int kTreeBucket = 4;
 
 struct TreeState {
   double scale;                  // 2^32 / side of the bounding square of the last pass
