@@ -417,7 +417,7 @@ def run_ours(args):
         "rmat": rmat_res,
         "tree": tree_res,
         "random_walk_P": rw_res,
-        "scale_3m": scale_res,
+        "scale": scale_res,
         "paper_context": "300K nodes / 1M edges in under 5 min (ShortestPath + t-SGNE, 32-core Xeon Gold 6338)",
     }
     print(json.dumps(line), flush=True)
@@ -516,34 +516,40 @@ def bench_random_walk(args, pkg, g, X, log_fn=log):
 
 
 def bench_scale(args, pkg, log_fn=log):
-    """A whole layout at the scale of the paper's largest LFR graph (3M
-    nodes, 4.94M edges) with the tree-code repulsion, end to end from pinned
-    host buffers: P build, 1,000 iterations, layout back to the host."""
+    """Whole layouts at the sizes of the paper's largest graphs with the
+    tree-code repulsion, end to end from pinned host buffers: P build,
+    1,000 iterations, layout back to the host."""
     import torch
 
-    t0 = time.perf_counter()
-    g, X = synth.workload("zipf3m", seed=args.seed)
-    log_fn(f"[bench] scale: n={g.n} edges={g.m // 2} ({time.perf_counter() - t0:.1f}s)")
-    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
-    col_h = torch.from_numpy(g.col).pin_memory()
-    X_h = torch.from_numpy(X).pin_memory()
-    Y_out = torch.empty((g.n, 2), dtype=torch.float32).pin_memory()
-    with pkg.Layout(repulsion=1, theta=args.tree_theta) as lay:
-        torch.cuda.synchronize()
+    cases = (("zipf3m", "3,000,000 nodes, 200 Zipf(1.2) blocks, 4.94M edges (10 % rewired), 64-d X",
+              "LFR 3M / 4,937,941 edges: t-SGNE 0:49:02 on an 8-core Apple M2 (context)"),
+             ("zipf4m", "3,997,962 nodes, 500 Zipf(1.2) blocks, 34.7M edges (10 % rewired), 32-d X",
+              "LiveJournal 3,997,962 / 34,681,189 edges: t-SGNE 2:05:51 on an 8-core Apple M2 (context)"))
+    out = {}
+    for name, desc, paper in cases:
         t0 = time.perf_counter()
-        lay.build_P(rp_h, col_h, X_h)
-        tb = time.perf_counter()
-        lay.init_Y(None)
-        lay.run(args.e2e_iters)
-        lay.get_Y(Y_out)
-        t1 = time.perf_counter()
-        kl = lay.kl()
-    out = {"workload": "zipf3m: 3,000,000 nodes, 200 Zipf(1.2) blocks, 4.94M edges (10 % rewired), 64-d X, "
-                       "perplexity 30", "theta": args.tree_theta, "iters": args.e2e_iters,
-           "build_P_s": tb - t0, "layout_s": t1 - t0, "iters_per_s": args.e2e_iters / (t1 - tb),
-           "kl_tree_Z": kl, "paper": "LFR 3M / 4,937,941 edges: t-SGNE 0:49:02 on an 8-core Apple M2 (context)"}
-    log_fn(f"[bench] scale: build {out['build_P_s']:.2f} s, layout {out['layout_s']:.2f} s "
-           f"({out['iters_per_s']:.0f} it/s)")
+        g, X = synth.workload(name, seed=args.seed)
+        log_fn(f"[bench] scale {name}: n={g.n} edges={g.m // 2} ({time.perf_counter() - t0:.1f}s)")
+        rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+        col_h = torch.from_numpy(g.col).pin_memory()
+        X_h = torch.from_numpy(X).pin_memory()
+        Y_out = torch.empty((g.n, 2), dtype=torch.float32).pin_memory()
+        with pkg.Layout(repulsion=1, theta=args.tree_theta) as lay:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lay.build_P(rp_h, col_h, X_h)
+            tb = time.perf_counter()
+            lay.init_Y(None)
+            lay.run(args.e2e_iters)
+            lay.get_Y(Y_out)
+            t1 = time.perf_counter()
+            kl = lay.kl()
+        out[name] = {"workload": f"{name}: {desc}, perplexity 30", "theta": args.tree_theta,
+                     "iters": args.e2e_iters, "build_P_s": tb - t0, "layout_s": t1 - t0,
+                     "iters_per_s": args.e2e_iters / (t1 - tb), "kl_tree_Z": kl, "paper": paper}
+        log_fn(f"[bench] scale {name}: build {tb - t0:.2f} s, layout {t1 - t0:.2f} s "
+               f"({out[name]['iters_per_s']:.0f} it/s)")
+        del g, X, rp_h, col_h, X_h, Y_out
     return out
 
 
@@ -756,7 +762,7 @@ def main():
     ap.add_argument("--rmat-scale", type=int, default=21)
     ap.add_argument("--only-rmat", action="store_true", help="run only the R-MAT section (profiling)")
     ap.add_argument("--only-tree", action="store_true", help="run only the tree-code section (profiling)")
-    ap.add_argument("--scale", action="store_true", help="also lay out a 3M-node graph with the tree code (~1 min)")
+    ap.add_argument("--scale", action="store_true", help="also lay out 3M- and 4M-node graphs with the tree code (a few minutes)")
     ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOAD,
                     help="zipf300k is the benchmark; the others are smaller cases for profiling")
     args = ap.parse_args()

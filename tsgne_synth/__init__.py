@@ -299,6 +299,8 @@ def workload(name: str, seed: int = 0):
     smaller case of the same kernels, for profiling).
     ``zipf3m``: the same recipe at the scale of the paper's largest LFR graph
     (3,000,000 nodes, 4,937,941 edges: mean degree 3.3), 200 blocks, 64-d X.
+    ``zipf4m``: the same recipe at the size of the paper's largest real graph
+    (3,997,962 nodes, 34,681,189 edges: mean degree 17.3), 500 blocks, 32-d X.
     """
     if name == "sbm2k":
         g = sbm_equal(2000, 10, 0.05, 0.0005, seed=seed)
@@ -312,6 +314,9 @@ def workload(name: str, seed: int = 0):
     if name == "zipf3m":
         g = sbm_zipf(3_000_000, 200, 4_937_941, 1.2, 0.10, seed=seed)
         return g, block_embedding(g.labels, 64, seed=seed)
+    if name == "zipf4m":
+        g = sbm_zipf(3_997_962, 500, 34_681_189, 1.2, 0.10, seed=seed)
+        return g, block_embedding(g.labels, 32, seed=seed)
     raise KeyError(name)
 
 
