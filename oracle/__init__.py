@@ -90,6 +90,8 @@ def _load():
             lib.tsgo_random_walk_pcond.restype = ctypes.c_int
             lib.tsgo_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             lib.tsgo_splitmix64.restype = ctypes.c_uint64
+            lib.tsgo_gradient_rows.argtypes = [_i32, _p, _p, _p, _p, _dbl, _dbl, _p, _i32, _p]
+            lib.tsgo_gradient_rows.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -230,6 +232,18 @@ def gradient_tree(n, rp, col, P, Y, alpha=1.0, theta=0.5, bucket=4):
                                     int(bucket), _ptr(G), ctypes.byref(z))
     _check(st, "gradient_tree")
     return G, z.value
+
+
+def gradient_rows(n, rp, col, P, Y, alpha, Z, rows):
+    """Gradient rows (Eq. 5 derivative) for a given Z; returns len(rows) x 2."""
+    rp, col, P, Yd = _c(rp, np.int64), _c(col, np.int32), _c(P, np.float64), _c(Y, np.float64)
+    rows = _c(rows, np.int32)
+    G = np.zeros((max(1, rows.size), 2))
+    st = _load().tsgo_gradient_rows(n, _ptr(rp), _ptr(col if col.size else np.zeros(1, np.int32)),
+                                    _ptr(P if P.size else np.zeros(1)), _ptr(Yd), float(alpha), float(Z), _ptr(rows),
+                                    rows.size, _ptr(G))
+    _check(st, "gradient_rows")
+    return G[: rows.size]
 
 
 def splitmix64(seed: int, k: int) -> int:

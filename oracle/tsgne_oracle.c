@@ -32,6 +32,8 @@
  *                       (an extension; the paper sums Eq. 4 exactly); its
  *                       steps are listed above the function
  *   tsgo_gradient_tree  tsgo_gradient with the tree code's F^r and Z
+ *   tsgo_gradient_rows  tsgo_gradient for listed rows and a given Z (sampled
+ *                       checks at sizes where Z is summed separately)
  *
  * Readings of the paper where it is silent (also listed in the design notes):
  *   - N(i) is the set of graph neighbours (k = graph edges), union of both
@@ -872,3 +874,34 @@ int tsgo_random_walk_pcond(int32_t n, const int64_t* wrp, const int32_t* wcol, c
 
 /* Output number k (k >= 1) of the SplitMix64 sequence seeded with seed. */
 uint64_t tsgo_splitmix64(uint64_t seed, uint64_t k) { return sm64_output(seed, k); }
+
+/*
+ * Gradient rows for a given normaliser Z (for sampled checks at sizes where
+ * the O(n^2) Z is computed separately): for each listed row i,
+ *   g_i = 4 (alpha sum_{j in N(i)} p_ij w_ij (y_i - y_j)
+ *            - (1/Z) sum_{j != i} w_ij^2 (y_i - y_j)).
+ * G is nrows x 2 in the order of rows.
+ */
+int tsgo_gradient_rows(int32_t n, const int64_t* rp, const int32_t* col, const double* P, const double* Y,
+                       double alpha, double Z, const int32_t* rows, int32_t nrows, double* G) {
+  for (int32_t r = 0; r < nrows; ++r) {
+    int64_t i = rows[r];
+    if (i < 0 || i >= n) return TSGO_EINVAL;
+    double ax = 0.0, ay = 0.0, rx = 0.0, ry = 0.0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int64_t j = col[e];
+      double w = kernel_w(Y, i, j);
+      ax += P[e] * w * (Y[2 * i] - Y[2 * j]);
+      ay += P[e] * w * (Y[2 * i + 1] - Y[2 * j + 1]);
+    }
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double w = kernel_w(Y, i, j);
+      rx += w * w * (Y[2 * i] - Y[2 * j]);
+      ry += w * w * (Y[2 * i + 1] - Y[2 * j + 1]);
+    }
+    G[2 * r] = 4.0 * (alpha * ax - rx / Z);
+    G[2 * r + 1] = 4.0 * (alpha * ay - ry / Z);
+  }
+  return TSGO_OK;
+}

@@ -1,0 +1,94 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (exact repulsion, FP32 with FP64 Z).
+
+300K-node block model (the iterations/s benchmark): the CSR structure
+bit-exact and P within 1e-5 relative of the oracle's build; Z within 1e-5 of
+the oracle's sum over all rows (rows split over the host's cores); the
+gradient on a sample of rows (hubs, isolated nodes, first / last, random)
+within 1e-4 relative L2.
+
+R-MAT 2^21 nodes / 2^24 edges: structure bit-exact and P within 1e-5 of the
+oracle's build; the gradient on sampled rows against the oracle's rows
+given the GPU's Z (the oracle's O(n^2) Z at 2M points is beyond a test's
+budget; Z itself is checked at 300K and below).
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2310_11186_gb300 as pkg  # noqa: E402
+import tsgne_synth as synth  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2310_11186_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+    yield
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def _sample_rows(rp, k, seed):
+    n = rp.size - 1
+    deg = np.diff(rp)
+    rng = np.random.default_rng(seed)
+    rows = set(np.argsort(deg)[-8:].tolist())  # hubs
+    rows |= set(np.flatnonzero(deg == 0)[:4].tolist())  # isolated
+    rows |= {0, n - 1}
+    rows |= set(rng.choice(n, size=k, replace=False).tolist())
+    return np.array(sorted(rows), np.int32)
+
+
+def _check_P(rp, col, P, orp, ocol, oP):
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    assert np.all(np.abs(P - oP) <= 1e-5 * oP + 1e-9 * oP.max())
+
+
+def test_full_size_zipf300k(record_property):
+    g, X = synth.workload("zipf300k")
+    Y = synth.spread_layout(g.labels, scale=30.0, seed=3)
+    with pkg.Layout() as lay:
+        lay.build_P(g.row_ptr, g.col, X)
+        rp, col, P = lay.get_P()
+        lay.init_Y(Y)
+        G, Z = lay.gradient(1.0)
+    orp, ocol, oP = oracle.build_P(g.n, g.row_ptr, g.col, X, 30.0)
+    _check_P(rp, col, P, orp, ocol, oP)
+    _, zr = oracle.repulsion_all(Y, threads=os.cpu_count() or 1)
+    oZ = float(zr.sum())
+    record_property("Z_rel", abs(Z - oZ) / oZ)
+    assert abs(Z - oZ) / oZ < 1e-5, (Z, oZ)
+    rows = _sample_rows(orp, 48, seed=1)
+    oG = oracle.gradient_rows(g.n, orp, ocol, oP, Y, 1.0, oZ, rows)
+    record_property("grad_rel_l2_sample", rel_l2(G[rows], oG))
+    assert rel_l2(G[rows], oG) < 1e-4, rel_l2(G[rows], oG)
+
+
+def test_full_size_rmat21(record_property):
+    g, X = synth.rmat(21, 1 << 24, seed=0)
+    Y = synth.spread_layout(g.labels, scale=30.0, seed=4)
+    with pkg.Layout() as lay:
+        lay.build_P(g.row_ptr, g.col, X)
+        rp, col, P = lay.get_P()
+        lay.init_Y(Y)
+        G, Z = lay.gradient(12.0)
+    orp, ocol, oP = oracle.build_P(g.n, g.row_ptr, g.col, X, 30.0)
+    _check_P(rp, col, P, orp, ocol, oP)
+    rows = _sample_rows(orp, 24, seed=2)
+    oG = oracle.gradient_rows(g.n, orp, ocol, oP, Y, 12.0, Z, rows)
+    record_property("grad_rel_l2_sample", rel_l2(G[rows], oG))
+    assert rel_l2(G[rows], oG) < 1e-4, rel_l2(G[rows], oG)

@@ -661,3 +661,17 @@ def test_random_walk_P_is_a_symmetric_distribution():
     assert np.all(P > 0)
     t = oracle.transpose_slots(n, rp, col)
     assert np.allclose(P, P[t], rtol=0, atol=0)
+
+
+def test_gradient_rows_equal_full_gradient():
+    g = synth.random_graph(400, 5.0, seed=12)
+    X = synth.block_embedding((np.arange(400) % 4).astype(np.int32), 8, seed=12)
+    rp, col, P = oracle.build_P(400, g.row_ptr, g.col, X, 5.0)
+    Y = synth.spread_layout((np.arange(400) % 4).astype(np.int32), scale=8.0, seed=12)
+    G, Z = oracle.gradient(400, rp, col, P, Y.astype(np.float64), 3.0)
+    rows = np.array([0, 5, 399, 200, 17], np.int32)
+    Gr = oracle.gradient_rows(400, rp, col, P, Y, 3.0, Z, rows)
+    assert np.abs(Gr - G[rows]).max() <= 1e-13 * np.abs(G).max()
+    # Z from the row sums of repulsion_all equals the full Z
+    _, zr = oracle.repulsion_all(Y, threads=3)
+    assert zr.sum() == pytest.approx(Z, rel=1e-13)
