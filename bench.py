@@ -59,6 +59,7 @@ FLOPS_PER_UNORDERED_PAIR = 16  # 2 sub, 3 for d^2+1, w^2, Z add, 8 for the two f
 REPULSION_SRCS = [os.path.join(ROOT, "paper_2310_11186_gb300", "csrc", f)
                   for f in ("repulsion_sym.cu", "sym_unit.cuh", "f32x2.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "repulsion_zipf300k.md")
+PIPES_FILE = os.path.join(ROOT, "profiles", "repulsion_sym_zipf100k_full.md")
 
 
 def repulsion_source_sha() -> str:
@@ -146,6 +147,23 @@ def traffic_per_launch():
     if not m_sha or not m_b:
         return None
     return float(m_b.group(1)) if repulsion_source_sha() == m_sha.group(1) else None
+
+
+def pipe_utilisation():
+    """FMA / MUFU pipe activity of the repulsion kernel from the committed ncu
+    summary (--set full on the 100K case), if it was taken on the current
+    kernel source (else None)."""
+    try:
+        txt = open(PIPES_FILE).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    m_f = re.search(r"fma_pipe_active_pct:\s*([0-9.]+)", txt)
+    m_x = re.search(r"xu_pipe_active_pct:\s*([0-9.]+)", txt)
+    if not (m_sha and m_f and m_x) or repulsion_source_sha() != m_sha.group(1):
+        return None
+    return {"fma_pipe_active_pct": float(m_f.group(1)), "mufu_pipe_active_pct": float(m_x.group(1)),
+            "target_fma_pct": 60.0, "source": os.path.relpath(PIPES_FILE, ROOT)}
 
 
 def oracle_sample(Y, n, target_s: float, threads: int = 1):
@@ -394,6 +412,7 @@ def run_ours(args):
             "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS,
             "traffic": tr,
+            "pipes_ncu": pipe_utilisation(),
             "flops_per_launch": flops,
             "ms_per_launch": rep_ms,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (unit counts and max clock)",
