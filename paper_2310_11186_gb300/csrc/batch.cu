@@ -59,7 +59,7 @@ struct BatchCtr {
 namespace {
 
 constexpr int kMaxT = 2048;  // largest tile (W = 8); member buffers are padded to it
-constexpr int kBG = 8;       // lanes per row in the update
+constexpr int kBG = 8;       // lanes per row in the update (as the single-layout kernel: same row sums)
 
 // Largest k with off[k] <= v over off[0..count) (off non-decreasing, off[0] = 0).
 __device__ __forceinline__ int find_owner(const int* __restrict__ off, int count, int v) {
