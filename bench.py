@@ -634,7 +634,7 @@ def bench_serving(args, pkg, log_fn=log):
     mk = lambda: [serve.Request(k, float(arr[k]), spec[k][0].row_ptr, spec[k][0].col, spec[k][1],
                                 synth.y_init(spec[k][0].n, seed=k)) for k in range(count)]
     log_fn(f"[bench] serving: {count} requests at {args.serve_rate}/s, n in [{ns.min()}, {ns.max()}]")
-    srv = serve.LayoutServer(iters=args.serve_iters, tick_iters=10, budget_bytes=80 * 2 ** 30, tile_warps=4,
+    srv = serve.LayoutServer(iters=args.serve_iters, tick_iters=10, budget_bytes=80 * 2 ** 30, tile_warps=2,
                              policy="srpt")
     try:
         served = srv.serve(mk())
@@ -645,7 +645,7 @@ def bench_serving(args, pkg, log_fn=log):
         "workload": (f"{count} requests, Poisson arrivals at {args.serve_rate}/s, stochastic block models with n "
                      f"log-uniform in [1000, 300000], mean degree 6, 128-d embeddings, {args.serve_iters} "
                      f"iterations each, 80 GB admission budget"),
-        "policy": "continuous batching, shortest remaining work first, tile 4 warps",
+        "policy": "continuous batching, shortest remaining work first, 1,024-point tiles (2 warps)",
         "layouts_per_s": served["layouts_per_s"],
         "p50_s": served["p50_s"],
         "p99_s": served["p99_s"],

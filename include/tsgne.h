@@ -262,7 +262,7 @@ tsgne_status tsgne_sync(tsgne_ctx* ctx);
  * runs (continuous batching), and evolves exactly as it would in a batch of
  * its own: the per-member arithmetic, including the order of every
  * reduction, does not depend on the other members.  All members share one
- * repulsion tile of 256 * tile_warps points (1, 2, 4 or 8; smaller tiles pad
+ * repulsion tile of 512 * tile_warps points (1, 2 or 4; smaller tiles pad
  * small graphs less, larger tiles amortise more per unit).  The same
  * conventions as the context API apply (status codes, one stream, not
  * thread-safe); the batch API has its own error string.
@@ -309,10 +309,10 @@ tsgne_status tsgne_batch_reset(tsgne_batch* b);
 
 /*
  * Tile autotuner: times trial_iters iterations of the current membership
- * with each tile (1, 2, 4, 8 warps), keeps the fastest, records it in a
+ * with each tile (1, 2, 4 warps), keeps the fastest, records it in a
  * process-wide cache keyed by (SM count, log2 of the pair count, log2 of the
  * member count), and resets every member (tsgne_batch_reset).  *chosen gets
- * the tile; ms_per_iter (may be NULL) gets the 4 measured times.
+ * the tile; ms_per_iter (may be NULL) gets the 3 measured times.
  */
 tsgne_status tsgne_batch_autotune(tsgne_batch* b, int32_t trial_iters, int32_t* chosen, float* ms_per_iter);
 
@@ -372,7 +372,7 @@ typedef struct {
   int32_t iters;        /* iterations per request (default 500; a multiple of tick_iters) */
   int32_t tick_iters;   /* iterations per tick (default 10) */
   int32_t max_members;  /* resident layouts at most (default 256) */
-  int32_t tile_warps;   /* repulsion tile of the batch: 1, 2, 4 or 8 warps (default 2) */
+  int32_t tile_warps;   /* repulsion tile of the batch: 1, 2 or 4 warps (default 2) */
   int32_t policy;       /* 0: advance every resident layout; 1: shortest remaining work first (default) */
   double fill_pairs;    /* policy 1: pairs per iteration that fill the GPU (default 4e9) */
 } tsgne_server_config;

@@ -634,10 +634,10 @@ class Batch:
 
     def autotune(self, trial_iters: int = 3):
         chosen = _i32()
-        ms = np.zeros(4, np.float32)
+        ms = np.zeros(3, np.float32)
         self._check(lib().tsgne_batch_autotune(self.h, int(trial_iters), ctypes.byref(chosen),
                                                ms.ctypes.data_as(_p)))
-        return chosen.value, dict(zip((1, 2, 4, 8), ms.tolist()))
+        return chosen.value, dict(zip((1, 2, 4), ms.tolist()))
 
     def cached_tile(self) -> int:
         w = _i32()

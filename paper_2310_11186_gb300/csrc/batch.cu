@@ -16,7 +16,7 @@
 // and may differ in size and in iteration count (each has its own t); the
 // current layout of a member is Y[t & 1], so one captured CUDA graph of the
 // four launches serves every iteration of a given membership.  All members of
-// a batch use the same tile size T = 256 W; tsgne_batch_autotune picks W.
+// a batch use the same tile size T = 512 W; tsgne_batch_autotune picks W.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -58,7 +58,7 @@ struct BatchCtr {
 
 namespace {
 
-constexpr int kMaxT = 2048;  // largest tile (W = 8); member buffers are padded to it
+constexpr int kMaxT = 2048;  // largest tile (W = 4); member buffers are padded to it
 constexpr int kBG = 8;       // lanes per row in the update (as the single-layout kernel: same row sums)
 
 // Largest k with off[k] <= v over off[0..count) (off non-decreasing, off[0] = 0).
@@ -181,7 +181,6 @@ size_t batch_smem() {
 
 size_t smem_for(int W) {
   switch (W) {
-    case 8: return batch_smem<8>();
     case 4: return batch_smem<4>();
     case 2: return batch_smem<2>();
     default: return batch_smem<1>();
@@ -191,7 +190,6 @@ size_t smem_for(int W) {
 tsgne_status prepare_w(int W) {
   const int bytes = (int)smem_for(W);
   switch (W) {
-    case 8: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
     case 4: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
     case 2: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
     default: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
@@ -266,8 +264,12 @@ tsgne_status bfail(tsgne_batch* b, tsgne_status st, const std::string& msg = std
     if (e__ != cudaSuccess) return bfail((b), cuda_fail(e__, #call, __FILE__, __LINE__));  \
   } while (0)
 
+// The kernels' tile (sym_unit: 32 lanes x kRI i-points x W warps); every
+// tile size divides kMaxT, so a member's n_pad never exceeds its buffers'.
+static_assert(kMaxT % (32 * kRI) == 0 && 32 * kRI * 4 <= kMaxT, "tiles of 1, 2 and 4 warps must divide kMaxT");
+
 void shape_member(Member& m, int W) {
-  const int T = 256 * W;
+  const int T = 32 * kRI * W;
   m.nt = (m.n + T - 1) / T;
   m.n_pad = m.nt * T;
   m.units = m.nt * (m.nt + 1) / 2;
@@ -342,7 +344,6 @@ tsgne_status enqueue_iteration(tsgne_batch* b) {
   const int grid = b->U < slots ? b->U : slots;
   const size_t sm = smem_for(W);
   switch (W) {
-    case 8: k_batch_repulsion<8><<<grid, 256, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
     case 4: k_batch_repulsion<4><<<grid, 128, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
     case 2: k_batch_repulsion<2><<<grid, 64, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
     default: k_batch_repulsion<1><<<grid, 32, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
@@ -420,7 +421,7 @@ tsgne_status tsgne_batch_create(tsgne_batch** out, const tsgne_config* cfg, int3
   if (cfg) c = *cfg; else tsgne_config_default(&c);
   if (!(c.perplexity > 1.f) || c.k_nn < 0 || c.k_nn > 256 || c.precision != 0 || c.repulsion != 0 || c.ee_iters < 0)
     return TSGNE_ERR_INVALID_ARG;
-  if (!(tile_warps == 0 || tile_warps == 1 || tile_warps == 2 || tile_warps == 4 || tile_warps == 8))
+  if (!(tile_warps == 0 || tile_warps == 1 || tile_warps == 2 || tile_warps == 4))
     return TSGNE_ERR_INVALID_ARG;
   tsgne_batch* b = new (std::nothrow) tsgne_batch();
   if (!b) return TSGNE_ERR_OOM;
@@ -440,7 +441,7 @@ tsgne_status tsgne_batch_create(tsgne_batch** out, const tsgne_config* cfg, int3
   if (st == TSGNE_OK) st = b->d_ctr.alloc(1);
   if (st == TSGNE_OK && cudaMemsetAsync(b->d_ctr.get(), 0, sizeof(BatchCtr), b->stream) != cudaSuccess)
     st = TSGNE_ERR_CUDA;
-  for (int w : {1, 2, 4, 8})
+  for (int w : {1, 2, 4})
     if (st == TSGNE_OK) st = prepare_w(w);
   if (st == TSGNE_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = TSGNE_ERR_CUDA;
   if (st != TSGNE_OK) {
@@ -590,8 +591,8 @@ tsgne_status tsgne_batch_set_active(tsgne_batch* b, int32_t id, int32_t active) 
 
 tsgne_status tsgne_batch_set_tile(tsgne_batch* b, int32_t tile_warps) {
   if (!b) return TSGNE_ERR_INVALID_ARG;
-  if (!(tile_warps == 1 || tile_warps == 2 || tile_warps == 4 || tile_warps == 8))
-    return bfail(b, TSGNE_ERR_INVALID_ARG, "tile_warps must be 1, 2, 4 or 8");
+  if (!(tile_warps == 1 || tile_warps == 2 || tile_warps == 4))
+    return bfail(b, TSGNE_ERR_INVALID_ARG, "tile_warps must be 1, 2 or 4");
   if (tile_warps == b->W) return TSGNE_OK;
   B_CUDA(b, cudaStreamSynchronize(b->stream));
   for (auto& m : b->members) B_TRY(b, alloc_scratch(*m, tile_warps));
@@ -616,11 +617,11 @@ tsgne_status tsgne_batch_autotune(tsgne_batch* b, int32_t trial_iters, int32_t* 
   const auto key = std::make_tuple(b->sms, (int)std::log2(pairs + 1.0), (int)std::log2((double)b->members.size() + 1.0));
   int best = -1;
   float best_ms = 0.f;
-  const int cand[4] = {1, 2, 4, 8};
+  const int cand[3] = {1, 2, 4};
   cudaEvent_t e0, e1;
   B_CUDA(b, cudaEventCreate(&e0));
   B_CUDA(b, cudaEventCreate(&e1));
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 3; ++k) {
     const int w = cand[k];
     tsgne_status st = tsgne_batch_set_tile(b, w);
     if (st == TSGNE_OK) st = run_iterations(b, 1, false);  // warm-up

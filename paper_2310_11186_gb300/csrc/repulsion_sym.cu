@@ -6,10 +6,13 @@
 // 5 lane-ops and half a reciprocal per ordered pair (the ordered kernel in
 // repulsion.cu spends 8 and 1).
 //
-// Decomposition.  Points are padded to n_pad = nt * T (T = 256 W) with the
+// Decomposition.  Points are padded to n_pad = nt * T (T = 512 W) with the
 // sentinel point.  A unit of work is a tile pair (a, b), a <= b; the units
 // are enumerated row by row and taken from a global work queue by a
-// persistent grid (24 warps per SM).  Unit (a, b), a < b, writes the forces
+// persistent grid (8 warps per SM; 2-warp CTAs once there are enough units,
+// else 1-warp CTAs).  Sixteen i-points per lane and few warps beat eight
+// i-points and 24 warps per SM on GB300: the longer independent chains per
+// lane hide the reciprocal latency better than more warps do.  Unit (a, b), a < b, writes the forces
 // of tile a's points into slot b and those of tile b's points into slot a of
 // part[slot][point]; the diagonal unit (t, t) evaluates its ordered pairs
 // with the i-side only and writes slot t.  Every slot of every point is
@@ -18,15 +21,15 @@
 // Each unit also writes its own FP64 Z partial; the last CTA adds them in unit
 // order, removes the n self terms w_ii = 1 and sets the iteration schedule.
 //
-// Inside a unit (a < b).  Each of the W warps holds 256 points of tile a in
-// registers (8 per lane, as four FP32x2 pairs).  Tile b sits in shared
+// Inside a unit (a < b).  Each of the W warps holds 512 points of tile a in
+// registers (16 per lane, as eight FP32x2 pairs).  Tile b sits in shared
 // memory as {-x, -x, -y, -y} plus an FP32 force accumulator per point, cut
-// into 4W groups of 64 points.  In phase p warp w works on group (w + p) mod
-// 4W, so no two warps touch the same accumulators at once and no atomics are
+// into 8W groups of 64 points.  In phase p warp w works on group (w + p) mod
+// 8W, so no two warps touch the same accumulators at once and no atomics are
 // needed.  Within a warp, lane l starts with the accumulators of the group's
-// points 2l and 2l+1; each of 32 steps evaluates the lane's 8 i-points
+// points 2l and 2l+1; each of 32 steps evaluates the lane's 16 i-points
 // against those 2 j-points, then passes the j accumulators one lane down the
-// ring (shuffle); after 32 steps every j has met all 256 i of the warp and
+// ring (shuffle); after 32 steps every j has met all 512 i of the warp and
 // its accumulators are back home.  Only sentinel points lie in the last tile,
 // and a < b means tile a never holds any, so sentinel-sentinel pairs (w = 1)
 // occur only in the diagonal unit, where they are masked out of Z.
@@ -116,8 +119,8 @@ tsgne_status launch(const RepShape& sh, int n, const void* Y, int y_bf16, float2
 
 RepShape repulsion_shape_sym(int n, int sm_count) {
   RepShape sh;
-  int W = 8;
-  for (int w : {8, 4, 2, 1}) {
+  int W = 2;
+  for (int w : {2, 1}) {
     W = w;
     const long T = 32L * kRI * w;
     const long nt = (n + T - 1) / T;
@@ -138,33 +141,20 @@ RepShape repulsion_shape_sym(int n, int sm_count) {
   sh.units = nt * (nt + 1) / 2;
   const int slots = sm_count * (kWarpsPerSm / W);
   sh.grid = sh.units < slots ? sh.units : slots;
-  switch (W) {
-    case 8: sh.smem = smem_bytes<8>(); break;
-    case 4: sh.smem = smem_bytes<4>(); break;
-    case 2: sh.smem = smem_bytes<2>(); break;
-    default: sh.smem = smem_bytes<1>(); break;
-  }
+  sh.smem = W == 2 ? smem_bytes<2>() : smem_bytes<1>();
   return sh;
 }
 
 tsgne_status repulsion_sym_prepare(const RepShape& sh) {
-  switch (sh.warps) {
-    case 8: return prepare<8>();
-    case 4: return prepare<4>();
-    case 2: return prepare<2>();
-    default: return prepare<1>();
-  }
+  return sh.warps == 2 ? prepare<2>() : prepare<1>();
 }
 
 tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, float2* frep_part,
                                   double* zpart, Sched* sched, int advance, float ee, int ee_iters, float mom0,
                                   float mom1, cudaStream_t s) {
-  switch (sh.warps) {
-    case 8: return launch<8>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
-    case 4: return launch<4>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
-    case 2: return launch<2>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
-    default: return launch<1>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
-  }
+  if (sh.warps == 2)
+    return launch<2>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+  return launch<1>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
 }
 
 }  // namespace tsgne

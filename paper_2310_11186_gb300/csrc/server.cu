@@ -123,7 +123,7 @@ void tsgne_server_config_default(tsgne_server_config* c) {
 
 int64_t tsgne_server_estimate_bytes(int32_t n, int64_t nnz, int32_t tile_warps) {
   if (n < 1 || nnz < 0 || tile_warps < 1) return -1;
-  const int64_t T = 256 * (int64_t)tile_warps;
+  const int64_t T = 512 * (int64_t)tile_warps;  // the batch tile: 32 lanes x 16 i-points per warp
   const int64_t n_pad_max = (n + 2047) / 2048 * 2048;
   const int64_t nt = (n + T - 1) / T;
   const int64_t n_pad = nt * T;
@@ -138,6 +138,7 @@ tsgne_status tsgne_server_create(tsgne_server** out, const tsgne_server_config* 
   tsgne_server_config c;
   if (scfg) c = *scfg; else tsgne_server_config_default(&c);
   if (c.iters < 1 || c.tick_iters < 1 || c.iters % c.tick_iters != 0 || c.max_members < 1 || c.budget_bytes < 1 ||
+      !(c.tile_warps == 1 || c.tile_warps == 2 || c.tile_warps == 4) ||
       !(c.policy == 0 || c.policy == 1) || !(c.fill_pairs > 0.0))
     return TSGNE_ERR_INVALID_ARG;
   tsgne_server* s = new (std::nothrow) tsgne_server();

@@ -9,9 +9,9 @@
 
 namespace tsgne {
 
-constexpr int kRI = 8;              // i-points per lane
+constexpr int kRI = 16;             // i-points per lane
 constexpr int kH = kRI / 2;         // FP32x2 pairs of i-points per lane
-constexpr int kWarpsPerSm = 24;     // resident warps per SM the grid is sized for
+constexpr int kWarpsPerSm = 8;      // resident warps per SM the grid is sized for
 constexpr int kGroup = 64;          // j-points per ring group (32 lanes x 2)
 
 __device__ __forceinline__ int row_start(int a, int nt) { return a * nt - (a * (a - 1)) / 2; }

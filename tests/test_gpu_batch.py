@@ -61,7 +61,7 @@ def test_batch_of_one_equals_context_path():
     assert np.array_equal(Yb, Yc)
 
 
-@pytest.mark.parametrize("tile", [1, 2, 8])
+@pytest.mark.parametrize("tile", [1, 2, 4])
 def test_members_in_a_mix_equal_alone(tile):
     gs = _graphs([700, 2000, 3500, 5003], seed=10)
     late = _graphs([1200], seed=40)[0]
@@ -111,7 +111,7 @@ def test_autotune_resets_and_caches():
         for g, X, Y0 in gs:
             b.add(g.row_ptr, g.col, X, Y0)
         chosen, times = b.autotune(trial_iters=2)
-        assert chosen in (1, 2, 4, 8) and all(t > 0 for t in times.values())
+        assert chosen in (1, 2, 4) and all(t > 0 for t in times.values())
         assert b.size()["tile_warps"] == chosen
         assert b.cached_tile() == chosen
         Y, it = b.get_Y(0)

@@ -11,7 +11,7 @@ def test_estimate_bytes_grows_with_size_and_tile():
     b = serve.estimate_bytes(10000, 60000, 2)
     assert b > a > 0
     # the repulsion slots scale as n^2 / tile: a smaller tile costs more memory
-    assert serve.estimate_bytes(50000, 300000, 1) > serve.estimate_bytes(50000, 300000, 8)
+    assert serve.estimate_bytes(50000, 300000, 1) > serve.estimate_bytes(50000, 300000, 4)
 
 
 def test_poisson_arrivals_rate():
