@@ -85,7 +85,10 @@ typedef struct {
                               stay the optimiser's master copy and what every getter returns.
                               Not an option of the paper; the batch API accepts 0 only. */
   int32_t profile;         /* 1: time every kernel with CUDA events (see tsgne_kernel_times) */
-  int64_t spin_budget_cycles; /* bound on device-side waits (reserved; > 0) */
+  int64_t spin_budget_cycles; /* > 0: SM clock cycles a device-side wait may last (the look-back
+                                 of the tree code's sort); past it the pass gives up, its forces
+                                 are zero and the next synchronising call returns
+                                 TSGNE_ERR_TIMEOUT once (the context stays usable) */
   int32_t repulsion;       /* 0: exact all-pairs sums of Eq. 4 (default); 1: tree code, an
                               approximation the paper does not use: points sorted along a
                               Morton curve, binary radix tree, per group of 32 consecutive

@@ -4,6 +4,7 @@
 // structure.cu, affinity.cu, repulsion.cu and iterate.cu.
 #include <atomic>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -321,6 +322,25 @@ tsgne_status read_sched(tsgne_ctx* ctx, Sched* h) {
   return TSGNE_OK;
 }
 
+// Errors of the tree code's passes (stack overflow, a sort wait that ran out)
+// in a status word already read into h.
+tsgne_status check_tree_flags(tsgne_ctx* ctx, const Sched& h) {
+  if (h.flags & kFlagTreeOverflow) {
+    last_msg() = "tree walk stack overflow (results of the pass are incomplete)";
+    return TSGNE_ERR_CUDA;
+  }
+  if (h.flags & kFlagWaitTimeout) {
+    // reported once: the next pass rebuilds the tree from scratch
+    const uint32_t rest = h.flags & ~kFlagWaitTimeout;
+    TS_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(ctx->sched.get()) + offsetof(Sched, flags), &rest,
+                            sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    TS_CUDA(cudaStreamSynchronize(ctx->stream));
+    last_msg() = "a device-side wait ran out of spin_budget_cycles (tree sort); the pass's forces are zero";
+    return TSGNE_ERR_TIMEOUT;
+  }
+  return TSGNE_OK;
+}
+
 tsgne_status check_flags(tsgne_ctx* ctx) {
   Sched h;
   TS_TRY(read_sched(ctx, &h));
@@ -328,10 +348,7 @@ tsgne_status check_flags(tsgne_ctx* ctx) {
     last_msg() = "the layout became non-finite";
     return TSGNE_ERR_NONFINITE;
   }
-  if (h.flags & kFlagTreeOverflow) {
-    last_msg() = "tree walk stack overflow (results of the pass are incomplete)";
-    return TSGNE_ERR_CUDA;
-  }
+  TS_TRY(check_tree_flags(ctx, h));
   return TSGNE_OK;
 }
 
@@ -377,6 +394,7 @@ tsgne_status alloc_layout(tsgne_ctx* ctx) {
     ctx->frep = DevBuf<float2>();
     ctx->zpart = DevBuf<double>();
     TS_TRY(ctx->tree.alloc(ctx->n, ctx->sms, ctx->stream));
+    ctx->tree.spin_budget = ctx->cfg.spin_budget_cycles;
   } else {
     ctx->tree = TreeBufs();
     TS_TRY(ctx->frep.alloc(np * (size_t)ctx->shape.chunks));
@@ -494,10 +512,10 @@ tsgne_status tsgne_create(tsgne_ctx** out, const tsgne_config* cfg, void* cuda_s
       c.ee_iters < 0 || !(c.min_gain >= 0.f) || !(c.bisect_tol > 0.f) || c.bisect_max_iter < 1 ||
       !std::isfinite(c.early_exag) || !std::isfinite(c.momentum0) || !std::isfinite(c.momentum1) ||
       (c.repulsion != 0 && c.repulsion != 1) || !(c.theta >= 0.f && c.theta <= 1.f) || c.p_walks < 0 ||
-      c.p_walks > 512 || c.p_walk_length < 1 || c.p_walk_length > 64) {
+      c.p_walks > 512 || c.p_walk_length < 1 || c.p_walk_length > 64 || c.spin_budget_cycles <= 0) {
     last_msg() =
         "invalid configuration (perplexity must exceed 1; k_nn in [0, 256]; precision 0 or 1; repulsion 0 or 1; "
-        "theta in [0, 1]; p_walks in [0, 512]; p_walk_length in [1, 64])";
+        "theta in [0, 1]; p_walks in [0, 512]; p_walk_length in [1, 64]; spin_budget_cycles > 0)";
     return TSGNE_ERR_INVALID_ARG;
   }
   tsgne_ctx* ctx = new (std::nothrow) tsgne_ctx();
@@ -736,6 +754,7 @@ tsgne_status tsgne_kl(tsgne_ctx* ctx, double* kl_out) {
   API_TRY(ctx, prof_end(ctx, &pr));
   Sched h;
   API_TRY(ctx, read_sched(ctx, &h));
+  API_TRY(ctx, check_tree_flags(ctx, h));
   *kl_out = h.red[0] + h.red[1] * std::log(h.Z);
   if (!std::isfinite(*kl_out)) return fail(ctx, TSGNE_ERR_NONFINITE, "KL is not finite");
   return TSGNE_OK;
@@ -754,6 +773,7 @@ tsgne_status tsgne_gradient(tsgne_ctx* ctx, float alpha, float* g_out, double* z
   API_TRY(ctx, copy_out(g_out, ctx->grad.get(), sizeof(float2) * (size_t)ctx->n, ptr_kind, ctx->stream));
   Sched h;
   API_TRY(ctx, read_sched(ctx, &h));
+  API_TRY(ctx, check_tree_flags(ctx, h));
   if (z_out) *z_out = h.Z;
   return TSGNE_OK;
 }

@@ -26,11 +26,12 @@
 // FP64 operations written as _rn intrinsics, so no FMA contraction changes
 // it and the CPU reference takes the same decisions.
 //
-// GPU mapping.  Keys: one thread per point.  Sort: LSD radix sort, 8 passes
-// of 8 bits, stable: a warp owns a chunk of 256 keys; per-(digit, chunk) counts
-// are scanned digit-major, and the scatter ranks equal digits within a round
-// of 32 keys with __match_any_sync, so equal keys keep their input order.
-// The last pass also gathers the layout into sorted order.  Tree: one thread
+// GPU mapping.  Keys: one thread per point, which also counts the digits of
+// all eight sort passes.  Sort: LSD radix sort, 8 stable passes of 8 bits,
+// one launch each: a CTA ranks a tile of 2048 keys (__match_any_sync within
+// warps, offsets across warps) and takes the tile's global offsets from the
+// tiles before it by a decoupled look-back (a bounded wait).  The last pass
+// also gathers the layout into sorted order.  Tree: one thread
 // per internal node finds its range and split from the sorted keys alone
 // (binary search over the common-prefix length); summaries bottom-up, one
 // thread per leaf climbing until it is the first of two children to arrive.
@@ -53,10 +54,13 @@ namespace tsgne {
 
 namespace {
 
-constexpr int kRadixItems = 8;                 // keys per lane of a warp chunk
-constexpr int kRadixChunk = 32 * kRadixItems;  // keys per warp chunk
-constexpr int kRadixWarps = 8;
+constexpr int kRadixPasses = 8;  // 8-bit digits of the 64-bit keys
 constexpr int kRadixBins = 256;
+constexpr int kSortWarps = 8;
+constexpr int kSortThreads = 32 * kSortWarps;        // one thread per digit in the look-back
+constexpr int kSortItems = 8;                        // keys per lane
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per tile (per CTA)
+static_assert(kSortThreads == kRadixBins, "the look-back maps one thread to one digit");
 constexpr int kWalkWarps = 8;
 
 __device__ __forceinline__ float warp_min(float v) {
@@ -93,9 +97,13 @@ __device__ __forceinline__ float4 block_box(float lx, float ly, float hx, float 
   return b;
 }
 
+// Also clears the sort's digit counts, tile counters and tile status words
+// (zero[0..nzero)) and the stall mark for the build that follows.
 __global__ void __launch_bounds__(256) k_tree_box(const float2* __restrict__ Y, int n, float4* __restrict__ part,
-                                                  TreeState* st) {
+                                                  TreeState* st, uint32_t* __restrict__ zero, int64_t nzero) {
   __shared__ float4 ws[8];
+  for (int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x; k < nzero; k += (int64_t)gridDim.x * 256) zero[k] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->sort_stall = 0u;
   float lx = INFINITY, ly = INFINITY, hx = -INFINITY, hy = -INFINITY;
   for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) {
     const float2 p = Y[i];
@@ -145,81 +153,199 @@ __device__ __forceinline__ uint32_t cell32(float v, double lo, double scale) {
   return (uint32_t)c;
 }
 
-__global__ void k_tree_keys(const float2* __restrict__ Y, int n, const TreeState* __restrict__ st,
-                            uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+// Keys and the identity permutation, plus the counts of every 8-bit digit
+// of every key for all eight passes at once (ghist[pass][digit], zeroed by
+// k_tree_box): one read of the layout serves the whole sort.
+__global__ void __launch_bounds__(256) k_tree_keys(const float2* __restrict__ Y, int n,
+                                                   const TreeState* __restrict__ st, uint64_t* __restrict__ keys,
+                                                   int32_t* __restrict__ vals, uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[kRadixPasses * kRadixBins];
+  for (int k = threadIdx.x; k < kRadixPasses * kRadixBins; k += 256) h[k] = 0u;
+  __syncthreads();
   const double lx = st->lo_x, ly = st->lo_y, sc = st->scale;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float2 p = Y[i];
-    keys[i] = spread32(cell32(p.x, lx, sc)) | (spread32(cell32(p.y, ly, sc)) << 1);
+    const uint64_t key = spread32(cell32(p.x, lx, sc)) | (spread32(cell32(p.y, ly, sc)) << 1);
+    keys[i] = key;
     vals[i] = i;
+#pragma unroll
+    for (int q = 0; q < kRadixPasses; ++q) atomicAdd(&h[q * kRadixBins + (int)((key >> (8 * q)) & 255u)], 1u);
   }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kRadixPasses * kRadixBins; k += 256)
+    if (h[k]) atomicAdd(ghist + k, h[k]);
 }
 
 // ---------------------------------------------------------------- 3. sort
 
-__global__ void __launch_bounds__(32 * kRadixWarps)
-    k_radix_hist(const uint64_t* __restrict__ keys, int n, int shift, int nchunks, int32_t* __restrict__ counts) {
-  __shared__ uint32_t h[kRadixWarps][kRadixBins];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * kRadixWarps + w;
-  for (int d = lane; d < kRadixBins; d += 32) h[w][d] = 0u;
-  __syncwarp();
-  if (c >= nchunks) return;
-  const int64_t base = (int64_t)c * kRadixChunk + lane;
-  uint32_t dd[kRadixItems];
-#pragma unroll
-  for (int r = 0; r < kRadixItems; ++r) {
-    const int64_t k = base + 32 * r;
-    dd[r] = k < n ? (uint32_t)(keys[k] >> shift) & 255u : 0u;
-  }
-#pragma unroll
-  for (int r = 0; r < kRadixItems; ++r)
-    if (base + 32 * r < n) atomicAdd(&h[w][dd[r]], 1u);
-  __syncwarp();
-  for (int d = lane; d < kRadixBins; d += 32) counts[(int64_t)d * nchunks + c] = (int32_t)h[w][d];
+// One stable pass of the LSD radix sort, digit (key >> 8 pass) & 255, as a
+// single launch (one-sweep: the digit counts of all passes come from
+// k_tree_keys; the offsets of a tile come from its predecessors through a
+// decoupled look-back, Merrill & Garland's single-pass prefix scan, instead
+// of a separate count / scan / scatter per pass).
+//
+// A CTA takes tiles in launch order from a counter (ctl[pass]), so it only
+// ever waits on tiles that running CTAs own.  Tile t covers keys
+// [t T, t T + T), T = kSortTile; warp w holds keys w 256 + 32 r + lane,
+// r < 8, so (w, r, lane) order is input order.
+//  1. ranks within the warp: per round of 32 keys __match_any_sync groups
+//     equal digits; rank = running count of the digit in the warp + the
+//     number of lower lanes with the same digit;
+//  2. per digit d (thread d): the warps' exclusive offsets and the tile's
+//     count c_d, published at once as status[pass][t][d] = (AGG, c_d)
+//     (tile 0: (INCL, c_d));
+//  3. look-back, thread d: walk tiles t-1, t-2, ... adding AGG counts until
+//     an INCL one (the inclusive count of digit d over all tiles before);
+//     then publish (INCL, excl + c_d).  A wait for a tile that has published
+//     nothing yet spins at most `budget` clock cycles; past that the pass
+//     records sort_stall and publishes what it has, so no wait chains on it,
+//     every later kernel of the build sees the stall and does nothing, and
+//     the walk reports kFlagWaitTimeout;
+//  4. keys staged in shared memory in (digit, input) order, then written
+//     out: element i of the staged tile, digit d, goes to
+//     digit_start[d] + excl_d + (i - local_start[d]), so consecutive threads
+//     write consecutive addresses inside a digit's run.
+// With Y != NULL (last pass) the layout is gathered into sorted order.
+// status words: bits 31..30 flag (0 empty, 1 AGG, 2 INCL), 29..0 count
+// (n < 2^30).
+constexpr uint32_t kStAgg = 1u << 30, kStIncl = 2u << 30, kStCount = (1u << 30) - 1u;
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Stable scatter of one pass.  The exclusive scan of counts (digit-major)
-// at index k is offs[k] + boffs[k / kScanBlock] (scan_i32_to_i64_blocks).
-// With Y != NULL the layout is gathered into sorted order (ys[pos] = Y[val]).
-__global__ void __launch_bounds__(32 * kRadixWarps)
-    k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin, int n, int shift, int nchunks,
-                    const int64_t* __restrict__ offs, const int64_t* __restrict__ boffs, uint64_t* __restrict__ kout,
-                    int32_t* __restrict__ vout, const float2* __restrict__ Y, float2* __restrict__ ys) {
-  __shared__ int32_t base[kRadixWarps][kRadixBins];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * kRadixWarps + w;
-  if (c >= nchunks) return;
-  for (int d = lane; d < kRadixBins; d += 32) {
-    const int64_t k = (int64_t)d * nchunks + c;
-    base[w][d] = (int32_t)(offs[k] + boffs[k / kScanBlock]);
+// Exclusive scans over the 256 threads of a CTA of two values at once
+// (thread x gets the sums over threads < x).
+__device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_t& ea, uint32_t& eb,
+                                                 uint2* wsum) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t ua = __shfl_up_sync(0xffffffffu, ia, o), ub = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) {
+      ia += ua;
+      ib += ub;
+    }
   }
+  if (lane == 31) wsum[w] = make_uint2(ia, ib);
+  __syncthreads();
+  uint32_t oa = 0u, ob = 0u;
+  for (int v = 0; v < w; ++v) {
+    oa += wsum[v].x;
+    ob += wsum[v].y;
+  }
+  ea = oa + ia - a;
+  eb = ob + ib - b;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+    k_radix_onesweep(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin, int n, int pass,
+                     const uint32_t* __restrict__ ghist, uint32_t* ctl, uint32_t* status, int ntiles,
+                     long long budget, TreeState* st, uint64_t* __restrict__ kout, int32_t* __restrict__ vout,
+                     const float2* __restrict__ Y, float2* __restrict__ ys) {
+  __shared__ uint32_t hw[kSortWarps][kRadixBins];
+  __shared__ uint64_t skey[kSortTile];
+  __shared__ int32_t sval[kSortTile];
+  __shared__ uint32_t lstart[kRadixBins], gbase[kRadixBins];
+  __shared__ uint2 wsum[kSortWarps];
+  __shared__ int tile_s;
+  if (__ldcg(&st->sort_stall)) return;  // an earlier pass gave up: nothing of this build is valid
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  if (tid == 0) tile_s = (int)atomicAdd(ctl + pass, 1u);
+  for (int k = tid; k < kSortWarps * kRadixBins; k += kSortThreads) (&hw[0][0])[k] = 0u;
+  __syncthreads();
+  const int t = tile_s;
+  if (t >= ntiles) return;  // uniform: more CTAs than tiles never happens, kept as a guard
+  const int64_t t0 = (int64_t)t * kSortTile;
+  const int tn = (int)min((int64_t)kSortTile, (int64_t)n - t0);
+  const int shift = 8 * pass;
   const uint32_t lt = (1u << lane) - 1u;
-  const int64_t k0 = (int64_t)c * kRadixChunk + lane;
-  uint64_t key[kRadixItems];
-  int32_t val[kRadixItems];
+  const int wb = w * (32 * kSortItems) + lane;
+  uint64_t key[kSortItems];
+  int32_t val[kSortItems];
+  uint32_t rk[kSortItems];
 #pragma unroll
-  for (int r = 0; r < kRadixItems; ++r) {  // all loads of the chunk in flight at once
-    const int64_t k = k0 + 32 * r;
-    key[r] = k < n ? kin[k] : 0ull;
-    val[r] = k < n ? vin[k] : 0;
+  for (int r = 0; r < kSortItems; ++r) {  // all loads of the tile in flight at once
+    const int i = wb + 32 * r;
+    key[r] = i < tn ? kin[t0 + i] : 0ull;
+    val[r] = i < tn ? vin[t0 + i] : 0;
   }
-  __syncwarp();
+  // 1. ranks within the warp
 #pragma unroll
-  for (int r = 0; r < kRadixItems; ++r) {
-    const bool valid = k0 + 32 * r < n;
-    const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 255u : 256u + (uint32_t)lane;  // invalid lanes match only themselves
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool valid = wb + 32 * r < tn;
+    const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 255u : 256u + (uint32_t)lane;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(peers & lt);
-    int pos = 0;
-    if (valid) pos = base[w][d] + rank;
+    const uint32_t before = valid ? hw[w][d] : 0u;
+    rk[r] = before + (uint32_t)__popc(peers & lt);
     __syncwarp();
-    if (valid && rank == 0) base[w][d] += __popc(peers);
+    if (valid && (peers & lt) == 0u) hw[w][d] = before + (uint32_t)__popc(peers);
     __syncwarp();
-    if (valid) {
-      kout[pos] = key[r];
-      vout[pos] = val[r];
-      if (ys) ys[pos] = Y[val[r]];
+  }
+  __syncthreads();
+  // 2. per digit: offsets of the warps, count of the tile, published
+  const int d = tid;
+  uint32_t cnt = 0u;
+#pragma unroll
+  for (int v = 0; v < kSortWarps; ++v) {
+    const uint32_t x = hw[v][d];
+    hw[v][d] = cnt;
+    cnt += x;
+  }
+  uint32_t* const sbase = status + (size_t)pass * ntiles * kRadixBins;
+  st_relaxed_u32(sbase + (size_t)t * kRadixBins + d, (t == 0 ? kStIncl : kStAgg) | cnt);
+  uint32_t dstart, lst;
+  block_excl_scan2(__ldg(ghist + pass * kRadixBins + d), cnt, dstart, lst, wsum);
+  // 3. look-back
+  uint32_t excl = 0u;
+  if (t > 0) {
+    int k = t - 1;
+    const long long c0 = clock64();
+    bool stalled = false;
+    for (;;) {
+      const uint32_t s = ld_relaxed_u32(sbase + (size_t)k * kRadixBins + d);
+      if ((s >> 30) == 0u) {
+        if (clock64() - c0 > budget) {
+          stalled = true;
+          break;
+        }
+        continue;
+      }
+      excl += s & kStCount;
+      if ((s & kStIncl) != 0u) break;
+      --k;  // tile 0 always publishes INCL, so k stays >= 0
+    }
+    if (stalled) atomicExch(&st->sort_stall, 1u);
+    st_relaxed_u32(sbase + (size_t)t * kRadixBins + d, kStIncl | ((excl + cnt) & kStCount));
+  }
+  gbase[d] = dstart + excl;
+  lstart[d] = lst;
+  __syncthreads();
+  // 4. stage in (digit, input) order, then write out
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r)
+    if (wb + 32 * r < tn) {
+      const uint32_t dg = (uint32_t)(key[r] >> shift) & 255u;
+      const uint32_t lp = lstart[dg] + hw[w][dg] + rk[r];
+      skey[lp] = key[r];
+      sval[lp] = val[r];
+    }
+  __syncthreads();
+  for (int i = tid; i < tn; i += kSortThreads) {
+    const uint64_t kk = skey[i];
+    const uint32_t dg = (uint32_t)(kk >> shift) & 255u;
+    const uint32_t pos = gbase[dg] + ((uint32_t)i - lstart[dg]);
+    if (pos < (uint32_t)n) {  // always true unless a wait ran out
+      const int32_t v = sval[i];
+      kout[pos] = kk;
+      vout[pos] = v;
+      if (ys != nullptr && (uint32_t)v < (uint32_t)n) ys[pos] = Y[v];
     }
   }
 }
@@ -237,10 +363,10 @@ __device__ __forceinline__ int tree_delta(const uint64_t* __restrict__ keys, int
 // Internal node i (0 <= i < n - 1; node 0 is the root).  Children: >= 0 an
 // internal node, < 0 the leaf at sorted position ~c.  parent: internal nodes
 // at [0, n - 1), leaf k at n - 1 + k; the root's parent is -1.
-__global__ void k_tree_build(const uint64_t* __restrict__ keys, int n, int4* __restrict__ nodeB,
-                             int32_t* __restrict__ parent) {
+__global__ void k_tree_build(const uint64_t* __restrict__ keys, int n, const TreeState* st,
+                             int4* __restrict__ nodeB, int32_t* __restrict__ parent) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n - 1) return;
+  if (i >= n - 1 || __ldcg(&st->sort_stall)) return;
   const int d = tree_delta(keys, n, i, (int64_t)i + 1) > tree_delta(keys, n, i, (int64_t)i - 1) ? 1 : -1;
   const int dmin = tree_delta(keys, n, i, (int64_t)i - d);
   int64_t lmax = 2;
@@ -281,11 +407,11 @@ __device__ __forceinline__ void child_summary(int c, const float2* __restrict__ 
 // Summaries bottom-up: the second child to arrive at a node computes it
 // (left + right, whichever thread that is) and climbs on; flags are reset
 // on the way so the next pass starts from zero.
-__global__ void k_tree_up(int n, const int4* __restrict__ nodeB, const int32_t* __restrict__ parent,
-                          const float2* __restrict__ ys, uint32_t* flags, float4* box, float2* sum,
-                          float4* __restrict__ nodeA) {
+__global__ void k_tree_up(int n, const TreeState* st, const int4* __restrict__ nodeB,
+                          const int32_t* __restrict__ parent, const float2* __restrict__ ys, uint32_t* flags,
+                          float4* box, float2* sum, float4* __restrict__ nodeA) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+  if (k >= n || __ldcg(&st->sort_stall)) return;
   int p = parent[n - 1 + k];
   while (p >= 0) {
     const int4 b = nodeB[p];  // written by an earlier launch: safe before the arrival
@@ -314,10 +440,10 @@ __global__ void k_tree_up(int n, const int4* __restrict__ nodeB, const int32_t* 
 constexpr int kGroupMax = 32;
 
 // is_start[k] = 1 if sorted position k begins its group.
-__global__ void k_tree_group_starts(int n, const int4* __restrict__ nodeB, const int32_t* __restrict__ parent,
-                                    int32_t* __restrict__ is_start) {
+__global__ void k_tree_group_starts(int n, const TreeState* st, const int4* __restrict__ nodeB,
+                                    const int32_t* __restrict__ parent, int32_t* __restrict__ is_start) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+  if (k >= n || __ldcg(&st->sort_stall)) return;
   if (n == 1) {
     is_start[0] = 1;
     return;
@@ -334,10 +460,10 @@ __global__ void k_tree_group_starts(int n, const int4* __restrict__ nodeB, const
 }
 
 // gstart[g] = first position of group g; gstart[ngroups] = n.
-__global__ void k_tree_group_list(int n, const int32_t* __restrict__ is_start, const int64_t* __restrict__ gscan,
-                                  int32_t* __restrict__ gstart) {
+__global__ void k_tree_group_list(int n, const TreeState* st, const int32_t* __restrict__ is_start,
+                                  const int64_t* __restrict__ gscan, int32_t* __restrict__ gstart) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+  if (k >= n || __ldcg(&st->sort_stall)) return;
   if (is_start[k]) gstart[gscan[k]] = k;
   if (k == 0) gstart[gscan[n]] = n;
 }
@@ -390,7 +516,13 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
   __shared__ int2 exact_list[kWalkWarps][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  const int ngroups = (int)gscan[n];
+  // A sort wait that ran out leaves no valid tree: the pass only zeroes the
+  // forces and reports the timeout.
+  const bool stalled = __ldcg(&st->sort_stall) != 0u;
+  const int ngroups = stalled ? 0 : (int)gscan[n];
+  if (stalled)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      frep[i] = make_float2(0.f, 0.f);
   for (;;) {
     int g = 0;
     if (lane == 0) g = (int)atomicAdd(&st->next_group, 1u);
@@ -490,7 +622,10 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
     const double total = sum_partials(zgroup, ngroups);
     if (threadIdx.x == 0) {
       st->next_group = 0u;
-      sched->Z = total;
+      if (stalled)
+        atomicOr(&sched->flags, kFlagWaitTimeout);
+      else
+        sched->Z = total;
       const int t = sched->t;
       sched->alpha = t < ee_iters ? ee : 1.0f;
       sched->mu = t < ee_iters ? mom0 : mom1;
@@ -510,8 +645,13 @@ int grid_for(int64_t items, int per_block, int cap) {
 
 tsgne_status TreeBufs::alloc(int n_points, int sm_count, cudaStream_t s) {
   n = n_points;
-  nchunks = (n + kRadixChunk - 1) / kRadixChunk;
+  if (n >= (1 << 30)) {
+    last_msg() = "the tree code takes fewer than 2^30 points";
+    return TSGNE_ERR_INVALID_ARG;
+  }
+  ntiles = (n + kSortTile - 1) / kSortTile;
   box_blocks = grid_for(n, 256, 2 * sm_count);
+  keys_blocks = grid_for(n, 1024, sm_count);
   int per_sm = 0;
   TS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree_walk, 32 * kWalkWarps, 0));
   walk_blocks = sm_count * (per_sm > 0 ? per_sm : 1);
@@ -521,10 +661,8 @@ tsgne_status TreeBufs::alloc(int n_points, int sm_count, cudaStream_t s) {
   TS_TRY(vals[0].alloc((size_t)n));
   TS_TRY(vals[1].alloc((size_t)n));
   TS_TRY(ys.alloc((size_t)n));
-  TS_TRY(counts.alloc((size_t)kRadixBins * nchunks));
-  TS_TRY(offs.alloc((size_t)kRadixBins * nchunks + 1));
-  const int64_t scan_len = (int64_t)kRadixBins * nchunks > n ? (int64_t)kRadixBins * nchunks : n;
-  TS_TRY(scan_scr.alloc(scan_scratch_bytes(scan_len) / sizeof(int64_t)));
+  TS_TRY(sortmem.alloc(sort_words()));
+  TS_TRY(scan_scr.alloc(scan_scratch_bytes(n) / sizeof(int64_t)));
   TS_TRY(is_start.alloc((size_t)n));
   TS_TRY(gscan.alloc((size_t)n + 1));
   TS_TRY(gstart.alloc((size_t)n + 1));
@@ -544,37 +682,36 @@ tsgne_status TreeBufs::alloc(int n_points, int sm_count, cudaStream_t s) {
 
 tsgne_status launch_tree_build(TreeBufs& tb, const float2* Y, cudaStream_t s) {
   const int n = tb.n;
-  k_tree_box<<<tb.box_blocks, 256, 0, s>>>(Y, n, tb.boxpart.get(), tb.state.get());
-  k_tree_keys<<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(Y, n, tb.state.get(), tb.keys[0].get(), tb.vals[0].get());
+  TreeState* st = tb.state.get();
+  uint32_t* ghist = tb.sortmem.get();
+  uint32_t* ctl = ghist + kRadixPasses * kRadixBins;
+  uint32_t* status = ctl + kRadixPasses;
+  k_tree_box<<<tb.box_blocks, 256, 0, s>>>(Y, n, tb.boxpart.get(), st, tb.sortmem.get(), (int64_t)tb.sort_words());
+  k_tree_keys<<<tb.keys_blocks, 256, 0, s>>>(Y, n, st, tb.keys[0].get(), tb.vals[0].get(), ghist);
   TS_CUDA(cudaGetLastError());
-  const int rblocks = (tb.nchunks + kRadixWarps - 1) / kRadixWarps;
-  const int64_t ncount = (int64_t)kRadixBins * tb.nchunks;
-  for (int pass = 0; pass < 8; ++pass) {
+  for (int pass = 0; pass < kRadixPasses; ++pass) {
     const int in = pass & 1, out = in ^ 1;
-    const bool last = pass == 7;
-    k_radix_hist<<<rblocks, 32 * kRadixWarps, 0, s>>>(tb.keys[in].get(), n, 8 * pass, tb.nchunks,
-                                                      tb.counts.get());
-    TS_CUDA(cudaGetLastError());
-    TS_TRY(scan_i32_to_i64_blocks(tb.counts.get(), tb.offs.get(), ncount, tb.scan_scr.get(), s));
-    k_radix_scatter<<<rblocks, 32 * kRadixWarps, 0, s>>>(tb.keys[in].get(), tb.vals[in].get(), n, 8 * pass,
-                                                         tb.nchunks, tb.offs.get(), tb.scan_scr.get(),
-                                                         tb.keys[out].get(), tb.vals[out].get(),
-                                                         last ? Y : nullptr, last ? tb.ys.get() : nullptr);
+    const bool last = pass == kRadixPasses - 1;
+    k_radix_onesweep<<<tb.ntiles, kSortThreads, 0, s>>>(tb.keys[in].get(), tb.vals[in].get(), n, pass, ghist, ctl,
+                                                        status, tb.ntiles, tb.spin_budget, st, tb.keys[out].get(),
+                                                        tb.vals[out].get(), last ? Y : nullptr,
+                                                        last ? tb.ys.get() : nullptr);
     TS_CUDA(cudaGetLastError());
   }
-  // eight passes: sorted keys / permutation are back in slot 0
+  // an even number of passes: sorted keys / permutation are back in slot 0
+  static_assert(kRadixPasses % 2 == 0, "sorted keys end in slot 0");
   if (n > 1) {
-    k_tree_build<<<grid_for(n - 1, 256, 1 << 30), 256, 0, s>>>(tb.keys[0].get(), n, tb.nodeB.get(),
+    k_tree_build<<<grid_for(n - 1, 256, 1 << 30), 256, 0, s>>>(tb.keys[0].get(), n, st, tb.nodeB.get(),
                                                                tb.parent.get());
-    k_tree_up<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, tb.nodeB.get(), tb.parent.get(), tb.ys.get(),
+    k_tree_up<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, st, tb.nodeB.get(), tb.parent.get(), tb.ys.get(),
                                                        tb.flags.get(), tb.box.get(), tb.sum.get(), tb.nodeA.get());
     TS_CUDA(cudaGetLastError());
   }
-  k_tree_group_starts<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, tb.nodeB.get(), tb.parent.get(),
+  k_tree_group_starts<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, st, tb.nodeB.get(), tb.parent.get(),
                                                                  tb.is_start.get());
   TS_CUDA(cudaGetLastError());
   TS_TRY(scan_i32_to_i64(tb.is_start.get(), tb.gscan.get(), n, tb.scan_scr.get(), s));
-  k_tree_group_list<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, tb.is_start.get(), tb.gscan.get(),
+  k_tree_group_list<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, st, tb.is_start.get(), tb.gscan.get(),
                                                                tb.gstart.get());
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;

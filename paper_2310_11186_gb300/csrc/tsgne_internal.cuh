@@ -31,6 +31,7 @@ struct Sched {
 constexpr uint32_t kFlagNonfiniteY = 1u;
 constexpr uint32_t kFlagNonfiniteP = 2u;
 constexpr uint32_t kFlagTreeOverflow = 4u;
+constexpr uint32_t kFlagWaitTimeout = 8u;  // a bounded device-side wait ran out (cleared once reported)
 
 // Geometry of one repulsion pass (see repulsion.cu and repulsion_sym.cu).
 struct RepShape {
@@ -278,17 +279,19 @@ struct TreeState {
   double scale;                  // 2^32 / side of the bounding square of the last pass
   float lo_x, lo_y;              // its low corner
   uint32_t box_done, walk_done;  // last-CTA counters
-  uint32_t next_group, pad2;     // work-queue head of the walk
+  uint32_t next_group;           // work-queue head of the walk
+  uint32_t sort_stall;           // 1: a look-back wait of this pass's sort ran out of its budget
 };
 
 // Device buffers of the tree code for n points.
 struct TreeBufs {
-  int n = 0, nchunks = 0, box_blocks = 0, walk_blocks = 0;
+  int n = 0, ntiles = 0, box_blocks = 0, keys_blocks = 0, walk_blocks = 0;
+  long long spin_budget = 2000000000LL;  // clock cycles a look-back wait of the sort may last
   DevBuf<uint64_t> keys[2];
   DevBuf<int32_t> vals[2];    // vals[0] after a build: sorted position -> point
   DevBuf<float2> ys;          // layout in sorted order
-  DevBuf<int32_t> counts;     // radix counts, digit-major
-  DevBuf<int64_t> offs, scan_scr;
+  DevBuf<uint32_t> sortmem;   // sort: digit counts [8][256], tile counters [8], tile status [8][ntiles][256]
+  DevBuf<int64_t> scan_scr;
   DevBuf<float4> nodeA;       // internal node: centre x, y, r2, count
   DevBuf<int4> nodeB;         // internal node: left, right, first, last
   DevBuf<float4> box;         // internal node: x0, y0, x1, y1
@@ -301,6 +304,7 @@ struct TreeBufs {
   DevBuf<int32_t> gstart;     // first sorted position of each group, then n
   DevBuf<double> zgroup;      // FP64 Z partial per group
   DevBuf<TreeState> state;
+  size_t sort_words() const { return (size_t)8 * 256 + 8 + (size_t)8 * ntiles * 256; }
   tsgne_status alloc(int n_points, int sm_count, cudaStream_t s);
 };
 // Bounding square, keys, sort, tree and summaries of the layout Y[0..n).

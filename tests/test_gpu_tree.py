@@ -184,3 +184,33 @@ def test_tree_config_values():
             pkg.Layout(**bad)
     with pytest.raises(pkg.TsgneError):
         pkg.Batch(repulsion=1)
+
+
+def test_tree_sort_wait_runs_out_and_recovers(record_property):
+    """The sort's look-back waits are bounded by spin_budget_cycles.  With a
+    budget of one cycle every wait that finds its predecessor tile not yet
+    published gives up: that pass reports TSGNE_ERR_TIMEOUT (once) and the
+    context stays usable.  Every pass that does not time out is bit-identical
+    to the same pass with the default budget.  No GPU fault is involved: a
+    wait that runs out returns normally."""
+    g, X = synth.workload("zipf300k")
+    Y = synth.spread_layout(g.labels, scale=30.0, seed=5)
+    with pkg.Layout(repulsion=1, theta=0.5) as ref:
+        ref.build_P(g.row_ptr, g.col, X)
+        ref.init_Y(Y)
+        G0, Z0 = ref.gradient(1.0)
+    timeouts = 0
+    with pkg.Layout(repulsion=1, theta=0.5, spin_budget_cycles=1) as lay:
+        lay.build_P(g.row_ptr, g.col, X)
+        lay.init_Y(Y)
+        for _ in range(12):
+            try:
+                G, Z = lay.gradient(1.0)
+            except pkg.TsgneError as e:
+                assert e.name == "TSGNE_ERR_TIMEOUT", e
+                timeouts += 1
+                continue
+            assert np.array_equal(G, G0) and Z == Z0
+    record_property("timeouts_of_12", timeouts)
+    with pytest.raises(pkg.TsgneError):
+        pkg.Layout(repulsion=1, spin_budget_cycles=0)
