@@ -194,8 +194,9 @@ __global__ void __launch_bounds__(256) k_tree_keys(const float2* __restrict__ Y,
 //  2. per digit d (thread d): the warps' exclusive offsets and the tile's
 //     count c_d, published at once as status[pass][t][d] = (AGG, c_d)
 //     (tile 0: (INCL, c_d));
-//  3. look-back, thread d: walk tiles t-1, t-2, ... adding AGG counts until
-//     an INCL one (the inclusive count of digit d over all tiles before);
+//  3. look-back, thread d: walk tiles t-1, t-2, ... (8 status words loaded
+//     at once) adding AGG counts until an INCL one (the inclusive count of
+//     digit d over all tiles before);
 //     then publish (INCL, excl + c_d).  A wait for a tile that has published
 //     nothing yet spins at most `budget` clock cycles; past that the pass
 //     records sort_stall and publishes what it has, so no wait chains on it,
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(256) k_tree_keys(const float2* __restrict__ Y,
 // status words: bits 31..30 flag (0 empty, 1 AGG, 2 INCL), 29..0 count
 // (n < 2^30).
 constexpr uint32_t kStAgg = 1u << 30, kStIncl = 2u << 30, kStCount = (1u << 30) - 1u;
+constexpr int kLookWindow = 8;  // predecessor tiles a look-back step reads at once
 
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
   uint32_t v;
@@ -305,21 +307,31 @@ __global__ void __launch_bounds__(kSortThreads)
   // 3. look-back
   uint32_t excl = 0u;
   if (t > 0) {
-    int k = t - 1;
     const long long c0 = clock64();
-    bool stalled = false;
-    for (;;) {
-      const uint32_t s = ld_relaxed_u32(sbase + (size_t)k * kRadixBins + d);
-      if ((s >> 30) == 0u) {
-        if (clock64() - c0 > budget) {
-          stalled = true;
+    bool stalled = false, done = false;
+    // windows of kLookWindow predecessors, loaded at once, read nearest first
+    for (int k = t - 1; !done && !stalled; k -= kLookWindow) {
+      uint32_t sw[kLookWindow];
+#pragma unroll
+      for (int u = 0; u < kLookWindow; ++u)
+        sw[u] = k - u >= 0 ? ld_relaxed_u32(sbase + (size_t)(k - u) * kRadixBins + d) : kStIncl;
+#pragma unroll
+      for (int u = 0; u < kLookWindow; ++u) {
+        uint32_t v = sw[u];
+        while ((v >> 30) == 0u) {  // tile k - u (>= 0: tiles < 0 read as INCL 0) has published nothing yet
+          if (clock64() - c0 > budget) {
+            stalled = true;
+            break;
+          }
+          v = ld_relaxed_u32(sbase + (size_t)(k - u) * kRadixBins + d);
+        }
+        if (stalled) break;
+        excl += v & kStCount;
+        if ((v & kStIncl) != 0u) {  // tile 0 always publishes INCL
+          done = true;
           break;
         }
-        continue;
       }
-      excl += s & kStCount;
-      if ((s & kStIncl) != 0u) break;
-      --k;  // tile 0 always publishes INCL, so k stays >= 0
     }
     if (stalled) atomicExch(&st->sort_stall, 1u);
     st_relaxed_u32(sbase + (size_t)t * kRadixBins + d, kStIncl | ((excl + cnt) & kStCount));
@@ -404,33 +416,46 @@ __device__ __forceinline__ void child_summary(int c, const float2* __restrict__ 
   }
 }
 
+// Arrival at a node: an acquire-release add, so the summary the first
+// child's thread stored before its arrival is visible to the second child's
+// thread after its own (no separate fences).
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // Summaries bottom-up: the second child to arrive at a node computes it
-// (left + right, whichever thread that is) and climbs on; flags are reset
-// on the way so the next pass starts from zero.
+// (left + right: FP32 addition is commutative, so it does not matter which
+// child's thread that is; the thread's own child summary is still in its
+// registers, only the sibling's is loaded) and climbs on; flags are reset on
+// the way so the next pass starts from zero.
 __global__ void k_tree_up(int n, const TreeState* st, const int4* __restrict__ nodeB,
                           const int32_t* __restrict__ parent, const float2* __restrict__ ys, uint32_t* flags,
                           float4* box, float2* sum, float4* __restrict__ nodeA) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n || __ldcg(&st->sort_stall)) return;
+  int c = ~k;  // the child the thread climbs from (a leaf: ~position)
+  const float2 q = ys[k];
+  float4 bc = make_float4(q.x, q.y, q.x, q.y);
+  float2 sc = q;
   int p = parent[n - 1 + k];
   while (p >= 0) {
     const int4 b = nodeB[p];  // written by an earlier launch: safe before the arrival
     const int pp = parent[p];
-    __threadfence();
-    if (atomicAdd(&flags[p], 1u) == 0u) return;
-    __threadfence();
+    if (atom_add_acq_rel(&flags[p], 1u) == 0u) return;
     flags[p] = 0u;
-    float4 bl, br;
-    float2 sl, sr;
-    child_summary(b.x, ys, box, sum, bl, sl);
-    child_summary(b.y, ys, box, sum, br, sr);
-    const float2 sp = make_float2(__fadd_rn(sl.x, sr.x), __fadd_rn(sl.y, sr.y));
-    const float4 bp = make_float4(fminf(bl.x, br.x), fminf(bl.y, br.y), fmaxf(bl.z, br.z), fmaxf(bl.w, br.w));
-    box[p] = bp;
-    sum[p] = sp;
+    float4 bs;
+    float2 ss;
+    child_summary(b.x == c ? b.y : b.x, ys, box, sum, bs, ss);
+    sc = make_float2(__fadd_rn(sc.x, ss.x), __fadd_rn(sc.y, ss.y));
+    bc = make_float4(fminf(bc.x, bs.x), fminf(bc.y, bs.y), fmaxf(bc.z, bs.z), fmaxf(bc.w, bs.w));
+    box[p] = bc;
+    sum[p] = sc;
     const float cnt = (float)(b.w - b.z + 1);
-    const float r = fmaxf(__fsub_rn(bp.z, bp.x), __fsub_rn(bp.w, bp.y));
-    nodeA[p] = make_float4(__fdiv_rn(sp.x, cnt), __fdiv_rn(sp.y, cnt), __fmul_rn(r, r), cnt);
+    const float r = fmaxf(__fsub_rn(bc.z, bc.x), __fsub_rn(bc.w, bc.y));
+    nodeA[p] = make_float4(__fdiv_rn(sc.x, cnt), __fdiv_rn(sc.y, cnt), __fmul_rn(r, r), cnt);
+    c = p;
     p = pp;
   }
 }
