@@ -440,11 +440,21 @@ __global__ void k_tree_up(int n, const TreeState* st, const int4* __restrict__ n
   float4 bc = make_float4(q.x, q.y, q.x, q.y);
   float2 sc = q;
   int p = parent[n - 1 + k];
-  while (p >= 0) {
-    const int4 b = nodeB[p];  // written by an earlier launch: safe before the arrival
-    const int pp = parent[p];
+  if (p < 0) return;
+  // nodeB and parent were written by an earlier launch: the records of the
+  // next node up are loaded together with the sibling's summary, one round
+  // trip per level instead of two
+  int4 b = nodeB[p];
+  int pp = parent[p];
+  for (;;) {
     if (atom_add_acq_rel(&flags[p], 1u) == 0u) return;
     flags[p] = 0u;
+    int4 bn = make_int4(0, 0, 0, 0);
+    int ppn = -1;
+    if (pp >= 0) {
+      bn = nodeB[pp];
+      ppn = parent[pp];
+    }
     float4 bs;
     float2 ss;
     child_summary(b.x == c ? b.y : b.x, ys, box, sum, bs, ss);
@@ -455,8 +465,11 @@ __global__ void k_tree_up(int n, const TreeState* st, const int4* __restrict__ n
     const float cnt = (float)(b.w - b.z + 1);
     const float r = fmaxf(__fsub_rn(bc.z, bc.x), __fsub_rn(bc.w, bc.y));
     nodeA[p] = make_float4(__fdiv_rn(sc.x, cnt), __fdiv_rn(sc.y, cnt), __fmul_rn(r, r), cnt);
+    if (pp < 0) return;
     c = p;
     p = pp;
+    b = bn;
+    pp = ppn;
   }
 }
 
@@ -506,39 +519,53 @@ __global__ void k_tree_group_list(int n, const TreeState* st, const int32_t* __r
 // never accepted by its own group (distance 0 to the box), which takes the
 // exact path with the self term removed.  The set of interactions is the
 // definition's; only the order of the sums differs from a depth-first walk.
-// Stack bound: a round pops up to 32 entries and pushes up to 64; above
-// kWalkStack - 200 entries rounds pop one entry (a depth-first walk, which
-// adds at most one entry per tree level, i.e. < 100), so kWalkStack is never
-// passed.
-constexpr int kWalkStack = 1024;
+// A round's interactions form one list: an accepted node is one item
+// (centre, count), an exact entry is one item per point (point, 1).  The
+// deciding lanes write their items at offsets from a warp scan of the item
+// counts, as negated x, negated y and weight arrays, so two items are read as
+// three FP32x2 words and go through the packed arithmetic unchanged.  A
+// lane's own point, when an exact entry holds it, is summed like any other
+// item: its force term is exactly zero (dx = dy = 0) and its Z term, 1 / (1 +
+// 0) as computed, is subtracted once at the end (the entries mark which lanes
+// they cover) instead of masking every item.  An accepted node may also hold
+// the group's own points (coincident points: a centre one rounding away from
+// them, a box of size zero); it is then one monopole term as the definition
+// says, with nothing subtracted.
+// Stack bound: a round that starts at <= kWalkStack - 200 entries pops up to
+// 32 and pushes up to 64, ending at <= kWalkStack - 168; above kWalkStack -
+// 200 rounds pop one entry (a depth-first walk, which adds at most one entry
+// per tree level, and the tree has at most 94 levels: 64 key bits and 30
+// index bits), so the stack stays below kWalkStack - 74.
+constexpr int kWalkStack = 512;
+constexpr int kWalkList = 32 * kTreeBucket + 4;  // items of one round at most, plus padding (even)
 
-// Two interactions at once on FP32x2 pairs: (qx0, qy0) weight c0 and
-// (qx1, qy1) weight c1 against p; FX, FY, Z hold two partial sums each.
-__device__ __forceinline__ void interact2(u64 PX, u64 PY, float qx0, float qy0, float c0, float qx1, float qy1,
-                                          float c1, u64& FX, u64& FY, u64& Z) {
-  const u64 dx = add2(PX, pk(-qx0, -qx1));
-  const u64 dy = add2(PY, pk(-qy0, -qy1));
+// Two interactions at once: items (-x, -y, c) packed in pairs against p; FX,
+// FY, Z hold two partial sums each.
+__device__ __forceinline__ void interact2(u64 PX, u64 PY, u64 NX, u64 NY, u64 C, u64& FX, u64& FY, u64& Z) {
+  const u64 dx = add2(PX, NX);
+  const u64 dy = add2(PY, NY);
   u64 q = fma2(dx, dx, pk(1.0f, 1.0f));
   q = fma2(dy, dy, q);
   float q0, q1;
   upk(q, q0, q1);
   const u64 w = pk(rcp_approx(q0), rcp_approx(q1));
-  const u64 cw = mul2(pk(c0, c1), w);
+  const u64 cw = mul2(C, w);
   Z = add2(Z, cw);
   const u64 cw2 = mul2(cw, w);
   FX = fma2(cw2, dx, FX);
   FY = fma2(cw2, dy, FY);
 }
 
-__global__ void __launch_bounds__(32 * kWalkWarps)
+__global__ void __launch_bounds__(32 * kWalkWarps, 4)
     k_tree_walk(int n, const float2* __restrict__ ys, const int32_t* __restrict__ perm,
                 const float4* __restrict__ nodeA, const int4* __restrict__ nodeB, const int32_t* __restrict__ gstart,
                 const int64_t* __restrict__ gscan, float theta2, float2* __restrict__ frep,
                 double* __restrict__ zgroup, Sched* sched, TreeState* st, int advance, float ee, int ee_iters,
                 float mom0, float mom1) {
   __shared__ int stk[kWalkWarps][kWalkStack];
-  __shared__ float4 acc_list[kWalkWarps][32];
-  __shared__ int2 exact_list[kWalkWarps][32];
+  __shared__ __align__(8) float lnx[kWalkWarps][kWalkList];
+  __shared__ __align__(8) float lny[kWalkWarps][kWalkList];
+  __shared__ __align__(8) float lc[kWalkWarps][kWalkList];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   // A sort wait that ran out leaves no valid tree: the pass only zeroes the
@@ -558,11 +585,11 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
     const bool act = k < k1;
     const float2 p = ys[act ? k : k0];
     const float gx0 = warp_min(p.x), gy0 = warp_min(p.y), gx1 = warp_max(p.x), gy1 = warp_max(p.y);
-    const float self = act ? 1.0f : 0.0f;
     const u64 PX = pk(p.x, p.x), PY = pk(p.y, p.y);
     u64 FX = 0ull, FY = 0ull;
     double zd = 0.0;
     bool overflow = false;
+    uint32_t seen = 0u;  // lanes whose own point an exact entry held
     if (lane == 0) stk[w][0] = n > 1 ? 0 : ~0;
     int sp = 1;
     while (sp > 0) {
@@ -588,12 +615,42 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
         const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
         kind = A.z < __fmul_rn(theta2, d2) ? 1 : (B.w - B.z + 1 <= kTreeBucket ? 2 : 3);
       }
-      const uint32_t ma = __ballot_sync(0xffffffffu, kind == 1);
-      const uint32_t mb = __ballot_sync(0xffffffffu, kind == 2);
       const uint32_t mo = __ballot_sync(0xffffffffu, kind == 3);
+      // list offsets: exclusive scan of the items per lane
+      const int cnt = kind == 1 ? 1 : (kind == 2 ? B.w - B.z + 1 : 0);
+      int off = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += u;
+      }
+      const int ni = __shfl_sync(0xffffffffu, off, 31);
+      off -= cnt;
+      if (kind == 1) {
+        lnx[w][off] = -A.x;
+        lny[w][off] = -A.y;
+        lc[w][off] = A.w;
+      }
+      uint32_t cover = 0u;
+      if (kind == 2) {
+#pragma unroll
+        for (int u = 0; u < kTreeBucket; ++u)
+          if (u < cnt) {
+            const float2 q = ys[B.z + u];
+            lnx[w][off + u] = -q.x;
+            lny[w][off + u] = -q.y;
+            lc[w][off + u] = 1.0f;
+          }
+        const int lo = max(B.z, k0) - k0, hi = min(B.w, k1 - 1) - k0;  // lanes whose points it holds
+        if (lo <= hi) cover = ((1u << (hi - lo + 1)) - 1u) << lo;  // hi - lo < kTreeBucket
+      }
+      seen |= __reduce_or_sync(0xffffffffu, cover);
+      if (lane == 0 && (ni & 1)) {  // pad to a whole pair with a zero-weight item
+        lnx[w][ni] = 0.f;
+        lny[w][ni] = 0.f;
+        lc[w][ni] = 0.f;
+      }
       __syncwarp();  // every lane has read its entry before the pushes reuse the slots
-      if (kind == 1) acc_list[w][__popc(ma & lt)] = A;
-      if (kind == 2) exact_list[w][__popc(mb & lt)] = make_int2(B.z, B.w);
       const int npush = 2 * __popc(mo);
       if (sp + npush <= kWalkStack) {
         if (kind == 3) {
@@ -607,29 +664,15 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
       }
       __syncwarp();
       u64 Z = 0ull;
-      const int na = __popc(ma);
-      for (int t = 0; t < na; t += 2) {
-        const float4 e0 = acc_list[w][t];
-        const float4 e1 = acc_list[w][t + 1 < na ? t + 1 : t];
-        interact2(PX, PY, e0.x, e0.y, act ? e0.w : 0.f, e1.x, e1.y, (act && t + 1 < na) ? e1.w : 0.f, FX, FY, Z);
-      }
-      const int nb = __popc(mb);
-      for (int t = 0; t < nb; ++t) {
-        const int2 r = exact_list[w][t];
-        for (int j = r.x; j <= r.y; j += 4) {
-          float2 q[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) q[u] = ys[min(j + u, r.y)];
-#pragma unroll
-          for (int u = 0; u < 4; u += 2)
-            interact2(PX, PY, q[u].x, q[u].y, (j + u <= r.y && j + u != k) ? self : 0.f, q[u + 1].x, q[u + 1].y,
-                      (j + u + 1 <= r.y && j + u + 1 != k) ? self : 0.f, FX, FY, Z);
-        }
-      }
+      for (int t = 0; t < ni; t += 2)
+        interact2(PX, PY, *reinterpret_cast<const u64*>(&lnx[w][t]), *reinterpret_cast<const u64*>(&lny[w][t]),
+                  *reinterpret_cast<const u64*>(&lc[w][t]), FX, FY, Z);
       float z0, z1;
       upk(Z, z0, z1);
       zd += (double)z0 + (double)z1;
     }
+    if ((seen >> lane) & 1u) zd -= (double)rcp_approx(1.0f);  // the lane's own term out
+    if (!act) zd = 0.0;                                          // idle lanes add nothing
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) zd += __shfl_xor_sync(0xffffffffu, zd, o);
     if (lane == 0) {

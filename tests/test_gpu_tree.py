@@ -76,7 +76,7 @@ def _gpu_gradient(rp, col, P, Y, alpha, theta):
 @pytest.mark.parametrize("n,theta,kind", [
     (2, 0.5, "spread"), (33, 0.5, "spread"), (1000, 0.0, "spread"), (1000, 0.5, "spread"),
     (5003, 0.3, "spread"), (5003, 0.5, "tiny"), (5003, 1.0, "spread"), (9000, 0.5, "coincident"),
-    (20000, 0.5, "spread"),
+    (9000, 1.0, "coincident"), (20000, 0.5, "spread"),
 ])
 def test_tree_gradient_matches_oracle_tree(n, theta, kind, record_property):
     labels, rp, col, P = _case(n, 6.0, seed=n)
