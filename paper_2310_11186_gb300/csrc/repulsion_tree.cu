@@ -31,13 +31,10 @@
 // one launch each: a CTA ranks a tile of 2048 keys (__match_any_sync within
 // warps, offsets across warps) and takes the tile's global offsets from the
 // tiles before it by a decoupled look-back (a bounded wait).  The last pass
-// also gathers the layout into sorted order.  Tree: one thread
-// per internal node finds its range and split from the sorted keys alone
-// (binary search over the common-prefix length); summaries bottom-up, one
-// thread per leaf climbing until it is the first of two children to arrive.
-// Groups: one thread per leaf climbs while the parent holds <= 32 points and
-// marks whether it starts its group; a scan numbers the groups in sorted
-// order.  Walk: a persistent grid takes groups from a queue, one warp per
+// also gathers the layout into sorted order.  Tree, summaries and group
+// starts: one bottom-up pass, one thread per leaf climbing (each node's
+// parent follows from two neighbouring key prefixes) until it is the first of
+// two children to arrive; a scan numbers the groups in sorted order.  Walk: a persistent grid takes groups from a queue, one warp per
 // group, lane = point; per round the lanes decide up to 32 stack entries at
 // once and then all apply the round's accepted nodes and exact points, so
 // the dependent node loads along the tree are issued 32 at a time.  Z: FP32
@@ -98,11 +95,14 @@ __device__ __forceinline__ float4 block_box(float lx, float ly, float hx, float 
 }
 
 // Also clears the sort's digit counts, tile counters and tile status words
-// (zero[0..nzero)) and the stall mark for the build that follows.
+// (zero[0..nzero)), the group starts (is_start[0..n)) and the stall mark for
+// the build that follows.
 __global__ void __launch_bounds__(256) k_tree_box(const float2* __restrict__ Y, int n, float4* __restrict__ part,
-                                                  TreeState* st, uint32_t* __restrict__ zero, int64_t nzero) {
+                                                  TreeState* st, uint32_t* __restrict__ zero, int64_t nzero,
+                                                  int32_t* __restrict__ is_start) {
   __shared__ float4 ws[8];
   for (int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x; k < nzero; k += (int64_t)gridDim.x * 256) zero[k] = 0u;
+  for (int k = blockIdx.x * 256 + threadIdx.x; k < n; k += gridDim.x * 256) is_start[k] = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) st->sort_stall = 0u;
   float lx = INFINITY, ly = INFINITY, hx = -INFINITY, hy = -INFINITY;
   for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) {
@@ -364,138 +364,109 @@ __global__ void __launch_bounds__(kSortThreads)
 
 // ---------------------------------------------------------------- 4. tree
 
-// Common-prefix length of the augmented keys of sorted positions i and j
-// (-1 when j is outside [0, n)).
-__device__ __forceinline__ int tree_delta(const uint64_t* __restrict__ keys, int n, int i, int64_t j) {
-  if (j < 0 || j >= n) return -1;
-  const uint64_t a = keys[i], b = keys[j];
-  return a != b ? __clzll((long long)(a ^ b)) : 64 + __clz((uint32_t)i ^ (uint32_t)j);
+// Tree, summaries and group starts in one bottom-up pass (agglomerative
+// construction of the binary radix tree, Apetrei 2014): the thread of leaf k
+// holds a node with range [L, R] and climbs.  The parent of [L, R] is the
+// node split between R and R + 1 if the augmented keys R, R + 1 share a
+// longer prefix than keys L - 1, L (a range end counts as -1), else the node
+// split between L - 1 and L; this gives exactly the tree of the definition
+// (the one whose node over [f, l] splits at the highest differing bit).
+// Internal node ids are their split positions (node g has children over
+// [f, g] and [g + 1, l]); leaves are ~position.  A child reaching its parent
+// exchanges (the end of the parent's range it knows, its own id) with the
+// parent's slot: the first arrival leaves, the second learns the sibling,
+// computes the parent (left + right: FP32 addition is commutative, so it
+// does not matter which child's thread that is) and climbs on.  A completed
+// node of more than kGroupMax points marks the first positions of its
+// children that hold at most kGroupMax (the groups: maximal subtrees of at
+// most kGroupMax points).
+constexpr int kGroupMax = 32;
+constexpr unsigned long long kSlotEmpty = ~0ull;
+
+// Common-prefix length of the augmented keys (ka, a) and (kb, b).
+__device__ __forceinline__ int aug_prefix(uint64_t ka, uint64_t kb, int a, int b) {
+  return ka != kb ? __clzll((long long)(ka ^ kb)) : 64 + __clz((uint32_t)a ^ (uint32_t)b);
 }
 
-// Internal node i (0 <= i < n - 1; node 0 is the root).  Children: >= 0 an
-// internal node, < 0 the leaf at sorted position ~c.  parent: internal nodes
-// at [0, n - 1), leaf k at n - 1 + k; the root's parent is -1.
-__global__ void k_tree_build(const uint64_t* __restrict__ keys, int n, const TreeState* st,
-                             int4* __restrict__ nodeB, int32_t* __restrict__ parent) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n - 1 || __ldcg(&st->sort_stall)) return;
-  const int d = tree_delta(keys, n, i, (int64_t)i + 1) > tree_delta(keys, n, i, (int64_t)i - 1) ? 1 : -1;
-  const int dmin = tree_delta(keys, n, i, (int64_t)i - d);
-  int64_t lmax = 2;
-  while (tree_delta(keys, n, i, (int64_t)i + lmax * d) > dmin) lmax <<= 1;
-  int64_t l = 0;
-  for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-    if (tree_delta(keys, n, i, (int64_t)i + (l + t) * d) > dmin) l += t;
-  const int64_t j = (int64_t)i + l * d;
-  const int dn = tree_delta(keys, n, i, j);
-  int64_t s = 0;
-  for (int64_t div = 2;; div <<= 1) {
-    const int64_t t = (l + div - 1) / div;
-    if (tree_delta(keys, n, i, (int64_t)i + (s + t) * d) > dn) s += t;
-    if (t <= 1) break;
-  }
-  const int64_t gamma = (int64_t)i + s * d + (d < 0 ? -1 : 0);
-  const int first = (int)(j < i ? j : i), last = (int)(j < i ? i : j);
-  const int left = first == gamma ? ~(int)gamma : (int)gamma;
-  const int right = last == gamma + 1 ? ~(int)(gamma + 1) : (int)(gamma + 1);
-  nodeB[i] = make_int4(left, right, first, last);
-  parent[left >= 0 ? left : n - 1 + ~left] = i;
-  parent[right >= 0 ? right : n - 1 + ~right] = i;
-  if (i == 0) parent[0] = -1;
-}
-
-__device__ __forceinline__ void child_summary(int c, const float2* __restrict__ ys, const float4* box,
-                                              const float2* sum, float4& b, float2& s) {
-  if (c < 0) {
-    const float2 q = ys[~c];
-    b = make_float4(q.x, q.y, q.x, q.y);
-    s = q;
-  } else {
-    b = __ldcg(box + c);
-    s = __ldcg(sum + c);
-  }
-}
-
-// Arrival at a node: an acquire-release add, so the summary the first
-// child's thread stored before its arrival is visible to the second child's
-// thread after its own (no separate fences).
-__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
-  uint32_t old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+// Exchange at a node: acquire-release, so the summary a child's thread
+// stored before its exchange is visible to the sibling's thread after its own.
+__device__ __forceinline__ unsigned long long atom_exch_acq_rel(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
   return old;
 }
 
-// Summaries bottom-up: the second child to arrive at a node computes it
-// (left + right: FP32 addition is commutative, so it does not matter which
-// child's thread that is; the thread's own child summary is still in its
-// registers, only the sibling's is loaded) and climbs on; flags are reset on
-// the way so the next pass starts from zero.
-__global__ void k_tree_up(int n, const TreeState* st, const int4* __restrict__ nodeB,
-                          const int32_t* __restrict__ parent, const float2* __restrict__ ys, uint32_t* flags,
-                          float4* box, float2* sum, float4* __restrict__ nodeA) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n || __ldcg(&st->sort_stall)) return;
-  int c = ~k;  // the child the thread climbs from (a leaf: ~position)
-  const float2 q = ys[k];
-  float4 bc = make_float4(q.x, q.y, q.x, q.y);
-  float2 sc = q;
-  int p = parent[n - 1 + k];
-  if (p < 0) return;
-  // nodeB and parent were written by an earlier launch: the records of the
-  // next node up are loaded together with the sibling's summary, one round
-  // trip per level instead of two
-  int4 b = nodeB[p];
-  int pp = parent[p];
-  for (;;) {
-    if (atom_add_acq_rel(&flags[p], 1u) == 0u) return;
-    flags[p] = 0u;
-    int4 bn = make_int4(0, 0, 0, 0);
-    int ppn = -1;
-    if (pp >= 0) {
-      bn = nodeB[pp];
-      ppn = parent[pp];
-    }
-    float4 bs;
-    float2 ss;
-    child_summary(b.x == c ? b.y : b.x, ys, box, sum, bs, ss);
-    sc = make_float2(__fadd_rn(sc.x, ss.x), __fadd_rn(sc.y, ss.y));
-    bc = make_float4(fminf(bc.x, bs.x), fminf(bc.y, bs.y), fmaxf(bc.z, bs.z), fmaxf(bc.w, bs.w));
-    box[p] = bc;
-    sum[p] = sc;
-    const float cnt = (float)(b.w - b.z + 1);
-    const float r = fmaxf(__fsub_rn(bc.z, bc.x), __fsub_rn(bc.w, bc.y));
-    nodeA[p] = make_float4(__fdiv_rn(sc.x, cnt), __fdiv_rn(sc.y, cnt), __fmul_rn(r, r), cnt);
-    if (pp < 0) return;
-    c = p;
-    p = pp;
-    b = bn;
-    pp = ppn;
-  }
-}
-
-// --------------------------------------------------------------- 6. groups
-
-constexpr int kGroupMax = 32;
-
-// is_start[k] = 1 if sorted position k begins its group.
-__global__ void k_tree_group_starts(int n, const TreeState* st, const int4* __restrict__ nodeB,
-                                    const int32_t* __restrict__ parent, int32_t* __restrict__ is_start) {
+__global__ void k_tree_climb(int n, const uint64_t* __restrict__ keys, const float2* __restrict__ ys,
+                             unsigned long long* slot, float4* box, float2* sum, float4* __restrict__ nodeA,
+                             int4* __restrict__ nodeB, int32_t* __restrict__ is_start, TreeState* st) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n || __ldcg(&st->sort_stall)) return;
   if (n == 1) {
     is_start[0] = 1;
+    st->root = ~0;
     return;
   }
-  int first = k;
-  int p = parent[n - 1 + k];
-  while (p >= 0) {  // at most kGroupMax steps: every step up adds a point
-    const int4 b = nodeB[p];
-    if (b.w - b.z + 1 > kGroupMax) break;
-    first = b.z;
-    p = parent[p];
+  int L = k, R = k, id = ~k;
+  const float2 q = ys[k];
+  float4 bc = make_float4(q.x, q.y, q.x, q.y);
+  float2 sc = q;
+  uint64_t kL = keys[k], kR = kL;
+  uint64_t kLm = k > 0 ? keys[k - 1] : 0ull, kRp = k < n - 1 ? keys[k + 1] : 0ull;
+  for (;;) {
+    const int dl = L > 0 ? aug_prefix(kLm, kL, L - 1, L) : -1;
+    const int dr = R < n - 1 ? aug_prefix(kR, kRp, R, R + 1) : -1;
+    const bool toward_right = dr > dl;  // this node is the left child
+    const int p = toward_right ? R : L - 1;
+    const int bound = toward_right ? L : R;
+    const unsigned long long old =
+        atom_exch_acq_rel(slot + p, ((unsigned long long)(uint32_t)bound << 32) | (uint32_t)id);
+    if (old == kSlotEmpty) return;
+    slot[p] = kSlotEmpty;  // both arrivals are in: ready for the next pass
+    const int sbound = (int)(old >> 32), sid = (int)(uint32_t)old;
+    const int pL = toward_right ? L : sbound, pR = toward_right ? sbound : R;
+    // the sibling's summary and the keys at the parent's new end, at once
+    float4 bs;
+    float2 ss;
+    if (sid < 0) {
+      const float2 t = ys[~sid];
+      bs = make_float4(t.x, t.y, t.x, t.y);
+      ss = t;
+    } else {
+      bs = __ldcg(box + sid);
+      ss = __ldcg(sum + sid);
+    }
+    if (toward_right) {
+      kR = keys[pR];
+      kRp = pR < n - 1 ? keys[pR + 1] : 0ull;
+    } else {
+      kL = keys[pL];
+      kLm = pL > 0 ? keys[pL - 1] : 0ull;
+    }
+    sc = make_float2(__fadd_rn(sc.x, ss.x), __fadd_rn(sc.y, ss.y));
+    bc = make_float4(fminf(bc.x, bs.x), fminf(bc.y, bs.y), fmaxf(bc.z, bs.z), fmaxf(bc.w, bs.w));
+    box[p] = bc;
+    sum[p] = sc;
+    const int cntp = pR - pL + 1;
+    const float cnt = (float)cntp;
+    const float r = fmaxf(__fsub_rn(bc.z, bc.x), __fsub_rn(bc.w, bc.y));
+    nodeA[p] = make_float4(__fdiv_rn(sc.x, cnt), __fdiv_rn(sc.y, cnt), __fmul_rn(r, r), cnt);
+    nodeB[p] = toward_right ? make_int4(id, sid, pL, pR) : make_int4(sid, id, pL, pR);
+    if (cntp > kGroupMax) {
+      if (p - pL + 1 <= kGroupMax) is_start[pL] = 1;     // left child [pL, p]
+      if (pR - p <= kGroupMax) is_start[p + 1] = 1;      // right child [p + 1, pR]
+    }
+    if (pL == 0 && pR == n - 1) {  // the root
+      st->root = p;
+      if (cntp <= kGroupMax) is_start[0] = 1;
+      return;
+    }
+    L = pL;
+    R = pR;
+    id = p;
   }
-  is_start[k] = first == k ? 1 : 0;
 }
+
+// --------------------------------------------------------------- 6. groups
 
 // gstart[g] = first position of group g; gstart[ngroups] = n.
 __global__ void k_tree_group_list(int n, const TreeState* st, const int32_t* __restrict__ is_start,
@@ -572,6 +543,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps, 4)
   // forces and reports the timeout.
   const bool stalled = __ldcg(&st->sort_stall) != 0u;
   const int ngroups = stalled ? 0 : (int)gscan[n];
+  const int root = __ldcg(&st->root);  // internal node id, or ~0 for a single point
   if (stalled)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
       frep[i] = make_float2(0.f, 0.f);
@@ -590,7 +562,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps, 4)
     double zd = 0.0;
     bool overflow = false;
     uint32_t seen = 0u;  // lanes whose own point an exact entry held
-    if (lane == 0) stk[w][0] = n > 1 ? 0 : ~0;
+    if (lane == 0) stk[w][0] = root;
     int sp = 1;
     while (sp > 0) {
       __syncwarp();
@@ -738,12 +710,11 @@ tsgne_status TreeBufs::alloc(int n_points, int sm_count, cudaStream_t s) {
   TS_TRY(nodeB.alloc(nn));
   TS_TRY(box.alloc(nn));
   TS_TRY(sum.alloc(nn));
-  TS_TRY(flags.alloc(nn));
-  TS_TRY(parent.alloc(2 * (size_t)n));
+  TS_TRY(slot.alloc(nn));
   TS_TRY(boxpart.alloc((size_t)box_blocks));
   TS_TRY(zgroup.alloc((size_t)n));
   TS_TRY(state.alloc(1));
-  TS_CUDA(cudaMemsetAsync(flags.get(), 0, sizeof(uint32_t) * nn, s));
+  TS_CUDA(cudaMemsetAsync(slot.get(), 0xff, sizeof(unsigned long long) * nn, s));  // every slot empty
   TS_CUDA(cudaMemsetAsync(state.get(), 0, sizeof(TreeState), s));
   return TSGNE_OK;
 }
@@ -754,7 +725,8 @@ tsgne_status launch_tree_build(TreeBufs& tb, const float2* Y, cudaStream_t s) {
   uint32_t* ghist = tb.sortmem.get();
   uint32_t* ctl = ghist + kRadixPasses * kRadixBins;
   uint32_t* status = ctl + kRadixPasses;
-  k_tree_box<<<tb.box_blocks, 256, 0, s>>>(Y, n, tb.boxpart.get(), st, tb.sortmem.get(), (int64_t)tb.sort_words());
+  k_tree_box<<<tb.box_blocks, 256, 0, s>>>(Y, n, tb.boxpart.get(), st, tb.sortmem.get(), (int64_t)tb.sort_words(),
+                                           tb.is_start.get());
   k_tree_keys<<<tb.keys_blocks, 256, 0, s>>>(Y, n, st, tb.keys[0].get(), tb.vals[0].get(), ghist);
   TS_CUDA(cudaGetLastError());
   for (int pass = 0; pass < kRadixPasses; ++pass) {
@@ -768,15 +740,9 @@ tsgne_status launch_tree_build(TreeBufs& tb, const float2* Y, cudaStream_t s) {
   }
   // an even number of passes: sorted keys / permutation are back in slot 0
   static_assert(kRadixPasses % 2 == 0, "sorted keys end in slot 0");
-  if (n > 1) {
-    k_tree_build<<<grid_for(n - 1, 256, 1 << 30), 256, 0, s>>>(tb.keys[0].get(), n, st, tb.nodeB.get(),
-                                                               tb.parent.get());
-    k_tree_up<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, st, tb.nodeB.get(), tb.parent.get(), tb.ys.get(),
-                                                       tb.flags.get(), tb.box.get(), tb.sum.get(), tb.nodeA.get());
-    TS_CUDA(cudaGetLastError());
-  }
-  k_tree_group_starts<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, st, tb.nodeB.get(), tb.parent.get(),
-                                                                 tb.is_start.get());
+  k_tree_climb<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, tb.keys[0].get(), tb.ys.get(), tb.slot.get(),
+                                                         tb.box.get(), tb.sum.get(), tb.nodeA.get(), tb.nodeB.get(),
+                                                         tb.is_start.get(), st);
   TS_CUDA(cudaGetLastError());
   TS_TRY(scan_i32_to_i64(tb.is_start.get(), tb.gscan.get(), n, tb.scan_scr.get(), s));
   k_tree_group_list<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(n, st, tb.is_start.get(), tb.gscan.get(),

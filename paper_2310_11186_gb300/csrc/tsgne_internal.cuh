@@ -281,6 +281,7 @@ struct TreeState {
   uint32_t box_done, walk_done;  // last-CTA counters
   uint32_t next_group;           // work-queue head of the walk
   uint32_t sort_stall;           // 1: a look-back wait of this pass's sort ran out of its budget
+  int32_t root;                  // root of the last tree: an internal node id, or ~0 (one point)
 };
 
 // Device buffers of the tree code for n points.
@@ -296,8 +297,7 @@ struct TreeBufs {
   DevBuf<int4> nodeB;         // internal node: left, right, first, last
   DevBuf<float4> box;         // internal node: x0, y0, x1, y1
   DevBuf<float2> sum;         // internal node: coordinate sums
-  DevBuf<uint32_t> flags;     // bottom-up arrival counters (kept at zero between passes)
-  DevBuf<int32_t> parent;     // internal nodes [0, n - 1), leaves after
+  DevBuf<unsigned long long> slot;  // bottom-up exchange slots (kept empty, all ones, between passes)
   DevBuf<float4> boxpart;
   DevBuf<int32_t> is_start;   // 1 where a group begins (sorted positions)
   DevBuf<int64_t> gscan;      // exclusive scan of is_start; gscan[n] = number of groups
