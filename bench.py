@@ -697,6 +697,9 @@ def bench_rmat(args, pkg, log_fn=log):
         "oracle_subgraph_nodes": int(sub.n),
     }
     arms = ((0, 0, "fp32"), (1, 0, "bf16"), (0, 1, "fp32_tree"))
+    if args.rmat_arms:
+        keep = set(args.rmat_arms.split(","))
+        arms = tuple(a for a in arms if a[2] in keep)
     for prec, rep, name in arms:
         lay = pkg.Layout(profile=1, precision=prec, repulsion=rep, theta=args.tree_theta)
         tb = time.perf_counter()
@@ -779,6 +782,7 @@ def main():
     ap.add_argument("--rmat", action="store_true", help="also run the R-MAT 2^21 workload (about a minute)")
     ap.add_argument("--rmat-steps", type=int, default=5)
     ap.add_argument("--rmat-scale", type=int, default=21)
+    ap.add_argument("--rmat-arms", default="", help="comma-separated subset of fp32,bf16,fp32_tree (default: all)")
     ap.add_argument("--only-rmat", action="store_true", help="run only the R-MAT section (profiling)")
     ap.add_argument("--only-tree", action="store_true", help="run only the tree-code section (profiling)")
     ap.add_argument("--scale", action="store_true", help="also lay out 3M- and 4M-node graphs with the tree code (a few minutes)")
