@@ -34,6 +34,25 @@ namespace {
 constexpr int kAttrCta = 256;
 constexpr int kG = 8;  // lanes per row
 
+// Exclusive scan of v over a CTA of kAttrCta threads into off[0..kAttrCta],
+// off[kAttrCta] = total (wsum: kAttrCta / 32 ints of scratch).  Ends with
+// a __syncthreads before off is complete for every thread: the caller syncs.
+__device__ __forceinline__ void block_excl_scan(int v, int* off, int* wsum) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += u;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  int base = 0;
+  for (int k = 0; k < w; ++k) base += wsum[k];
+  off[threadIdx.x] = base + x - v;
+  if (threadIdx.x == kAttrCta - 1) off[kAttrCta] = base + x;
+}
+
 // Gradient of row i from its attraction sum fa, then (EXPORT) the gradient
 // export or the optimiser step into the next layout.
 template <bool EXPORT>
@@ -66,10 +85,16 @@ __device__ __forceinline__ void finish_row(int64_t i, float2 fa, const float2* _
   if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&sched->flags, kFlagNonfiniteY);
 }
 
-// Two phases per CTA of kAttrCta rows: (1) groups of G lanes gather the
-// attraction of the CTA's rows into shared memory; (2) one thread per row
-// reads F^r, the optimiser state and Y_i and writes the update, so the state
-// traffic is fully coalesced.
+// Three phases per CTA of kAttrCta rows.  A short row's attraction is, by
+// definition of the sum order, G slot partials -- slot s accumulates entries
+// s, s + G, ... with an fmaf chain (attract_entries with lane = s) -- added
+// in the order of the G-lane xor butterfly.  (1) each row counts its slots
+// in use (min(degree, G)); (2) one thread per (row, slot) in use, packed
+// over the CTA's rows, computes the slot partials into shared memory, so
+// short rows leave no lane idle and a thread has its own gathers in flight;
+// (3) one thread per row adds its slots in the butterfly's order, reads F^r,
+// the optimiser state and Y_i and writes the update (coalesced).  The sums
+// are the bits G lanes per row with group_sum<G> produce.
 //
 // FUSED (update only): the first heavy_blocks CTAs instead take the chunks
 // of the long rows (more than kHeavyDeg entries), one warp per chunk; the
@@ -85,9 +110,10 @@ __global__ void __launch_bounds__(kAttrCta, 6)
               bf162* __restrict__ Ynext16, float2* __restrict__ upd, float2* __restrict__ gains,
               const float2* __restrict__ frep_part, int chunks, int n_pad, Sched* sched, float eta, float min_gain,
               float alpha_export, float2* __restrict__ g_out, HeavyRows hv, int heavy_blocks) {
-  constexpr int NGRP = kAttrCta / G;
-  __shared__ float2 sfa[kAttrCta];
+  __shared__ float2 spart[kAttrCta][G];
   __shared__ int64_t srp[kAttrCta + 1];
+  __shared__ int soff[kAttrCta + 1];
+  __shared__ int swarp[kAttrCta / 32];
   if (FUSED && (int)blockIdx.x < heavy_blocks) {
     const int lane = threadIdx.x & 31;
     const int stride = heavy_blocks * (kAttrCta / 32);
@@ -120,40 +146,69 @@ __global__ void __launch_bounds__(kAttrCta, 6)
     return;
   }
   const int64_t row0 = (int64_t)(blockIdx.x - (FUSED ? heavy_blocks : 0)) * kAttrCta;
-  const int grp = threadIdx.x / G, lane = threadIdx.x % G;
-  for (int t = threadIdx.x; t <= kAttrCta; t += kAttrCta) srp[t] = row0 + t <= n ? rp[row0 + t] : 0;
+  const int tid = threadIdx.x;
+  for (int t = tid; t <= kAttrCta; t += kAttrCta) srp[t] = row0 + t <= n ? rp[row0 + t] : 0;
   __syncthreads();
-  for (int r = grp; r < kAttrCta; r += NGRP) {
-    const int64_t i = row0 + r;
-    float ax = 0.f, ay = 0.f;
-    if (i < n) {
-      if (srp[r + 1] - srp[r] > kHeavyDeg) {
-        if (!FUSED && lane == 0) {  // chunk sums from k_attract_heavy, in chunk order
-          int lo = 0, hi = hv.count - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (hv.rows[mid] < i) lo = mid + 1; else hi = mid;
-          }
-          for (int c = hv.chunk_off[lo]; c < hv.chunk_off[lo + 1]; ++c) {
-            const float2 f = hv.fa[c];
-            ax += f.x;
-            ay += f.y;
-          }
-        }
-      } else {
-        attract_entries<G, PT, YT>(srp[r], srp[r + 1], col, P, Ycur, i, lane, ld_y(Ycur, i), ax, ay);
+  // (1) the slots of this thread's row: slot s < G sums entries s, s + G, ...
+  // of the row (short rows only); a hub row's chunk sums go to slot 0
+  const int64_t i = row0 + tid;
+  int ns = 0;
+#pragma unroll
+  for (int q = 0; q < G; ++q) spart[tid][q] = make_float2(0.f, 0.f);
+  if (i < n) {
+    const int64_t d = srp[tid + 1] - srp[tid];
+    if (d <= kHeavyDeg) {
+      ns = (int)(d < G ? d : G);
+    } else if (!FUSED) {  // chunk sums from k_attract_heavy, in chunk order
+      int lo = 0, hi = hv.count - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (hv.rows[mid] < i) lo = mid + 1; else hi = mid;
       }
+      float ax = 0.f, ay = 0.f;
+      for (int c = hv.chunk_off[lo]; c < hv.chunk_off[lo + 1]; ++c) {
+        const float2 f = hv.fa[c];
+        ax += f.x;
+        ay += f.y;
+      }
+      spart[tid][0] = make_float2(ax, ay);
     }
-    ax = group_sum<G>(ax);
-    ay = group_sum<G>(ay);
-    if (lane == 0) sfa[r] = make_float2(ax, ay);
+  }
+  block_excl_scan(ns, soff, swarp);
+  __syncthreads();
+  // (2) one thread per (row, slot) in use, packed over the CTA's rows
+  const int nslots = soff[kAttrCta];
+  for (int q = tid; q < nslots; q += kAttrCta) {
+    int lo = 0, hi = kAttrCta - 1;  // the row: largest r with soff[r] <= q
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (soff[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const int64_t ir = row0 + lo;
+    float ax = 0.f, ay = 0.f;
+    attract_entries<G, PT, YT>(srp[lo], srp[lo + 1], col, P, Ycur, ir, q - soff[lo], ld_y(Ycur, ir), ax, ay);
+    spart[lo][q - soff[lo]] = make_float2(ax, ay);
   }
   __syncthreads();
-  const int64_t i = row0 + threadIdx.x;
   if (i >= n) return;
-  if (FUSED && srp[threadIdx.x + 1] - srp[threadIdx.x] > kHeavyDeg) return;  // updated by its last chunk
-  finish_row<EXPORT>(i, sfa[threadIdx.x], frep_part, chunks, n_pad, sched, alpha_export, g_out, Ym, Ynext, Ynext16,
-                     upd, gains, eta, min_gain);
+  if (FUSED && srp[tid + 1] - srp[tid] > kHeavyDeg) return;  // updated by its last chunk
+  // (3) the row's sum in the order of group_sum<G> (xor butterfly: slot l
+  // plus slot l ^ o for o = G/2, ..., 1), then the update
+  float vx[G], vy[G];
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    vx[q] = spart[tid][q].x;
+    vy[q] = spart[tid][q].y;
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int l = 0; l < o; ++l) {
+      vx[l] = vx[l] + vx[l + o];
+      vy[l] = vy[l] + vy[l + o];
+    }
+  finish_row<EXPORT>(i, make_float2(vx[0], vy[0]), frep_part, chunks, n_pad, sched, alpha_export, g_out, Ym, Ynext,
+                     Ynext16, upd, gains, eta, min_gain);
 }
 
 // Attraction of the long rows (more than kHeavyDeg entries), in chunks of at
