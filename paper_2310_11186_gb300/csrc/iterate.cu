@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256)
     const int64_t i = hv.chunk_row[c];
     const float2 yi = ld_y(Y, i);
     float ax = 0.f, ay = 0.f;
-    attract_entries<32, PT, YT>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Y, i, lane, yi, ax, ay);
+    attract_entries_pipelined<32, PT, YT>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Y, i, lane, yi, ax, ay);
     ax = group_sum<32>(ax);
     ay = group_sum<32>(ay);
     if (lane == 0) hv.fa[c] = make_float2(ax, ay);

@@ -46,6 +46,61 @@ __device__ __forceinline__ void attract_entries(int64_t a, int64_t b, const int3
   }
 }
 
+// attract_entries with the column / P loads of the next batch issued before
+// the current batch's gathers are used (software pipelining), for the long
+// rows' chunks where a lane runs through many batches.  Same terms in the
+// same order: the same result.  Used where registers are not capped (the
+// separate hub-row kernel); under the fused kernel's cap it spills and is
+// slower.
+template <int G, class PT = float, class YT = float2>
+__device__ __forceinline__ void attract_entries_pipelined(int64_t a, int64_t b, const int32_t* __restrict__ col,
+                                                          const PT* __restrict__ P, const YT* __restrict__ Y,
+                                                          int64_t i, int lane, float2 yi, float& ax, float& ay) {
+  constexpr int U = 4;
+  int64_t e0 = a + lane;
+  if (e0 >= b) return;
+  int32_t j[U];
+  float p[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t e = e0 + (int64_t)u * G;
+    j[u] = e < b ? col[e] : (int32_t)i;
+    p[u] = e < b ? ld_p(P, e) : 0.f;
+  }
+  for (;;) {
+    float2 yj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) yj[u] = ld_y(Y, j[u]);
+    const int64_t e1 = e0 + U * G;
+    const bool more = e1 < b;
+    int32_t jn[U];
+    float pn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = e1 + (int64_t)u * G;
+      jn[u] = e < b ? col[e] : (int32_t)i;
+      pn[u] = e < b ? ld_p(P, e) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (e0 + (int64_t)u * G < b) {
+        const float dx = yi.x - yj[u].x, dy = yi.y - yj[u].y;
+        const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
+        const float pw = p[u] * w;
+        ax = fmaf(pw, dx, ax);
+        ay = fmaf(pw, dy, ay);
+      }
+    }
+    if (!more) break;
+    e0 = e1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      j[u] = jn[u];
+      p[u] = pn[u];
+    }
+  }
+}
+
 template <int G>
 __device__ __forceinline__ void attract_row(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                             const float* __restrict__ P, const float2* __restrict__ Y, int64_t i,
