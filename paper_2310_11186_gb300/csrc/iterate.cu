@@ -194,21 +194,23 @@ __global__ void __launch_bounds__(kAttrCta, 6)
   if (FUSED && srp[tid + 1] - srp[tid] > kHeavyDeg) return;  // updated by its last chunk
   // (3) the row's sum in the order of group_sum<G> (xor butterfly: slot l
   // plus slot l ^ o for o = G/2, ..., 1), then the update
-  float vx[G], vy[G];
-#pragma unroll
-  for (int q = 0; q < G; ++q) {
-    vx[q] = spart[tid][q].x;
-    vy[q] = spart[tid][q].y;
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1)
-#pragma unroll
-    for (int l = 0; l < o; ++l) {
-      vx[l] = vx[l] + vx[l + o];
-      vy[l] = vy[l] + vy[l + o];
-    }
-  finish_row<EXPORT>(i, make_float2(vx[0], vy[0]), frep_part, chunks, n_pad, sched, alpha_export, g_out, Ym, Ynext,
-                     Ynext16, upd, gains, eta, min_gain);
+  static_assert(G == 8, "the butterfly below is written out for 8 slots");
+  const float2* sp = spart[tid];
+  float2 a0 = sp[0], a1 = sp[1], t = sp[4];
+  a0 = make_float2(a0.x + t.x, a0.y + t.y);  // o = 4: slot l + slot l + 4
+  t = sp[5];
+  a1 = make_float2(a1.x + t.x, a1.y + t.y);
+  float2 a2 = sp[2];
+  t = sp[6];
+  a2 = make_float2(a2.x + t.x, a2.y + t.y);
+  float2 a3 = sp[3];
+  t = sp[7];
+  a3 = make_float2(a3.x + t.x, a3.y + t.y);
+  a0 = make_float2(a0.x + a2.x, a0.y + a2.y);  // o = 2
+  a1 = make_float2(a1.x + a3.x, a1.y + a3.y);
+  const float2 fa = make_float2(a0.x + a1.x, a0.y + a1.y);  // o = 1
+  finish_row<EXPORT>(i, fa, frep_part, chunks, n_pad, sched, alpha_export, g_out, Ym, Ynext, Ynext16, upd, gains,
+                     eta, min_gain);
 }
 
 // Attraction of the long rows (more than kHeavyDeg entries), in chunks of at
