@@ -32,6 +32,8 @@ namespace tsgne {
 namespace {
 
 constexpr int kAttrCta = 256;
+constexpr int kAttrPairs = 3;  // (row, slot) pairs a thread has in flight at once
+static_assert(kAttrCta <= 256, "rows of a CTA are numbered in one byte");
 constexpr int kG = 8;  // lanes per row
 
 // Exclusive scan of v over a CTA of kAttrCta threads into off[0..kAttrCta],
@@ -114,6 +116,8 @@ __global__ void __launch_bounds__(kAttrCta, 6)
   __shared__ int64_t srp[kAttrCta + 1];
   __shared__ int soff[kAttrCta + 1];
   __shared__ int swarp[kAttrCta / 32];
+  __shared__ uint8_t srow[kAttrCta * G];  // (row, slot) pair -> row
+  __shared__ int slevels;
   if (FUSED && (int)blockIdx.x < heavy_blocks) {
     const int lane = threadIdx.x & 31;
     const int stride = heavy_blocks * (kAttrCta / 32);
@@ -148,6 +152,7 @@ __global__ void __launch_bounds__(kAttrCta, 6)
   const int64_t row0 = (int64_t)(blockIdx.x - (FUSED ? heavy_blocks : 0)) * kAttrCta;
   const int tid = threadIdx.x;
   for (int t = tid; t <= kAttrCta; t += kAttrCta) srp[t] = row0 + t <= n ? rp[row0 + t] : 0;
+  if (tid == 0) slevels = 0;
   __syncthreads();
   // (1) the slots of this thread's row: slot s < G sums entries s, s + G, ...
   // of the row (short rows only); a hub row's chunk sums go to slot 0
@@ -159,6 +164,7 @@ __global__ void __launch_bounds__(kAttrCta, 6)
     const int64_t d = srp[tid + 1] - srp[tid];
     if (d <= kHeavyDeg) {
       ns = (int)(d < G ? d : G);
+      if (d > 0) atomicMax(&slevels, (int)((d + G - 1) / G));  // entries per slot, at most
     } else if (!FUSED) {  // chunk sums from k_attract_heavy, in chunk order
       int lo = 0, hi = hv.count - 1;
       while (lo < hi) {
@@ -176,19 +182,58 @@ __global__ void __launch_bounds__(kAttrCta, 6)
   }
   block_excl_scan(ns, soff, swarp);
   __syncthreads();
-  // (2) one thread per (row, slot) in use, packed over the CTA's rows
-  const int nslots = soff[kAttrCta];
-  for (int q = tid; q < nslots; q += kAttrCta) {
-    int lo = 0, hi = kAttrCta - 1;  // the row: largest r with soff[r] <= q
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (soff[mid] <= q) lo = mid; else hi = mid - 1;
+  for (int q = 0; q < ns; ++q) srow[soff[tid] + q] = (uint8_t)tid;
+  __syncthreads();
+  // (2) the (row, slot) pairs in use, packed over the CTA's rows, level by
+  // level: level k adds entry s + G k of each slot to its partial (the
+  // fmaf chain of attract_entries, in the same order).  A pair belongs to
+  // one thread at every level; each thread keeps kAttrPairs pairs' loads in
+  // flight at once.
+  const int nslots = soff[kAttrCta], levels = slevels;
+  for (int k = 0; k < levels; ++k)
+    for (int q0 = tid; q0 < nslots; q0 += kAttrPairs * kAttrCta) {
+      int r[kAttrPairs], sl[kAttrPairs];
+      int64_t e[kAttrPairs];
+      bool ok[kAttrPairs];
+#pragma unroll
+      for (int m = 0; m < kAttrPairs; ++m) {
+        const int q = q0 + m * kAttrCta;
+        ok[m] = false;
+        r[m] = 0;
+        sl[m] = 0;
+        e[m] = 0;
+        if (q < nslots) {
+          r[m] = srow[q];
+          sl[m] = q - soff[r[m]];
+          e[m] = srp[r[m]] + sl[m] + (int64_t)G * k;
+          ok[m] = e[m] < srp[r[m] + 1];
+        }
+      }
+      int32_t j[kAttrPairs];
+      float pe[kAttrPairs];
+#pragma unroll
+      for (int m = 0; m < kAttrPairs; ++m) {
+        j[m] = ok[m] ? col[e[m]] : 0;
+        pe[m] = ok[m] ? ld_p(P, e[m]) : 0.f;
+      }
+      float2 yj[kAttrPairs], yi[kAttrPairs];
+#pragma unroll
+      for (int m = 0; m < kAttrPairs; ++m) {
+        yj[m] = ok[m] ? ld_y(Ycur, j[m]) : make_float2(0.f, 0.f);
+        yi[m] = ok[m] ? ld_y(Ycur, row0 + r[m]) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int m = 0; m < kAttrPairs; ++m)
+        if (ok[m]) {
+          float2 acc = spart[r[m]][sl[m]];
+          const float dx = yi[m].x - yj[m].x, dy = yi[m].y - yj[m].y;
+          const float w = 1.0f / fmaf(dy, dy, fmaf(dx, dx, 1.0f));
+          const float pw = pe[m] * w;
+          acc.x = fmaf(pw, dx, acc.x);
+          acc.y = fmaf(pw, dy, acc.y);
+          spart[r[m]][sl[m]] = acc;
+        }
     }
-    const int64_t ir = row0 + lo;
-    float ax = 0.f, ay = 0.f;
-    attract_entries<G, PT, YT>(srp[lo], srp[lo + 1], col, P, Ycur, ir, q - soff[lo], ld_y(Ycur, ir), ax, ay);
-    spart[lo][q - soff[lo]] = make_float2(ax, ay);
-  }
   __syncthreads();
   if (i >= n) return;
   if (FUSED && srp[tid + 1] - srp[tid] > kHeavyDeg) return;  // updated by its last chunk
