@@ -36,6 +36,12 @@ constexpr int kAttrPairs = 3;  // (row, slot) pairs a thread has in flight at on
 static_assert(kAttrCta <= 256, "rows of a CTA are numbered in one byte");
 constexpr int kG = 8;  // lanes per row
 
+__device__ __forceinline__ uint32_t atom_add_acq_rel_u32(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // Exclusive scan of v over a CTA of kAttrCta threads into off[0..kAttrCta],
 // off[kAttrCta] = total (wsum: kAttrCta / 32 ints of scratch).  Ends with
 // a __syncthreads before off is complete for every thread: the caller syncs.
@@ -132,9 +138,9 @@ __global__ void __launch_bounds__(kAttrCta, 6)
         hv.fa[c] = make_float2(ax, ay);
         const int h = hv.chunk_heavy[c];
         const int c0 = hv.chunk_off[h], c1 = hv.chunk_off[h + 1];
-        __threadfence();
-        if (atomicAdd(&hv.arrivals[h], 1u) == (unsigned)(c1 - c0 - 1)) {  // last chunk of the row
-          __threadfence();
+        // acquire-release arrival: the chunk sums stored before it are
+        // visible to the last chunk's warp after its own (no separate fences)
+        if (atom_add_acq_rel_u32(&hv.arrivals[h], 1u) == (unsigned)(c1 - c0 - 1)) {  // last chunk of the row
           hv.arrivals[h] = 0u;
           float sx = 0.f, sy = 0.f;
           for (int q = c0; q < c1; ++q) {
