@@ -259,12 +259,16 @@ tsgne_status tsgne_sync(tsgne_ctx* ctx);
 /*
  * ---------------------------------------------------------------- batches
  * Many layouts advanced together: every iteration of every member runs in
- * four kernel launches (replayed as one CUDA graph per membership) instead of
- * two launches per member.  Each member keeps its own P, layout, optimiser
+ * four kernel launches (five when a member has rows of more than 32
+ * entries; replayed as one CUDA graph per membership) instead of two
+ * launches per member.  Each member keeps its own P, layout, optimiser
  * state and iteration counter on the device, may be added or removed between
  * runs (continuous batching), and evolves exactly as it would in a batch of
  * its own: the per-member arithmetic, including the order of every
- * reduction, does not depend on the other members.  All members share one
+ * reduction, does not depend on the other members.  The attraction sums
+ * rows as the single-layout path does (rows above 32 entries in 1024-entry
+ * warp chunks added in chunk order), so a batch of one equals tsgne_run at
+ * the same repulsion tile.  All members share one
  * repulsion tile of 512 * tile_warps points (1, 2 or 4; smaller tiles pad
  * small graphs less, larger tiles amortise more per unit).  The same
  * conventions as the context API apply (status codes, one stream, not
@@ -384,7 +388,8 @@ void tsgne_server_config_default(tsgne_server_config* cfg);
 
 /* Device bytes a resident layout of n points and nnz affinities holds in a
  * batch with the given tile (P, layout, optimiser state, initial layout,
- * per-tile repulsion slots, Z partials); -1 for invalid arguments.  Host
+ * per-tile repulsion slots, Z partials, an upper bound for the hub-row
+ * chunk lists); -1 for invalid arguments.  Host
  * arithmetic only (no GPU needed). */
 int64_t tsgne_server_estimate_bytes(int32_t n, int64_t nnz, int32_t tile_warps);
 

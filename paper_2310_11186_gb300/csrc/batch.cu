@@ -1,5 +1,6 @@
 // Many layouts per launch: the t-SGNE iteration of every member of a batch
-// runs in four launches, whatever the number and sizes of the members.
+// runs in four launches (five when a member has rows above 32 entries),
+// whatever the number and sizes of the members.
 //
 //   k_batch_repulsion  one global work queue over the tile pairs of all
 //                      members (prefix offsets per member); each unit is the
@@ -10,12 +11,16 @@
 //                      partials minus n, schedule (alpha, mu) from its own
 //                      iteration counter t, t += 1
 //   k_batch_reduce     fixed-order sum of each point's partial-force slots
-//   k_batch_attract    attraction + gradient + optimiser step per row
+//   k_batch_hubs       (members with rows above 32 entries) one warp per
+//                      1024-entry chunk of such a row, over all members'
+//                      chunks: the single-layout path's chunk sums
+//   k_batch_attract    attraction + gradient + optimiser step per row (a hub
+//                      row adds its chunk sums in chunk order)
 //
 // Members keep their P, layout and optimiser state resident on the device
 // and may differ in size and in iteration count (each has its own t); the
 // current layout of a member is Y[t & 1], so one captured CUDA graph of the
-// four launches serves every iteration of a given membership.  All members of
+// launches serves every iteration of a given membership.  All members of
 // a batch use the same tile size T = 512 W; tsgne_batch_autotune picks W.
 #include <algorithm>
 #include <chrono>
@@ -46,6 +51,7 @@ struct GraphDesc {
   float2* fsum;
   double* zunit;
   Sched* sched;
+  HeavyRows hv;  // rows above kHeavyDeg entries, in kHeavyChunk-entry chunks (as the single-layout path)
   int n, nt, n_pad, units;
   float eta;
   int pad_;
@@ -138,6 +144,28 @@ __global__ void k_batch_reduce(const GraphDesc* __restrict__ descs, const int* _
   }
 }
 
+// One warp per chunk of every member's hub rows (global chunk index c over
+// the members' chunk offsets), at the layout the update reads: the chunk's
+// 32-lane sum, as k_attract_heavy computes it for one layout.
+__global__ void __launch_bounds__(256) k_batch_hubs(const GraphDesc* __restrict__ descs,
+                                                    const int* __restrict__ chunk_off, int members, int C) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < C; c += warps) {
+    const int g = find_owner(chunk_off, members, c);
+    const GraphDesc& d = descs[g];
+    const int lc = c - chunk_off[g];
+    const int64_t i = d.hv.chunk_row[lc];
+    const float2* Ycur = d.Y[(d.sched->t - 1) & 1];  // t already advanced by k_batch_finalize
+    float ax = 0.f, ay = 0.f;
+    attract_entries_pipelined<32>(d.hv.chunk_begin[lc], d.hv.chunk_end[lc], d.col, d.P, Ycur, i, lane, Ycur[i], ax,
+                                  ay);
+    ax = group_sum<32>(ax);
+    ay = group_sum<32>(ay);
+    if (lane == 0) d.hv.fa[lc] = make_float2(ax, ay);
+  }
+}
+
 template <int G>
 __global__ void __launch_bounds__(256) k_batch_attract(const GraphDesc* __restrict__ descs,
                                                        const int* __restrict__ row_off, int members, int R,
@@ -156,7 +184,22 @@ __global__ void __launch_bounds__(256) k_batch_attract(const GraphDesc* __restri
     t = d.sched->t;  // already advanced by k_batch_finalize
     const float2* Ycur = d.Y[(t - 1) & 1];
     yi = Ycur[i];
-    attract_row<G>(d.rp, d.col, d.P, Ycur, i, lane, yi, ax, ay);
+    if (d.rp[i + 1] - d.rp[i] > kHeavyDeg) {
+      if (lane == 0) {  // chunk sums from k_batch_hubs, in chunk order
+        int lo = 0, hi = d.hv.count - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (d.hv.rows[mid] < i) lo = mid + 1; else hi = mid;
+        }
+        for (int c = d.hv.chunk_off[lo]; c < d.hv.chunk_off[lo + 1]; ++c) {
+          const float2 f = d.hv.fa[c];
+          ax += f.x;
+          ay += f.y;
+        }
+      }
+    } else {
+      attract_row<G>(d.rp, d.col, d.P, Ycur, i, lane, yi, ax, ay);
+    }
   }
   ax = group_sum<G>(ax);
   ay = group_sum<G>(ay);
@@ -211,6 +254,7 @@ struct Member {
   DevBuf<float2> part;
   DevBuf<double> zunit;
   DevBuf<Sched> sched;
+  HeavyStore hv;                     // hub rows and their chunks
   int nt = 0, n_pad = 0, units = 0;  // for the batch's current tile
   DevBuf<float2> Y0;                 // initial layout (autotune restores it)
   bool active = true;
@@ -234,9 +278,9 @@ struct tsgne_batch {
   int next_id = 0;
   std::vector<std::unique_ptr<Member>> members;
   DevBuf<GraphDesc> d_desc;
-  DevBuf<int> d_unit_off, d_row_off;
+  DevBuf<int> d_unit_off, d_row_off, d_chunk_off;
   DevBuf<BatchCtr> d_ctr;
-  int U = 0, R = 0, G = 0;  // of the active members
+  int U = 0, R = 0, G = 0, C = 0;  // of the active members (C: hub-row chunks)
   bool dirty = true;
   cudaGraphExec_t graph = nullptr;
   ~tsgne_batch() {
@@ -299,7 +343,7 @@ tsgne_status refresh(tsgne_batch* b) {
   const int G = (int)act.size();
   b->G = G;
   std::vector<GraphDesc> h(G > 0 ? G : 1);
-  std::vector<int> uo(G + 1, 0), ro(G + 1, 0);
+  std::vector<int> uo(G + 1, 0), ro(G + 1, 0), co(G + 1, 0);
   for (int k = 0; k < G; ++k) {
     Member& m = *act[k];
     GraphDesc d{};
@@ -314,6 +358,7 @@ tsgne_status refresh(tsgne_batch* b) {
     d.fsum = m.fsum.get();
     d.zunit = m.zunit.get();
     d.sched = m.sched.get();
+    d.hv = m.hv.view();
     d.n = m.n;
     d.nt = m.nt;
     d.n_pad = m.n_pad;
@@ -322,15 +367,19 @@ tsgne_status refresh(tsgne_batch* b) {
     h[k] = d;
     uo[k + 1] = uo[k] + m.units;
     ro[k + 1] = ro[k] + m.n;
+    co[k + 1] = co[k] + m.hv.chunks;
   }
   b->U = uo[G];
   b->R = ro[G];
+  b->C = co[G];
   TS_TRY(b->d_desc.alloc(h.size()));
   TS_TRY(b->d_unit_off.alloc(uo.size()));
   TS_TRY(b->d_row_off.alloc(ro.size()));
+  TS_TRY(b->d_chunk_off.alloc(co.size()));
   TS_CUDA(cudaMemcpyAsync(b->d_desc.get(), h.data(), sizeof(GraphDesc) * h.size(), cudaMemcpyHostToDevice, b->stream));
   TS_CUDA(cudaMemcpyAsync(b->d_unit_off.get(), uo.data(), sizeof(int) * uo.size(), cudaMemcpyHostToDevice, b->stream));
   TS_CUDA(cudaMemcpyAsync(b->d_row_off.get(), ro.data(), sizeof(int) * ro.size(), cudaMemcpyHostToDevice, b->stream));
+  TS_CUDA(cudaMemcpyAsync(b->d_chunk_off.get(), co.data(), sizeof(int) * co.size(), cudaMemcpyHostToDevice, b->stream));
   TS_CUDA(cudaStreamSynchronize(b->stream));
   b->dirty = false;
   return TSGNE_OK;
@@ -353,6 +402,10 @@ tsgne_status enqueue_iteration(tsgne_batch* b) {
   k_batch_finalize<<<G, 32 * W, 0, b->stream>>>(b->d_desc.get(), c.early_exag, c.ee_iters, c.momentum0, c.momentum1);
   const int rgrid = std::max(1, std::min((b->R + 255) / 256, b->sms * 16));
   k_batch_reduce<<<rgrid, 256, 0, b->stream>>>(b->d_desc.get(), b->d_row_off.get(), G, b->R);
+  if (b->C > 0) {
+    const int hgrid = std::min((b->C + 7) / 8, 4096);  // one warp per chunk
+    k_batch_hubs<<<hgrid, 256, 0, b->stream>>>(b->d_desc.get(), b->d_chunk_off.get(), G, b->C);
+  }
   const int64_t threads = (int64_t)b->R * kBG;
   const int agrid = (int)std::max<int64_t>(1, (threads + 255) / 256);
   k_batch_attract<kBG><<<agrid, 256, 0, b->stream>>>(b->d_desc.get(), b->d_row_off.get(), G, b->R, c.min_gain);
@@ -493,6 +546,7 @@ tsgne_status tsgne_batch_add(tsgne_batch* b, int32_t n, const int64_t* row_ptr, 
   B_CUDA(b, cudaMemsetAsync(mb.sched.get(), 0, sizeof(Sched), b->stream));
   B_TRY(b, build_neighbor_structure(n, rp_in.get(), col_in.get(), m, b->cfg.k_nn, mb.rp, mb.col, tslot, &mb.nnz,
                                     b->stream));
+  B_TRY(b, find_heavy_rows(n, mb.rp.get(), mb.hv, b->stream));
   B_TRY(b, mb.P.alloc((size_t)mb.nnz));
   B_TRY(b, build_affinities(n, mb.rp.get(), mb.col.get(), tslot.get(), mb.nnz, X_in.get(), d, b->cfg.perplexity,
                             b->cfg.bisect_tol, b->cfg.bisect_max_iter, mb.P.get(), mb.sched.get(), b->stream));

@@ -128,7 +128,11 @@ int64_t tsgne_server_estimate_bytes(int32_t n, int64_t nnz, int32_t tile_warps) 
   const int64_t nt = (n + T - 1) / T;
   const int64_t n_pad = nt * T;
   const int64_t units = nt * (nt + 1) / 2;
-  return 8 * ((int64_t)n + 1) + 8 * nnz + 5 * 8 * n_pad_max + 8 * (int64_t)n + 8 * nt * n_pad + 8 * units + 256;
+  // hub rows (more than 32 entries: at most nnz / 33 of them) and their
+  // 1024-entry chunks: 12 B per row, 32 B per chunk
+  const int64_t hub_rows = nnz / 33 + 1, hub_chunks = nnz / 1024 + hub_rows;
+  return 8 * ((int64_t)n + 1) + 8 * nnz + 5 * 8 * n_pad_max + 8 * (int64_t)n + 8 * nt * n_pad + 8 * units +
+         12 * hub_rows + 32 * hub_chunks + 256;
 }
 
 tsgne_status tsgne_server_create(tsgne_server** out, const tsgne_server_config* scfg, const tsgne_config* cfg,

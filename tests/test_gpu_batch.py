@@ -61,6 +61,35 @@ def test_batch_of_one_equals_context_path():
     assert np.array_equal(Yb, Yc)
 
 
+def test_hub_rows_batch_equals_context_and_mix():
+    """A power-law graph whose hub rows hold thousands of entries (summed in
+    1024-entry warp chunks): a batch of one equals the single-layout path bit
+    for bit, and in a mix with graphs without hub rows every member still
+    equals itself alone."""
+    g, X = synth.rmat(12, 1 << 17, seed=5)
+    Y0 = synth.y_init(g.n, seed=5)
+    with pkg.Layout() as lay:
+        lay.build_P(g.row_ptr, g.col, X)
+        rp, _, _ = lay.get_P()
+        assert np.diff(rp).max() > 2 * 1024  # rows of several chunks
+        lay.init_Y(Y0)
+        tile = lay.repulsion_shape()["block"] // 32
+        lay.run(30)
+        Yc = lay.get_Y()
+    Yb = _alone(g, X, Y0, tile, 30)
+    assert np.array_equal(Yb, Yc)
+    others = _graphs([900, 2500], seed=77)
+    with pkg.Batch(tile_warps=tile) as b:
+        ids = [b.add(gg.row_ptr, gg.col, XX, YY) for gg, XX, YY in others]
+        hid = b.add(g.row_ptr, g.col, X, Y0)
+        b.run(30)
+        Yh, _ = b.get_Y(hid)
+        Yo = [b.get_Y(i)[0] for i in ids]
+    assert np.array_equal(Yh, Yb)
+    for (gg, XX, YY), Y in zip(others, Yo):
+        assert np.array_equal(Y, _alone(gg, XX, YY, tile, 30))
+
+
 @pytest.mark.parametrize("tile", [1, 2, 4])
 def test_members_in_a_mix_equal_alone(tile):
     gs = _graphs([700, 2000, 3500, 5003], seed=10)
