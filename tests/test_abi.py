@@ -52,6 +52,17 @@ def test_host_only_calls(built):
     assert ei.value.status == 1
 
 
+@pytest.mark.parametrize("bad", [
+    dict(spin_budget_cycles=0), dict(spin_budget_cycles=-5), dict(repulsion=2), dict(theta=-0.1),
+    dict(theta=1.5), dict(precision=2), dict(p_walks=513), dict(p_walks=-1), dict(p_walk_length=0),
+    dict(p_walk_length=65), dict(k_nn=257), dict(min_gain=-1.0),
+])
+def test_invalid_configurations_are_rejected_before_device_work(built, bad):
+    with pytest.raises(pkg.TsgneError) as ei:
+        pkg.tsgne_create(pkg.tsgne_config_default(**bad))
+    assert ei.value.status == 1  # INVALID_ARG, no CUDA call needed to decide it
+
+
 def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(pkg, "_lib", None)
     monkeypatch.setattr(pkg, "library_path", "/nonexistent/libtsgne.so")

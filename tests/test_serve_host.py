@@ -37,3 +37,11 @@ def test_summary_percentiles():
         reqs.append(r)
     s = serve.summarize(reqs, 10.0)
     assert s["layouts"] == 4 and s["p50_s"] == 2.5 and abs(s["layouts_per_s"] - 0.4) < 1e-12
+
+
+def test_estimate_bytes_bounds_the_hub_row_chunks():
+    """The estimate carries an upper bound for the hub-row chunk lists: it
+    grows with nnz at a fixed n (a denser graph can hold more hub rows)."""
+    a = serve.estimate_bytes(4096, 1 << 15, 1)
+    b = serve.estimate_bytes(4096, 1 << 18, 1)
+    assert b - a >= 8 * ((1 << 18) - (1 << 15))  # col + P at least
