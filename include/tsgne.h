@@ -91,12 +91,13 @@ typedef struct {
                                  TSGNE_ERR_TIMEOUT once (the context stays usable) */
   int32_t repulsion;       /* 0: exact all-pairs sums of Eq. 4 (default); 1: tree code, an
                               approximation the paper does not use: points sorted along a
-                              Morton curve, binary radix tree, per group of 32 consecutive
-                              points a walk that takes a node with box side r and centre at
-                              distance d from the group's box as one interaction when
-                              r < theta * d; opened nodes of <= 4 points are summed exactly.
-                              Z and the forces are both approximated; the batch API accepts
-                              0 only */
+                              Morton curve, binary radix tree, per group (a maximal subtree
+                              of at most 32 points) a walk that takes a node with box side r
+                              and centre at distance d from the group's box as one
+                              interaction when r < theta * d; opened nodes of <= 4 points
+                              are summed exactly.  Z and the forces are both approximated;
+                              n must be below 2^30 (else INVALID_ARG when P is built); the
+                              batch API accepts 0 only */
   float theta;             /* opening angle of the tree code, [0, 1] (default 0.5; 0 sums
                               every pair exactly through the tree) */
   int32_t p_walks;         /* 0: p_{j|i} by the perplexity bisection of Eq. 2 (default);
