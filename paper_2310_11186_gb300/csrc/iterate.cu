@@ -1,13 +1,14 @@
 // Per-iteration kernels other than the repulsion.
 //
-// k_attract (S3 + S5 fused): G lanes per row i gather the row's neighbours
-//   (float2 loads of Y, int32 columns, FP32 P) into shared memory, then one
-//   thread per row applies the update:
+// k_attract (S3 + S5 fused): the attraction of a CTA's rows (short rows as
+//   G slot partials per row computed by (row, slot) pairs packed over the
+//   CTA; long rows in 1024-entry warp chunks), then one thread per row
+//   applies the update:
 //     F^a_i = sum_{j in N(i)} p_ij w_ij (y_i - y_j),  w = (1 + ||y_i-y_j||^2)^-1,
 //   add the repulsion forces of the row (chunk order), and form the
 //   gradient of Eq. 5 with P scaled by alpha (early exaggeration):
 //     g_i = 4 (alpha F^a_i - F^r_i / Z).
-//   In update mode lane 0 then applies the optimiser (the paper gives none;
+//   In update mode the row's thread then applies the optimiser (the paper gives none;
 //   the published t-SNE rule): per coordinate gain += 0.2 if g and the
 //   previous update have opposite signs, else gain *= 0.8, floored at
 //   min_gain; upd = mu upd - eta gain g; y_next = y + upd.  Reading Y_cur and
