@@ -4,6 +4,8 @@
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -68,3 +70,26 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(pkg, "library_path", "/nonexistent/libtsgne.so")
     with pytest.raises(RuntimeError):
         pkg.lib()
+
+
+@pytest.mark.parametrize("lang,std", [("c", "c99"), ("c++", "c++11")])
+def test_header_is_valid_plain_c_and_cpp(tmp_path, lang, std):
+    """The boundary is a C ABI: the header compiles as strict C99 (and as
+    C++11) with every warning an error, and its entry points can be called."""
+    cc = shutil.which("gcc") if lang == "c" else shutil.which("g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / "use.c"
+    src.write_text(
+        '#include "tsgne.h"\n'
+        "int main(void) {\n"
+        "  tsgne_config c;\n"
+        "  tsgne_config_default(&c);\n"
+        "  tsgne_ctx* ctx = 0;\n"
+        "  tsgne_status s = tsgne_create(&ctx, &c, 0);\n"
+        "  if (s == TSGNE_OK) tsgne_destroy(ctx);\n"
+        "  return tsgne_server_estimate_bytes(1000, 6000, 2) > 0 ? 0 : 1;\n"
+        "}\n")
+    r = subprocess.run([cc, "-x", lang, f"-std={std}", "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
+                        "-I", os.path.dirname(HEADER), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
