@@ -93,3 +93,31 @@ def test_header_is_valid_plain_c_and_cpp(tmp_path, lang, std):
     r = subprocess.run([cc, "-x", lang, f"-std={std}", "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
                         "-I", os.path.dirname(HEADER), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_a_c_program_links_and_calls_the_library(built, tmp_path):
+    """A plain C program links against libtsgne.so and calls the host-only
+    entry points (no GPU needed for these)."""
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / "main.c"
+    src.write_text(
+        '#include <string.h>\n#include "tsgne.h"\n'
+        "int main(void) {\n"
+        "  tsgne_config c;\n"
+        "  tsgne_config_default(&c);\n"
+        "  if (c.perplexity != 30.0f || c.repulsion != 0 || c.spin_budget_cycles <= 0) return 1;\n"
+        "  if (strcmp(tsgne_status_string(TSGNE_ERR_TIMEOUT), \"TSGNE_ERR_TIMEOUT\") != 0) return 2;\n"
+        "  c.perplexity = 1.0f;\n"
+        "  tsgne_ctx* ctx = 0;\n"
+        "  if (tsgne_create(&ctx, &c, 0) != TSGNE_ERR_INVALID_ARG || ctx != 0) return 3;\n"
+        "  return tsgne_server_estimate_bytes(1000, 6000, 2) > 0 ? 0 : 4;\n"
+        "}\n")
+    libdir = os.path.dirname(pkg.library_path)
+    exe = tmp_path / "main"
+    r = subprocess.run([cc, "-std=c99", str(src), "-I", os.path.dirname(HEADER), "-L", libdir, "-ltsgne",
+                        f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
