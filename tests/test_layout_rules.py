@@ -42,6 +42,8 @@ def test_committed_code_does_not_use_the_scratch_folder():
     for rel in tracked.split():
         if not rel.endswith((".py", ".cu", ".cuh", ".h", ".c", ".sh")) or rel.startswith("_work/"):
             continue
+        if os.path.abspath(os.path.join(ROOT, rel)) == os.path.abspath(__file__):
+            continue  # this file names the folder to look for it
         src = open(os.path.join(ROOT, rel), encoding="utf-8").read()
         if re.search(r"['\"/]_work[/'\"]|\b_work\.", src):
             bad.append(rel)
