@@ -126,7 +126,10 @@ tsgne_status tsgne_create(tsgne_ctx** out, const tsgne_config* cfg, void* cuda_s
 /* Frees every device buffer of the context.  NULL is ignored. */
 void tsgne_destroy(tsgne_ctx* ctx);
 
-/* Message of the last failed call on ctx ("" if none).  Valid until the next call. */
+/* Message of the last failed call on ctx ("" if none).  Valid until the next
+ * call.  With ctx = NULL: the message of the calling thread's last failed
+ * call of an entry point that takes no context (tsgne_repulsion_noalloc,
+ * tsgne_shortest_path_embedding), valid until that thread's next call. */
 const char* tsgne_last_error(const tsgne_ctx* ctx);
 
 /* Static name of a status code. */
@@ -448,7 +451,10 @@ tsgne_status tsgne_server_usage(tsgne_server* s, int64_t* used_bytes, int32_t* r
  *
  * Temporaries live in one static device array of about 8.6 MiB that every GPU
  * loading the library holds until the process exits.  2 <= n <=
- * TSGNE_NOALLOC_MAX_N, else TSGNE_ERR_INVALID_ARG before any work.  The first
+ * TSGNE_NOALLOC_MAX_N, and Y, frep_out and z_out 8-byte aligned, else
+ * TSGNE_ERR_INVALID_ARG before any work; tsgne_last_error(NULL) then says
+ * why.  The array's address is cached per device for the life of the
+ * process and does not survive cudaDeviceReset.  The first
  * call on a device looks up that array's address with the device current:
  * make it before any stream capture.  All calls share the array (each call
  * clears what must start at zero and overwrites what it reads), so calls

@@ -431,6 +431,8 @@ def tsgne_repulsion_noalloc(Y, frep_out=None, z_out=None, stream=None):
     torch = _torch()
     if torch is None or not isinstance(Y, torch.Tensor) or not Y.is_cuda:
         raise ValueError("Y must be a CUDA tensor")
+    if Y.dim() != 2 or Y.shape[1] != 2:
+        raise ValueError(f"Y must have shape (n, 2), got {tuple(Y.shape)}")
     Yc = Y.contiguous().float()
     n = int(Yc.shape[0])
     if frep_out is None:
@@ -439,16 +441,19 @@ def tsgne_repulsion_noalloc(Y, frep_out=None, z_out=None, stream=None):
         z_out = torch.empty((1,), dtype=torch.float64, device=Yc.device)
     if not (frep_out.is_cuda and frep_out.dtype == torch.float32 and frep_out.is_contiguous()):
         raise ValueError("frep_out must be a contiguous float32 CUDA tensor")
-    if not (z_out.is_cuda and z_out.dtype == torch.float64):
-        raise ValueError("z_out must be a float64 CUDA tensor")
-    s = stream if stream is not None else torch.cuda.current_stream(Yc.device)
-    handle = ctypes.c_void_p(getattr(s, "cuda_stream", s))
-    st = lib().tsgne_repulsion_noalloc(n, ctypes.c_void_p(Yc.data_ptr()), ctypes.c_void_p(frep_out.data_ptr()),
-                                       ctypes.c_void_p(z_out.data_ptr()), handle)
+    if tuple(frep_out.shape) != (n, 2):
+        raise ValueError(f"frep_out must have shape ({n}, 2), got {tuple(frep_out.shape)}")
+    if not (z_out.is_cuda and z_out.dtype == torch.float64) or z_out.numel() < 1:
+        raise ValueError("z_out must be a float64 CUDA tensor with at least one element")
+    if frep_out.device != Yc.device or z_out.device != Yc.device:
+        raise ValueError("Y, frep_out and z_out must be on the same device")
+    with torch.cuda.device(Yc.device):
+        s = stream if stream is not None else torch.cuda.current_stream(Yc.device)
+        handle = ctypes.c_void_p(getattr(s, "cuda_stream", s))
+        st = lib().tsgne_repulsion_noalloc(n, ctypes.c_void_p(Yc.data_ptr()), ctypes.c_void_p(frep_out.data_ptr()),
+                                           ctypes.c_void_p(z_out.data_ptr()), handle)
     if st != 0:
-        why = (f"n = {n} exceeds the no-allocation maximum of {NOALLOC_MAX_N} points" if n > NOALLOC_MAX_N
-               else "tsgne_repulsion_noalloc failed")
-        raise TsgneError(st, why)
+        raise TsgneError(st, lib().tsgne_last_error(None).decode() or "tsgne_repulsion_noalloc failed")
     return frep_out, z_out
 
 

@@ -554,7 +554,7 @@ void tsgne_destroy(tsgne_ctx* ctx) {
   delete ctx;
 }
 
-const char* tsgne_last_error(const tsgne_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+const char* tsgne_last_error(const tsgne_ctx* ctx) { return ctx ? ctx->err.c_str() : last_msg().c_str(); }
 
 tsgne_status tsgne_build_P(tsgne_ctx* ctx, int32_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* X,
                            int32_t d, int32_t ptr_kind) {

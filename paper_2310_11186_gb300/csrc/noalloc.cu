@@ -16,11 +16,20 @@
 //   - the first call on each device looks up the array's device address
 //     (cudaGetSymbolAddress, with that device current); make that first call
 //     before any stream capture;
+//   - Y, frep_out and z_out must be 8-byte aligned (Y and frep_out are read
+//     and written as float pairs, z_out as a double); a misaligned pointer
+//     is rejected with TSGNE_ERR_INVALID_ARG before any work is enqueued;
+//   - the device address of the array is cached per device ordinal for the
+//     life of the process; it does not survive cudaDeviceReset (or any other
+//     teardown of the device's primary context), after which this entry
+//     point must not be called again in that process;
 //   - all calls share the one array and it keeps the last call's contents:
 //     every call clears the counters it needs and overwrites every region it
 //     reads, so consecutive calls on one stream are independent, but calls
 //     that overlap on the GPU (two streams, or two threads) race on it.
+#include <cstdint>
 #include <mutex>
+#include <string>
 
 #include "tsgne_internal.cuh"
 
@@ -88,7 +97,12 @@ tsgne_status repulsion_noalloc(int32_t n, const float* Y, float* frep_out, doubl
     return TSGNE_ERR_INVALID_ARG;
   }
   if (n > kNoAllocMaxN) {
-    last_msg() = "n exceeds TSGNE_NOALLOC_MAX_N (65536 points)";
+    last_msg() = "n = " + std::to_string(n) + " exceeds the no-allocation maximum of TSGNE_NOALLOC_MAX_N = " +
+                 std::to_string(kNoAllocMaxN) + " points";
+    return TSGNE_ERR_INVALID_ARG;
+  }
+  if (((uintptr_t)Y | (uintptr_t)frep_out | (uintptr_t)z_out) & 7u) {
+    last_msg() = "Y, frep_out and z_out must be 8-byte aligned";
     return TSGNE_ERR_INVALID_ARG;
   }
   int dev = 0, sms = 1;
@@ -127,5 +141,6 @@ tsgne_status repulsion_noalloc(int32_t n, const float* Y, float* frep_out, doubl
 
 extern "C" tsgne_status tsgne_repulsion_noalloc(int32_t n, const float* Y, float* frep_out, double* z_out,
                                                 void* cuda_stream) {
+  tsgne::last_msg().clear();
   return tsgne::repulsion_noalloc(n, Y, frep_out, z_out, static_cast<cudaStream_t>(cuda_stream));
 }

@@ -151,9 +151,12 @@ extern "C" tsgne_status tsgne_shortest_path_embedding(int32_t n, const int64_t* 
                                                       const int32_t* targets, int32_t d, int32_t l0, float* X_out,
                                                       int32_t ptr_kind, void* cuda_stream) {
   using namespace tsgne;
+  last_msg().clear();
   if (n < 1 || d < 1 || d > 1024 || !row_ptr || !targets || !X_out ||
-      !(ptr_kind == TSGNE_PTR_HOST || ptr_kind == TSGNE_PTR_DEVICE))
+      !(ptr_kind == TSGNE_PTR_HOST || ptr_kind == TSGNE_PTR_DEVICE)) {
+    last_msg() = "need n >= 1, 1 <= d <= 1024, non-NULL row_ptr, targets and X_out, and a valid ptr_kind";
     return TSGNE_ERR_INVALID_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const cudaMemcpyKind kin = ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   int64_t first = 0, m = 0;

@@ -48,7 +48,7 @@ def test_host_only_calls(built):
     assert c.perplexity == 30.0 and c.ee_iters == 250 and c.early_exag == 12.0
     assert abs(c.momentum0 - 0.5) < 1e-7 and abs(c.momentum1 - 0.8) < 1e-7
     assert pkg.tsgne_status_string(2) == "TSGNE_ERR_BAD_CSR"
-    assert pkg.tsgne_last_error(None) == ""
+    assert isinstance(pkg.tsgne_last_error(None), str)
     with pytest.raises(pkg.TsgneError) as ei:
         pkg.tsgne_create(pkg.tsgne_config_default(perplexity=1.0))
     assert ei.value.status == 1
@@ -63,6 +63,25 @@ def test_invalid_configurations_are_rejected_before_device_work(built, bad):
     with pytest.raises(pkg.TsgneError) as ei:
         pkg.tsgne_create(pkg.tsgne_config_default(**bad))
     assert ei.value.status == 1  # INVALID_ARG, no CUDA call needed to decide it
+
+
+def test_noalloc_rejects_bad_arguments_before_device_work(built):
+    """tsgne_repulsion_noalloc checks sizes and pointer alignment before it
+    touches the GPU (these pointers are never dereferenced), and says why
+    through tsgne_last_error(NULL)."""
+    lib = pkg.lib()
+    f = lib.tsgne_repulsion_noalloc
+    vp = ctypes.c_void_p
+    # Y misaligned by 4 bytes (a float pair at an odd float offset)
+    assert f(100, vp(0x100004), vp(0x200000), vp(0x300000), None) == 1
+    assert "aligned" in lib.tsgne_last_error(None).decode()
+    assert f(100, vp(0x100000), vp(0x200002), vp(0x300000), None) == 1
+    assert f(100, vp(0x100000), vp(0x200000), vp(0x300004), None) == 1
+    # too many points, then too few
+    assert f(pkg.NOALLOC_MAX_N + 1, vp(0x100000), vp(0x200000), vp(0x300000), None) == 1
+    assert "maximum" in lib.tsgne_last_error(None).decode()
+    assert f(1, vp(0x100000), vp(0x200000), vp(0x300000), None) == 1
+    assert f(100, None, vp(0x200000), vp(0x300000), None) == 1
 
 
 def test_missing_library_fails_loudly(monkeypatch):
