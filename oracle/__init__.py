@@ -82,6 +82,10 @@ def _load():
             lib.tsgo_bfs_knn.restype = ctypes.c_int
             lib.tsgo_repulsion_tree.argtypes = [_i32, _p, _dbl, _i32, _p, _p, _p]
             lib.tsgo_repulsion_tree.restype = ctypes.c_int
+            lib.tsgo_repulsion_tree_bounds.argtypes = [_i32, _p, _dbl, _i32, _p, _p, _p, _p]
+            lib.tsgo_repulsion_tree_bounds.restype = ctypes.c_int
+            lib.tsgo_tree_mutation.argtypes = [_i32]
+            lib.tsgo_tree_mutation.restype = None
             lib.tsgo_gradient_tree.argtypes = [_i32, _p, _p, _p, _p, _dbl, _dbl, _i32, _p, _p]
             lib.tsgo_gradient_tree.restype = ctypes.c_int
             lib.tsgo_random_walk_counts.argtypes = [_i32, _p, _p, _p, _i32, _i32, _i32, ctypes.c_uint64, _p, _p, _p]
@@ -220,6 +224,28 @@ def repulsion_tree(Y, theta, bucket=4):
     _check(_load().tsgo_repulsion_tree(n, _ptr(Yd), float(theta), int(bucket), _ptr(F), _ptr(zr), ctypes.byref(z)),
            "repulsion_tree")
     return F, zr, z.value
+
+
+def repulsion_tree_bounds(Y, theta, bucket=4):
+    """repulsion_tree plus per-row error bounds against the exact sums:
+    returns (F_rep, zrow, Z, bZ, bF) where bZ and bF are n x 2 arrays
+    (centre-rounding part, second-order remainder part) bounding
+    |zrow_i - exact zrow_i| and the Euclidean |F_i - exact F_i|."""
+    Yd = _c(Y, np.float64)
+    n = Yd.shape[0]
+    F = np.zeros((n, 2))
+    zr = np.zeros(n)
+    b = np.zeros((n, 4))
+    z = ctypes.c_double(0.0)
+    _check(_load().tsgo_repulsion_tree_bounds(n, _ptr(Yd), float(theta), int(bucket), _ptr(F), _ptr(zr),
+                                              ctypes.byref(z), _ptr(b)), "repulsion_tree_bounds")
+    return F, zr, z.value, b[:, 0:2].copy(), b[:, 2:4].copy()
+
+
+def tree_mutation(which: int) -> None:
+    """Plants one of the tree code's numbered mistakes (0 = none); for the
+    tests that show the bound check catches them."""
+    _load().tsgo_tree_mutation(int(which))
 
 
 def gradient_tree(n, rp, col, P, Y, alpha=1.0, theta=0.5, bucket=4):

@@ -31,6 +31,10 @@
  *   tsgo_repulsion_tree tree-code approximation of the repulsive sums and Z
  *                       (an extension; the paper sums Eq. 4 exactly); its
  *                       steps are listed above the function
+ *   tsgo_repulsion_tree_bounds  tsgo_repulsion_tree plus, per row, a bound on
+ *                       its distance from the exact sums (second-order
+ *                       remainder of the monopole expansion, derived above
+ *                       the function)
  *   tsgo_gradient_tree  tsgo_gradient with the tree code's F^r and Z
  *   tsgo_gradient_rows  tsgo_gradient for listed rows and a given Z (sampled
  *                       checks at sizes where Z is summed separately)
@@ -507,6 +511,11 @@ int tsgo_bfs_knn(int32_t n, const int64_t* rp, const int32_t* col, int32_t k, in
 typedef struct {
   int32_t first, last, left, right; /* left/right: node ids, -1 for a leaf */
   float sx, sy, x0, y0, x1, y1, cx, cy, r2;
+  /* For the error bound only (FP64, from the node's points; no effect on
+   * the sums): s2 = sum_j |c - y_j|^2 about the FP32 centre c; cerr = |c -
+   * mean|, the rounding of the FP32 centre; a = largest distance from c to a
+   * corner of the box, which bounds |c - y_j|. */
+  double s2, cerr, a;
 } tsgo_tnode;
 
 typedef struct {
@@ -540,6 +549,32 @@ static int aug_bit(uint64_t key, uint32_t pos, int b) {
   return b >= 32 ? (int)((key >> (b - 32)) & 1u) : (int)((pos >> b) & 1u);
 }
 
+/* Moments of an internal node's points about its FP32 centre (bound only). */
+static void node_moments(tsgo_tnode* t, const float* xs, const float* ys) {
+  double mx = 0.0, my = 0.0, s2 = 0.0;
+  const double m = (double)(t->last - t->first + 1);
+  for (int32_t k = t->first; k <= t->last; ++k) {
+    mx += xs[k];
+    my += ys[k];
+  }
+  mx /= m;
+  my /= m;
+  for (int32_t k = t->first; k <= t->last; ++k) {
+    const double dx = (double)t->cx - xs[k], dy = (double)t->cy - ys[k];
+    s2 += dx * dx + dy * dy;
+  }
+  t->s2 = s2;
+  t->cerr = hypot((double)t->cx - mx, (double)t->cy - my);
+  double a2 = 0.0;
+  const float bx[2] = {t->x0, t->x1}, by[2] = {t->y0, t->y1};
+  for (int p = 0; p < 2; ++p)
+    for (int q = 0; q < 2; ++q) {
+      const double dx = (double)t->cx - bx[p], dy = (double)t->cy - by[q];
+      if (dx * dx + dy * dy > a2) a2 = dx * dx + dy * dy;
+    }
+  t->a = sqrt(a2);
+}
+
 /* Builds the subtree over sorted positions [f, l]; returns its node id. */
 static int32_t tree_build(const uint64_t* keys, const float* xs, const float* ys, int32_t f, int32_t l,
                           tsgo_tnode* nodes, int32_t* count) {
@@ -552,6 +587,7 @@ static int32_t tree_build(const uint64_t* keys, const float* xs, const float* ys
     t->sx = t->x0 = t->x1 = t->cx = xs[f];
     t->sy = t->y0 = t->y1 = t->cy = ys[f];
     t->r2 = 0.0f;
+    t->s2 = t->cerr = t->a = 0.0;
     return id;
   }
   int bit = 95;
@@ -576,7 +612,63 @@ static int32_t tree_build(const uint64_t* keys, const float* xs, const float* ys
   t->cy = t->sy / cnt;
   float r = fmaxf(t->x1 - t->x0, t->y1 - t->y0);
   t->r2 = r * r;
+  node_moments(t, xs, ys);
   return id;
+}
+
+/*
+ * Error bound of one accepted node (used by tsgo_repulsion_tree_bounds).
+ *
+ * A node of m points y_j with centre c stands for the m exact terms
+ * f(y_i - y_j) by m f(y_i - c), for f = w (the Z row) and f = w^2 u (the
+ * force), w(u) = 1 / (1 + |u|^2).  Write y_i - y_j = u + delta_j with
+ * u = y_i - c and delta_j = c - y_j.  Taylor's theorem with the integral
+ * remainder along the segment from u to u + delta_j gives
+ *   f(u + delta_j) = f(u) + Df(u)[delta_j] + R_j,
+ *   |R_j| <= 1/2 |delta_j|^2 sup_{t in [0,1]} ||D^2 f(u + t delta_j)||.
+ * Summed over the node, the first-order terms add up to m Df(u)[c - mean],
+ * which vanishes when c is the mean of the points (the node's centre is
+ * their coordinate sum over the count, so only its FP32 rounding remains),
+ * and every point of the segment lies at distance >= rho = max(|u| - a, 0)
+ * from the origin, a >= |delta_j| being the largest distance from c to a
+ * corner of the node's box.  Hence
+ *   |sum_j f(y_i - y_j) - m f(u)| <= m ||Df(u)|| |c - mean|
+ *                                    + 1/2 (sum_j |delta_j|^2) G_f(rho),
+ * with G_f(rho) = sup_{|x| >= rho} ||D^2 f(x)|| (operator norm on unit
+ * directions).  The derivatives, with s = |x|^2:
+ *   w:      Dw = -2 w^2 x, so ||Dw|| = 2 |x| w^2;
+ *           D^2 w = -2 w^2 I + 8 w^3 x x^T, eigenvalues -2 w^2 and
+ *           2 w^3 (3 s - 1), so ||D^2 w|| = 2 w^2 for s <= 1 and
+ *           2 w^3 (3 s - 1) for s > 1 -- non-increasing in |x|, so G_w(rho)
+ *           is its value at rho;
+ *   w^2 x:  D[h] = w^2 h - 4 w^3 (x.h) x, eigenvalues w^2 and w^2 (1 - 3 s) /
+ *           (1 + s), so ||D|| = w^2 max(1, |1 - 3 s| / (1 + s));
+ *           D^2[h, h] = 24 w^4 (x.h)^2 x - 4 w^3 x - 8 w^3 (x.h) h for |h| = 1,
+ *           of norm <= 12 w^3 |x| + 24 w^4 |x|^3 = (12 t + 36 t^3) / (1 + t^2)^4
+ *           at t = |x|; this rises up to t = 1/sqrt(3) and falls after it, so
+ *           G(rho) is its value at max(rho, 1/sqrt(3)).
+ * If the node holds point i itself, the monopole also stands for the j = i
+ * term that the exact sums leave out: w(0) = 1 in the Z row, 0 in the force.
+ * The bound is returned in two parts per row: the centre-rounding (first
+ * order) part and the remainder (second order) part.
+ */
+/* Planted mistakes for the tests that show the bound check catches them
+ * (0 = none, the default): 1 = a node's count taken one short, 2 = the
+ * node's box centre used in place of its centre of mass, 3 = the force of an
+ * accepted node with the wrong sign, 4 = a point paired with itself in the
+ * exact sums of an opened bucket.  Test infrastructure only. */
+static int g_tree_mutation = 0;
+void tsgo_tree_mutation(int32_t which) { g_tree_mutation = which; }
+
+static double bound_w_hess(double rho) {
+  const double s = rho * rho, w = 1.0 / (1.0 + s);
+  return s <= 1.0 ? 2.0 * w * w : 2.0 * w * w * w * (3.0 * s - 1.0);
+}
+
+static double bound_f_hess(double rho) {
+  double t = rho > 0.57735026918962576 ? rho : 0.57735026918962576;
+  const double q = 1.0 + t * t;
+  return (12.0 * t + 36.0 * t * t * t) / (q * q * q * q);
 }
 
 typedef struct {
@@ -588,7 +680,22 @@ typedef struct {
   int32_t bucket;
   double* F;    /* per sorted position */
   double* zrow; /* per sorted position */
+  double* bnd;  /* NULL, or per sorted position: Z first / second order, F first / second order */
 } tsgo_walk;
+
+static void node_bound(const tsgo_walk* w, const tsgo_tnode* t, int32_t i) {
+  const double m = (double)(t->last - t->first + 1);
+  const double ux = (double)w->xs[i] - (double)t->cx, uy = (double)w->ys[i] - (double)t->cy;
+  const double s = ux * ux + uy * uy, D = sqrt(s), k = 1.0 / (1.0 + s);
+  double rho = D - t->a;
+  if (rho < 0.0) rho = 0.0;
+  double* b = w->bnd + 4 * (size_t)i;
+  const double lin_f = fabs(1.0 - 3.0 * s) / (1.0 + s);
+  b[0] += m * 2.0 * D * k * k * t->cerr;
+  b[1] += 0.5 * t->s2 * bound_w_hess(rho) + ((i >= t->first && i <= t->last) ? 1.0 : 0.0);
+  b[2] += m * k * k * (lin_f > 1.0 ? lin_f : 1.0) * t->cerr;
+  b[3] += 0.5 * t->s2 * bound_f_hess(rho);
+}
 
 static void exact_pairs(const tsgo_walk* w, int32_t j) {
   for (int32_t i = w->g0; i < w->g1; ++i) {
@@ -613,18 +720,29 @@ static void tree_walk(const tsgo_walk* w, int32_t id) {
   float d2 = dx * dx + dy * dy;
   if (t->r2 < w->theta2 * d2) {
     double c = (double)(t->last - t->first + 1);
+    double mx = t->cx, my = t->cy, sg = 1.0;
+    if (g_tree_mutation == 1) c -= 1.0;
+    if (g_tree_mutation == 2) {
+      mx = 0.5 * ((double)t->x0 + (double)t->x1);
+      my = 0.5 * ((double)t->y0 + (double)t->y1);
+    }
+    if (g_tree_mutation == 3) sg = -1.0;
     for (int32_t i = w->g0; i < w->g1; ++i) {
-      double ex = (double)w->xs[i] - (double)t->cx;
-      double ey = (double)w->ys[i] - (double)t->cy;
+      if (w->bnd) node_bound(w, t, i);
+      double ex = (double)w->xs[i] - mx;
+      double ey = (double)w->ys[i] - my;
       double k = 1.0 / (1.0 + ex * ex + ey * ey);
       w->zrow[i] += c * k;
-      w->F[2 * i] += c * k * k * ex;
-      w->F[2 * i + 1] += c * k * k * ey;
+      w->F[2 * i] += sg * c * k * k * ex;
+      w->F[2 * i + 1] += sg * c * k * k * ey;
     }
     return;
   }
   if (t->last - t->first + 1 <= w->bucket) {
-    for (int32_t j = t->first; j <= t->last; ++j) exact_pairs(w, j);
+    for (int32_t j = t->first; j <= t->last; ++j) {
+      exact_pairs(w, j);
+      if (g_tree_mutation == 4 && j >= w->g0 && j < w->g1) w->zrow[j] += 1.0;
+    }
     return;
   }
   tree_walk(w, t->left);
@@ -647,10 +765,10 @@ static void collect_groups(const tsgo_tnode* nodes, int32_t id, int32_t* gfirst,
 /*
  * Y: n x 2 layout (FP32 values carried in doubles); theta >= 0; bucket >= 1.
  * Frep (n x 2) and zrow (n) come back in the input order; returns Z through
- * *Z_out.
+ * *Z_out.  bnd: NULL, or n x 4 (input order) for tsgo_repulsion_tree_bounds.
  */
-int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket, double* Frep, double* zrow,
-                        double* Z_out) {
+static int tree_pass(int32_t n, const double* Y, double theta, int32_t bucket, double* Frep, double* zrow,
+                     double* Z_out, double* bnd) {
   if (n < 1 || !(theta >= 0.0) || bucket < 1) return TSGO_EINVAL;
   float* xs = (float*)malloc(sizeof(float) * (size_t)n);
   float* ys = (float*)malloc(sizeof(float) * (size_t)n);
@@ -659,10 +777,11 @@ int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket
   tsgo_tnode* nodes = (tsgo_tnode*)malloc(sizeof(tsgo_tnode) * (size_t)(2 * n - 1));
   double* F = (double*)calloc(2 * (size_t)n, sizeof(double));
   double* zr = (double*)calloc((size_t)n, sizeof(double));
+  double* bs = bnd ? (double*)calloc(4 * (size_t)n, sizeof(double)) : NULL;
   int32_t* gfirst = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
   int32_t* glast = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-  if (!xs || !ys || !kv || !keys || !nodes || !F || !zr || !gfirst || !glast) {
-    free(xs); free(ys); free(kv); free(keys); free(nodes); free(F); free(zr); free(gfirst); free(glast);
+  if (!xs || !ys || !kv || !keys || !nodes || !F || !zr || !gfirst || !glast || (bnd && !bs)) {
+    free(xs); free(ys); free(kv); free(keys); free(nodes); free(F); free(zr); free(gfirst); free(glast); free(bs);
     return TSGO_ENOMEM;
   }
   /* 1-2: bounding square and keys */
@@ -701,6 +820,7 @@ int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket
   w.bucket = bucket;
   w.F = F;
   w.zrow = zr;
+  w.bnd = bs;
   int32_t ng = 0;
   collect_groups(nodes, root, gfirst, glast, &ng);
   for (int32_t g = 0; g < ng; ++g) {
@@ -723,11 +843,31 @@ int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket
     Frep[2 * i] = F[2 * k];
     Frep[2 * i + 1] = F[2 * k + 1];
     if (zrow) zrow[i] = zr[k];
+    if (bnd)
+      for (int q = 0; q < 4; ++q) bnd[4 * (size_t)i + q] = bs[4 * (size_t)k + q];
     Z += zr[k];
   }
   if (Z_out) *Z_out = Z;
-  free(xs); free(ys); free(kv); free(keys); free(nodes); free(F); free(zr); free(gfirst); free(glast);
+  free(xs); free(ys); free(kv); free(keys); free(nodes); free(F); free(zr); free(gfirst); free(glast); free(bs);
   return TSGO_OK;
+}
+
+int tsgo_repulsion_tree(int32_t n, const double* Y, double theta, int32_t bucket, double* Frep, double* zrow,
+                        double* Z_out) {
+  return tree_pass(n, Y, theta, bucket, Frep, zrow, Z_out, NULL);
+}
+
+/*
+ * tsgo_repulsion_tree with, per row i (input order), bnd[4 i .. 4 i + 3] =
+ * bounds on |zrow_i - exact zrow_i| (centre-rounding part, remainder part)
+ * and on |F_i - exact F_i| (Euclidean norm; the same two parts), summed over
+ * the nodes the walk accepted for i's group (derivation above node_bound).
+ * Rows whose group accepted no node are exact: their bounds are 0.
+ */
+int tsgo_repulsion_tree_bounds(int32_t n, const double* Y, double theta, int32_t bucket, double* Frep,
+                               double* zrow, double* Z_out, double* bnd) {
+  if (!bnd) return TSGO_EINVAL;
+  return tree_pass(n, Y, theta, bucket, Frep, zrow, Z_out, bnd);
 }
 
 /*
