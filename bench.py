@@ -149,6 +149,28 @@ def traffic_per_launch():
     return float(m_b.group(1)) if repulsion_source_sha() == m_sha.group(1) else None
 
 
+ATTRACT_SRCS = [os.path.join(ROOT, "paper_2310_11186_gb300", "csrc", f)
+                for f in ("iterate.cu", "row_update.cuh", "storage.cuh")]
+ATTRACT_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "attract_rmat21.md")
+
+
+def attraction_traffic():
+    """DRAM bytes per attraction+update launch at R-MAT 2^21 from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    try:
+        txt = open(ATTRACT_TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_b:
+        return None
+    h = hashlib.sha256()
+    for f in ATTRACT_SRCS:
+        h.update(open(f, "rb").read())
+    return float(m_b.group(1)) if h.hexdigest() == m_sha.group(1) else None
+
+
 def pipe_utilisation():
     """FMA / MUFU pipe activity of the repulsion kernel from the committed ncu
     summary (--set full on the 100K case), if it was taken on the current
@@ -372,7 +394,7 @@ def run_ours(args):
         batched = bench_batched(args, pkg)
     if rank == 0 and not args.no_serving:
         serving = bench_serving(args, pkg)
-    rmat_res = bench_rmat(args, pkg) if (rank == 0 and args.rmat) else None
+    rmat_res = bench_rmat(args, pkg) if (rank == 0 and not args.no_rmat) else None
     tree_res = bench_tree(args, pkg, g, X, Y0, Yt) if (rank == 0 and not args.no_tree) else None
     rw_res = bench_random_walk(args, pkg, g, X) if (rank == 0 and not args.no_tree) else None
     scale_res = bench_scale(args, pkg) if (rank == 0 and args.scale) else None
@@ -418,6 +440,7 @@ def run_ours(args):
             "ms_per_launch": rep_ms,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (unit counts and max clock)",
         },
+        "roofline_hbm": roofline_hbm(rmat_res, n, nnz_P, upd_ms),
         "kernels_ms_per_step": {"repulsion": rep_ms, "attract_update": upd_ms},
         "cpu_baseline": cpu,
         "e2e": {"value": ws * e2e_iters / e2e_s, "unit": UNIT,
@@ -445,6 +468,27 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def roofline_hbm(rmat_res, n, nnz, att_ms):
+    """The attraction+update kernel (S3+S5, HBM-bound) against the measured
+    HBM copy bandwidth: at R-MAT 2^21 (P and its structure larger than L2:
+    the measurement) when that section ran, with the 300K benchmark's figure
+    beside it for context (its 22 MB mostly stay in L2)."""
+    peak, src = hbm_peak()
+    b300 = attraction_bytes(n, nnz, 0)
+    ctx = {"bytes_per_launch": b300, "ms_per_launch": att_ms,
+           "achieved": b300 / (att_ms * 1e-3) / 1e9 if att_ms > 0 else None}
+    if rmat_res is None or "fp32" not in rmat_res:
+        return {"bound": "hbm", "kernel": "attract_update (S3+S5)", "achieved": ctx["achieved"], "peak": peak,
+                "unit": "GB/s", "frac": (ctx["achieved"] / peak) if ctx["achieved"] else None, "traffic": None,
+                "peak_source": src, "workload": "zipf300k (R-MAT section skipped)"}
+    r = rmat_res["fp32"]["attraction_roofline"]
+    return {"bound": "hbm", "kernel": "attract_update (S3+S5)", "achieved": r["achieved"], "peak": peak,
+            "unit": "GB/s", "frac": r["achieved"] / peak, "traffic": attraction_traffic(),
+            "peak_source": src, "workload": "R-MAT 2^21 nodes / 2^24 edges, FP32",
+            "bytes_per_launch": r["bytes_per_launch"], "ms_per_launch": r["ms_per_launch"],
+            "zipf300k_context": ctx}
 
 
 def bench_config0(args, pkg, log_fn=log):
@@ -521,14 +565,20 @@ def bench_tree(args, pkg, g, X, Y0, Yt, log_fn=log):
         ev[1].synchronize()
         ms += ev[0].elapsed_time(ev[1])
     kt = lay.kernel_times(reset=True)
-    # gradient at the exact path's timed layout, tree vs exact
-    lay.set_state(Yt)
+    # gradient, tree vs exact, at a spread layout (block centres N(0, 30^2 I),
+    # the scale of a converged layout) and at the exact path's timed layout
+    Ysp = synth.spread_layout(g.labels, scale=30.0, seed=args.seed + 1)
+    lay.set_state(Ysp)
     Gt, Zt = lay.gradient(1.0)
+    lay.set_state(Yt)
+    Gt2, Zt2 = lay.gradient(1.0)
     lay.close()
     with pkg.Layout() as ex:
         ex.build_P(g.row_ptr, g.col, X)
-        ex.set_state(Yt)
+        ex.set_state(Ysp)
         Ge, Ze = ex.gradient(1.0)
+        ex.set_state(Yt)
+        Ge2, Ze2 = ex.gradient(1.0)
         # whole layout with the tree code, then scored by the exact KL
         with pkg.Layout(repulsion=1, theta=theta) as lt:
             torch.cuda.synchronize()
@@ -552,10 +602,15 @@ def bench_tree(args, pkg, g, X, Y0, Yt, log_fn=log):
                                 "attract_update": per("attract_update")},
         "grad_rel_l2_vs_exact": float(np.linalg.norm(Gt - Ge) / np.linalg.norm(Ge)),
         "Z_rel_vs_exact": abs(Zt - Ze) / Ze,
+        "error_layout": "spread layout: block centres N(0, 30^2 I) plus N(0, I) per point",
+        "at_timed_layout": {"grad_rel_l2_vs_exact": float(np.linalg.norm(Gt2 - Ge2) / np.linalg.norm(Ge2)),
+                            "Z_rel_vs_exact": abs(Zt2 - Ze2) / Ze2,
+                            "layout": f"the exact path's layout after {args.warmup + args.steps} iterations"},
         "layout_s": wall,
         "layout_iters": args.e2e_iters,
         "kl_exact_of_tree_layout": kl_tree,
-        "note": "approximate repulsion (not the paper's exact Eq. 4 sum); parity is against the oracle's tree code",
+        "note": ("approximate repulsion (not the paper's exact Eq. 4 sum); parity: the exact sums under the "
+                 "derived per-row error bound of the monopole approximation"),
     }
     log_fn(f"[bench] tree theta={theta}: {out['iters_per_s']:.1f} it/s, build {out['kernels_ms_per_step']['tree_build']:.3f} ms, "
            f"walk {out['kernels_ms_per_step']['tree_walk']:.3f} ms, grad err {out['grad_rel_l2_vs_exact']:.2e}")
@@ -716,12 +771,30 @@ def hbm_peak():
         return 6800.0, "fallback 6.8 TB/s"
 
 
+def attraction_bytes(n, nnz, prec):
+    """Algorithmic bytes of one attraction+update launch: row_ptr, col and P
+    once; per point F^r, update and gains read, Y_next, update and gains
+    written, and Y_i read (FP32: 8 B; BF16: the 4-B shadow for the forces
+    plus the 8-B master for the update, and a 4-B shadow write).  Neighbour
+    gathers of Y are L2 hits after the first read (the layout is 16.8 MB in
+    FP32 at 2^21 points, 8.4 MB in BF16)."""
+    if prec == 0:
+        return 8 * (n + 1) + 8 * nnz + 7 * 8 * n
+    return 8 * (n + 1) + 6 * nnz + 8 * 8 * n
+
+
 def bench_rmat(args, pkg, log_fn=log):
-    """R-MAT 2^21 nodes / 2^24 edges in both storage precisions (FP32; BF16
-    P and Y reads with FP32 arithmetic and FP64 Z) and with the tree-code
-    repulsion: the attraction+update kernel against the HBM roofline, and
-    each arm's gradient / KL error against the exact FP64 oracle on a
-    20K-node induced subgraph (BFS ball from the highest-degree node)."""
+    """Config 4, R-MAT 2^21 nodes / 2^24 edges.
+
+    Timing: the attraction+update kernel (S3+S5) against the HBM roofline in
+    both storage precisions (FP32; BF16 P and Y reads with FP32 arithmetic),
+    over --rmat-steps iterations whose repulsion is the tree code (the
+    attraction kernel is the same whichever repulsion runs, and tree
+    iterations take milliseconds instead of the exact pass's 0.7 s); the
+    exact all-pairs repulsion pass is timed separately over --rmat-exact-steps
+    iterations.  Error: FP32, BF16 and tree-code arms against the exact FP64
+    oracle on the 20K-node induced subgraph (BFS ball from the highest-degree
+    node): gradient relative L2, KL and Z."""
     import torch
     import oracle
 
@@ -732,30 +805,20 @@ def bench_rmat(args, pkg, log_fn=log):
            f"({time.perf_counter() - t0:.1f}s)")
     peak, src = hbm_peak()
     flush = torch.empty(320 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
-    nodes, sub = synth.induced_bfs_ball(g, 20_000)
-    Xs = X[nodes]
-    Ys = synth.spread_layout(sub.labels, scale=25.0, seed=args.seed)
-    orp, ocol, oP = oracle.build_P(sub.n, sub.row_ptr, sub.col, Xs, 30.0)
-    oG, oZ = oracle.gradient(sub.n, orp, ocol, oP, Ys.astype(np.float64), 1.0)
-    okl, _ = oracle.kl(sub.n, orp, ocol, oP, Ys.astype(np.float64))
     out = {
         "workload": f"R-MAT scale {scale} ({1 << scale} nodes), 2^{scale + 3} distinct undirected edges, a=0.57 "
                     f"b=c=0.19, 64-d embedding of 64 recursion communities, perplexity 30",
         "l2": "flushed (320 MB write) before every step",
-        "oracle_subgraph_nodes": int(sub.n),
     }
-    arms = ((0, 0, "fp32"), (1, 0, "bf16"), (0, 1, "fp32_tree"))
-    if args.rmat_arms:
-        keep = set(args.rmat_arms.split(","))
-        arms = tuple(a for a in arms if a[2] in keep)
-    for prec, rep, name in arms:
-        lay = pkg.Layout(profile=1, precision=prec, repulsion=rep, theta=args.tree_theta)
+    # ---- attraction roofline, both precisions (tree-code iterations)
+    for prec, name in ((0, "fp32"), (1, "bf16")):
+        lay = pkg.Layout(profile=1, precision=prec, repulsion=1, theta=args.tree_theta)
         tb = time.perf_counter()
         lay.build_P(g.row_ptr, g.col, X)
         build_ms = (time.perf_counter() - tb) * 1e3
         n, nnz = lay.sizes()
         lay.init_Y(synth.y_init(n, seed=args.seed))
-        for _ in range(2):
+        for _ in range(3):
             lay.step()
         lay.sync()
         lay.kernel_times(reset=True)
@@ -769,39 +832,56 @@ def bench_rmat(args, pkg, log_fn=log):
         lay.close()
         att_ms = kt["attract_update"][0] / kt["attract_update"][1]
         hub_ms = kt["attract_hubs"][0] / max(kt["attract_hubs"][1], 1)
-        rep_ms = kt["repulsion"][0] / kt["repulsion"][1]
-        if rep:
-            rep_ms += kt["tree_build"][0] / kt["tree_build"][1]
-        # algorithmic bytes of one attraction+update launch: row_ptr, col and
-        # P once; per point F^r, update and gains read, Y_next, update and
-        # gains written, and Y_i read (FP32: 8 B; BF16: the 4-B shadow for
-        # the forces plus the 8-B master for the update, and a 4-B shadow
-        # write).  Neighbour gathers of Y hit L2 (16.8 MB FP32, 8.4 MB BF16).
-        if prec == 0:
-            att_bytes = 8 * (n + 1) + 8 * nnz + 7 * 8 * n
-        else:
-            att_bytes = 8 * (n + 1) + 6 * nnz + 8 * 8 * n
+        att_bytes = attraction_bytes(n, nnz, prec)
         achieved = att_bytes / ((att_ms + hub_ms) * 1e-3) / 1e9
+        out[name] = {
+            "nnz_P": int(nnz),
+            "build_ms": build_ms,
+            "tree_repulsion_ms": (kt["tree_build"][0] / kt["tree_build"][1] + kt["repulsion"][0] / kt["repulsion"][1]),
+            "attraction_roofline": {"bound": "hbm", "kernel": "attract_update (S3+S5)", "achieved": achieved,
+                                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
+                                    "bytes_per_launch": att_bytes, "ms_per_launch": att_ms + hub_ms,
+                                    "launches_timed": int(kt["attract_update"][1]),
+                                    "ms_split": {"rows_and_update": att_ms, "hub_row_chunks": hub_ms}},
+            "clocks": clk.summary(),
+        }
+        log_fn(f"[bench] rmat {name}: attraction {att_ms + hub_ms:.3f} ms ({achieved:.0f} GB/s, "
+               f"{achieved / peak:.3f} of peak)")
+    # ---- the exact repulsion pass at this size (FP32)
+    if args.rmat_exact_steps > 0:
+        with pkg.Layout(profile=1) as lay:
+            lay.build_P(g.row_ptr, g.col, X)
+            lay.init_Y(synth.y_init(g.n, seed=args.seed))
+            lay.step()
+            lay.sync()
+            lay.kernel_times(reset=True)
+            for _ in range(args.rmat_exact_steps):
+                lay.step()
+            lay.sync()
+            kt = lay.kernel_times(reset=True)
+        rep_ms = kt["repulsion"][0] / kt["repulsion"][1]
+        fl = FLOPS_PER_UNORDERED_PAIR * g.n * (g.n - 1) / 2.0
+        out["fp32"]["exact_repulsion_ms"] = rep_ms
+        out["fp32"]["exact_repulsion_tflops"] = fl / (rep_ms * 1e-3) / 1e12
+        log_fn(f"[bench] rmat exact repulsion: {rep_ms:.1f} ms ({fl / (rep_ms * 1e-3) / 1e12:.1f} TFLOP/s)")
+    # ---- error arms on the 20K-node induced subgraph against the FP64 oracle
+    nodes, sub = synth.induced_bfs_ball(g, 20_000)
+    Xs = X[nodes]
+    Ys = synth.spread_layout(sub.labels, scale=25.0, seed=args.seed)
+    orp, ocol, oP = oracle.build_P(sub.n, sub.row_ptr, sub.col, Xs, 30.0)
+    oG, oZ = oracle.gradient(sub.n, orp, ocol, oP, Ys.astype(np.float64), 1.0)
+    okl, _ = oracle.kl(sub.n, orp, ocol, oP, Ys.astype(np.float64))
+    errs = {"oracle_subgraph_nodes": int(sub.n), "layout": "spread layout, block centres N(0, 25^2 I)"}
+    for prec, rep, name in ((0, 0, "fp32"), (1, 0, "bf16"), (0, 1, f"fp32_tree_theta{args.tree_theta}")):
         with pkg.Layout(precision=prec, repulsion=rep, theta=args.tree_theta) as l2:
             l2.build_P(sub.row_ptr, sub.col, Xs)
             l2.init_Y(Ys)
             G, Z = l2.gradient(1.0)
             kl = l2.kl()
-        out[name] = {
-            "nnz_P": int(nnz),
-            "build_ms": build_ms,
-            "repulsion_ms": rep_ms,
-            "repulsion": f"tree code, theta {args.tree_theta} (build + walk)" if rep else "exact all pairs",
-            "attraction_roofline": {"bound": "hbm", "kernel": "attract_update (S3+S5)", "achieved": achieved,
-                                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
-                                    "bytes_per_launch": att_bytes, "ms_per_launch": att_ms + hub_ms,
-                                    "ms_split": {"rows_and_update": att_ms, "hub_row_chunks": hub_ms}},
-            "clocks": clk.summary(),
-            "vs_fp64_oracle_20k": {"grad_rel_l2": float(np.linalg.norm(G - oG) / np.linalg.norm(oG)),
-                                   "kl_rel": abs(kl - okl) / okl, "Z_rel": abs(Z - oZ) / oZ},
-        }
-        log_fn(f"[bench] rmat {name}: attraction {att_ms + hub_ms:.3f} ms ({achieved:.0f} GB/s), "
-               f"repulsion {rep_ms:.1f} ms, grad err {out[name]['vs_fp64_oracle_20k']['grad_rel_l2']:.2e}")
+        errs[name] = {"grad_rel_l2": float(np.linalg.norm(G - oG) / np.linalg.norm(oG)),
+                      "kl_rel": abs(kl - okl) / okl, "Z_rel": abs(Z - oZ) / oZ}
+        log_fn(f"[bench] rmat error {name}: grad {errs[name]['grad_rel_l2']:.2e}, KL {errs[name]['kl_rel']:.2e}")
+    out["vs_fp64_oracle_20k"] = errs
     return out
 
 
@@ -829,10 +909,10 @@ def main():
     ap.add_argument("--tree-theta", type=float, default=0.5)
     ap.add_argument("--rw-walks", type=int, default=64)
     ap.add_argument("--rw-length", type=int, default=3)
-    ap.add_argument("--rmat", action="store_true", help="also run the R-MAT 2^21 workload (about a minute)")
-    ap.add_argument("--rmat-steps", type=int, default=5)
+    ap.add_argument("--no-rmat", action="store_true", help="skip the R-MAT 2^21 section (config 4)")
+    ap.add_argument("--rmat-steps", type=int, default=20)
+    ap.add_argument("--rmat-exact-steps", type=int, default=2)
     ap.add_argument("--rmat-scale", type=int, default=21)
-    ap.add_argument("--rmat-arms", default="", help="comma-separated subset of fp32,bf16,fp32_tree (default: all)")
     ap.add_argument("--only-rmat", action="store_true", help="run only the R-MAT section (profiling)")
     ap.add_argument("--only-tree", action="store_true", help="run only the tree-code section (profiling)")
     ap.add_argument("--scale", action="store_true", help="also lay out 3M- and 4M-node graphs with the tree code (a few minutes)")

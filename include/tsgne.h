@@ -228,7 +228,7 @@ tsgne_status tsgne_set_state(tsgne_ctx* ctx, const float* Y, const float* update
  * of each kernel class since the last reset, measured with CUDA events on
  * the context's stream.  Classes: 0 repulsion (the tree walk when
  * cfg.repulsion = 1), 1 attraction+update (hub-row chunks included), 2
- * gradient export, 3 KL, 4 build, 5 repulsion slot reduction, 6 hub-row
+ * gradient export, 3 KL, 4 build, 5 repulsion force conversion, 6 hub-row
  * attraction chunks of the gradient export, 7 tree build
  * (bounding box, keys, sort, tree, summaries).  ms and launches hold n
  * entries (n <= 8).
@@ -392,7 +392,7 @@ void tsgne_server_config_default(tsgne_server_config* cfg);
 
 /* Device bytes a resident layout of n points and nnz affinities holds in a
  * batch with the given tile (P, layout, optimiser state, initial layout,
- * per-tile repulsion slots, Z partials, an upper bound for the hub-row
+ * fixed-point repulsion accumulators, Z partials, an upper bound for the hub-row
  * chunk lists); -1 for invalid arguments.  Host
  * arithmetic only (no GPU needed). */
 int64_t tsgne_server_estimate_bytes(int32_t n, int64_t nnz, int32_t tile_warps);

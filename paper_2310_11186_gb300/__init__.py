@@ -64,7 +64,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_PKG, "lib", "libtsgne.so")
 
 PTR_HOST, PTR_DEVICE = 0, 1
-KERNEL_CLASSES = ("repulsion", "attract_update", "gradient", "kl", "build", "reduce_slots", "attract_hubs",
+KERNEL_CLASSES = ("repulsion", "attract_update", "gradient", "kl", "build", "fix_forces", "attract_hubs",
                   "tree_build")
 
 STATUS = {

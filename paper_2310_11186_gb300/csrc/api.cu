@@ -58,7 +58,7 @@ __global__ void k_cmp_i32(const int32_t* a, const int32_t* b, int64_t n, uint32_
     if (a[k] != b[k]) atomicOr(neq, 1u);
 }
 
-constexpr int kClasses = 8;  // repulsion, attraction+update, gradient, KL, build, slot reduction, hub rows, tree build
+constexpr int kClasses = 8;  // repulsion, attraction+update, gradient, KL, build, force conversion, hub rows, tree build
 
 struct ProfRec {
   int cls;
@@ -91,7 +91,8 @@ struct tsgne_ctx {
   DevBuf<float> P;
   DevBuf<float2> Y[2];
   int cur = 0;
-  DevBuf<float2> upd, gains, frep, fsum, grad;
+  DevBuf<float2> upd, gains, fsum, grad;
+  DevBuf<unsigned long long> facc;  // exact repulsion: fixed-point force accumulators (2 per point)
   // BF16 storage (cfg.precision = 1): P and a shadow of the layout, read by
   // every force kernel; the FP32 master layout is what the update advances
   bool bf16 = false;
@@ -258,14 +259,13 @@ tsgne_status enqueue_repulsion(tsgne_ctx* ctx, int advance) {
     return prof_end(ctx, &pr);
   }
   TS_TRY(prof_begin(ctx, 0, &pr));
-  TS_TRY(launch_repulsion_sym(ctx->shape, ctx->n, ctx->Yread(ctx->cur), ctx->bf16 ? 1 : 0, ctx->frep.get(),
+  TS_TRY(launch_repulsion_sym(ctx->shape, ctx->n, ctx->Yread(ctx->cur), ctx->bf16 ? 1 : 0, ctx->facc.get(),
                               ctx->zpart.get(), ctx->sched.get(), advance, c.early_exag, c.ee_iters, c.momentum0,
                               c.momentum1, ctx->stream));
   TS_TRY(prof_end(ctx, &pr));
   ProfRec pr2;
   TS_TRY(prof_begin(ctx, 5, &pr2));
-  TS_TRY(launch_reduce_slots(ctx->n, ctx->frep.get(), ctx->shape.chunks, ctx->shape.n_pad, ctx->fsum.get(),
-                             ctx->stream));
+  TS_TRY(launch_fix_forces(ctx->n, ctx->facc.get(), ctx->fsum.get(), ctx->stream));
   return prof_end(ctx, &pr2);
 }
 
@@ -391,13 +391,14 @@ tsgne_status alloc_layout(tsgne_ctx* ctx) {
   TS_TRY(ctx->fsum.alloc(np));
   ctx->use_tree = ctx->cfg.repulsion == 1;
   if (ctx->use_tree) {
-    ctx->frep = DevBuf<float2>();
+    ctx->facc = DevBuf<unsigned long long>();
     ctx->zpart = DevBuf<double>();
     TS_TRY(ctx->tree.alloc(ctx->n, ctx->sms, ctx->stream));
     ctx->tree.spin_budget = ctx->cfg.spin_budget_cycles;
   } else {
     ctx->tree = TreeBufs();
-    TS_TRY(ctx->frep.alloc(np * (size_t)ctx->shape.chunks));
+    TS_TRY(ctx->facc.alloc(2 * np));
+    TS_CUDA(cudaMemsetAsync(ctx->facc.get(), 0, 2 * np * sizeof(unsigned long long), ctx->stream));
     TS_TRY(ctx->zpart.alloc((size_t)ctx->shape.units));
   }
   TS_TRY(ctx->klpart.alloc(2 * (size_t)kl_partial_count(ctx->sms)));

@@ -10,7 +10,8 @@
 //   k_batch_finalize   one CTA per member: Z = fixed-order sum of its unit
 //                      partials minus n, schedule (alpha, mu) from its own
 //                      iteration counter t, t += 1
-//   k_batch_reduce     fixed-order sum of each point's partial-force slots
+//   k_batch_reduce     each point's fixed-point force accumulators to F^r,
+//                      cleared for the next iteration
 //   k_batch_hubs       (members with rows above 32 entries) one warp per
 //                      1024-entry chunk of such a row, over all members'
 //                      chunks: the single-layout path's chunk sums
@@ -47,14 +48,14 @@ struct GraphDesc {
   float2* Y[2];
   float2* upd;
   float2* gains;
-  float2* part;
+  unsigned long long* acc;  // fixed-point force accumulators, 2 per point (scale fix_scale(n))
   float2* fsum;
   double* zunit;
   Sched* sched;
   HeavyRows hv;  // rows above kHeavyDeg entries, in kHeavyChunk-entry chunks (as the single-layout path)
   int n, nt, n_pad, units;
   float eta;
-  int pad_;
+  float fscale, funscale;
 };
 
 struct BatchCtr {
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
     if (u >= U) break;
     const GraphDesc& d = descs[g];
     const float2* Y = d.Y[d.sched->t & 1];
-    const double zt = sym_unit<W>(Y, d.n, d.n_pad, d.part, a, b, sj, sacc);
+    const double zt = sym_unit<W>(Y, d.n, d.acc, d.fscale, a, b, sj, sacc);
     const double zb = block_sum_d(zt);
     if (tid == 0) d.zunit[u - unit_off[g]] = zb;
     __syncthreads();
@@ -134,13 +135,10 @@ __global__ void k_batch_reduce(const GraphDesc* __restrict__ descs, const int* _
     const int g = find_owner(row_off, members, r);
     const GraphDesc& d = descs[g];
     const int i = r - row_off[g];
-    float fx = 0.f, fy = 0.f;
-    for (int k = 0; k < d.nt; ++k) {
-      const float2 f = d.part[(size_t)k * d.n_pad + i];
-      fx += f.x;
-      fy += f.y;
-    }
-    d.fsum[i] = make_float2(fx, fy);
+    ulonglong2* a = reinterpret_cast<ulonglong2*>(d.acc) + i;
+    const ulonglong2 v = *a;
+    d.fsum[i] = make_float2(__ll2float_rn((long long)v.x) * d.funscale, __ll2float_rn((long long)v.y) * d.funscale);
+    *a = make_ulonglong2(0ull, 0ull);
   }
 }
 
@@ -251,7 +249,7 @@ struct Member {
   DevBuf<int32_t> col;
   DevBuf<float> P;
   DevBuf<float2> Y[2], upd, gains, fsum;
-  DevBuf<float2> part;
+  DevBuf<unsigned long long> acc;  // fixed-point force accumulators (2 per point), zero between iterations
   DevBuf<double> zunit;
   DevBuf<Sched> sched;
   HeavyStore hv;                     // hub rows and their chunks
@@ -321,7 +319,6 @@ void shape_member(Member& m, int W) {
 
 tsgne_status alloc_scratch(Member& m, int W) {
   shape_member(m, W);
-  TS_TRY(m.part.alloc((size_t)m.nt * m.n_pad));
   TS_TRY(m.zunit.alloc((size_t)m.units));
   return TSGNE_OK;
 }
@@ -354,7 +351,7 @@ tsgne_status refresh(tsgne_batch* b) {
     d.Y[1] = m.Y[1].get();
     d.upd = m.upd.get();
     d.gains = m.gains.get();
-    d.part = m.part.get();
+    d.acc = m.acc.get();
     d.fsum = m.fsum.get();
     d.zunit = m.zunit.get();
     d.sched = m.sched.get();
@@ -364,6 +361,8 @@ tsgne_status refresh(tsgne_batch* b) {
     d.n_pad = m.n_pad;
     d.units = m.units;
     d.eta = m.eta;
+    d.fscale = fix_scale(m.n);
+    d.funscale = fix_unscale(m.n);
     h[k] = d;
     uo[k + 1] = uo[k] + m.units;
     ro[k + 1] = ro[k] + m.n;
@@ -561,6 +560,8 @@ tsgne_status tsgne_batch_add(tsgne_batch* b, int32_t n, const int64_t* row_ptr, 
   B_TRY(b, mb.upd.alloc(np));
   B_TRY(b, mb.gains.alloc(np));
   B_TRY(b, mb.fsum.alloc(np));
+  B_TRY(b, mb.acc.alloc(2 * (size_t)n));
+  B_CUDA(b, cudaMemsetAsync(mb.acc.get(), 0, 2 * (size_t)n * sizeof(unsigned long long), b->stream));
   B_TRY(b, mb.Y0.alloc((size_t)n));
   B_TRY(b, launch_fill_sentinel(mb.Y[0].get(), 0, (int)np, b->stream));
   B_TRY(b, launch_fill_sentinel(mb.Y[1].get(), 0, (int)np, b->stream));

@@ -14,8 +14,9 @@
 //   min_gain; upd = mu upd - eta gain g; y_next = y + upd.  Reading Y_cur and
 //   writing Y_next (double buffer) keeps every row's neighbours at the old
 //   layout.  In export mode it writes g and changes nothing.
-// k_reduce_slots (end of S4): adds the repulsion's partial-force slots of each
-//   point in slot order into F^r (the update then reads one float2 per row).
+// k_fix_forces (end of S4): converts each point's fixed-point repulsion
+//   accumulators into F^r (the update then reads one float2 per row) and
+//   clears them for the next pass.
 // k_kl (S6): sum_e p_e ln(p_e / w_e) and sum_e p_e in FP64 (terms in FP32),
 //   fixed-order totals; KL = first + second * ln Z on the host (Eq. 5 with
 //   q = w / Z).
@@ -306,19 +307,16 @@ __global__ void k_heavy_scatter(int n, const int32_t* __restrict__ flag, const i
     if (flag[i]) rows[pos[i]] = (int32_t)i;
 }
 
-// F^r_i = sum over the partial-force slots in slot order (fixed order, so the
-// forces are bit-reproducible); one thread per point, coalesced per slot.
+// F^r_i from the fixed-point accumulators (one rounding of the exact integer
+// sum), which are cleared for the next pass; one thread per point.
 __global__ void __launch_bounds__(kAttrCta)
-    k_reduce_slots(int n, const float2* __restrict__ part, int slots, int n_pad, float2* __restrict__ out) {
+    k_fix_forces(int n, unsigned long long* __restrict__ acc, float unscale, float2* __restrict__ out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    float fx = 0.f, fy = 0.f;
-    for (int k = 0; k < slots; ++k) {
-      const float2 f = __ldcs(part + (size_t)k * n_pad + i);  // streamed: keep Y resident in L2
-      fx += f.x;
-      fy += f.y;
-    }
-    out[i] = make_float2(fx, fy);
+    ulonglong2* a = reinterpret_cast<ulonglong2*>(acc) + i;
+    const ulonglong2 v = *a;
+    out[i] = make_float2(__ll2float_rn((long long)v.x) * unscale, __ll2float_rn((long long)v.y) * unscale);
+    *a = make_ulonglong2(0ull, 0ull);
   }
 }
 
@@ -411,9 +409,9 @@ int grid_rows(int64_t n, int per_cta) {
 
 int kl_partial_count(int sm_count) { return sm_count * 4; }
 
-tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad, float2* out, cudaStream_t s) {
+tsgne_status launch_fix_forces(int n, unsigned long long* acc, float2* out, cudaStream_t s) {
   const int g = grid_rows(n, kAttrCta);
-  k_reduce_slots<<<g, kAttrCta, 0, s>>>(n, part, slots, n_pad, out);
+  k_fix_forces<<<g, kAttrCta, 0, s>>>(n, acc, fix_unscale(n), out);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }

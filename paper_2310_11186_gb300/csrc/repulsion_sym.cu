@@ -4,7 +4,10 @@
 //   Z += 2 w  (Z sums ordered pairs k != l).
 // Per unordered pair this is 10 FP32 lane-ops and one MUFU reciprocal, i.e.
 // 5 lane-ops and half a reciprocal per ordered pair (the ordered kernel in
-// repulsion.cu spends 8 and 1).
+// repulsion.cu spends 8 and 1).  Forces go to per-point fixed-point
+// accumulators with integer atomics (sym_unit.cuh), so the pass needs 16
+// bytes per point whatever the number of tiles, and its result does not
+// depend on the order in which units finish.
 //
 // Decomposition.  Points are padded to n_pad = nt * T (T = 512 W) with the
 // sentinel point.  A unit of work is a tile pair (a, b), a <= b; the units
@@ -12,14 +15,12 @@
 // persistent grid (8 warps per SM; 2-warp CTAs once there are enough units,
 // else 1-warp CTAs).  Sixteen i-points per lane and few warps beat eight
 // i-points and 24 warps per SM on GB300: the longer independent chains per
-// lane hide the reciprocal latency better than more warps do.  Unit (a, b), a < b, writes the forces
-// of tile a's points into slot b and those of tile b's points into slot a of
-// part[slot][point]; the diagonal unit (t, t) evaluates its ordered pairs
-// with the i-side only and writes slot t.  Every slot of every point is
-// written exactly once per pass, so the update kernel's fixed-order sum over
-// the nt slots gives bit-reproducible forces whatever CTA ran which unit.
-// Each unit also writes its own FP64 Z partial; the last CTA adds them in unit
-// order, removes the n self terms w_ii = 1 and sets the iteration schedule.
+// lane hide the reciprocal latency better than more warps do.  Unit (a, b),
+// a < b, adds the forces of tile a's points and of tile b's points into
+// their accumulators; the diagonal unit (t, t) evaluates its ordered pairs
+// with the i-side only.  Each unit also writes its own FP64 Z partial; the
+// last CTA adds them in unit order, removes the n self terms w_ii = 1 and
+// sets the iteration schedule.
 //
 // Inside a unit (a < b).  Each of the W warps holds 512 points of tile a in
 // registers (16 per lane, as eight FP32x2 pairs).  Tile b sits in shared
@@ -44,7 +45,7 @@ namespace {
 
 template <int W, class YT>
 __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
-    k_repulsion_sym(const YT* __restrict__ Y, int n, int nt, int n_pad, float2* __restrict__ part,
+    k_repulsion_sym(const YT* __restrict__ Y, int n, int nt, unsigned long long* __restrict__ acc, float fscale,
                     double* __restrict__ zunit, Sched* sched, int advance, float ee, int ee_iters, float mom0,
                     float mom1) {
   constexpr int T = W * 32 * kRI;
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
     __syncthreads();
     const int u = s_unit, a = s_a, b = s_b;
     if (u >= units) break;
-    const double zt = sym_unit<W, YT>(Y, n, n_pad, part, a, b, sj, sacc);
+    const double zt = sym_unit<W, YT>(Y, n, acc, fscale, a, b, sj, sacc);
     const double zb = block_sum_d(zt);
     if (tid == 0) zunit[u] = zb;
     __syncthreads();  // shared tiles are rewritten by the next unit
@@ -102,15 +103,15 @@ tsgne_status prepare() {
 }
 
 template <int W>
-tsgne_status launch(const RepShape& sh, int n, const void* Y, int y_bf16, float2* part, double* zunit, Sched* sched,
-                    int advance, float ee, int ee_iters, float mom0, float mom1, cudaStream_t s) {
+tsgne_status launch(const RepShape& sh, int n, const void* Y, int y_bf16, unsigned long long* acc, double* zunit,
+                    Sched* sched, int advance, float ee, int ee_iters, float mom0, float mom1, cudaStream_t s) {
+  const float fs = fix_scale(n);
   if (y_bf16)
-    k_repulsion_sym<W, bf162><<<sh.grid, W * 32, sh.smem, s>>>(static_cast<const bf162*>(Y), n, sh.chunks, sh.n_pad,
-                                                               part, zunit, sched, advance, ee, ee_iters, mom0, mom1);
+    k_repulsion_sym<W, bf162><<<sh.grid, W * 32, sh.smem, s>>>(static_cast<const bf162*>(Y), n, sh.chunks, acc, fs,
+                                                               zunit, sched, advance, ee, ee_iters, mom0, mom1);
   else
-    k_repulsion_sym<W, float2><<<sh.grid, W * 32, sh.smem, s>>>(static_cast<const float2*>(Y), n, sh.chunks,
-                                                                sh.n_pad, part, zunit, sched, advance, ee, ee_iters,
-                                                                mom0, mom1);
+    k_repulsion_sym<W, float2><<<sh.grid, W * 32, sh.smem, s>>>(static_cast<const float2*>(Y), n, sh.chunks, acc,
+                                                                fs, zunit, sched, advance, ee, ee_iters, mom0, mom1);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }
@@ -149,12 +150,11 @@ tsgne_status repulsion_sym_prepare(const RepShape& sh) {
   return sh.warps == 2 ? prepare<2>() : prepare<1>();
 }
 
-tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, float2* frep_part,
+tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, unsigned long long* acc,
                                   double* zpart, Sched* sched, int advance, float ee, int ee_iters, float mom0,
                                   float mom1, cudaStream_t s) {
-  if (sh.warps == 2)
-    return launch<2>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
-  return launch<1>(sh, n, Y, y_bf16, frep_part, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+  if (sh.warps == 2) return launch<2>(sh, n, Y, y_bf16, acc, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+  return launch<1>(sh, n, Y, y_bf16, acc, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
 }
 
 }  // namespace tsgne

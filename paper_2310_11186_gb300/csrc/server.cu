@@ -126,12 +126,14 @@ int64_t tsgne_server_estimate_bytes(int32_t n, int64_t nnz, int32_t tile_warps) 
   const int64_t T = 512 * (int64_t)tile_warps;  // the batch tile: 32 lanes x 16 i-points per warp
   const int64_t n_pad_max = (n + 2047) / 2048 * 2048;
   const int64_t nt = (n + T - 1) / T;
-  const int64_t n_pad = nt * T;
   const int64_t units = nt * (nt + 1) / 2;
   // hub rows (more than 32 entries: at most nnz / 33 of them) and their
   // 1024-entry chunks: 12 B per row, 32 B per chunk
   const int64_t hub_rows = nnz / 33 + 1, hub_chunks = nnz / 1024 + hub_rows;
-  return 8 * ((int64_t)n + 1) + 8 * nnz + 5 * 8 * n_pad_max + 8 * (int64_t)n + 8 * nt * n_pad + 8 * units +
+  // row_ptr, col + P, Y x 2 / update / gains / F^r (n_pad_max float2 each),
+  // the initial layout, the fixed-point force accumulators (16 B per
+  // point), the unit Z partials, the hub-row chunk lists
+  return 8 * ((int64_t)n + 1) + 8 * nnz + 5 * 8 * n_pad_max + 8 * (int64_t)n + 16 * (int64_t)n + 8 * units +
          12 * hub_rows + 32 * hub_chunks + 256;
 }
 

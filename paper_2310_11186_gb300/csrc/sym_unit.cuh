@@ -1,6 +1,21 @@
 // Device code shared by the single-layout and the multi-layout symmetric
 // repulsion kernels: the work of one tile pair (see repulsion_sym.cu for the
 // decomposition and the ring schedule).
+//
+// Forces leave a unit as fixed-point integers: each FP32 partial (one
+// point's sum over the other tile) is scaled by 2^s, rounded to the nearest
+// int64 and added with an integer atomic into the point's accumulator
+// acc[2 p + {0, 1}].  Integer addition is associative, so the total is the
+// same bits whatever order the units finish in, and the accumulators take
+// 16 bytes per point instead of one partial per tile.  fix_shift() picks s
+// from n so that no sum can overflow (see tsgne_internal.cuh).
+//
+// Z: each lane's FP32 partial of a point covers one 64-point ring group
+// (64 terms w in (0, 1]), is then added into a second FP32 partial over the
+// unit's groups (at most 16 for 1,024-point tiles) and leaves the unit in
+// FP64.  The worst-case relative rounding of a unit's row sum is then about
+// (63 + 15) 2^-24 = 4.6e-6, against 1,023 2^-24 = 6.1e-5 for one FP32 sum over
+// the whole tile.
 #pragma once
 
 #include "f32x2.cuh"
@@ -47,15 +62,22 @@ __device__ __forceinline__ void ring_pair(const float4 q, float& accx, float& ac
   accy = a0 + a1;
 }
 
+// Adds v (one coordinate of a partial force) to a fixed-point accumulator.
+__device__ __forceinline__ void red_fix(unsigned long long* p, float v, float scale) {
+  const long long q = __float2ll_rn(v * scale);  // v * 2^s is exact: scale is a power of two
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"((unsigned long long)q) : "memory");
+}
+
 // One tile pair (a, b), a <= b, of one layout: stages tile b, evaluates the
-// pairs and writes tile a's forces into slot b and (a < b) tile b's forces
-// into slot a of part[slot * n_pad + point].  Returns this thread's share of
-// the unit's Z (ordered pairs; the diagonal unit includes the w_ii = 1 terms
-// of its real points).  Every thread of the CTA must call it; it ends with the
-// shared tiles free for reuse only after a __syncthreads by the caller.
+// pairs and adds tile a's forces and (a < b) tile b's forces into the
+// fixed-point accumulators acc[2 p], acc[2 p + 1] of their real points
+// (p < n).  Returns this thread's share of the unit's Z (ordered pairs; the
+// diagonal unit includes the w_ii = 1 terms of its real points).  Every
+// thread of the CTA must call it; it ends with the shared tiles free for reuse
+// only after a __syncthreads by the caller.
 template <int W, class YT = float2>
-__device__ __forceinline__ double sym_unit(const YT* __restrict__ Y, int n, int n_pad, float2* __restrict__ part,
-                                           int a, int b, float4* sj, float2* sacc) {
+__device__ __forceinline__ double sym_unit(const YT* __restrict__ Y, int n, unsigned long long* __restrict__ acc,
+                                           float fscale, int a, int b, float4* sj, float2* sacc) {
   constexpr int T = W * 32 * kRI;
   constexpr int G = T / kGroup;  // = 4W groups
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -69,14 +91,14 @@ __device__ __forceinline__ double sym_unit(const YT* __restrict__ Y, int n, int 
   }
   // i points of tile a: lane holds i = a*T + warp*256 + r*32 + lane, r = 0..7
   const int ibase = a * T + warp * (32 * kRI) + lane;
-  u64 X2[kH], Y2[kH], FX[kH], FY[kH], Z2[kH];
+  u64 X2[kH], Y2[kH], FX[kH], FY[kH], Z2[kH], ZG[kH];
 #pragma unroll
   for (int h = 0; h < kH; ++h) {
     const float2 p0 = ld_y(Y, ibase + (2 * h) * 32);
     const float2 p1 = ld_y(Y, ibase + (2 * h + 1) * 32);
     X2[h] = pk(p0.x, p1.x);
     Y2[h] = pk(p0.y, p1.y);
-    FX[h] = FY[h] = Z2[h] = 0ull;
+    FX[h] = FY[h] = Z2[h] = ZG[h] = 0ull;
   }
   __syncthreads();
 
@@ -103,59 +125,80 @@ __device__ __forceinline__ double sym_unit(const YT* __restrict__ Y, int n, int 
       }
       ga[2 * lane] = make_float2(ax0, ay0);
       ga[2 * lane + 1] = make_float2(ax1, ay1);
+#pragma unroll
+      for (int h = 0; h < kH; ++h) {  // the group's 64 terms into the unit's partial
+        ZG[h] = add2(ZG[h], Z2[h]);
+        Z2[h] = 0ull;
+      }
       __syncthreads();
     }
 #pragma unroll
     for (int h = 0; h < kH; ++h) {
       float z0, z1;
-      upk(Z2[h], z0, z1);
+      upk(ZG[h], z0, z1);
       zt += 2.0 * ((double)z0 + (double)z1);  // tile a holds no padding
     }
-    // j side: F_j = -sum_i w^2 (y_i - y_j), into slot a of tile b's points
-    float2* outj = part + (size_t)a * n_pad + (size_t)b * T;
-    for (int k = tid; k < T; k += W * 32) {
-      const float2 v = sacc[k];
-      outj[k] = make_float2(-v.x, -v.y);
-    }
+    // j side: F_j = -sum_i w^2 (y_i - y_j) for tile b's real points
+    const int jb = b * T;
+    for (int k = tid; k < T; k += W * 32)
+      if (jb + k < n) {
+        const float2 v = sacc[k];
+        red_fix(acc + 2 * (size_t)(jb + k), -v.x, fscale);
+        red_fix(acc + 2 * (size_t)(jb + k) + 1, -v.y, fscale);
+      }
   } else {
-    // diagonal unit: ordered pairs within the tile, i side only
+    // diagonal unit: ordered pairs within the tile, i side only, in groups
+    // of 64 j-points for Z
+    for (int j0 = 0; j0 < T; j0 += kGroup) {
 #pragma unroll 2
-    for (int j = 0; j < T; ++j) {
-      const float4 q = sj[j];
-      const u64 nx = pk(q.x, q.y);
-      const u64 ny = pk(q.z, q.w);
+      for (int j = j0; j < j0 + kGroup; ++j) {
+        const float4 q = sj[j];
+        const u64 nx = pk(q.x, q.y);
+        const u64 ny = pk(q.z, q.w);
+#pragma unroll
+        for (int h = 0; h < kH; ++h) {
+          const u64 dx = add2(X2[h], nx);
+          const u64 dy = add2(Y2[h], ny);
+          u64 qq = fma2(dx, dx, one2);
+          qq = fma2(dy, dy, qq);
+          float q0, q1;
+          upk(qq, q0, q1);
+          const u64 w = pk(rcp_approx(q0), rcp_approx(q1));
+          Z2[h] = add2(Z2[h], w);
+          const u64 w2 = mul2(w, w);
+          FX[h] = fma2(w2, dx, FX[h]);
+          FY[h] = fma2(w2, dy, FY[h]);
+        }
+      }
 #pragma unroll
       for (int h = 0; h < kH; ++h) {
-        const u64 dx = add2(X2[h], nx);
-        const u64 dy = add2(Y2[h], ny);
-        u64 qq = fma2(dx, dx, one2);
-        qq = fma2(dy, dy, qq);
-        float q0, q1;
-        upk(qq, q0, q1);
-        const u64 w = pk(rcp_approx(q0), rcp_approx(q1));
-        Z2[h] = add2(Z2[h], w);
-        const u64 w2 = mul2(w, w);
-        FX[h] = fma2(w2, dx, FX[h]);
-        FY[h] = fma2(w2, dy, FY[h]);
+        ZG[h] = add2(ZG[h], Z2[h]);
+        Z2[h] = 0ull;
       }
     }
 #pragma unroll
     for (int h = 0; h < kH; ++h) {
       float z0, z1;
-      upk(Z2[h], z0, z1);
+      upk(ZG[h], z0, z1);
       if (ibase + (2 * h) * 32 < n) zt += (double)z0;
       if (ibase + (2 * h + 1) * 32 < n) zt += (double)z1;
     }
   }
-  // i side of tile a into slot b
-  float2* outi = part + (size_t)b * n_pad;
+  // i side of tile a's real points
 #pragma unroll
   for (int h = 0; h < kH; ++h) {
     float fx0, fx1, fy0, fy1;
     upk(FX[h], fx0, fx1);
     upk(FY[h], fy0, fy1);
-    outi[ibase + (2 * h) * 32] = make_float2(fx0, fy0);
-    outi[ibase + (2 * h + 1) * 32] = make_float2(fx1, fy1);
+    const int p0 = ibase + (2 * h) * 32, p1 = ibase + (2 * h + 1) * 32;
+    if (p0 < n) {
+      red_fix(acc + 2 * (size_t)p0, fx0, fscale);
+      red_fix(acc + 2 * (size_t)p0 + 1, fy0, fscale);
+    }
+    if (p1 < n) {
+      red_fix(acc + 2 * (size_t)p1, fx1, fscale);
+      red_fix(acc + 2 * (size_t)p1 + 1, fy1, fscale);
+    }
   }
   return zt;
 }

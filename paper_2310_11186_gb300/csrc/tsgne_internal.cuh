@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -14,6 +15,19 @@ namespace tsgne {
 // Padding point of the repulsion tiles: its squared distance to any real
 // point overflows to +inf in FP32, so its Student-t kernel value is exactly 0.
 constexpr float kSentinel = 1e30f;
+
+// Fixed-point scale of the exact repulsion's force accumulators: 2^s with
+// s = 62 - ceil(log2 n).  Every term w^2 (y_i - y_j) has length r / (1 + r^2)^2
+// <= 3 sqrt(3) / 16 < 0.33 (its maximum, at r = 1 / sqrt(3)), so any partial
+// or total force component is below n / 2 in magnitude and below 2^61 once
+// scaled: no int64 sum can overflow.  Resolution 2^-s (1.1e-13 at 300K points).
+inline int fix_shift(int n) {
+  int c = 0;
+  while (c < 62 && (1LL << c) < (long long)n) ++c;
+  return 62 - c;
+}
+inline float fix_scale(int n) { return ldexpf(1.0f, fix_shift(n)); }
+inline float fix_unscale(int n) { return ldexpf(1.0f, -fix_shift(n)); }
 
 // Device-resident scalars of the iteration (one per context).
 struct Sched {
@@ -39,7 +53,7 @@ struct RepShape {
   int block = 0;     // threads per CTA
   int R = 0;         // i-points per thread
   int jtile = 0;     // j-points staged in shared memory per tile
-  int chunks = 0;    // partial force slots per point (ordered: j-chunks; symmetric: tiles)
+  int chunks = 0;    // ordered: partial force slots (j-chunks) per point; symmetric: tiles
   int n_pad = 0;     // padded length of Y buffers
   int n_iblk = 0;    // i-blocks of block*R points
   int n_jtiles = 0;  // j-tiles of jtile points
@@ -173,16 +187,22 @@ tsgne_status launch_repulsion(const RepShape& sh, int n, const float2* Y, float2
                               Sched* sched, int advance, float ee, int ee_iters, float mom0, float mom1,
                               cudaStream_t s);
 
-// Symmetric pass: every unordered pair once (repulsion_sym.cu).  Same
-// outputs as launch_repulsion with chunks = number of tiles; zpart needs
-// sh.units doubles.  repulsion_sym_prepare sets kernel attributes (call it
-// outside stream capture, once per shape).
+// Symmetric pass: every unordered pair once (repulsion_sym.cu).  Adds the
+// forces of the n real points into the fixed-point accumulators acc[2 n]
+// (int64 pairs at scale fix_scale(n); zero before the pass, read and
+// cleared by launch_fix_forces after it); Z and the schedule into sched as
+// launch_repulsion does; zpart needs sh.units doubles.
+// repulsion_sym_prepare sets kernel attributes (call it outside stream
+// capture, once per shape).
 RepShape repulsion_shape_sym(int n, int sm_count);
 tsgne_status repulsion_sym_prepare(const RepShape& sh);
 // Y is float2[n_pad] (y_bf16 = 0) or __nv_bfloat162[n_pad] (y_bf16 = 1).
-tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, float2* frep_part,
+tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, unsigned long long* acc,
                                   double* zpart, Sched* sched, int advance, float ee, int ee_iters, float mom0,
                                   float mom1, cudaStream_t s);
+// F^r[i] = acc[2 i .. 2 i + 1] / fix_scale(n) (one FP32 rounding of the exact
+// integer sum), and the accumulators back to zero for the next pass.
+tsgne_status launch_fix_forces(int n, unsigned long long* acc, float2* out, cudaStream_t s);
 
 // ------------------------------------------------------------ iteration
 // Rows with more than kHeavyDeg entries get their attraction from chunks of
@@ -229,8 +249,6 @@ tsgne_status find_heavy_rows(int n, const int64_t* rp, HeavyStore& hs, cudaStrea
 // L2 prefetch of a buffer (no-op below 1 MB).
 tsgne_status launch_prefetch_l2(const void* p, int64_t bytes, cudaStream_t s);
 
-// F^r[i] = sum_k part[k * n_pad + i] for k < slots, in slot order.
-tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad, float2* out, cudaStream_t s);
 // Attraction + gradient + optimiser update: reads Ycur, writes Ynext.
 // Arguments of the attraction / update pass.  P is float[nnz] (p_bf16 = 0)
 // or bf16[nnz]; Yr is the layout the forces read: float2 (y_bf16 = 0) or the

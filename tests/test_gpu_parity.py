@@ -175,6 +175,26 @@ def test_gradient_parity_fixed_Y(n, deg, scale, alpha):
     assert np.abs(G.astype(np.float64).sum(0)).max() < 1e-3 * np.abs(G).sum(0).max() + 1e-12
 
 
+@pytest.mark.parametrize("sigma", [1e-3, 0.3])
+def test_Z_in_a_tight_cloud(sigma):
+    """The FP32 worst case for Z: 20,000 points in a cloud so tight that
+    every term w is close to 1, so every FP32 partial grows with the number
+    of its terms.  Partials of at most 64 terms, added in FP32 over at most
+    16 groups and then in FP64, bound the relative rounding of Z by about
+    (63 + 15) 2^-24 = 4.6e-6 in the worst case; random rounding keeps it far
+    below that, and Z must agree with the oracle's FP64 sum within 1e-6."""
+    n = 20000
+    Y = synth.y_init(n, sigma=sigma, seed=17)
+    _, zr = oracle.repulsion_all(Y.astype(np.float64))
+    oZ = float(zr.sum())
+    rp = np.zeros(n + 1, np.int64)
+    with pkg.Layout() as lay:
+        lay.set_P(rp, np.zeros(0, np.int32), np.zeros(0, np.float32))
+        lay.init_Y(Y)
+        _, Z = lay.gradient(1.0)
+    assert abs(Z - oZ) / oZ < 1e-6, (Z, oZ, abs(Z - oZ) / oZ)
+
+
 def test_gradient_two_nodes_vanishes():
     """2-node graph: p = q, the KL gradient is 0 for any layout."""
     with pkg.Layout() as lay:

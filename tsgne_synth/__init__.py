@@ -123,14 +123,13 @@ def csr_from_edges(n: int, u: np.ndarray, v: np.ndarray) -> tuple[np.ndarray, np
     """CSR holding each listed pair in both directions, rows sorted by column."""
     u = np.asarray(u, dtype=np.int64)
     v = np.asarray(v, dtype=np.int64)
-    src = np.concatenate([u, v])
-    dst = np.concatenate([v, u])
-    order = np.lexsort((dst, src))
-    src, dst = src[order], dst[order]
+    # one int64 key per directed pair (row major), sorted: rows in order,
+    # columns ascending within a row
+    key = np.concatenate([u * n + v, v * n + u])
+    key.sort()
     row_ptr = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(row_ptr, src + 1, 1)
-    np.cumsum(row_ptr, out=row_ptr)
-    return row_ptr, dst.astype(np.int32)
+    row_ptr[1:] = np.cumsum(np.bincount(key // n, minlength=n))
+    return row_ptr, (key % n).astype(np.int32)
 
 
 def _equal_blocks(n: int, blocks: int) -> np.ndarray:
