@@ -436,6 +436,48 @@ tsgne_status tsgne_server_cancel(tsgne_server* s, int64_t request_id);
 tsgne_status tsgne_server_usage(tsgne_server* s, int64_t* used_bytes, int32_t* resident, int32_t* queued);
 
 /*
+ * ---------------------------------------------------------------------------
+ * One layout over several GPUs (one context per GPU, same P and layout on
+ * every context).  The paper runs on one CPU and describes no distribution;
+ * the split follows from the form of Eq. 4: the repulsive forces and Z are
+ * sums over the unordered pairs, which the exact pass evaluates in tile
+ * pairs ("units", nt (nt + 1) / 2 of them for nt tiles of the layout), so the
+ * units can be divided among contexts and the sums added afterwards.  Each
+ * context holds the whole (O(n + nnz)) state and updates every row itself;
+ * only the O(n^2) repulsion is divided.
+ *
+ * An iteration on context r of w (rank and world set by tsgne_shard_set):
+ *   1. tsgne_shard_repulsion: enqueues units [u0, u1) = [U r / w, U (r+1) / w)
+ *      on the context's stream and returns two device buffers that the
+ *      caller must sum element-wise over the w contexts, in place, after
+ *      that work (an all-reduce on the same stream, or after synchronising
+ *      it): acc, 2 n int64 fixed-point force accumulators (sum as int64:
+ *      exact, wrapping), and zunit, U doubles with the unit partials of Z
+ *      (units of other contexts hold 0 here, so the sum is exact too);
+ *   2. tsgne_shard_step_finish: Z, the schedule, F^r and the attraction /
+ *      update of every row.
+ * Because both sums are exact, every context then holds the same bits as a
+ * single context running tsgne_step (for any w).  tsgne_shard_gradient_finish
+ * ends a pass without advancing and exports the gradient (parity hook).
+ * Exact repulsion only (cfg.repulsion = 0); TSGNE_ERR_INVALID_ARG otherwise,
+ * or when a share is enqueued before the previous one was finished.
+ * tsgne_step / tsgne_run / tsgne_kl / tsgne_gradient keep computing every
+ * unit locally.
+ */
+tsgne_status tsgne_shard_set(tsgne_ctx* ctx, int32_t rank, int32_t world);
+/* units: U; [*u0, *u1): this context's units; *acc: device int64[*acc_count]
+ * (2 n); *zunit: device double[U].  Both buffers belong to the context. */
+tsgne_status tsgne_shard_repulsion(tsgne_ctx* ctx, int64_t* units, int32_t* u0, int32_t* u1, void** acc,
+                                   int64_t* acc_count, void** zunit);
+tsgne_status tsgne_shard_step_finish(tsgne_ctx* ctx);
+/* g_out: float[n*2] (host or device per ptr_kind); z_out: may be NULL.  Synchronises. */
+tsgne_status tsgne_shard_gradient_finish(tsgne_ctx* ctx, float alpha, float* g_out, double* z_out,
+                                         int32_t ptr_kind);
+/* The cudaStream_t the context runs on (its private stream if it was created
+ * with NULL), for callers that order their own work or collectives on it. */
+tsgne_status tsgne_stream(tsgne_ctx* ctx, void** cuda_stream);
+
+/*
  * Repulsion pass that allocates no device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc, e.g. code running inside a framework or plugin host that owns

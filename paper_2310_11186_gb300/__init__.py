@@ -47,9 +47,14 @@ __all__ = [
     "tsgne_repulsion_shape",
     "tsgne_sync",
     "tsgne_repulsion_noalloc",
+    "tsgne_shard_set",
+    "tsgne_shard_repulsion",
+    "tsgne_shard_step_finish",
+    "tsgne_shard_gradient_finish",
     "tsgne_shortest_path_embedding",
     "tsgne_build_P_shortest_path",
     "NOALLOC_MAX_N",
+    "DeviceArray",
     "Layout",
     "Batch",
     "ServerConfig",
@@ -140,6 +145,12 @@ EXPORTS = {
     "tsgne_repulsion_shape": (_st, [_p] + [ctypes.POINTER(_i32)] * 6),
     "tsgne_sync": (_st, [_p]),
     "tsgne_repulsion_noalloc": (_st, [_i32, _p, _p, _p, _p]),
+    "tsgne_shard_set": (_st, [_p, _i32, _i32]),
+    "tsgne_shard_repulsion": (_st, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                    ctypes.POINTER(_p), ctypes.POINTER(_i64), ctypes.POINTER(_p)]),
+    "tsgne_shard_step_finish": (_st, [_p]),
+    "tsgne_shard_gradient_finish": (_st, [_p, ctypes.c_float, _p, ctypes.POINTER(ctypes.c_double), _i32]),
+    "tsgne_stream": (_st, [_p, ctypes.POINTER(_p)]),
     "tsgne_batch_create": (_st, [ctypes.POINTER(_p), ctypes.POINTER(Config), _i32, _p]),
     "tsgne_batch_destroy": (None, [_p]),
     "tsgne_batch_last_error": (ctypes.c_char_p, [_p]),
@@ -368,6 +379,52 @@ def tsgne_gradient(ctx, alpha: float = 1.0, out=None):
     out, buf = _out(n, out)
     z = ctypes.c_double()
     _check(ctx, lib().tsgne_gradient(ctx, float(alpha), buf[0], ctypes.byref(z), buf[1]))
+    return out, z.value
+
+
+def tsgne_shard_set(ctx, rank: int, world: int):
+    _check(ctx, lib().tsgne_shard_set(ctx, int(rank), int(world)))
+
+
+class DeviceArray:
+    """A borrowed device buffer of the library (pointer, length, dtype),
+    exposed through __cuda_array_interface__ so torch can wrap it in place
+    (torch.as_tensor(arr, device=...)) without a copy."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.ptr, self.count, self.typestr = int(ptr), int(count), typestr
+
+    @property
+    def __cuda_array_interface__(self):
+        return {"shape": (self.count,), "typestr": self.typestr, "data": (self.ptr, False), "version": 3,
+                "strides": None, "stream": None}
+
+
+def tsgne_shard_repulsion(ctx):
+    """Enqueues this context's share of the exact repulsion pass; returns
+    (units, u0, u1, acc, zunit): acc (int64, 2 n) and zunit (float64, units)
+    are the context's device buffers to be summed over all shares in place."""
+    U = _i64()
+    u0 = _i32()
+    u1 = _i32()
+    acc = _p()
+    cnt = _i64()
+    z = _p()
+    _check(ctx, lib().tsgne_shard_repulsion(ctx, ctypes.byref(U), ctypes.byref(u0), ctypes.byref(u1),
+                                            ctypes.byref(acc), ctypes.byref(cnt), ctypes.byref(z)))
+    return (U.value, u0.value, u1.value, DeviceArray(acc.value, cnt.value, "<i8"),
+            DeviceArray(z.value, U.value, "<f8"))
+
+
+def tsgne_shard_step_finish(ctx):
+    _check(ctx, lib().tsgne_shard_step_finish(ctx))
+
+
+def tsgne_shard_gradient_finish(ctx, alpha: float = 1.0, out=None):
+    n, _ = tsgne_get_sizes(ctx)
+    out, buf = _out(n, out)
+    z = ctypes.c_double()
+    _check(ctx, lib().tsgne_shard_gradient_finish(ctx, float(alpha), buf[0], ctypes.byref(z), buf[1]))
     return out, z.value
 
 

@@ -107,6 +107,11 @@ struct tsgne_ctx {
   HeavyRows heavy() const { return hub.view(); }
   DevBuf<double> zpart, klpart;
   DevBuf<Sched> sched;
+  // sharding of the exact repulsion over several contexts (tsgne_shard_*):
+  // this context evaluates tile-pair units [shard_u0, shard_u1)
+  int shard_rank = 0, shard_world = 1;
+  int shard_u0 = 0, shard_u1 = 0;
+  bool shard_pending = false;  // a share was enqueued and awaits its finish call
 
   cudaGraphExec_t g2[2] = {nullptr, nullptr};  // two iterations starting from buffer 0 / 1
 
@@ -295,8 +300,9 @@ tsgne_status sync_shadow(tsgne_ctx* ctx, int k) {
                         2 * (int64_t)ctx->shape.n_pad, ctx->stream);
 }
 
-tsgne_status enqueue_step(tsgne_ctx* ctx) {
-  TS_TRY(enqueue_repulsion(ctx, 1));
+// Attraction + update of every row from the forces of the last repulsion
+// pass, into the other layout buffer.
+tsgne_status enqueue_update(tsgne_ctx* ctx) {
   ProfRec pr;
   // the layout is pulled into L2 before the gathers
   const int nxt = ctx->cur ^ 1;
@@ -314,6 +320,11 @@ tsgne_status enqueue_step(tsgne_ctx* ctx) {
   TS_TRY(prof_end(ctx, &pr));
   ctx->cur = nxt;
   return TSGNE_OK;
+}
+
+tsgne_status enqueue_step(tsgne_ctx* ctx) {
+  TS_TRY(enqueue_repulsion(ctx, 1));
+  return enqueue_update(ctx);
 }
 
 tsgne_status read_sched(tsgne_ctx* ctx, Sched* h) {
@@ -853,6 +864,94 @@ tsgne_status tsgne_repulsion_shape(tsgne_ctx* ctx, int32_t* grid, int32_t* block
   if (j_tile) *j_tile = ctx->shape.jtile;
   if (j_chunks) *j_chunks = ctx->shape.chunks;
   if (n_pad) *n_pad = ctx->shape.n_pad;
+  return TSGNE_OK;
+}
+
+// ------------------------------------------------------------- sharding
+
+tsgne_status tsgne_shard_set(tsgne_ctx* ctx, int32_t rank, int32_t world) {
+  TS_TRY(enter(ctx));
+  if (world < 1 || rank < 0 || rank >= world)
+    return fail(ctx, TSGNE_ERR_INVALID_ARG, "need 0 <= rank < world");
+  if (ctx->cfg.repulsion != 0)
+    return fail(ctx, TSGNE_ERR_INVALID_ARG, "sharding applies to the exact repulsion (cfg.repulsion = 0)");
+  if (ctx->shard_pending) return fail(ctx, TSGNE_ERR_INVALID_ARG, "a share is awaiting its finish call");
+  ctx->shard_rank = rank;
+  ctx->shard_world = world;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_shard_repulsion(tsgne_ctx* ctx, int64_t* units, int32_t* u0, int32_t* u1, void** acc,
+                                   int64_t* acc_count, void** zunit) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!ctx->have_P || !ctx->have_Y) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P and set Y first");
+  if (ctx->use_tree) return fail(ctx, TSGNE_ERR_INVALID_ARG, "sharding applies to the exact repulsion");
+  if (ctx->shard_pending) return fail(ctx, TSGNE_ERR_INVALID_ARG, "the previous share has not been finished");
+  const int64_t U = ctx->shape.units;
+  ctx->shard_u0 = (int)(U * ctx->shard_rank / ctx->shard_world);
+  ctx->shard_u1 = (int)(U * (ctx->shard_rank + 1) / ctx->shard_world);
+  // units of the other shares contribute 0 here, so the sum over the
+  // shares holds every unit's partial exactly once
+  API_CUDA(ctx, cudaMemsetAsync(ctx->zpart.get(), 0, sizeof(double) * (size_t)U, ctx->stream));
+  ProfRec pr;
+  API_TRY(ctx, prof_begin(ctx, 0, &pr));
+  API_TRY(ctx, launch_repulsion_sym_units(ctx->shape, ctx->n, ctx->Yread(ctx->cur), ctx->bf16 ? 1 : 0,
+                                          ctx->facc.get(), ctx->zpart.get(), ctx->sched.get(), ctx->shard_u0,
+                                          ctx->shard_u1, ctx->stream));
+  API_TRY(ctx, prof_end(ctx, &pr));
+  ctx->shard_pending = true;
+  if (units) *units = U;
+  if (u0) *u0 = ctx->shard_u0;
+  if (u1) *u1 = ctx->shard_u1;
+  if (acc) *acc = ctx->facc.get();
+  if (acc_count) *acc_count = 2 * (int64_t)ctx->n;
+  if (zunit) *zunit = ctx->zpart.get();
+  return TSGNE_OK;
+}
+
+namespace {
+// Z, schedule and F^r after the shares were summed (advance: an iteration).
+tsgne_status shard_close(tsgne_ctx* ctx, int advance) {
+  const tsgne_config& c = ctx->cfg;
+  TS_TRY(launch_finalize_z(ctx->shape, ctx->n, ctx->zpart.get(), ctx->sched.get(), advance, c.early_exag, c.ee_iters,
+                           c.momentum0, c.momentum1, ctx->stream));
+  ProfRec pr;
+  TS_TRY(prof_begin(ctx, 5, &pr));
+  TS_TRY(launch_fix_forces(ctx->n, ctx->facc.get(), ctx->fsum.get(), ctx->stream));
+  TS_TRY(prof_end(ctx, &pr));
+  ctx->shard_pending = false;
+  return TSGNE_OK;
+}
+}  // namespace
+
+tsgne_status tsgne_shard_step_finish(tsgne_ctx* ctx) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!ctx->shard_pending) return fail(ctx, TSGNE_ERR_INVALID_ARG, "no share awaits its finish call");
+  API_TRY(ctx, shard_close(ctx, 1));
+  API_TRY(ctx, enqueue_update(ctx));
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_shard_gradient_finish(tsgne_ctx* ctx, float alpha, float* g_out, double* z_out,
+                                         int32_t ptr_kind) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!g_out || !valid_kind(ptr_kind)) return fail(ctx, TSGNE_ERR_INVALID_ARG, "g_out is NULL or bad ptr_kind");
+  if (!ctx->shard_pending) return fail(ctx, TSGNE_ERR_INVALID_ARG, "no share awaits its finish call");
+  API_TRY(ctx, shard_close(ctx, 0));
+  API_TRY(ctx, launch_gradient(attract_args(ctx), alpha, ctx->grad.get(), ctx->stream));
+  API_TRY(ctx, copy_out(g_out, ctx->grad.get(), sizeof(float2) * (size_t)ctx->n, ptr_kind, ctx->stream));
+  Sched h;
+  API_TRY(ctx, read_sched(ctx, &h));
+  if (z_out) *z_out = h.Z;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_stream(tsgne_ctx* ctx, void** cuda_stream) {
+  if (!ctx || !cuda_stream) return TSGNE_ERR_INVALID_ARG;
+  *cuda_stream = ctx->stream;
   return TSGNE_OK;
 }
 

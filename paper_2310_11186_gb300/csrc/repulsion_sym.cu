@@ -43,11 +43,33 @@ namespace tsgne {
 
 namespace {
 
+// Z and the schedule of the iteration from the unit partials: the fixed-order
+// sum of zunit[0..units) minus the n self terms; alpha / mu for iteration
+// sched->t, which advance != 0 increments.  Called by every thread of one CTA
+// (the last one of the pass, or the finalize launch of a sharded pass: with
+// the same block size both give the same bits).
+__device__ __forceinline__ void finalize_z(const double* zunit, int units, int n, Sched* sched, int advance,
+                                           float ee, int ee_iters, float mom0, float mom1) {
+  const double total = sum_partials(zunit, units);
+  if (threadIdx.x == 0) {
+    sched->work_next = 0u;
+    sched->Z = total - (double)n;
+    const int t = sched->t;
+    sched->alpha = t < ee_iters ? ee : 1.0f;
+    sched->mu = t < ee_iters ? mom0 : mom1;
+    if (advance) sched->t = t + 1;
+  }
+}
+
+// Units [u0, u1) of the nt (nt + 1) / 2 tile pairs (all of them on one GPU;
+// one rank's share when the pass is sharded).  finalize != 0: the last CTA
+// also sets Z and the schedule (one GPU); else the caller sums the unit
+// partials over the ranks and launches k_finalize_z.
 template <int W, class YT>
 __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
     k_repulsion_sym(const YT* __restrict__ Y, int n, int nt, unsigned long long* __restrict__ acc, float fscale,
-                    double* __restrict__ zunit, Sched* sched, int advance, float ee, int ee_iters, float mom0,
-                    float mom1) {
+                    double* __restrict__ zunit, Sched* sched, int u0, int u1, int finalize, int advance, float ee,
+                    int ee_iters, float mom0, float mom1) {
   constexpr int T = W * 32 * kRI;
   extern __shared__ float4 smem[];
   float4* sj = smem;                                   // T x {-x, -x, -y, -y}
@@ -58,16 +80,16 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
 
   for (;;) {
     if (tid == 0) {
-      const int u = (int)atomicAdd(&sched->work_next, 1u);
+      const int u = u0 + (int)atomicAdd(&sched->work_next, 1u);
       int a = 0, b = 0;
-      if (u < units) unit_tiles(u, nt, &a, &b);
+      if (u < u1) unit_tiles(u, nt, &a, &b);
       s_unit = u;
       s_a = a;
       s_b = b;
     }
     __syncthreads();
     const int u = s_unit, a = s_a, b = s_b;
-    if (u >= units) break;
+    if (u >= u1) break;
     const double zt = sym_unit<W, YT>(Y, n, acc, fscale, a, b, sj, sacc);
     const double zb = block_sum_d(zt);
     if (tid == 0) zunit[u] = zb;
@@ -75,16 +97,16 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
   }
 
   if (arrive_last(&sched->rep_done)) {
-    const double total = sum_partials(zunit, units);
-    if (tid == 0) {
+    if (finalize)
+      finalize_z(zunit, units, n, sched, advance, ee, ee_iters, mom0, mom1);
+    else if (tid == 0)
       sched->work_next = 0u;
-      sched->Z = total - (double)n;
-      const int t = sched->t;
-      sched->alpha = t < ee_iters ? ee : 1.0f;
-      sched->mu = t < ee_iters ? mom0 : mom1;
-      if (advance) sched->t = t + 1;
-    }
   }
+}
+
+__global__ void k_finalize_z(const double* __restrict__ zunit, int units, int n, Sched* sched, int advance, float ee,
+                             int ee_iters, float mom0, float mom1) {
+  finalize_z(zunit, units, n, sched, advance, ee, ee_iters, mom0, mom1);
 }
 
 template <int W>
@@ -103,15 +125,18 @@ tsgne_status prepare() {
 }
 
 template <int W>
-tsgne_status launch(const RepShape& sh, int n, const void* Y, int y_bf16, unsigned long long* acc, double* zunit,
-                    Sched* sched, int advance, float ee, int ee_iters, float mom0, float mom1, cudaStream_t s) {
+tsgne_status launch(const RepShape& sh, int grid, int n, const void* Y, int y_bf16, unsigned long long* acc,
+                    double* zunit, Sched* sched, int u0, int u1, int finalize, int advance, float ee, int ee_iters,
+                    float mom0, float mom1, cudaStream_t s) {
   const float fs = fix_scale(n);
   if (y_bf16)
-    k_repulsion_sym<W, bf162><<<sh.grid, W * 32, sh.smem, s>>>(static_cast<const bf162*>(Y), n, sh.chunks, acc, fs,
-                                                               zunit, sched, advance, ee, ee_iters, mom0, mom1);
+    k_repulsion_sym<W, bf162><<<grid, W * 32, sh.smem, s>>>(static_cast<const bf162*>(Y), n, sh.chunks, acc, fs,
+                                                            zunit, sched, u0, u1, finalize, advance, ee, ee_iters,
+                                                            mom0, mom1);
   else
-    k_repulsion_sym<W, float2><<<sh.grid, W * 32, sh.smem, s>>>(static_cast<const float2*>(Y), n, sh.chunks, acc,
-                                                                fs, zunit, sched, advance, ee, ee_iters, mom0, mom1);
+    k_repulsion_sym<W, float2><<<grid, W * 32, sh.smem, s>>>(static_cast<const float2*>(Y), n, sh.chunks, acc, fs,
+                                                             zunit, sched, u0, u1, finalize, advance, ee, ee_iters,
+                                                             mom0, mom1);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }
@@ -153,8 +178,28 @@ tsgne_status repulsion_sym_prepare(const RepShape& sh) {
 tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, unsigned long long* acc,
                                   double* zpart, Sched* sched, int advance, float ee, int ee_iters, float mom0,
                                   float mom1, cudaStream_t s) {
-  if (sh.warps == 2) return launch<2>(sh, n, Y, y_bf16, acc, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
-  return launch<1>(sh, n, Y, y_bf16, acc, zpart, sched, advance, ee, ee_iters, mom0, mom1, s);
+  if (sh.warps == 2)
+    return launch<2>(sh, sh.grid, n, Y, y_bf16, acc, zpart, sched, 0, sh.units, 1, advance, ee, ee_iters, mom0, mom1,
+                     s);
+  return launch<1>(sh, sh.grid, n, Y, y_bf16, acc, zpart, sched, 0, sh.units, 1, advance, ee, ee_iters, mom0, mom1,
+                   s);
+}
+
+tsgne_status launch_repulsion_sym_units(const RepShape& sh, int n, const void* Y, int y_bf16,
+                                        unsigned long long* acc, double* zpart, Sched* sched, int u0, int u1,
+                                        cudaStream_t s) {
+  if (u1 <= u0) return TSGNE_OK;
+  const int slots = sh.grid > 0 ? sh.grid : 1;  // persistent grid of the full pass: one CTA per slot
+  const int grid = (u1 - u0) < slots ? (u1 - u0) : slots;
+  if (sh.warps == 2) return launch<2>(sh, grid, n, Y, y_bf16, acc, zpart, sched, u0, u1, 0, 0, 1.f, 0, 0.f, 0.f, s);
+  return launch<1>(sh, grid, n, Y, y_bf16, acc, zpart, sched, u0, u1, 0, 0, 1.f, 0, 0.f, 0.f, s);
+}
+
+tsgne_status launch_finalize_z(const RepShape& sh, int n, const double* zpart, Sched* sched, int advance, float ee,
+                               int ee_iters, float mom0, float mom1, cudaStream_t s) {
+  k_finalize_z<<<1, sh.block, 0, s>>>(zpart, sh.units, n, sched, advance, ee, ee_iters, mom0, mom1);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
 }
 
 }  // namespace tsgne

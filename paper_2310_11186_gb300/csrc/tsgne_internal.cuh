@@ -200,6 +200,17 @@ tsgne_status repulsion_sym_prepare(const RepShape& sh);
 tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, unsigned long long* acc,
                                   double* zpart, Sched* sched, int advance, float ee, int ee_iters, float mom0,
                                   float mom1, cudaStream_t s);
+// A share of the pass for sharding one layout over several GPUs: only units
+// [u0, u1) of the sh.units tile pairs (forces into acc, unit partials into
+// zpart[u0..u1)); Z and the schedule are left to launch_finalize_z, after
+// the caller has summed acc and zpart over the shares.
+tsgne_status launch_repulsion_sym_units(const RepShape& sh, int n, const void* Y, int y_bf16,
+                                        unsigned long long* acc, double* zpart, Sched* sched, int u0, int u1,
+                                        cudaStream_t s);
+// Z = fixed-order sum of zpart[0..sh.units) - n and the schedule, as the last
+// CTA of a whole pass sets them (same block size, so the same bits).
+tsgne_status launch_finalize_z(const RepShape& sh, int n, const double* zpart, Sched* sched, int advance, float ee,
+                               int ee_iters, float mom0, float mom1, cudaStream_t s);
 // F^r[i] = acc[2 i .. 2 i + 1] / fix_scale(n) (one FP32 rounding of the exact
 // integer sum), and the accumulators back to zero for the next pass.
 tsgne_status launch_fix_forces(int n, unsigned long long* acc, float2* out, cudaStream_t s);
