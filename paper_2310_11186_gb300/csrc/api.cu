@@ -105,6 +105,7 @@ struct tsgne_ctx {
   TreeBufs tree;
   HeavyStore hub;
   HeavyRows heavy() const { return hub.view(); }
+  AttractPlan plan;  // schedule of the attraction + update pass (fixed with P)
   DevBuf<double> zpart, klpart;
   DevBuf<Sched> sched;
   // sharding of the exact repulsion over several contexts (tsgne_shard_*):
@@ -316,7 +317,7 @@ tsgne_status enqueue_update(tsgne_ctx* ctx) {
   const int64_t ybytes = (int64_t)ctx->n * (ctx->bf16 ? 4 : 8);
   TS_TRY(prof_begin(ctx, 1, &pr));
   TS_TRY(launch_prefetch_l2(a.Yr, ybytes, ctx->stream));
-  TS_TRY(launch_attract_update(a, ctx->stream));  // hub-row chunks included (one launch)
+  TS_TRY(launch_attract_plan(a, ctx->plan.view(), ctx->stream));  // hub-row chunks included (one launch)
   TS_TRY(prof_end(ctx, &pr));
   ctx->cur = nxt;
   return TSGNE_OK;
@@ -448,6 +449,8 @@ tsgne_status install(tsgne_ctx* ctx, int n, int64_t nnz, DevBuf<int64_t>& rp, De
     ctx->P16 = DevBuf<tsgne::bf16>();
   }
   TS_TRY(find_heavy_rows(n, ctx->rp.get(), ctx->hub, ctx->stream));
+  TS_TRY(build_attract_plan(n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->bf16 ? ctx->P16.get() : nullptr,
+                            ctx->hub, ctx->plan, ctx->stream));
   ctx->have_P = true;
   return TSGNE_OK;
 }

@@ -38,12 +38,6 @@ constexpr int kAttrPairs = 3;  // (row, slot) pairs a thread has in flight at on
 static_assert(kAttrCta <= 256, "rows of a CTA are numbered in one byte");
 constexpr int kG = 8;  // lanes per row
 
-__device__ __forceinline__ uint32_t atom_add_acq_rel_u32(uint32_t* p, uint32_t v) {
-  uint32_t old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-
 // Exclusive scan of v over a CTA of kAttrCta threads into off[0..kAttrCta],
 // off[kAttrCta] = total (wsum: kAttrCta / 32 ints of scratch).  Ends with
 // a __syncthreads before off is complete for every thread: the caller syncs.
@@ -61,38 +55,6 @@ __device__ __forceinline__ void block_excl_scan(int v, int* off, int* wsum) {
   for (int k = 0; k < w; ++k) base += wsum[k];
   off[threadIdx.x] = base + x - v;
   if (threadIdx.x == kAttrCta - 1) off[kAttrCta] = base + x;
-}
-
-// Gradient of row i from its attraction sum fa, then (EXPORT) the gradient
-// export or the optimiser step into the next layout.
-template <bool EXPORT>
-__device__ __forceinline__ void finish_row(int64_t i, float2 fa, const float2* __restrict__ frep_part, int chunks,
-                                           int n_pad, Sched* sched, float alpha_export, float2* __restrict__ g_out,
-                                           const float2* __restrict__ Ym, float2* __restrict__ Ynext,
-                                           bf162* __restrict__ Ynext16, float2* __restrict__ upd,
-                                           float2* __restrict__ gains, float eta, float min_gain) {
-  float rx = 0.f, ry = 0.f;
-  for (int c = 0; c < chunks; ++c) {
-    const float2 f = frep_part[(size_t)c * n_pad + i];
-    rx += f.x;
-    ry += f.y;
-  }
-  const float invZ = (float)(1.0 / sched->Z);
-  const float alpha = EXPORT ? alpha_export : sched->alpha;
-  const float gx = 4.0f * (alpha * fa.x - rx * invZ);
-  const float gy = 4.0f * (alpha * fa.y - ry * invZ);
-  if (EXPORT) {
-    g_out[i] = make_float2(gx, gy);
-    return;
-  }
-  const float mu = sched->mu;
-  float2 u = upd[i], gn = gains[i];
-  const float2 y = optimizer_step(gx, gy, u, gn, mu, eta, min_gain, Ym[i]);
-  upd[i] = u;
-  gains[i] = gn;
-  Ynext[i] = y;
-  if (Ynext16) Ynext16[i] = __float22bfloat162_rn(y);
-  if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&sched->flags, kFlagNonfiniteY);
 }
 
 // Three phases per CTA of kAttrCta rows.  A short row's attraction is, by

@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "storage.cuh"
+#include "tsgne_internal.cuh"
 
 namespace tsgne {
 
@@ -130,6 +131,44 @@ __device__ __forceinline__ float2 optimizer_step(float gx, float gy, float2& u, 
   u.x = mu * u.x - eta * gn.x * gx;
   u.y = mu * u.y - eta * gn.y * gy;
   return make_float2(yi.x + u.x, yi.y + u.y);
+}
+
+__device__ __forceinline__ uint32_t atom_add_acq_rel_u32(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Gradient of row i from its attraction sum fa, then (EXPORT) the gradient
+// export or the optimiser step into the next layout.
+template <bool EXPORT>
+__device__ __forceinline__ void finish_row(int64_t i, float2 fa, const float2* __restrict__ frep_part, int chunks,
+                                           int n_pad, Sched* sched, float alpha_export, float2* __restrict__ g_out,
+                                           const float2* __restrict__ Ym, float2* __restrict__ Ynext,
+                                           bf162* __restrict__ Ynext16, float2* __restrict__ upd,
+                                           float2* __restrict__ gains, float eta, float min_gain) {
+  float rx = 0.f, ry = 0.f;
+  for (int c = 0; c < chunks; ++c) {
+    const float2 f = frep_part[(size_t)c * n_pad + i];
+    rx += f.x;
+    ry += f.y;
+  }
+  const float invZ = (float)(1.0 / sched->Z);
+  const float alpha = EXPORT ? alpha_export : sched->alpha;
+  const float gx = 4.0f * (alpha * fa.x - rx * invZ);
+  const float gy = 4.0f * (alpha * fa.y - ry * invZ);
+  if (EXPORT) {
+    g_out[i] = make_float2(gx, gy);
+    return;
+  }
+  const float mu = sched->mu;
+  float2 u = upd[i], gn = gains[i];
+  const float2 y = optimizer_step(gx, gy, u, gn, mu, eta, min_gain, Ym[i]);
+  upd[i] = u;
+  gains[i] = gn;
+  Ynext[i] = y;
+  if (Ynext16) Ynext16[i] = __float22bfloat162_rn(y);
+  if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&sched->flags, kFlagNonfiniteY);
 }
 
 }  // namespace tsgne

@@ -203,15 +203,20 @@ __device__ __forceinline__ double sym_unit(const YT* __restrict__ Y, int n, unsi
   return zt;
 }
 
-// (a, b) of unit u of a layout with nt tiles (row-major upper triangle).
+// (a, b) of unit u of a layout with nt tiles, numbered diagonal by diagonal:
+// diagonal d = b - a holds the nt - d units (0, d), (1, d + 1), ..., so it
+// starts at sum_{d' < d} (nt - d') = row_start(d, nt).  Units taken one after
+// the other by the persistent grid then touch different tiles: the integer
+// atomics of concurrently finishing units go to different points instead of
+// all to the shared tile a of one row of the triangle.
 __device__ __forceinline__ void unit_tiles(int u, int nt, int* a_out, int* b_out) {
-  int lo = 0, hi = nt - 1;  // largest a with row_start(a) <= u
+  int lo = 0, hi = nt - 1;  // largest d with row_start(d) <= u
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (row_start(mid, nt) <= u) lo = mid; else hi = mid - 1;
   }
-  *a_out = lo;
-  *b_out = lo + (u - row_start(lo, nt));
+  *a_out = u - row_start(lo, nt);
+  *b_out = *a_out + lo;
 }
 
 }  // namespace tsgne

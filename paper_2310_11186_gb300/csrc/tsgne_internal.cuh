@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libtsgne.so.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -287,6 +288,49 @@ struct AttractArgs {
   HeavyRows hv;
 };
 tsgne_status launch_attract_update(const AttractArgs& a, cudaStream_t s);
+// Schedule of the attraction + update pass fixed when P is installed
+// (attract_plan.cu): rows of at most 32 entries in CTAs of 256 consecutive
+// rows, rows of 33..128 entries in CTAs of 64 listed rows, their slot chains
+// one thread each with coalesced copies of col and P; rows above 128 entries
+// one warp per hub chunk.  Same sums, same order as k_attract.
+constexpr int kMedDeg = 128;
+struct PlanCta {
+  int64_t ent;    // first entry of the CTA's chains in colS / PS
+  int32_t pair;   // first chain code
+  int32_t rows;   // medium CTAs: first index into med_rows
+  int32_t nrows;  // rows of the CTA
+  int32_t pad_;
+  int32_t cnt[4];  // chains of more than k entries, k = 0..3 (cnt[0]: all chains)
+};
+struct PlanView {
+  const PlanCta* med = nullptr;     // [n_med]
+  const PlanCta* shorts = nullptr;  // [n_short]
+  const uint16_t* code = nullptr;   // chain codes: (row in CTA << 3 | slot) or (<< 5 | slot)
+  const int32_t* colS = nullptr;    // col in chain order
+  const void* PS = nullptr;         // P in chain order (float, or bf16 with BF16 storage)
+  const int32_t* med_rows = nullptr;
+  const int32_t* big = nullptr;     // hub chunks of the rows above 128 entries
+  int n_med = 0, n_short = 0, n_big = 0;
+};
+struct AttractPlan {
+  DevBuf<PlanCta> cta;  // medium CTAs, then short CTAs
+  DevBuf<uint16_t> code;
+  DevBuf<int32_t> colS, med_rows, big;
+  DevBuf<float> PS;
+  DevBuf<__nv_bfloat16> PS16;
+  int n_med = 0, n_short = 0, n_big = 0;
+  int64_t entries = 0;
+  bool ready = false;
+  PlanView view() const;
+};
+// Builds the plan for the structure (rp, col) and P (FP32, or its BF16 copy
+// when P16 is not NULL); hs must hold the hub rows of the same structure.
+// Synchronises the stream.
+tsgne_status build_attract_plan(int n, const int64_t* rp, const int32_t* col, const float* P,
+                                const __nv_bfloat16* P16, const HeavyStore& hs, AttractPlan& plan, cudaStream_t s);
+// The attraction + update pass on the plan (the update mode of
+// launch_attract_update: same results, bit for bit).
+tsgne_status launch_attract_plan(const AttractArgs& a, const PlanView& pv, cudaStream_t s);
 // Gradient export g = 4 (alpha F^a - F^r / Z) without state change.
 tsgne_status launch_gradient(const AttractArgs& a, float alpha, float2* g, cudaStream_t s);
 // Hub-row chunks for the layout a reads (the update then adds their sums).

@@ -50,8 +50,8 @@ def _fix_shift(n):
 
 
 def _unit_tiles(units, nt):
-    """(a, b) of units in row-major order of the upper triangle a <= b."""
-    ab = [(a, b) for a in range(nt) for b in range(a, nt)]
+    """(a, b) of units in the library's order: diagonal d = b - a by diagonal."""
+    ab = [(a, a + d) for d in range(nt) for a in range(nt - d)]
     assert len(ab) == units
     return ab
 
