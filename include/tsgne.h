@@ -385,6 +385,8 @@ typedef struct {
   int32_t max_members;  /* resident layouts at most (default 256) */
   int32_t tile_warps;   /* repulsion tile of the batch: 1, 2 or 4 warps (default 2) */
   int32_t policy;       /* 0: advance every resident layout; 1: shortest remaining work first (default) */
+  int32_t aging_ticks;  /* policy 1: a resident layout left out of this many ticks in a row is
+                           chosen first, oldest first (default 20; 0: no aging) */
   double fill_pairs;    /* policy 1: pairs per iteration that fill the GPU (default 4e9) */
 } tsgne_server_config;
 

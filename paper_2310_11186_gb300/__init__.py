@@ -736,6 +736,7 @@ class ServerConfig(ctypes.Structure):
         ("max_members", ctypes.c_int32),
         ("tile_warps", ctypes.c_int32),
         ("policy", ctypes.c_int32),
+        ("aging_ticks", ctypes.c_int32),
         ("fill_pairs", ctypes.c_double),
     ]
 

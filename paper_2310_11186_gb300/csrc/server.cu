@@ -7,9 +7,12 @@
 //      memory (the first request is admitted whatever its size when nothing
 //      is resident, so no request starves);
 //   2. selects the resident layouts to advance: all of them (policy 0), or
-//      (policy 1, shortest remaining work first) those with the least
-//      remaining iterations x n^2 until their pairs per iteration reach
-//      fill_pairs, enough tile pairs to keep every SM busy;
+//      (policy 1, shortest remaining work first with aging) first the
+//      layouts left out of aging_ticks ticks in a row, longest waiting
+//      first, then those with the least remaining iterations x n^2, until
+//      their pairs per iteration reach fill_pairs, enough tile pairs to keep
+//      every SM busy (without aging a stream of small requests could hold
+//      a large one back indefinitely);
 //   3. runs tick_iters iterations of the selected layouts in one batched call;
 //   4. retires the layouts that reached their iterations: the layout is
 //      copied to server-owned host memory and the member's device memory is
@@ -26,6 +29,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "tsgne.h"
@@ -44,6 +48,7 @@ struct Req {
   int32_t iters = 0;
   int32_t member = -1;
   int64_t bytes = 0;
+  int32_t waited = 0;  // ticks in a row this resident layout was not advanced
 };
 
 }  // namespace
@@ -118,6 +123,7 @@ void tsgne_server_config_default(tsgne_server_config* c) {
   c->max_members = 256;
   c->tile_warps = 2;
   c->policy = 1;
+  c->aging_ticks = 20;
   c->fill_pairs = 4e9;
 }
 
@@ -145,7 +151,7 @@ tsgne_status tsgne_server_create(tsgne_server** out, const tsgne_server_config* 
   if (scfg) c = *scfg; else tsgne_server_config_default(&c);
   if (c.iters < 1 || c.tick_iters < 1 || c.iters % c.tick_iters != 0 || c.max_members < 1 || c.budget_bytes < 1 ||
       !(c.tile_warps == 1 || c.tile_warps == 2 || c.tile_warps == 4) ||
-      !(c.policy == 0 || c.policy == 1) || !(c.fill_pairs > 0.0))
+      !(c.policy == 0 || c.policy == 1) || c.aging_ticks < 0 || !(c.fill_pairs > 0.0))
     return TSGNE_ERR_INVALID_ARG;
   tsgne_server* s = new (std::nothrow) tsgne_server();
   if (!s) return TSGNE_ERR_OOM;
@@ -203,14 +209,23 @@ tsgne_status tsgne_server_tick(tsgne_server* s, int32_t* resident, int32_t* queu
     const tsgne_status st = admit(s);
     if (st != TSGNE_OK) return st;
   }
-  std::vector<std::pair<double, int64_t>> res;  // (remaining work, id)
+  // (aged first, -ticks waited, remaining work, id): the overdue layouts
+  // longest waiting first, then shortest remaining work first
+  std::vector<std::pair<std::tuple<int, int, double>, int64_t>> order;
+  const int aging = s->cfg.aging_ticks;
   for (const auto& kv : s->reqs)
-    if (kv.second.state == kResident)
-      res.emplace_back((double)(s->cfg.iters - kv.second.iters) * (double)kv.second.n * (double)kv.second.n,
-                       kv.first);
+    if (kv.second.state == kResident) {
+      const Req& r = kv.second;
+      const bool overdue = aging > 0 && r.waited >= aging;
+      order.push_back({std::make_tuple(overdue ? 0 : 1, overdue ? -r.waited : 0,
+                                       (double)(s->cfg.iters - r.iters) * (double)r.n * (double)r.n),
+                       kv.first});
+    }
+  std::vector<std::pair<double, int64_t>> res;  // selection order
   int32_t done_now = 0;
-  if (!res.empty()) {
-    std::sort(res.begin(), res.end());
+  if (!order.empty()) {
+    std::sort(order.begin(), order.end());
+    for (const auto& o : order) res.emplace_back(std::get<2>(o.first), o.second);
     std::vector<int64_t> chosen;
     double pairs = 0.0;
     for (const auto& w : res) {
@@ -220,7 +235,9 @@ tsgne_status tsgne_server_tick(tsgne_server* s, int32_t* resident, int32_t* queu
     }
     for (const auto& w : res) {
       const bool want = std::find(chosen.begin(), chosen.end(), w.second) != chosen.end();
-      const tsgne_status st = tsgne_batch_set_active(s->batch, s->reqs[w.second].member, want ? 1 : 0);
+      Req& r = s->reqs[w.second];
+      r.waited = want ? 0 : r.waited + 1;
+      const tsgne_status st = tsgne_batch_set_active(s->batch, r.member, want ? 1 : 0);
       if (st != TSGNE_OK) return batch_fail(s, st);
     }
     tsgne_status st = tsgne_batch_run(s->batch, s->cfg.tick_iters);

@@ -62,11 +62,12 @@ class LayoutServer:
     ``"srpt"`` (shortest remaining processing time first) advances the
     resident layouts with the least remaining work (remaining iterations x
     n^2) until their pairs per iteration reach ``fill_pairs``; the others
-    wait, resident.  Both run in the library."""
+    wait, resident, and a layout left out of ``aging_ticks`` ticks in a row
+    goes first at the next tick (0: no aging).  Both run in the library."""
 
     def __init__(self, iters: int = 500, tick_iters: int = 10, budget_bytes: int = 80 * 2 ** 30,
                  max_members: int = 256, tile_warps: int = 2, config=None, stream=None, policy: str = "srpt",
-                 fill_pairs: float = 4e9):
+                 fill_pairs: float = 4e9, aging_ticks: int = 20):
         if policy not in ("all", "srpt"):
             raise ValueError("policy must be 'all' or 'srpt'")
         self.iters = iters
@@ -75,7 +76,8 @@ class LayoutServer:
         self.config = config if config is not None else tsgne_config_default()
         self.server = Server(self.config, stream=stream, budget_bytes=int(budget_bytes), iters=int(iters),
                              tick_iters=int(tick_iters), max_members=int(max_members), tile_warps=int(tile_warps),
-                             policy=1 if policy == "srpt" else 0, fill_pairs=float(fill_pairs))
+                             policy=1 if policy == "srpt" else 0, fill_pairs=float(fill_pairs),
+                             aging_ticks=int(aging_ticks))
         self.ticks = 0
 
     def serve(self, requests: list[Request], clock=time.perf_counter) -> dict:
