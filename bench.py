@@ -150,7 +150,7 @@ def traffic_per_launch():
 
 
 ATTRACT_SRCS = [os.path.join(ROOT, "paper_2310_11186_gb300", "csrc", f)
-                for f in ("iterate.cu", "row_update.cuh", "storage.cuh")]
+                for f in ("attract_plan.cu", "row_update.cuh", "storage.cuh")]
 ATTRACT_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "attract_rmat21.md")
 
 

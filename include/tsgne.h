@@ -53,7 +53,9 @@ typedef enum {
   TSGNE_ERR_NOT_BUILT = 5,   /* call needs P (tsgne_build_P / tsgne_set_P) or Y first */
   TSGNE_ERR_NONFINITE = 6,   /* NaN / Inf met in X, P or the layout */
   TSGNE_ERR_TIMEOUT = 7,     /* a bounded device-side wait ran out */
-  TSGNE_ERR_CANCELLED = 8    /* work cancelled by the caller */
+  TSGNE_ERR_CANCELLED = 8,   /* work cancelled by the caller */
+  TSGNE_ERR_INDEX = 9        /* debug build (libtsgne_debug.so) only: an index check failed and its
+                                access was skipped; the results of that pass are not valid */
 } tsgne_status;
 
 typedef enum { TSGNE_PTR_HOST = 0, TSGNE_PTR_DEVICE = 1 } tsgne_ptr_kind;

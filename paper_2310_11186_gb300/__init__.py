@@ -66,7 +66,9 @@ __all__ = [
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-library_path = os.path.join(_PKG, "lib", "libtsgne.so")
+# TSGNE_DEBUG=1 selects the index-checking debug build (build.build(debug=True))
+library_path = os.path.join(_PKG, "lib", "libtsgne_debug.so" if os.environ.get("TSGNE_DEBUG") == "1"
+                            else "libtsgne.so")
 
 PTR_HOST, PTR_DEVICE = 0, 1
 KERNEL_CLASSES = ("repulsion", "attract_update", "gradient", "kl", "build", "fix_forces", "attract_hubs",
@@ -82,6 +84,7 @@ STATUS = {
     6: "TSGNE_ERR_NONFINITE",
     7: "TSGNE_ERR_TIMEOUT",
     8: "TSGNE_ERR_CANCELLED",
+    9: "TSGNE_ERR_INDEX",
 }
 
 

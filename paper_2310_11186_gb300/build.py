@@ -1,6 +1,13 @@
 """Builds libtsgne.so in-tree with nvcc for sm_103a (GB300).
 
-    python -m paper_2310_11186_gb300.build
+    python -m paper_2310_11186_gb300.build            # libtsgne.so
+    python -m paper_2310_11186_gb300.build --debug    # libtsgne_debug.so
+
+The debug library is compiled with -DTSGNE_DEBUG: index checks in the
+kernels record a status bit and skip the access instead of reading or
+writing out of bounds, and the next synchronising call reports
+TSGNE_ERR_INDEX.  The binding loads it instead of libtsgne.so when the
+environment variable TSGNE_DEBUG is 1.
 
 Each translation unit of ``csrc/`` is compiled in parallel into ``_build/``
 and linked into ``paper_2310_11186_gb300/lib/libtsgne.so``.  A unit is
@@ -24,6 +31,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "tsgne")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libtsgne.so")
+BUILD_DEBUG = os.path.join(ROOT, "_build", "tsgne_debug")
+LIB_DEBUG = os.path.join(LIBDIR, "libtsgne_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
@@ -43,16 +52,17 @@ def _needs(obj: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra_flags: list[str] | None = None, debug: bool = False) -> str:
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
     cc = nvcc()
-    flags = NVCC_FLAGS + (extra_flags or [])
+    flags = NVCC_FLAGS + (["-DTSGNE_DEBUG"] if debug else []) + (extra_flags or [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(build_dir, os.path.basename(src).replace(".cu", ".o"))
         if _needs(obj, [src, *headers, __file__]):
             cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
             if verbose:
@@ -66,17 +76,17 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    if _needs(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if _needs(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -337,6 +337,14 @@ tsgne_status read_sched(tsgne_ctx* ctx, Sched* h) {
 // Errors of the tree code's passes (stack overflow, a sort wait that ran out)
 // in a status word already read into h.
 tsgne_status check_tree_flags(tsgne_ctx* ctx, const Sched& h) {
+  if (h.flags & kFlagIndexCheck) {  // debug build only; reported once
+    const uint32_t rest = h.flags & ~kFlagIndexCheck;
+    TS_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(ctx->sched.get()) + offsetof(Sched, flags), &rest,
+                            sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    TS_CUDA(cudaStreamSynchronize(ctx->stream));
+    last_msg() = "an index check of the debug build failed and its access was skipped; the pass is not valid";
+    return TSGNE_ERR_INDEX;
+  }
   if (h.flags & kFlagTreeOverflow) {
     last_msg() = "tree walk stack overflow (results of the pass are incomplete)";
     return TSGNE_ERR_CUDA;
@@ -514,6 +522,7 @@ const char* tsgne_status_string(tsgne_status s) {
     case TSGNE_ERR_NONFINITE: return "TSGNE_ERR_NONFINITE";
     case TSGNE_ERR_TIMEOUT: return "TSGNE_ERR_TIMEOUT";
     case TSGNE_ERR_CANCELLED: return "TSGNE_ERR_CANCELLED";
+    case TSGNE_ERR_INDEX: return "TSGNE_ERR_INDEX";
   }
   return "TSGNE_ERR_UNKNOWN";
 }

@@ -72,15 +72,20 @@ __global__ void __launch_bounds__(kPlanThreads, 6)
   const PT* __restrict__ P = static_cast<const PT*>(a.P);
   const YT* __restrict__ Y = static_cast<const YT*>(a.Yr);
   bf162* Ynext16 = static_cast<bf162*>(a.Ynext16);
+  uint32_t* dbg = &a.sched->flags;  // index checks of the debug build
+  (void)dbg;
 
   if ((int)blockIdx.x < big_blocks) {  // one warp per chunk of a row above 128 entries
     const HeavyRows& hv = a.hv;
     const int stride = big_blocks * (kPlanThreads / 32);
     for (int k = blockIdx.x * (kPlanThreads / 32) + warp; k < pv.n_big; k += stride) {
       const int c = pv.big[k];
+      if (!TS_IN(c, 0, hv.chunks, dbg)) continue;
       const int64_t i = hv.chunk_row[c];
+      if (!TS_IN(i, 0, a.n, dbg)) continue;
       float ax = 0.f, ay = 0.f;
-      attract_entries<32, PT, YT>(hv.chunk_begin[c], hv.chunk_end[c], a.col, P, Y, i, lane, ld_y(Y, i), ax, ay);
+      attract_entries<32, PT, YT>(hv.chunk_begin[c], hv.chunk_end[c], a.col, P, Y, i, lane, ld_y(Y, i), ax, ay,
+                                  a.n, dbg);
       ax = group_sum<32>(ax);
       ay = group_sum<32>(ay);
       if (lane == 0) {
@@ -114,17 +119,22 @@ __global__ void __launch_bounds__(kPlanThreads, 6)
   // the chains: thread per chain, every entry's loads issued up front
   const int64_t off1 = m.cnt[0], off2 = off1 + m.cnt[1], off3 = off2 + m.cnt[2];
   for (int q = tid; q < m.cnt[0]; q += kPlanThreads) {
+    if (!TS_IN(m.pair + q, 0, pv.n_codes, dbg)) continue;
     const int code = pv.code[m.pair + q];
     const int r = code >> shift, s = code & ((1 << shift) - 1);
+    if (!TS_IN(r, 0, m.nrows, dbg) || (med && !TS_IN(m.rows + r, 0, pv.n_med_rows, dbg))) continue;
     const int64_t i = med ? (int64_t)pv.med_rows[m.rows + r] : row0 + r;
+    if (!TS_IN(i, 0, a.n, dbg)) continue;
     const int depth = 1 + (q < m.cnt[1]) + (q < m.cnt[2]) + (q < m.cnt[3]);
     const int64_t e[4] = {m.ent + q, m.ent + off1 + q, m.ent + off2 + q, m.ent + off3 + q};
     int32_t j[4];
     float p[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      j[k] = k < depth ? pv.colS[e[k]] : (int32_t)i;
-      p[k] = k < depth ? ld_p(static_cast<const PT*>(pv.PS), e[k]) : 0.f;
+      const bool ld = k < depth && TS_IN(e[k], 0, pv.entries, dbg);
+      j[k] = ld ? pv.colS[e[k]] : (int32_t)i;
+      p[k] = ld ? ld_p(static_cast<const PT*>(pv.PS), e[k]) : 0.f;
+      if (!TS_IN(j[k], 0, a.n, dbg)) j[k] = (int32_t)i;
     }
     const float2 yi = ld_y(Y, i);
     float2 yj[4];
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(kPlanThreads, 6)
     if (lane == 0) sfa[r] = make_float2(0.f + ax, 0.f + ay);
   }
   __syncthreads();
-  if (tid < m.nrows)
+  if (tid < m.nrows && TS_IN(m.rows + tid, 0, pv.n_med_rows, dbg))
     finish_row<false>(pv.med_rows[m.rows + tid], sfa[tid], a.frep, a.chunks, a.n_pad, a.sched, 0.f, nullptr, a.Ym,
                       a.Ynext, Ynext16, a.upd, a.gains, a.eta, a.min_gain);
 }
@@ -269,6 +279,8 @@ tsgne_status build_attract_plan(int n, const int64_t* rp_dev, const int32_t* col
   plan.n_short = (int)shorts.size();
   plan.n_big = (int)big.size();
   plan.entries = (int64_t)perm.size();
+  plan.n_codes = (int64_t)code.size();
+  plan.n_med_rows = (int64_t)med_rows.size();
   std::vector<PlanCta> ctas(med);
   ctas.insert(ctas.end(), shorts.begin(), shorts.end());
   TS_TRY(plan.cta.alloc(ctas.size()));
@@ -318,6 +330,9 @@ PlanView AttractPlan::view() const {
   v.n_med = n_med;
   v.n_short = n_short;
   v.n_big = n_big;
+  v.entries = entries;
+  v.n_codes = n_codes;
+  v.n_med_rows = n_med_rows;
   return v;
 }
 

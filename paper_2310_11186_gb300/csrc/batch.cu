@@ -105,6 +105,11 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
     const int u = s_unit, g = s_g, a = s_a, b = s_b;
     if (u >= U) break;
     const GraphDesc& d = descs[g];
+    if (!(TS_IN(a, 0, d.nt, &d.sched->flags) && TS_IN(b, a, d.nt, &d.sched->flags))) {  // debug build only
+      if (tid == 0) d.zunit[u - unit_off[g]] = 0.0;
+      __syncthreads();
+      continue;
+    }
     const float2* Y = d.Y[d.sched->t & 1];
     const double zt = sym_unit<W>(Y, d.n, d.acc, d.fscale, a, b, sj, sacc);
     const double zb = block_sum_d(zt);

@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(kAttrCta)
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) {
       const float p = ld_p(P, e);
       if (!(p > 0.f)) continue;
+      if (!TS_IN(col[e], 0, n, &sched->flags)) continue;
       const float2 yj = ld_y(Y, col[e]);
       const float dx = yi.x - yj.x, dy = yi.y - yj.y;
       // ln(p / w) = ln p + ln(1 + d^2)

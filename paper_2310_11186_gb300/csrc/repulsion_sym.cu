@@ -90,6 +90,11 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
     __syncthreads();
     const int u = s_unit, a = s_a, b = s_b;
     if (u >= u1) break;
+    if (!(TS_IN(a, 0, nt, &sched->flags) && TS_IN(b, a, nt, &sched->flags))) {  // debug build only
+      if (tid == 0) zunit[u] = 0.0;
+      __syncthreads();
+      continue;
+    }
     const double zt = sym_unit<W, YT>(Y, n, acc, fscale, a, b, sj, sacc);
     const double zb = block_sum_d(zt);
     if (tid == 0) zunit[u] = zb;

@@ -573,7 +573,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps, 4)
       int kind = 0;  // 1 accept, 2 exact, 3 open
       float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
       int4 B = make_int4(0, 0, 0, 0);
-      if (has) {
+      const bool vok = !has || (v < 0 ? TS_IN(~v, 0, n, &sched->flags) : TS_IN(v, 0, n - 1, &sched->flags));
+      if (has && vok) {
         if (v < 0) {
           const float2 q = ys[~v];
           A = make_float4(q.x, q.y, 0.f, 1.f);
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps, 4)
       }
       const int ni = __shfl_sync(0xffffffffu, off, 31);
       off -= cnt;
-      if (kind == 1) {
+      if (kind == 1 && TS_IN(off, 0, kWalkList, &sched->flags)) {
         lnx[w][off] = -A.x;
         lny[w][off] = -A.y;
         lc[w][off] = A.w;
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps, 4)
       if (kind == 2) {
 #pragma unroll
         for (int u = 0; u < kTreeBucket; ++u)
-          if (u < cnt) {
+          if (u < cnt && TS_IN(B.z + u, 0, n, &sched->flags) && TS_IN(off + u, 0, kWalkList, &sched->flags)) {
             const float2 q = ys[B.z + u];
             lnx[w][off + u] = -q.x;
             lny[w][off + u] = -q.y;
@@ -617,7 +618,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps, 4)
         if (lo <= hi) cover = ((1u << (hi - lo + 1)) - 1u) << lo;  // hi - lo < kTreeBucket
       }
       seen |= __reduce_or_sync(0xffffffffu, cover);
-      if (lane == 0 && (ni & 1)) {  // pad to a whole pair with a zero-weight item
+      if (lane == 0 && (ni & 1) && TS_IN(ni, 0, kWalkList, &sched->flags)) {  // pad to a whole pair with a zero-weight item
         lnx[w][ni] = 0.f;
         lny[w][ni] = 0.f;
         lc[w][ni] = 0.f;
@@ -625,7 +626,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps, 4)
       __syncwarp();  // every lane has read its entry before the pushes reuse the slots
       const int npush = 2 * __popc(mo);
       if (sp + npush <= kWalkStack) {
-        if (kind == 3) {
+        if (kind == 3 && TS_IN(sp + 2 * __popc(mo & lt) + 1, 0, kWalkStack, &sched->flags)) {
           const int slot = sp + 2 * __popc(mo & lt);
           stk[w][slot] = B.y;  // right below, left on top
           stk[w][slot + 1] = B.x;
@@ -636,7 +637,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps, 4)
       }
       __syncwarp();
       u64 Z = 0ull;
-      for (int t = 0; t < ni; t += 2)
+      for (int t = 0; t < ni && TS_IN(t + 1, 0, kWalkList, &sched->flags); t += 2)
         interact2(PX, PY, *reinterpret_cast<const u64*>(&lnx[w][t]), *reinterpret_cast<const u64*>(&lny[w][t]),
                   *reinterpret_cast<const u64*>(&lc[w][t]), FX, FY, Z);
       float z0, z1;
@@ -655,7 +656,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps, 4)
       float fx0, fx1, fy0, fy1;
       upk(FX, fx0, fx1);
       upk(FY, fy0, fy1);
-      frep[perm[k]] = make_float2(fx0 + fx1, fy0 + fy1);
+      if (TS_IN(perm[k], 0, n, &sched->flags)) frep[perm[k]] = make_float2(fx0 + fx1, fy0 + fy1);
     }
   }
   if (arrive_last(&st->walk_done)) {

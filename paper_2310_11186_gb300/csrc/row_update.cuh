@@ -16,10 +16,12 @@ namespace tsgne {
 // Entries [a, b) of the row; 4 entries per lane are in flight at once (their
 // column / P loads, then their gathers), accumulated in entry order, so the
 // result is the same as one entry at a time.
+// dbg (debug build only): status word for the check 0 <= column < nY.
 template <int G, class PT = float, class YT = float2>
 __device__ __forceinline__ void attract_entries(int64_t a, int64_t b, const int32_t* __restrict__ col,
                                                 const PT* __restrict__ P, const YT* __restrict__ Y,
-                                                int64_t i, int lane, float2 yi, float& ax, float& ay) {
+                                                int64_t i, int lane, float2 yi, float& ax, float& ay,
+                                                int64_t nY = 0, uint32_t* dbg = nullptr) {
   constexpr int U = 4;
   for (int64_t e0 = a + lane; e0 < b; e0 += U * G) {
     int32_t j[U];
@@ -30,6 +32,7 @@ __device__ __forceinline__ void attract_entries(int64_t a, int64_t b, const int3
       const bool ok = e < b;
       j[u] = ok ? col[e] : (int32_t)i;
       p[u] = ok ? ld_p(P, e) : 0.f;
+      if (dbg && !TS_IN(j[u], 0, nY, dbg)) j[u] = (int32_t)i;
     }
     float2 yj[U];
 #pragma unroll

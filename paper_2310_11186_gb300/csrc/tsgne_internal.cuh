@@ -47,6 +47,23 @@ constexpr uint32_t kFlagNonfiniteY = 1u;
 constexpr uint32_t kFlagNonfiniteP = 2u;
 constexpr uint32_t kFlagTreeOverflow = 4u;
 constexpr uint32_t kFlagWaitTimeout = 8u;  // a bounded device-side wait ran out (cleared once reported)
+constexpr uint32_t kFlagIndexCheck = 16u;  // debug build: an index check failed (cleared once reported)
+
+// Index checks of the debug build (compiled with -DTSGNE_DEBUG into
+// libtsgne_debug.so).  TS_IN(v, lo, hi, flags) is true when lo <= v < hi;
+// otherwise it records kFlagIndexCheck in the status word *flags (if not
+// NULL) and is false, and the caller skips the access it guards.  Nothing
+// traps.  In the regular build it is the constant true and compiles away.
+#ifdef TSGNE_DEBUG
+__device__ __forceinline__ bool ts_in(long long v, long long lo, long long hi, uint32_t* flags) {
+  const bool ok = v >= lo && v < hi;
+  if (!ok && flags) atomicOr(flags, kFlagIndexCheck);
+  return ok;
+}
+#define TS_IN(v, lo, hi, flags) ::tsgne::ts_in((long long)(v), (long long)(lo), (long long)(hi), (flags))
+#else
+#define TS_IN(v, lo, hi, flags) true
+#endif
 
 // Geometry of one repulsion pass (see repulsion.cu and repulsion_sym.cu).
 struct RepShape {
@@ -311,6 +328,7 @@ struct PlanView {
   const int32_t* med_rows = nullptr;
   const int32_t* big = nullptr;     // hub chunks of the rows above 128 entries
   int n_med = 0, n_short = 0, n_big = 0;
+  int64_t entries = 0, n_codes = 0, n_med_rows = 0;  // array lengths (index checks)
 };
 struct AttractPlan {
   DevBuf<PlanCta> cta;  // medium CTAs, then short CTAs
@@ -319,7 +337,7 @@ struct AttractPlan {
   DevBuf<float> PS;
   DevBuf<__nv_bfloat16> PS16;
   int n_med = 0, n_short = 0, n_big = 0;
-  int64_t entries = 0;
+  int64_t entries = 0, n_codes = 0, n_med_rows = 0;
   bool ready = false;
   PlanView view() const;
 };
