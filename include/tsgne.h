@@ -274,7 +274,8 @@ tsgne_status tsgne_sync(tsgne_ctx* ctx);
  * reduction, does not depend on the other members.  The attraction sums
  * rows as the single-layout path does (rows above 32 entries in 1024-entry
  * warp chunks added in chunk order), so a batch of one equals tsgne_run at
- * the same repulsion tile.  All members share one
+ * the same repulsion tile.  cfg.repulsion = 1 makes every member a tree-code
+ * member (see tsgne_batch_add_ex); precision must be 0.  All members share one
  * repulsion tile of 512 * tile_warps points (1, 2 or 4; smaller tiles pad
  * small graphs less, larger tiles amortise more per unit).  The same
  * conventions as the context API apply (status codes, one stream, not
@@ -294,6 +295,16 @@ const char* tsgne_batch_last_error(const tsgne_batch* b);
  */
 tsgne_status tsgne_batch_add(tsgne_batch* b, int32_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* X,
                              int32_t d, const float* Y0, int32_t ptr_kind, int32_t* id_out);
+
+/* tsgne_batch_add with the member's repulsion chosen here (0: exact,
+ * 1: tree code with the batch's theta) instead of by the batch's
+ * cfg.repulsion.  A tree member takes no part in the shared exact pass: its
+ * tree is built and walked by its own launches, on a branch of the
+ * iteration that runs concurrently with the other members'; its layout is
+ * the same as the single-layout tree code's for the same inputs. */
+tsgne_status tsgne_batch_add_ex(tsgne_batch* b, int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                const float* X, int32_t d, const float* Y0, int32_t ptr_kind, int32_t repulsion,
+                                int32_t* id_out);
 
 /* Removes a member and frees its device memory. */
 tsgne_status tsgne_batch_remove(tsgne_batch* b, int32_t id);
@@ -390,6 +401,8 @@ typedef struct {
   int32_t aging_ticks;  /* policy 1: a resident layout left out of this many ticks in a row is
                            chosen first, oldest first (default 20; 0: no aging) */
   double fill_pairs;    /* policy 1: pairs per iteration that fill the GPU (default 4e9) */
+  int32_t tree_min_n;   /* requests of at least this many points run the tree code with cfg.theta
+                           (tsgne_batch_add_ex); 0 (default): every request runs the exact pass */
 } tsgne_server_config;
 
 void tsgne_server_config_default(tsgne_server_config* cfg);
@@ -397,7 +410,8 @@ void tsgne_server_config_default(tsgne_server_config* cfg);
 /* Device bytes a resident layout of n points and nnz affinities holds in a
  * batch with the given tile (P, layout, optimiser state, initial layout,
  * fixed-point repulsion accumulators, Z partials, an upper bound for the hub-row
- * chunk lists); -1 for invalid arguments.  Host
+ * chunk lists); -1 for invalid arguments.  A tree-code member holds about
+ * 144 bytes per point more (its tree); the server adds them.  Host
  * arithmetic only (no GPU needed). */
 int64_t tsgne_server_estimate_bytes(int32_t n, int64_t nnz, int32_t tile_warps);
 

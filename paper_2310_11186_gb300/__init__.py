@@ -158,6 +158,7 @@ EXPORTS = {
     "tsgne_batch_destroy": (None, [_p]),
     "tsgne_batch_last_error": (ctypes.c_char_p, [_p]),
     "tsgne_batch_add": (_st, [_p, _i32, _p, _p, _p, _i32, _p, _i32, ctypes.POINTER(_i32)]),
+    "tsgne_batch_add_ex": (_st, [_p, _i32, _p, _p, _p, _i32, _p, _i32, _i32, ctypes.POINTER(_i32)]),
     "tsgne_batch_remove": (_st, [_p, _i32]),
     "tsgne_batch_size": (_st, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "tsgne_batch_run": (_st, [_p, _i32]),
@@ -653,7 +654,9 @@ class Batch:
         if st != 0:
             raise TsgneError(st, lib().tsgne_batch_last_error(self.h).decode())
 
-    def add(self, row_ptr, col, X, Y0=None) -> int:
+    def add(self, row_ptr, col, X, Y0=None, repulsion=None) -> int:
+        """Adds a member; repulsion 0 (exact) or 1 (tree code), default the
+        batch configuration's."""
         rp = _as_buffer(row_ptr, np.int64)
         ci = _as_buffer(col, np.int32)
         x = _as_buffer(X, np.float32)
@@ -661,8 +664,12 @@ class Batch:
         kind = _same_kind(rp, ci, x, y)
         out = _i32()
         n = len(row_ptr) - 1
-        self._check(lib().tsgne_batch_add(self.h, n, rp[0], ci[0], x[0], int(X.shape[1]), y[0], kind,
-                                          ctypes.byref(out)))
+        if repulsion is None:
+            self._check(lib().tsgne_batch_add(self.h, n, rp[0], ci[0], x[0], int(X.shape[1]), y[0], kind,
+                                              ctypes.byref(out)))
+        else:
+            self._check(lib().tsgne_batch_add_ex(self.h, n, rp[0], ci[0], x[0], int(X.shape[1]), y[0], kind,
+                                                 int(repulsion), ctypes.byref(out)))
         self.sizes[out.value] = n
         return out.value
 
@@ -741,6 +748,7 @@ class ServerConfig(ctypes.Structure):
         ("policy", ctypes.c_int32),
         ("aging_ticks", ctypes.c_int32),
         ("fill_pairs", ctypes.c_double),
+        ("tree_min_n", ctypes.c_int32),
     ]
 
 

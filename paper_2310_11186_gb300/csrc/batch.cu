@@ -18,6 +18,15 @@
 //   k_batch_attract    attraction + gradient + optimiser step per row (a hub
 //                      row adds its chunk sums in chunk order)
 //
+// Tree-code members (cfg.repulsion = 1, or per member through
+// tsgne_batch_add_ex) take no units of k_batch_repulsion: each runs the
+// single-layout tree code's build and walk on its own current layout, as
+// its own chain of launches on a branch of the iteration (auxiliary
+// streams, forked from and joined back into the batch stream, so in the
+// captured graph the members' trees are built and walked concurrently),
+// and the walk sets its forces, Z and schedule as k_batch_finalize does for
+// the others.  Attraction and update are the shared launches above.
+//
 // Members keep their P, layout and optimiser state resident on the device
 // and may differ in size and in iteration count (each has its own t); the
 // current layout of a member is Y[t & 1], so one captured CUDA graph of the
@@ -56,6 +65,8 @@ struct GraphDesc {
   int n, nt, n_pad, units;
   float eta;
   float fscale, funscale;
+  int tree;  // 1: tree-code repulsion (no units; forces and Z from its walk)
+  int pad_;
 };
 
 struct BatchCtr {
@@ -122,6 +133,7 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
 __global__ void k_batch_finalize(const GraphDesc* __restrict__ descs, float ee, int ee_iters, float mom0,
                                  float mom1) {
   const GraphDesc& d = descs[blockIdx.x];
+  if (d.tree) return;  // its walk set Z and the schedule
   const double total = sum_partials(d.zunit, d.units);
   if (threadIdx.x == 0) {
     Sched* s = d.sched;
@@ -140,11 +152,19 @@ __global__ void k_batch_reduce(const GraphDesc* __restrict__ descs, const int* _
     const int g = find_owner(row_off, members, r);
     const GraphDesc& d = descs[g];
     const int i = r - row_off[g];
+    if (d.tree) continue;  // its walk wrote F^r
     ulonglong2* a = reinterpret_cast<ulonglong2*>(d.acc) + i;
     const ulonglong2 v = *a;
     d.fsum[i] = make_float2(__ll2float_rn((long long)v.x) * d.funscale, __ll2float_rn((long long)v.y) * d.funscale);
     *a = make_ulonglong2(0ull, 0ull);
   }
+}
+
+// A tree member's current layout Y[t & 1] into the buffer its tree build reads.
+__global__ void k_member_cur_Y(const float2* __restrict__ Y0, const float2* __restrict__ Y1, const Sched* sched, int n,
+                               float2* __restrict__ out) {
+  const float2* Y = (sched->t & 1) ? Y1 : Y0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = Y[i];
 }
 
 // One warp per chunk of every member's hub rows (global chunk index c over
@@ -261,6 +281,9 @@ struct Member {
   int nt = 0, n_pad = 0, units = 0;  // for the batch's current tile
   DevBuf<float2> Y0;                 // initial layout (autotune restores it)
   bool active = true;
+  bool tree = false;                 // tree-code repulsion
+  TreeBufs tb;                       // its tree (tree members)
+  DevBuf<float2> Ytree;              // its current layout, copied for the tree build
 };
 
 std::mutex g_cache_mu;
@@ -286,8 +309,13 @@ struct tsgne_batch {
   int U = 0, R = 0, G = 0, C = 0;  // of the active members (C: hub-row chunks)
   bool dirty = true;
   cudaGraphExec_t graph = nullptr;
+  std::vector<Member*> trees;     // active tree members (refresh)
+  std::vector<cudaStream_t> aux;  // branches of the tree members' launches
+  std::vector<cudaEvent_t> ev;    // fork event, then one join event per tree member
   ~tsgne_batch() {
     if (graph) cudaGraphExecDestroy(graph);
+    for (auto e : ev) cudaEventDestroy(e);
+    for (auto a : aux) cudaStreamDestroy(a);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
 };
@@ -319,7 +347,7 @@ void shape_member(Member& m, int W) {
   const int T = 32 * kRI * W;
   m.nt = (m.n + T - 1) / T;
   m.n_pad = m.nt * T;
-  m.units = m.nt * (m.nt + 1) / 2;
+  m.units = m.tree ? 0 : m.nt * (m.nt + 1) / 2;
 }
 
 tsgne_status alloc_scratch(Member& m, int W) {
@@ -340,8 +368,12 @@ void invalidate(tsgne_batch* b) {
 tsgne_status refresh(tsgne_batch* b) {
   if (!b->dirty) return TSGNE_OK;
   std::vector<Member*> act;
+  b->trees.clear();
   for (auto& m : b->members)
-    if (m->active) act.push_back(m.get());
+    if (m->active) {
+      act.push_back(m.get());
+      if (m->tree) b->trees.push_back(m.get());
+    }
   const int G = (int)act.size();
   b->G = G;
   std::vector<GraphDesc> h(G > 0 ? G : 1);
@@ -368,6 +400,7 @@ tsgne_status refresh(tsgne_batch* b) {
     d.eta = m.eta;
     d.fscale = fix_scale(m.n);
     d.funscale = fix_unscale(m.n);
+    d.tree = m.tree ? 1 : 0;
     h[k] = d;
     uo[k + 1] = uo[k] + m.units;
     ro[k + 1] = ro[k] + m.n;
@@ -389,23 +422,61 @@ tsgne_status refresh(tsgne_batch* b) {
   return TSGNE_OK;
 }
 
+constexpr int kAuxStreams = 8;
+
+// Streams and events for the tree members' branches (created on first use).
+tsgne_status ensure_aux(tsgne_batch* b, int ntree) {
+  while ((int)b->aux.size() < std::min(ntree, kAuxStreams)) {
+    cudaStream_t st = nullptr;
+    TS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    b->aux.push_back(st);
+  }
+  while ((int)b->ev.size() < ntree + 1) {
+    cudaEvent_t e = nullptr;
+    TS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    b->ev.push_back(e);
+  }
+  return TSGNE_OK;
+}
+
 tsgne_status enqueue_iteration(tsgne_batch* b) {
   const int G = b->G;
   if (G == 0) return TSGNE_OK;
+  const tsgne_config& c = b->cfg;
+  // tree members: copy of the current layout, tree build and walk (forces,
+  // Z, schedule), each member on a branch forked from the batch stream
+  const int ntree = (int)b->trees.size();
+  if (ntree > 0) {
+    TS_TRY(ensure_aux(b, ntree));
+    TS_CUDA(cudaEventRecord(b->ev[0], b->stream));
+    for (int k = 0; k < ntree; ++k) {
+      Member& m = *b->trees[k];
+      cudaStream_t s = b->aux[k % b->aux.size()];
+      TS_CUDA(cudaStreamWaitEvent(s, b->ev[0], 0));
+      k_member_cur_Y<<<std::max(1, std::min((m.n + 255) / 256, 1024)), 256, 0, s>>>(m.Y[0].get(), m.Y[1].get(),
+                                                                                     m.sched.get(), m.n,
+                                                                                     m.Ytree.get());
+      TS_CUDA(cudaGetLastError());
+      TS_TRY(launch_tree_build(m.tb, m.Ytree.get(), s));
+      TS_TRY(launch_tree_walk(m.tb, c.theta, m.fsum.get(), m.sched.get(), 1, c.early_exag, c.ee_iters, c.momentum0,
+                              c.momentum1, s));
+      TS_CUDA(cudaEventRecord(b->ev[1 + k], s));
+    }
+  }
   const int W = b->W;
   const int slots = b->sms * (kWarpsPerSm / W);
   const int grid = b->U < slots ? b->U : slots;
   const size_t sm = smem_for(W);
-  switch (W) {
+  if (b->U > 0) switch (W) {
     case 4: k_batch_repulsion<4><<<grid, 128, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
     case 2: k_batch_repulsion<2><<<grid, 64, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
     default: k_batch_repulsion<1><<<grid, 32, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
   }
-  const tsgne_config& c = b->cfg;
   // 32 W threads: the same reduction tree as the single-layout pass's last CTA
   k_batch_finalize<<<G, 32 * W, 0, b->stream>>>(b->d_desc.get(), c.early_exag, c.ee_iters, c.momentum0, c.momentum1);
   const int rgrid = std::max(1, std::min((b->R + 255) / 256, b->sms * 16));
   k_batch_reduce<<<rgrid, 256, 0, b->stream>>>(b->d_desc.get(), b->d_row_off.get(), G, b->R);
+  for (int k = 0; k < ntree; ++k) TS_CUDA(cudaStreamWaitEvent(b->stream, b->ev[1 + k], 0));  // join
   if (b->C > 0) {
     const int hgrid = std::min((b->C + 7) / 8, 4096);  // one warp per chunk
     k_batch_hubs<<<hgrid, 256, 0, b->stream>>>(b->d_desc.get(), b->d_chunk_off.get(), G, b->C);
@@ -476,7 +547,8 @@ tsgne_status tsgne_batch_create(tsgne_batch** out, const tsgne_config* cfg, int3
   *out = nullptr;
   tsgne_config c;
   if (cfg) c = *cfg; else tsgne_config_default(&c);
-  if (!(c.perplexity > 1.f) || c.k_nn < 0 || c.k_nn > 256 || c.precision != 0 || c.repulsion != 0 || c.ee_iters < 0)
+  if (!(c.perplexity > 1.f) || c.k_nn < 0 || c.k_nn > 256 || c.precision != 0 || c.ee_iters < 0 ||
+      !(c.repulsion == 0 || c.repulsion == 1) || !(c.theta >= 0.f && c.theta <= 1.f) || c.spin_budget_cycles < 1)
     return TSGNE_ERR_INVALID_ARG;
   if (!(tile_warps == 0 || tile_warps == 1 || tile_warps == 2 || tile_warps == 4))
     return TSGNE_ERR_INVALID_ARG;
@@ -520,7 +592,15 @@ const char* tsgne_batch_last_error(const tsgne_batch* b) { return b ? b->err.c_s
 tsgne_status tsgne_batch_add(tsgne_batch* b, int32_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* X,
                              int32_t d, const float* Y0, int32_t ptr_kind, int32_t* id_out) {
   if (!b) return TSGNE_ERR_INVALID_ARG;
+  return tsgne_batch_add_ex(b, n, row_ptr, col_idx, X, d, Y0, ptr_kind, b->cfg.repulsion, id_out);
+}
+
+tsgne_status tsgne_batch_add_ex(tsgne_batch* b, int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                const float* X, int32_t d, const float* Y0, int32_t ptr_kind, int32_t repulsion,
+                                int32_t* id_out) {
+  if (!b) return TSGNE_ERR_INVALID_ARG;
   b->err.clear();
+  if (!(repulsion == 0 || repulsion == 1)) return bfail(b, TSGNE_ERR_INVALID_ARG, "repulsion must be 0 or 1");
   if (n < 2 || d < 1 || !row_ptr || !X || !(ptr_kind == TSGNE_PTR_HOST || ptr_kind == TSGNE_PTR_DEVICE))
     return bfail(b, TSGNE_ERR_INVALID_ARG, "need n >= 2, d >= 1, row_ptr, X and a valid ptr_kind");
   const cudaMemcpyKind kin = ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -574,6 +654,12 @@ tsgne_status tsgne_batch_add(tsgne_batch* b, int32_t n, const int64_t* row_ptr, 
     B_CUDA(b, cudaMemcpyAsync(mb.Y0.get(), Y0, sizeof(float2) * (size_t)n, kin, b->stream));
   } else {
     B_TRY(b, launch_init_Y(n, b->cfg.seed, 1e-4f, mb.Y0.get(), b->stream));
+  }
+  mb.tree = repulsion == 1;
+  if (mb.tree) {
+    B_TRY(b, mb.tb.alloc(n, b->sms, b->stream));
+    mb.tb.spin_budget = b->cfg.spin_budget_cycles;
+    B_TRY(b, mb.Ytree.alloc((size_t)n));
   }
   B_TRY(b, alloc_scratch(mb, b->W));
   B_TRY(b, reset_member_state(mb, b->stream));

@@ -13,7 +13,9 @@
 //      their pairs per iteration reach fill_pairs, enough tile pairs to keep
 //      every SM busy (without aging a stream of small requests could hold
 //      a large one back indefinitely);
-//   3. runs tick_iters iterations of the selected layouts in one batched call;
+//   3. runs tick_iters iterations of the selected layouts in one batched call
+//      (requests of at least tree_min_n points are tree-code members, whose
+//      trees are built and walked concurrently within each iteration);
 //   4. retires the layouts that reached their iterations: the layout is
 //      copied to server-owned host memory and the member's device memory is
 //      freed.
@@ -24,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -49,7 +52,19 @@ struct Req {
   int32_t member = -1;
   int64_t bytes = 0;
   int32_t waited = 0;  // ticks in a row this resident layout was not advanced
+  int32_t repulsion = 0;  // 0 exact, 1 tree code
 };
+
+// Work of one iteration in exact-pass pairs: n^2 / 2 for the exact pass; for
+// the tree code about 250 n log2 n (measured: 300K points take 1/35 of the
+// exact pass's time).  Only orders requests and sizes a tick.
+double iter_pairs(const Req& r) {
+  const double n = (double)r.n;
+  return r.repulsion ? 250.0 * n * std::log2(n > 2.0 ? n : 2.0) : 0.5 * n * n;
+}
+
+// Device bytes of a tree-code member's tree (TreeBufs) and layout copy.
+int64_t tree_bytes(int64_t n) { return 144 * n + 4096; }
 
 }  // namespace
 
@@ -87,14 +102,16 @@ tsgne_status admit(tsgne_server* s) {
   for (const auto& kv : s->reqs) members += kv.second.state == kResident;
   while (!s->queue.empty()) {
     Req& r = s->reqs[s->queue.front()];
-    const int64_t need = tsgne_server_estimate_bytes(r.n, 2 * r.rp[r.n], s->cfg.tile_warps);
+    r.repulsion = (s->cfg.tree_min_n > 0 && r.n >= s->cfg.tree_min_n) ? 1 : 0;
+    const int64_t need =
+        tsgne_server_estimate_bytes(r.n, 2 * r.rp[r.n], s->cfg.tile_warps) + (r.repulsion ? tree_bytes(r.n) : 0);
     if (members > 0 && (members >= s->cfg.max_members || s->used + need > s->cfg.budget_bytes ||
                         need > free_device_bytes(s->cfg.budget_bytes)))
       break;
     int32_t mid = -1;
-    const tsgne_status st = tsgne_batch_add(s->batch, r.n, r.rp.data(), r.col.empty() ? nullptr : r.col.data(),
-                                            r.X.data(), r.d, r.Y0.empty() ? nullptr : r.Y0.data(), TSGNE_PTR_HOST,
-                                            &mid);
+    const tsgne_status st = tsgne_batch_add_ex(s->batch, r.n, r.rp.data(), r.col.empty() ? nullptr : r.col.data(),
+                                               r.X.data(), r.d, r.Y0.empty() ? nullptr : r.Y0.data(), TSGNE_PTR_HOST,
+                                               r.repulsion, &mid);
     if (st != TSGNE_OK) return batch_fail(s, st);
     r.member = mid;
     r.state = kResident;
@@ -125,6 +142,7 @@ void tsgne_server_config_default(tsgne_server_config* c) {
   c->policy = 1;
   c->aging_ticks = 20;
   c->fill_pairs = 4e9;
+  c->tree_min_n = 0;
 }
 
 int64_t tsgne_server_estimate_bytes(int32_t n, int64_t nnz, int32_t tile_warps) {
@@ -151,7 +169,7 @@ tsgne_status tsgne_server_create(tsgne_server** out, const tsgne_server_config* 
   if (scfg) c = *scfg; else tsgne_server_config_default(&c);
   if (c.iters < 1 || c.tick_iters < 1 || c.iters % c.tick_iters != 0 || c.max_members < 1 || c.budget_bytes < 1 ||
       !(c.tile_warps == 1 || c.tile_warps == 2 || c.tile_warps == 4) ||
-      !(c.policy == 0 || c.policy == 1) || c.aging_ticks < 0 || !(c.fill_pairs > 0.0))
+      !(c.policy == 0 || c.policy == 1) || c.aging_ticks < 0 || !(c.fill_pairs > 0.0) || c.tree_min_n < 0)
     return TSGNE_ERR_INVALID_ARG;
   tsgne_server* s = new (std::nothrow) tsgne_server();
   if (!s) return TSGNE_ERR_OOM;
@@ -218,7 +236,7 @@ tsgne_status tsgne_server_tick(tsgne_server* s, int32_t* resident, int32_t* queu
       const Req& r = kv.second;
       const bool overdue = aging > 0 && r.waited >= aging;
       order.push_back({std::make_tuple(overdue ? 0 : 1, overdue ? -r.waited : 0,
-                                       (double)(s->cfg.iters - r.iters) * (double)r.n * (double)r.n),
+                                       (double)(s->cfg.iters - r.iters) * iter_pairs(r)),
                        kv.first});
     }
   std::vector<std::pair<double, int64_t>> res;  // selection order
@@ -230,7 +248,7 @@ tsgne_status tsgne_server_tick(tsgne_server* s, int32_t* resident, int32_t* queu
     double pairs = 0.0;
     for (const auto& w : res) {
       chosen.push_back(w.second);
-      pairs += 0.5 * (double)s->reqs[w.second].n * (double)s->reqs[w.second].n;
+      pairs += iter_pairs(s->reqs[w.second]);
       if (s->cfg.policy == 1 && pairs >= s->cfg.fill_pairs) break;
     }
     for (const auto& w : res) {

@@ -63,11 +63,13 @@ class LayoutServer:
     resident layouts with the least remaining work (remaining iterations x
     n^2) until their pairs per iteration reach ``fill_pairs``; the others
     wait, resident, and a layout left out of ``aging_ticks`` ticks in a row
-    goes first at the next tick (0: no aging).  Both run in the library."""
+    goes first at the next tick (0: no aging).  Both run in the library.
+    Requests of at least ``tree_min_n`` points (0: none) run the tree-code
+    repulsion (the configuration's theta); the others the exact pass."""
 
     def __init__(self, iters: int = 500, tick_iters: int = 10, budget_bytes: int = 80 * 2 ** 30,
                  max_members: int = 256, tile_warps: int = 2, config=None, stream=None, policy: str = "srpt",
-                 fill_pairs: float = 4e9, aging_ticks: int = 20):
+                 fill_pairs: float = 4e9, aging_ticks: int = 20, tree_min_n: int = 0):
         if policy not in ("all", "srpt"):
             raise ValueError("policy must be 'all' or 'srpt'")
         self.iters = iters
@@ -77,7 +79,7 @@ class LayoutServer:
         self.server = Server(self.config, stream=stream, budget_bytes=int(budget_bytes), iters=int(iters),
                              tick_iters=int(tick_iters), max_members=int(max_members), tile_warps=int(tile_warps),
                              policy=1 if policy == "srpt" else 0, fill_pairs=float(fill_pairs),
-                             aging_ticks=int(aging_ticks))
+                             aging_ticks=int(aging_ticks), tree_min_n=int(tree_min_n))
         self.ticks = 0
 
     def serve(self, requests: list[Request], clock=time.perf_counter) -> dict:
@@ -136,12 +138,19 @@ def summarize(done: list[Request], wall: float) -> dict:
     }
 
 
-def serial_baseline(requests: list[Request], iters: int, config=None, clock=time.perf_counter) -> dict:
+def serial_baseline(requests: list[Request], iters: int, config=None, clock=time.perf_counter,
+                    tree_min_n: int = 0) -> dict:
     """The same trace served one layout at a time (first come, first served)
-    with the single-layout context API: the plain-run comparison point."""
+    with the single-layout context API: the plain-run comparison point.
+    Requests of at least ``tree_min_n`` points (0: none) run the tree code,
+    as the server runs them, so both arms compute the same layouts."""
+    import copy
+
     from . import Layout
 
     cfg = config if config is not None else tsgne_config_default()
+    tcfg = copy.copy(cfg)
+    tcfg.repulsion = 1
     pending = sorted(requests, key=lambda r: r.arrival)
     t0 = clock()
     lats = []
@@ -149,7 +158,7 @@ def serial_baseline(requests: list[Request], iters: int, config=None, clock=time
         now = clock() - t0
         if now < r.arrival:
             time.sleep(r.arrival - now)
-        with Layout(cfg) as lay:
+        with Layout(tcfg if (tree_min_n > 0 and r.n >= tree_min_n) else cfg) as lay:
             lay.build_P(r.row_ptr, r.col, r.X)
             lay.init_Y(r.Y0)
             lay.run(iters)

@@ -196,6 +196,74 @@ def test_srpt_runs_short_jobs_first_and_results_stay_exact():
         assert np.array_equal(r.Y, _alone(g, X, Y0, 2, 30))
 
 
+def _tree_alone(g, X, Y0, iters, theta=0.5):
+    with pkg.Layout(repulsion=1, theta=theta) as lay:
+        lay.build_P(g.row_ptr, g.col, X)
+        lay.init_Y(Y0)
+        lay.run(iters)
+        return lay.get_Y()
+
+
+def test_tree_members_equal_the_single_layout_tree_code():
+    """Tree-code members (their trees built and walked on branches of the
+    batched iteration) evolve exactly as the single-layout tree code does,
+    alone and in a mix with exact members and other tree members."""
+    gs = _graphs([5000, 2600, 1200, 7000], seed=100)
+    ref = [_tree_alone(g, X, Y0, 30) for g, X, Y0 in gs]
+    with pkg.Batch(tile_warps=2, repulsion=1, theta=0.5) as b:  # every member a tree member
+        ids = [b.add(g.row_ptr, g.col, X, Y0) for g, X, Y0 in gs]
+        b.run(30)
+        for mid, Yr in zip(ids, ref):
+            assert np.array_equal(b.get_Y(mid)[0], Yr)
+    with pkg.Batch(tile_warps=2, theta=0.5) as b:  # a mix: 0 and 2 tree, 1 and 3 exact
+        ids = [b.add(g.row_ptr, g.col, X, Y0, repulsion=1 - (k % 2)) for k, (g, X, Y0) in enumerate(gs)]
+        b.run(30)
+        assert np.array_equal(b.get_Y(ids[0])[0], ref[0]) and np.array_equal(b.get_Y(ids[2])[0], ref[2])
+        for k in (1, 3):
+            g, X, Y0 = gs[k]
+            assert np.array_equal(b.get_Y(ids[k])[0], _alone(g, X, Y0, 2, 30))
+
+
+def test_serving_with_tree_members_equals_alone():
+    """Requests of at least tree_min_n points are served as tree-code
+    members; every result equals the same request run alone with the same
+    repulsion (the serial comparison runs them the same way)."""
+    gs = _graphs([900, 6000, 2200, 5000], seed=110)
+    reqs = [serve.Request(k, 0.0, g.row_ptr, g.col, X, Y0) for k, (g, X, Y0) in enumerate(gs)]
+    srv = serve.LayoutServer(iters=40, tick_iters=10, tile_warps=2, tree_min_n=4000)
+    try:
+        summary = srv.serve(reqs)
+    finally:
+        srv.close()
+    assert summary["layouts"] == 4
+    for r, (g, X, Y0) in zip(reqs, gs):
+        want = _tree_alone(g, X, Y0, 40) if g.n >= 4000 else _alone(g, X, Y0, 2, 40)
+        assert np.array_equal(r.Y, want)
+
+
+@pytest.mark.parametrize("aging", [0, 2])
+def test_aging_bounds_how_long_a_large_request_waits(aging):
+    """One layout per tick (fill_pairs = 1), four requests of 4 ticks each
+    submitted together.  Shortest remaining work first runs the three small
+    ones first, so without aging the large one has not advanced after 6
+    ticks; with aging_ticks = 2 it is chosen once it has been left out twice,
+    so it has advanced by then.  Results stay those of each request alone."""
+    gs = _graphs([6000, 700, 900, 800], seed=120)
+    with pkg.Server(iters=40, tick_iters=10, tile_warps=2, policy=1, fill_pairs=1.0, aging_ticks=aging) as srv:
+        ids = [srv.submit(g.row_ptr, g.col, X, Y0) for g, X, Y0 in gs]
+        for _ in range(6):
+            srv.tick()
+        big_iters = srv.status(ids[0])[1]
+        if aging == 0:
+            assert big_iters == 0
+        else:
+            assert big_iters >= 10
+        while srv.usage()["resident"] or srv.usage()["queued"]:
+            srv.tick()
+        for i, (g, X, Y0) in zip(ids, gs):
+            assert np.array_equal(srv.result(i), _alone(g, X, Y0, 2, 40))
+
+
 def test_server_cancel_and_bookkeeping():
     """Cancelling a resident and a queued request frees them at once and their
     results report CANCELLED; the others finish exactly as alone, and the

@@ -275,8 +275,11 @@ def test_tree_config_values():
     for bad in (dict(repulsion=2), dict(repulsion=1, theta=-0.1), dict(repulsion=1, theta=1.5)):
         with pytest.raises(pkg.TsgneError):
             pkg.Layout(**bad)
-    with pytest.raises(pkg.TsgneError):
-        pkg.Batch(repulsion=1)
+    for bad in (dict(repulsion=1, precision=1), dict(repulsion=1, theta=1.5)):
+        with pytest.raises(pkg.TsgneError):
+            pkg.Batch(**bad)
+    with pkg.Batch(repulsion=1):  # tree-code members are allowed in batches
+        pass
 
 
 def test_tree_sort_wait_runs_out_and_recovers(record_property):
