@@ -753,18 +753,45 @@ def bench_serving(args, pkg, log_fn=log):
     mk = lambda: [serve.Request(k, float(arr[k]), spec[k][0].row_ptr, spec[k][0].col, spec[k][1],
                                 synth.y_init(spec[k][0].n, seed=k)) for k in range(count)]
     log_fn(f"[bench] serving: {count} requests at {args.serve_rate}/s, n in [{ns.min()}, {ns.max()}]")
+    cfg = pkg.tsgne_config_default(theta=args.tree_theta)
     srv = serve.LayoutServer(iters=args.serve_iters, tick_iters=10, budget_bytes=80 * 2 ** 30, tile_warps=2,
-                             policy="srpt")
+                             policy="srpt", config=cfg, tree_min_n=args.serve_tree_min_n)
     try:
         served = srv.serve(mk())
     finally:
         srv.close()
-    serial = serve.serial_baseline(mk(), args.serve_iters)
+    serial = serve.serial_baseline(mk(), args.serve_iters, config=cfg, tree_min_n=args.serve_tree_min_n)
+    n_tree = int((ns >= args.serve_tree_min_n).sum()) if args.serve_tree_min_n > 0 else 0
+    # capacity: the same requests all present at time 0 (the offered rate no
+    # longer caps the served arm)
+    sat = None
+    if args.serve_saturated:
+        def mk0():
+            rs = mk()
+            for r in rs:
+                r.arrival = 0.0
+            return rs
+        srv = serve.LayoutServer(iters=args.serve_iters, tick_iters=10, budget_bytes=80 * 2 ** 30, tile_warps=2,
+                                 policy="srpt", config=cfg, tree_min_n=args.serve_tree_min_n)
+        try:
+            sat_served = srv.serve(mk0())
+        finally:
+            srv.close()
+        sat_serial = serve.serial_baseline(mk0(), args.serve_iters, config=cfg, tree_min_n=args.serve_tree_min_n)
+        sat = {"note": "every request present at time 0: layouts/s is the capacity of each arm",
+               "served": sat_served, "serial_one_at_a_time": sat_serial,
+               "speedup": sat_served["layouts_per_s"] / sat_serial["layouts_per_s"]}
+        log_fn(f"[bench] serving at saturation: {sat_served['layouts_per_s']:.1f} vs "
+               f"{sat_serial['layouts_per_s']:.1f} layouts/s")
     return {
         "workload": (f"{count} requests, Poisson arrivals at {args.serve_rate}/s, stochastic block models with n "
                      f"log-uniform in [1000, 300000], mean degree 6, 128-d embeddings, {args.serve_iters} "
                      f"iterations each, 80 GB admission budget"),
-        "policy": "continuous batching, shortest remaining work first, 1,024-point tiles (2 warps)",
+        "policy": ("continuous batching, shortest remaining work first with aging (20 ticks), 1,024-point tiles "
+                   "(2 warps)"),
+        "repulsion": (f"tree code (theta {args.tree_theta}) for the {n_tree} requests of at least "
+                      f"{args.serve_tree_min_n} points, exact pass for the others, in both arms"
+                      if args.serve_tree_min_n > 0 else "exact pass for every request"),
         "layouts_per_s": served["layouts_per_s"],
         "p50_s": served["p50_s"],
         "p99_s": served["p99_s"],
@@ -775,6 +802,7 @@ def bench_serving(args, pkg, log_fn=log):
         "max_sustainable_per_s": (served["layouts_per_s"] if served["layouts_per_s"] < 0.9 * args.serve_rate
                                   else None),
         "serial_one_at_a_time": serial,
+        "saturated": sat,
     }
 
 
@@ -916,9 +944,12 @@ def main():
     ap.add_argument("--batch-graphs", type=int, default=256)
     ap.add_argument("--batch-iters", type=int, default=20)
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-tree-min-n", type=int, default=20000,
+                    help="requests of at least this many points use the tree code in both serving arms (0: none)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-iters", type=int, default=500)
+    ap.add_argument("--serve-saturated", type=int, default=1, help="also serve the trace with every request at t=0")
     ap.add_argument("--no-tree", action="store_true", help="skip the tree-code repulsion section")
     ap.add_argument("--no-config0", action="store_true",
                     help="skip the 2,000-node, 1,000-iteration layout against the oracle's whole run")
