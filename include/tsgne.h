@@ -306,6 +306,27 @@ tsgne_status tsgne_batch_add_ex(tsgne_batch* b, int32_t n, const int64_t* row_pt
                                 const float* X, int32_t d, const float* Y0, int32_t ptr_kind, int32_t repulsion,
                                 int32_t* id_out);
 
+/*
+ * tsgne_batch_add_ex in two steps, so that a new member's build overlaps
+ * with the batch's running iterations.  tsgne_batch_prepare builds the
+ * member (structure, P, buffers, state; same arguments as
+ * tsgne_batch_add_ex) on cuda_stream (not NULL, not the batch's stream)
+ * without touching the batch's membership, so it may run on another thread
+ * while tsgne_batch_run runs; its device memory is allocated stream-ordered
+ * on cuda_stream (cudaMallocAsync), which must outlive the member.  It
+ * synchronises cuda_stream; on error *out is NULL and tsgne_last_error(NULL)
+ * on that thread says why.  tsgne_batch_attach adds a prepared member (it
+ * joins at the next run) and consumes the handle; tsgne_batch_discard frees
+ * one that will not be attached.  Calls on one batch other than prepare
+ * stay single-threaded.
+ */
+typedef struct tsgne_member tsgne_member;
+tsgne_status tsgne_batch_prepare(tsgne_batch* b, int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                 const float* X, int32_t d, const float* Y0, int32_t ptr_kind, int32_t repulsion,
+                                 void* cuda_stream, tsgne_member** out);
+tsgne_status tsgne_batch_attach(tsgne_batch* b, tsgne_member* m, int32_t* id_out);
+void tsgne_batch_discard(tsgne_member* m);
+
 /* Removes a member and frees its device memory. */
 tsgne_status tsgne_batch_remove(tsgne_batch* b, int32_t id);
 

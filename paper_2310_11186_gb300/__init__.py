@@ -159,6 +159,9 @@ EXPORTS = {
     "tsgne_batch_last_error": (ctypes.c_char_p, [_p]),
     "tsgne_batch_add": (_st, [_p, _i32, _p, _p, _p, _i32, _p, _i32, ctypes.POINTER(_i32)]),
     "tsgne_batch_add_ex": (_st, [_p, _i32, _p, _p, _p, _i32, _p, _i32, _i32, ctypes.POINTER(_i32)]),
+    "tsgne_batch_prepare": (_st, [_p, _i32, _p, _p, _p, _i32, _p, _i32, _i32, _p, ctypes.POINTER(_p)]),
+    "tsgne_batch_attach": (_st, [_p, _p, ctypes.POINTER(_i32)]),
+    "tsgne_batch_discard": (None, [_p]),
     "tsgne_batch_remove": (_st, [_p, _i32]),
     "tsgne_batch_size": (_st, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "tsgne_batch_run": (_st, [_p, _i32]),

@@ -20,6 +20,11 @@ std::string& last_msg() {
   return m;
 }
 
+cudaStream_t& alloc_stream() {
+  thread_local cudaStream_t s = nullptr;
+  return s;
+}
+
 namespace {
 std::atomic<int64_t> g_dev_bytes{0};
 std::atomic<int64_t> g_dev_limit{0};  // 0: no limit

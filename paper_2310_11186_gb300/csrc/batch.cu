@@ -294,6 +294,10 @@ std::map<std::tuple<int, int, int>, int> g_tile_cache;  // (SMs, log2 pairs, log
 
 using namespace tsgne;
 
+struct tsgne_member {
+  std::unique_ptr<tsgne::Member> m;
+};
+
 struct tsgne_batch {
   tsgne_config cfg{};
   cudaStream_t stream = nullptr;
@@ -313,6 +317,7 @@ struct tsgne_batch {
   std::vector<cudaStream_t> aux;  // branches of the tree members' launches
   std::vector<cudaEvent_t> ev;    // fork event, then one join event per tree member
   ~tsgne_batch() {
+    members.clear();  // stream-ordered frees need their streams
     if (graph) cudaGraphExecDestroy(graph);
     for (auto e : ev) cudaEventDestroy(e);
     for (auto a : aux) cudaStreamDestroy(a);
@@ -536,6 +541,100 @@ tsgne_status reset_member_state(Member& m, cudaStream_t s) {
   return TSGNE_OK;
 }
 
+// A member built from its inputs on stream s: structure, P, hub rows, its
+// layout buffers and state (and its tree, repulsion = 1); everything but the
+// per-tile scratch, which depends on the batch's tile (attach_member).
+// Touches no batch state, so it may run on another thread while the batch
+// runs.  Synchronises s.
+tsgne_status prepare_member(const tsgne_config& cfg, int sms, int32_t n, const int64_t* row_ptr,
+                            const int32_t* col_idx, const float* X, int32_t d, const float* Y0, int32_t ptr_kind,
+                            int32_t repulsion, cudaStream_t s, std::unique_ptr<Member>& out) {
+  auto fail_ = [](tsgne_status st, const char* m) {
+    last_msg() = m;
+    return st;
+  };
+  if (!(repulsion == 0 || repulsion == 1)) return fail_(TSGNE_ERR_INVALID_ARG, "repulsion must be 0 or 1");
+  if (n < 2 || d < 1 || !row_ptr || !X || !(ptr_kind == TSGNE_PTR_HOST || ptr_kind == TSGNE_PTR_DEVICE))
+    return fail_(TSGNE_ERR_INVALID_ARG, "need n >= 2, d >= 1, row_ptr, X and a valid ptr_kind");
+  const cudaMemcpyKind kin = ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  int64_t first = 0, m = 0;
+  if (ptr_kind == TSGNE_PTR_HOST) {
+    first = row_ptr[0];
+    m = row_ptr[n];
+  } else {
+    TS_CUDA(cudaMemcpyAsync(&first, row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaMemcpyAsync(&m, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaStreamSynchronize(s));
+  }
+  if (first != 0 || m < 0) return fail_(TSGNE_ERR_BAD_CSR, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+  if (m > 0 && !col_idx) return fail_(TSGNE_ERR_INVALID_ARG, "col_idx is NULL");
+  auto mem = std::make_unique<Member>();
+  Member& mb = *mem;
+  mb.n = n;
+  DevBuf<int64_t> rp_in, tslot;
+  DevBuf<int32_t> col_in;
+  DevBuf<float> X_in;
+  TS_TRY(rp_in.alloc((size_t)n + 1));
+  TS_TRY(col_in.alloc((size_t)m));
+  TS_TRY(X_in.alloc((size_t)n * d));
+  TS_CUDA(cudaMemcpyAsync(rp_in.get(), row_ptr, sizeof(int64_t) * ((size_t)n + 1), kin, s));
+  if (m > 0) TS_CUDA(cudaMemcpyAsync(col_in.get(), col_idx, sizeof(int32_t) * (size_t)m, kin, s));
+  TS_CUDA(cudaMemcpyAsync(X_in.get(), X, sizeof(float) * (size_t)n * d, kin, s));
+  TS_TRY(mb.sched.alloc(1));
+  TS_CUDA(cudaMemsetAsync(mb.sched.get(), 0, sizeof(Sched), s));
+  TS_TRY(build_neighbor_structure(n, rp_in.get(), col_in.get(), m, cfg.k_nn, mb.rp, mb.col, tslot, &mb.nnz,
+                                    s));
+  TS_TRY(find_heavy_rows(n, mb.rp.get(), mb.hv, s));
+  TS_TRY(mb.P.alloc((size_t)mb.nnz));
+  TS_TRY(build_affinities(n, mb.rp.get(), mb.col.get(), tslot.get(), mb.nnz, X_in.get(), d, cfg.perplexity,
+                            cfg.bisect_tol, cfg.bisect_max_iter, mb.P.get(), mb.sched.get(), s));
+  Sched hs;
+  TS_CUDA(cudaMemcpyAsync(&hs, mb.sched.get(), sizeof(Sched), cudaMemcpyDeviceToHost, s));
+  TS_CUDA(cudaStreamSynchronize(s));
+  if (hs.flags & kFlagNonfiniteP) return fail_(TSGNE_ERR_NONFINITE, "non-finite affinity (check X)");
+  mb.n_pad_max = ((n + kMaxT - 1) / kMaxT) * kMaxT;
+  const size_t np = (size_t)mb.n_pad_max;
+  TS_TRY(mb.Y[0].alloc(np));
+  TS_TRY(mb.Y[1].alloc(np));
+  TS_TRY(mb.upd.alloc(np));
+  TS_TRY(mb.gains.alloc(np));
+  TS_TRY(mb.fsum.alloc(np));
+  TS_TRY(mb.acc.alloc(2 * (size_t)n));
+  TS_CUDA(cudaMemsetAsync(mb.acc.get(), 0, 2 * (size_t)n * sizeof(unsigned long long), s));
+  TS_TRY(mb.Y0.alloc((size_t)n));
+  TS_TRY(launch_fill_sentinel(mb.Y[0].get(), 0, (int)np, s));
+  TS_TRY(launch_fill_sentinel(mb.Y[1].get(), 0, (int)np, s));
+  if (Y0) {
+    TS_CUDA(cudaMemcpyAsync(mb.Y0.get(), Y0, sizeof(float2) * (size_t)n, kin, s));
+  } else {
+    TS_TRY(launch_init_Y(n, cfg.seed, 1e-4f, mb.Y0.get(), s));
+  }
+  mb.tree = repulsion == 1;
+  if (mb.tree) {
+    TS_TRY(mb.tb.alloc(n, sms, s));
+    mb.tb.spin_budget = cfg.spin_budget_cycles;
+    TS_TRY(mb.Ytree.alloc((size_t)n));
+  }
+  TS_TRY(reset_member_state(mb, s));
+  const float ee = cfg.early_exag > 0.f ? cfg.early_exag : 1.f;
+  mb.eta = cfg.learning_rate > 0.f ? cfg.learning_rate : std::fmax((float)n / ee / 4.0f, 50.0f);
+  TS_CUDA(cudaStreamSynchronize(s));
+  out = std::move(mem);
+  return TSGNE_OK;
+}
+
+// Adds a prepared member to the batch (its per-tile scratch for the current
+// tile); the membership changes at the next run.
+tsgne_status attach_member(tsgne_batch* b, std::unique_ptr<Member> mem, int32_t* id_out) {
+  TS_TRY(alloc_scratch(*mem, b->W));
+  mem->id = b->next_id++;
+  if (id_out) *id_out = mem->id;
+  b->members.push_back(std::move(mem));
+  invalidate(b);
+  return TSGNE_OK;
+}
+
+
 bool capturable_stream(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
 
 }  // namespace
@@ -600,78 +699,47 @@ tsgne_status tsgne_batch_add_ex(tsgne_batch* b, int32_t n, const int64_t* row_pt
                                 int32_t* id_out) {
   if (!b) return TSGNE_ERR_INVALID_ARG;
   b->err.clear();
-  if (!(repulsion == 0 || repulsion == 1)) return bfail(b, TSGNE_ERR_INVALID_ARG, "repulsion must be 0 or 1");
-  if (n < 2 || d < 1 || !row_ptr || !X || !(ptr_kind == TSGNE_PTR_HOST || ptr_kind == TSGNE_PTR_DEVICE))
-    return bfail(b, TSGNE_ERR_INVALID_ARG, "need n >= 2, d >= 1, row_ptr, X and a valid ptr_kind");
-  const cudaMemcpyKind kin = ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  int64_t first = 0, m = 0;
-  if (ptr_kind == TSGNE_PTR_HOST) {
-    first = row_ptr[0];
-    m = row_ptr[n];
-  } else {
-    B_CUDA(b, cudaMemcpy(&first, row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost));
-    B_CUDA(b, cudaMemcpy(&m, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost));
-  }
-  if (first != 0 || m < 0) return bfail(b, TSGNE_ERR_BAD_CSR, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
-  if (m > 0 && !col_idx) return bfail(b, TSGNE_ERR_INVALID_ARG, "col_idx is NULL");
-  auto mem = std::make_unique<Member>();
-  Member& mb = *mem;
-  mb.n = n;
-  DevBuf<int64_t> rp_in, tslot;
-  DevBuf<int32_t> col_in;
-  DevBuf<float> X_in;
-  B_TRY(b, rp_in.alloc((size_t)n + 1));
-  B_TRY(b, col_in.alloc((size_t)m));
-  B_TRY(b, X_in.alloc((size_t)n * d));
-  B_CUDA(b, cudaMemcpyAsync(rp_in.get(), row_ptr, sizeof(int64_t) * ((size_t)n + 1), kin, b->stream));
-  if (m > 0) B_CUDA(b, cudaMemcpyAsync(col_in.get(), col_idx, sizeof(int32_t) * (size_t)m, kin, b->stream));
-  B_CUDA(b, cudaMemcpyAsync(X_in.get(), X, sizeof(float) * (size_t)n * d, kin, b->stream));
-  B_TRY(b, mb.sched.alloc(1));
-  B_CUDA(b, cudaMemsetAsync(mb.sched.get(), 0, sizeof(Sched), b->stream));
-  B_TRY(b, build_neighbor_structure(n, rp_in.get(), col_in.get(), m, b->cfg.k_nn, mb.rp, mb.col, tslot, &mb.nnz,
-                                    b->stream));
-  B_TRY(b, find_heavy_rows(n, mb.rp.get(), mb.hv, b->stream));
-  B_TRY(b, mb.P.alloc((size_t)mb.nnz));
-  B_TRY(b, build_affinities(n, mb.rp.get(), mb.col.get(), tslot.get(), mb.nnz, X_in.get(), d, b->cfg.perplexity,
-                            b->cfg.bisect_tol, b->cfg.bisect_max_iter, mb.P.get(), mb.sched.get(), b->stream));
-  Sched hs;
-  B_CUDA(b, cudaMemcpyAsync(&hs, mb.sched.get(), sizeof(Sched), cudaMemcpyDeviceToHost, b->stream));
-  B_CUDA(b, cudaStreamSynchronize(b->stream));
-  if (hs.flags & kFlagNonfiniteP) return bfail(b, TSGNE_ERR_NONFINITE, "non-finite affinity (check X)");
-  mb.n_pad_max = ((n + kMaxT - 1) / kMaxT) * kMaxT;
-  const size_t np = (size_t)mb.n_pad_max;
-  B_TRY(b, mb.Y[0].alloc(np));
-  B_TRY(b, mb.Y[1].alloc(np));
-  B_TRY(b, mb.upd.alloc(np));
-  B_TRY(b, mb.gains.alloc(np));
-  B_TRY(b, mb.fsum.alloc(np));
-  B_TRY(b, mb.acc.alloc(2 * (size_t)n));
-  B_CUDA(b, cudaMemsetAsync(mb.acc.get(), 0, 2 * (size_t)n * sizeof(unsigned long long), b->stream));
-  B_TRY(b, mb.Y0.alloc((size_t)n));
-  B_TRY(b, launch_fill_sentinel(mb.Y[0].get(), 0, (int)np, b->stream));
-  B_TRY(b, launch_fill_sentinel(mb.Y[1].get(), 0, (int)np, b->stream));
-  if (Y0) {
-    B_CUDA(b, cudaMemcpyAsync(mb.Y0.get(), Y0, sizeof(float2) * (size_t)n, kin, b->stream));
-  } else {
-    B_TRY(b, launch_init_Y(n, b->cfg.seed, 1e-4f, mb.Y0.get(), b->stream));
-  }
-  mb.tree = repulsion == 1;
-  if (mb.tree) {
-    B_TRY(b, mb.tb.alloc(n, b->sms, b->stream));
-    mb.tb.spin_budget = b->cfg.spin_budget_cycles;
-    B_TRY(b, mb.Ytree.alloc((size_t)n));
-  }
-  B_TRY(b, alloc_scratch(mb, b->W));
-  B_TRY(b, reset_member_state(mb, b->stream));
-  const float ee = b->cfg.early_exag > 0.f ? b->cfg.early_exag : 1.f;
-  mb.eta = b->cfg.learning_rate > 0.f ? b->cfg.learning_rate : std::fmax((float)n / ee / 4.0f, 50.0f);
-  B_CUDA(b, cudaStreamSynchronize(b->stream));
-  mb.id = b->next_id++;
-  if (id_out) *id_out = mb.id;
-  b->members.push_back(std::move(mem));
-  invalidate(b);
+  last_msg().clear();
+  std::unique_ptr<Member> mem;
+  B_TRY(b, prepare_member(b->cfg, b->sms, n, row_ptr, col_idx, X, d, Y0, ptr_kind, repulsion, b->stream, mem));
+  B_TRY(b, attach_member(b, std::move(mem), id_out));
   return TSGNE_OK;
 }
+
+tsgne_status tsgne_batch_prepare(tsgne_batch* b, int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                 const float* X, int32_t d, const float* Y0, int32_t ptr_kind, int32_t repulsion,
+                                 void* cuda_stream, tsgne_member** out) {
+  if (!b || !out || !cuda_stream) return TSGNE_ERR_INVALID_ARG;
+  *out = nullptr;
+  last_msg().clear();
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  TS_CUDA(cudaGetDevice(&dev));
+  if (dev != b->device) TS_CUDA(cudaSetDevice(b->device));
+  cudaStream_t& as = alloc_stream();
+  const cudaStream_t saved = as;
+  as = s;  // stream-ordered allocations: no device-wide wait in cudaFree
+  std::unique_ptr<Member> mem;
+  const tsgne_status st = prepare_member(b->cfg, b->sms, n, row_ptr, col_idx, X, d, Y0, ptr_kind, repulsion, s, mem);
+  as = saved;
+  if (st != TSGNE_OK) return st;
+  tsgne_member* h = new (std::nothrow) tsgne_member();
+  if (!h) return TSGNE_ERR_OOM;
+  h->m = std::move(mem);
+  *out = h;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_attach(tsgne_batch* b, tsgne_member* m, int32_t* id_out) {
+  if (!b || !m || !m->m) return TSGNE_ERR_INVALID_ARG;
+  b->err.clear();
+  last_msg().clear();
+  B_TRY(b, attach_member(b, std::move(m->m), id_out));
+  delete m;
+  return TSGNE_OK;
+}
+
+void tsgne_batch_discard(tsgne_member* m) { delete m; }
 
 tsgne_status tsgne_batch_remove(tsgne_batch* b, int32_t id) {
   if (!b) return TSGNE_ERR_INVALID_ARG;

@@ -19,6 +19,13 @@
 //   4. retires the layouts that reached their iterations: the layout is
 //      copied to server-owned host memory and the member's device memory is
 //      freed.
+// Admission overlaps with the running iterations: an admitted request is
+// handed to a worker thread that builds its member (structure, P, buffers,
+// tree) with tsgne_batch_prepare on the worker's own stream, with
+// stream-ordered allocations (cudaFree would wait for the whole device),
+// while the tick launches the resident layouts' iterations; prepared members
+// are attached at the start of the next tick.  A tick with nothing resident
+// waits for the first prepared member instead of running nothing.
 // Every member's arithmetic is independent of the others (batch.cu), so a
 // request's layout is the same whatever else is resident.  Cancelling a
 // queued or resident request frees it at once; its result reports
@@ -27,11 +34,14 @@
 
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -39,7 +49,9 @@
 
 namespace {
 
-enum ReqState : int32_t { kQueued = 0, kResident = 1, kDone = 2, kCancelled = 3 };
+// kPreparing (admitted, its member being built by the worker) is reported
+// as queued.
+enum ReqState : int32_t { kQueued = 0, kResident = 1, kDone = 2, kCancelled = 3, kPreparing = 4 };
 
 struct Req {
   int64_t id = 0;
@@ -71,12 +83,23 @@ int64_t tree_bytes(int64_t n) { return 144 * n + 4096; }
 struct tsgne_server {
   tsgne_server_config cfg{};
   tsgne_batch* batch = nullptr;
-  std::map<int64_t, Req> reqs;
+  std::map<int64_t, Req> reqs;  // inserted / erased under mu (the worker looks requests up)
   std::deque<int64_t> queue;
   std::vector<int64_t> finished;  // retired since the last tsgne_server_finished
   int64_t next_id = 1;
   int64_t used = 0;
   std::string msg;
+  // admission worker
+  int device = 0;
+  cudaStream_t prep = nullptr;  // the worker's stream (its members' memory is ordered on it)
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_ready;
+  std::deque<int64_t> prep_q;                                // admitted, to prepare (under mu)
+  std::vector<std::pair<int64_t, tsgne_member*>> ready;      // prepared (under mu)
+  std::vector<std::pair<int64_t, std::string>> failed;      // prepare errors (under mu)
+  bool stop = false;                                         // (under mu)
+  int32_t preparing = 0;                                     // admitted, not yet attached
 };
 
 namespace {
@@ -98,7 +121,7 @@ int64_t free_device_bytes(int64_t fallback) {
 }
 
 tsgne_status admit(tsgne_server* s) {
-  int32_t members = 0;
+  int32_t members = s->preparing;
   for (const auto& kv : s->reqs) members += kv.second.state == kResident;
   while (!s->queue.empty()) {
     Req& r = s->reqs[s->queue.front()];
@@ -108,23 +131,93 @@ tsgne_status admit(tsgne_server* s) {
     if (members > 0 && (members >= s->cfg.max_members || s->used + need > s->cfg.budget_bytes ||
                         need > free_device_bytes(s->cfg.budget_bytes)))
       break;
-    int32_t mid = -1;
-    const tsgne_status st = tsgne_batch_add_ex(s->batch, r.n, r.rp.data(), r.col.empty() ? nullptr : r.col.data(),
-                                               r.X.data(), r.d, r.Y0.empty() ? nullptr : r.Y0.data(), TSGNE_PTR_HOST,
-                                               r.repulsion, &mid);
-    if (st != TSGNE_OK) return batch_fail(s, st);
-    r.member = mid;
-    r.state = kResident;
+    r.state = kPreparing;
     r.bytes = need;
     s->used += need;
     ++members;
+    ++s->preparing;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->prep_q.push_back(r.id);
+    }
+    s->cv_work.notify_one();
     s->queue.pop_front();
+  }
+  return TSGNE_OK;
+}
+
+// Prepares admitted requests' members while the ticks run.
+void worker_main(tsgne_server* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    Req* r = nullptr;
+    int64_t id = 0;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [s] { return s->stop || !s->prep_q.empty(); });
+      if (s->stop) return;
+      id = s->prep_q.front();
+      s->prep_q.pop_front();
+      r = &s->reqs[id];  // not erased while preparing; its inputs are not touched by the ticks
+    }
+    tsgne_member* m = nullptr;
+    const tsgne_status st = tsgne_batch_prepare(s->batch, r->n, r->rp.data(), r->col.empty() ? nullptr : r->col.data(),
+                                                r->X.data(), r->d, r->Y0.empty() ? nullptr : r->Y0.data(),
+                                                TSGNE_PTR_HOST, r->repulsion, s->prep, &m);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (st == TSGNE_OK)
+        s->ready.emplace_back(id, m);
+      else
+        s->failed.emplace_back(id, std::string(tsgne_status_string(st)) + ": " + tsgne_last_error(nullptr));
+    }
+    s->cv_ready.notify_all();
+  }
+}
+
+// Attaches the members the worker has prepared (waiting for one if nothing
+// is resident and some are being prepared).
+tsgne_status attach_ready(tsgne_server* s, bool wait_for_one) {
+  std::vector<std::pair<int64_t, tsgne_member*>> got;
+  std::vector<std::pair<int64_t, std::string>> bad;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (wait_for_one)
+      s->cv_ready.wait(lk, [s] { return !s->ready.empty() || !s->failed.empty(); });
+    got.swap(s->ready);
+    bad.swap(s->failed);
+  }
+  tsgne_status first_err = TSGNE_OK;
+  for (auto& f : bad) {
+    Req& r = s->reqs[f.first];
+    --s->preparing;
+    s->used -= r.bytes;
+    const bool was_cancelled = r.state == kCancelled;
+    r.state = kCancelled;  // its result reports CANCELLED; the tick reports why
+    if (!was_cancelled && first_err == TSGNE_OK) {
+      s->msg = "building request " + std::to_string(f.first) + " failed: " + f.second;
+      first_err = TSGNE_ERR_CUDA;
+    }
+  }
+  for (auto& g : got) {
+    Req& r = s->reqs[g.first];
+    --s->preparing;
+    if (r.state == kCancelled) {  // cancelled while it was being prepared
+      tsgne_batch_discard(g.second);
+      s->used -= r.bytes;
+      continue;
+    }
+    int32_t mid = -1;
+    const tsgne_status st = tsgne_batch_attach(s->batch, g.second, &mid);
+    if (st != TSGNE_OK) return batch_fail(s, st);
+    r.member = mid;
+    r.state = kResident;
     std::vector<int64_t>().swap(r.rp);  // the batch holds its own copy now
     std::vector<int32_t>().swap(r.col);
     std::vector<float>().swap(r.X);
     std::vector<float>().swap(r.Y0);
   }
-  return TSGNE_OK;
+  return first_err;
 }
 
 }  // namespace
@@ -179,13 +272,38 @@ tsgne_status tsgne_server_create(tsgne_server** out, const tsgne_server_config* 
     delete s;
     return st;
   }
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->prep, cudaStreamNonBlocking) != cudaSuccess) {
+    tsgne_batch_destroy(s->batch);
+    delete s;
+    return TSGNE_ERR_CUDA;
+  }
+  try {
+    s->worker = std::thread(worker_main, s);
+  } catch (...) {
+    tsgne_batch_destroy(s->batch);
+    cudaStreamDestroy(s->prep);
+    delete s;
+    return TSGNE_ERR_OOM;
+  }
   *out = s;
   return TSGNE_OK;
 }
 
 void tsgne_server_destroy(tsgne_server* s) {
   if (!s) return;
-  tsgne_batch_destroy(s->batch);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto& g : s->ready) tsgne_batch_discard(g.second);
+  tsgne_batch_destroy(s->batch);  // frees members whose memory is ordered on prep
+  if (s->prep) {
+    cudaStreamSynchronize(s->prep);
+    cudaStreamDestroy(s->prep);
+  }
   delete s;
 }
 
@@ -212,6 +330,7 @@ tsgne_status tsgne_server_submit(tsgne_server* s, int32_t n, const int64_t* row_
     if (m > 0) r.col.assign(col_idx, col_idx + m);
     r.X.assign(X, X + (size_t)n * d);
     if (Y0) r.Y0.assign(Y0, Y0 + 2 * (size_t)n);
+    std::lock_guard<std::mutex> lk(s->mu);
     s->queue.push_back(r.id);
     s->reqs.emplace(r.id, std::move(r));
   } catch (const std::bad_alloc&) {
@@ -224,7 +343,12 @@ tsgne_status tsgne_server_submit(tsgne_server* s, int32_t n, const int64_t* row_
 tsgne_status tsgne_server_tick(tsgne_server* s, int32_t* resident, int32_t* queued, int32_t* retired) {
   if (!s) return TSGNE_ERR_INVALID_ARG;
   {
-    const tsgne_status st = admit(s);
+    tsgne_status st = attach_ready(s, false);
+    if (st == TSGNE_OK) st = admit(s);
+    if (st != TSGNE_OK) return st;
+    int32_t nres = 0;
+    for (const auto& kv : s->reqs) nres += kv.second.state == kResident;
+    if (nres == 0 && s->preparing > 0) st = attach_ready(s, true);  // nothing to run meanwhile
     if (st != TSGNE_OK) return st;
   }
   // (aged first, -ticks waited, remaining work, id): the overdue layouts
@@ -285,7 +409,7 @@ tsgne_status tsgne_server_tick(tsgne_server* s, int32_t* resident, int32_t* queu
   int32_t nres = 0;
   for (const auto& kv : s->reqs) nres += kv.second.state == kResident;
   if (resident) *resident = nres;
-  if (queued) *queued = (int32_t)s->queue.size();
+  if (queued) *queued = (int32_t)s->queue.size() + s->preparing;
   if (retired) *retired = done_now;
   return TSGNE_OK;
 }
@@ -303,7 +427,7 @@ tsgne_status tsgne_server_status(tsgne_server* s, int64_t request_id, int32_t* s
   if (!s) return TSGNE_ERR_INVALID_ARG;
   auto it = s->reqs.find(request_id);
   if (it == s->reqs.end()) return sfail(s, TSGNE_ERR_INVALID_ARG, "unknown request id");
-  if (state) *state = it->second.state;
+  if (state) *state = it->second.state == kPreparing ? kQueued : it->second.state;
   if (iterations) *iterations = it->second.iters;
   return TSGNE_OK;
 }
@@ -314,12 +438,14 @@ tsgne_status tsgne_server_result(tsgne_server* s, int64_t request_id, float* Y_o
   if (it == s->reqs.end()) return sfail(s, TSGNE_ERR_INVALID_ARG, "unknown request id");
   Req& r = it->second;
   if (r.state == kCancelled) {
+    std::lock_guard<std::mutex> lk(s->mu);
     s->reqs.erase(it);
     return sfail(s, TSGNE_ERR_CANCELLED, "the request was cancelled");
   }
   if (r.state != kDone) return sfail(s, TSGNE_ERR_NOT_BUILT, "the request has not finished");
   if (!Y_out) return sfail(s, TSGNE_ERR_INVALID_ARG, "Y_out is NULL");
   std::memcpy(Y_out, r.Y.data(), sizeof(float) * r.Y.size());
+  std::lock_guard<std::mutex> lk(s->mu);
   s->reqs.erase(it);
   return TSGNE_OK;
 }
@@ -331,6 +457,18 @@ tsgne_status tsgne_server_cancel(tsgne_server* s, int64_t request_id) {
   Req& r = it->second;
   if (r.state == kQueued) {
     s->queue.erase(std::find(s->queue.begin(), s->queue.end(), request_id));
+  } else if (r.state == kPreparing) {
+    // the worker may be building it: its member is discarded (and its bytes
+    // returned) when it comes back, or now if the worker has not taken it
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto q = std::find(s->prep_q.begin(), s->prep_q.end(), request_id);
+    if (q != s->prep_q.end()) {
+      s->prep_q.erase(q);
+      --s->preparing;
+      s->used -= r.bytes;
+    }
+    r.state = kCancelled;
+    return TSGNE_OK;
   } else if (r.state == kResident) {
     const tsgne_status st = tsgne_batch_remove(s->batch, r.member);
     if (st != TSGNE_OK) return batch_fail(s, st);
@@ -353,7 +491,7 @@ tsgne_status tsgne_server_usage(tsgne_server* s, int64_t* used_bytes, int32_t* r
   for (const auto& kv : s->reqs) nres += kv.second.state == kResident;
   if (used_bytes) *used_bytes = s->used;
   if (resident) *resident = nres;
-  if (queued) *queued = (int32_t)s->queue.size();
+  if (queued) *queued = (int32_t)s->queue.size() + s->preparing;
   return TSGNE_OK;
 }
 

@@ -104,27 +104,36 @@ tsgne_status cuda_fail(cudaError_t e, const char* what, const char* file, int li
 bool device_bytes_reserve(size_t bytes);
 void device_bytes_release(size_t bytes);
 
-// Owning device buffer released with cudaFree.
+// Stream for stream-ordered allocation by the calling thread (NULL: plain
+// cudaMalloc / cudaFree).  cudaFree waits for the whole device, so a thread
+// that prepares work while kernels of others run (the server's admission
+// worker) allocates with cudaMallocAsync / cudaFreeAsync on its own stream.
+cudaStream_t& alloc_stream();
+
+// Owning device buffer released with cudaFree (or cudaFreeAsync on the
+// stream it was allocated on, if the thread's alloc_stream was set then).
 template <class T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  cudaStream_t as = nullptr;  // stream of a stream-ordered allocation
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), as(o.as) { o.p = nullptr; o.n = 0; o.as = nullptr; }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { reset(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    if (this != &o) { reset(); p = o.p; n = o.n; as = o.as; o.p = nullptr; o.n = 0; o.as = nullptr; }
     return *this;
   }
   ~DevBuf() { reset(); }
   void reset() {
     if (p) {
-      cudaFree(p);
+      if (as) cudaFreeAsync(p, as); else cudaFree(p);
       device_bytes_release(n * sizeof(T));
     }
     p = nullptr;
     n = 0;
+    as = nullptr;
   }
   tsgne_status alloc(size_t count) {
     reset();
@@ -133,7 +142,9 @@ struct DevBuf {
       last_msg() = "device memory limit reached (tsgne_set_device_memory_limit)";
       return TSGNE_ERR_OOM;
     }
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    cudaStream_t s = alloc_stream();
+    cudaError_t e = s ? cudaMallocAsync(&p, count * sizeof(T), s) : cudaMalloc(&p, count * sizeof(T));
+    if (e == cudaSuccess) as = s;
     if (e != cudaSuccess) {
       p = nullptr;
       device_bytes_release(count * sizeof(T));

@@ -264,6 +264,34 @@ def test_aging_bounds_how_long_a_large_request_waits(aging):
             assert np.array_equal(srv.result(i), _alone(g, X, Y0, 2, 40))
 
 
+def test_requests_are_prepared_while_others_run():
+    """A request admitted while another is resident is built by the
+    server's worker thread during the tick (it is reported queued until it
+    is attached at a later tick); one cancelled while it is being prepared
+    is discarded when it comes back and its bytes are returned; every
+    finished result equals its run alone."""
+    gs = _graphs([5000, 1200, 900], seed=130)
+    with pkg.Server(iters=60, tick_iters=10, tile_warps=2) as srv:
+        a = srv.submit(gs[0][0].row_ptr, gs[0][0].col, gs[0][1], gs[0][2])
+        srv.tick()  # nothing resident yet: the tick waits for a's member, then runs it
+        assert srv.status(a) == ("resident", 10)
+        one = srv.usage()["used_bytes"]
+        b = srv.submit(gs[1][0].row_ptr, gs[1][0].col, gs[1][1], gs[1][2])
+        c = srv.submit(gs[2][0].row_ptr, gs[2][0].col, gs[2][1], gs[2][2])
+        srv.tick()  # admits b and c (prepared by the worker) while a advances
+        assert srv.status(a) == ("resident", 20)
+        srv.cancel(c)  # being prepared or prepared, not yet attached
+        while srv.usage()["resident"] or srv.usage()["queued"]:
+            srv.tick()
+        assert srv.usage()["used_bytes"] == 0 and one > 0
+        for rid, (g, X, Y0) in ((a, gs[0]), (b, gs[1])):
+            assert srv.status(rid) == ("done", 60)
+            assert np.array_equal(srv.result(rid), _alone(g, X, Y0, 2, 60))
+        with pytest.raises(pkg.TsgneError) as e:
+            srv.result(c)
+        assert e.value.status == 8
+
+
 def test_server_cancel_and_bookkeeping():
     """Cancelling a resident and a queued request frees them at once and their
     results report CANCELLED; the others finish exactly as alone, and the
