@@ -320,6 +320,15 @@ def run_ours(args):
     build(g.row_ptr, g.col, X)
     build_ms = (time.perf_counter() - tb) * 1e3
     lay.init_Y(Y0)
+    # the library's autotuner over the exact pass's shapes (symmetric 1 or 2
+    # warps x 8 or 16 i-points per lane, or the ordered-pair kernel); the
+    # sharded path keeps the symmetric default
+    tune = None
+    if ws == 1 and not args.no_autotune:
+        chosen, tms = lay.autotune(3)
+        tune = {"chosen": {"tile_warps": chosen[0], "i_per_lane": chosen[1], "symmetric": bool(chosen[2])},
+                "ms_per_pass": tms}
+        log(f"[bench] autotune: {chosen} {tms}")
     shape = lay.repulsion_shape()
     for _ in range(args.warmup):
         step()
@@ -442,6 +451,7 @@ def run_ours(args):
             "parallelism": (f"one layout over {ws} GPUs: repulsion tile pairs divided, int64 forces and Z "
                             f"partials summed by an NCCL all-reduce per iteration" if ws > 1 else "single GPU"),
             "repulsion_launch": shape,
+            "repulsion_autotune": tune,
         },
         "roofline": {
             "bound": "alu",
@@ -705,7 +715,7 @@ def bench_batched(args, pkg, log_fn=log):
     with pkg.Batch() as b:
         for (g, X), Y0 in zip(graphs, Y0s):
             b.add(g.row_ptr, g.col, X, Y0)
-        chosen, tune = b.autotune(trial_iters=2)
+        chosen, tune = b.autotune_shapes(trial_iters=2)
         b.run(2)
         t0 = _t.perf_counter()
         b.run(iters)
@@ -724,7 +734,7 @@ def bench_batched(args, pkg, log_fn=log):
         "workload": (f"{L} stochastic block models, n log-uniform in [500, 50000] (total {n_tot}), mean degree "
                      f"U[4, 12], 5-40 equal blocks, 10% rewired, 64-d embeddings, perplexity 30"),
         "iters_timed": iters,
-        "tile_warps": chosen,
+        "tile_shape": {"tile_warps": chosen[0], "i_per_lane": chosen[1]},
         "autotune_ms_per_iter": tune,
         "batched_ms_per_iter": batched_s * 1e3,
         "one_context_per_graph_ms_per_iter": per_graph * 1e3,
@@ -951,6 +961,7 @@ def main():
     ap.add_argument("--serve-iters", type=int, default=500)
     ap.add_argument("--serve-saturated", type=int, default=1, help="also serve the trace with every request at t=0")
     ap.add_argument("--no-tree", action="store_true", help="skip the tree-code repulsion section")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default shape of the exact pass")
     ap.add_argument("--no-config0", action="store_true",
                     help="skip the 2,000-node, 1,000-iteration layout against the oracle's whole run")
     ap.add_argument("--tree-theta", type=float, default=0.5)

@@ -259,6 +259,24 @@ int64_t tsgne_device_memory_in_use(void);
 tsgne_status tsgne_repulsion_shape(tsgne_ctx* ctx, int32_t* grid, int32_t* block, int32_t* i_per_thread,
                                    int32_t* j_tile, int32_t* j_chunks, int32_t* n_pad);
 
+/*
+ * Shape of the exact repulsion pass (cfg.repulsion = 0), after P is built.
+ * symmetric = 1: each unordered pair once, tile_warps 1 or 2 warps per CTA,
+ * i_per_lane 8 or 16 i-points per lane (the default is chosen from n:
+ * 16 i-points, 2 warps once the tile pairs fill four waves of the grid);
+ * symmetric = 0: the ordered-pair kernel (every ordered pair, partial forces
+ * per j-chunk; FP32 storage only; tile_warps / i_per_lane ignored).  Results
+ * depend on the shape only through the order of FP32 partial sums.
+ * tsgne_autotune times trial_passes repulsion passes of each shape (in the
+ * order (2, 16, 1), (1, 16, 1), (2, 8, 1), (1, 8, 1), (-, -, 0); -1 in
+ * ms_per_pass, 5 floats, for a shape that does not apply), keeps the
+ * fastest and records it per (SM count, ceil log2 n, storage); the layout
+ * and the iteration counter are unchanged.  Synchronises.
+ */
+tsgne_status tsgne_set_repulsion_shape(tsgne_ctx* ctx, int32_t tile_warps, int32_t i_per_lane, int32_t symmetric);
+tsgne_status tsgne_autotune(tsgne_ctx* ctx, int32_t trial_passes, int32_t* tile_warps, int32_t* i_per_lane,
+                            int32_t* symmetric, float* ms_per_pass);
+
 /* Waits for all work of the context; reports a pending NONFINITE layout. */
 tsgne_status tsgne_sync(tsgne_ctx* ctx);
 
@@ -349,6 +367,15 @@ tsgne_status tsgne_batch_set_active(tsgne_batch* b, int32_t id, int32_t active);
 /* Changes the repulsion tile of the batch (members' states are kept). */
 tsgne_status tsgne_batch_set_tile(tsgne_batch* b, int32_t tile_warps);
 
+/* Changes the shape of the batched exact pass: tile_warps 1, 2 or 4 warps
+ * per CTA and i_per_lane 8 or 16 i-points per lane (the tile is 32 x
+ * i_per_lane x tile_warps points; 8 i-points need half the registers, so
+ * twice as many warps per SM are launched).  Members' states are kept; a
+ * member's results depend on the shape (the order of its FP32 partial sums)
+ * but not on the other members. */
+tsgne_status tsgne_batch_set_shape(tsgne_batch* b, int32_t tile_warps, int32_t i_per_lane);
+tsgne_status tsgne_batch_shape(tsgne_batch* b, int32_t* tile_warps, int32_t* i_per_lane);
+
 /* Resets every member to its initial layout, updates 0, gains 1, iteration 0. */
 tsgne_status tsgne_batch_reset(tsgne_batch* b);
 
@@ -360,6 +387,13 @@ tsgne_status tsgne_batch_reset(tsgne_batch* b);
  * the tile; ms_per_iter (may be NULL) gets the 3 measured times.
  */
 tsgne_status tsgne_batch_autotune(tsgne_batch* b, int32_t trial_iters, int32_t* chosen, float* ms_per_iter);
+
+/* The autotuner over every compiled shape of the batched pass: (tile_warps,
+ * i_per_lane) = (1, 16), (2, 16), (4, 16), (1, 8), (2, 8), (4, 8), in that
+ * order in ms_per_iter (6 floats, may be NULL); keeps and caches the fastest
+ * as tsgne_batch_autotune does and resets every member. */
+tsgne_status tsgne_batch_autotune_shapes(tsgne_batch* b, int32_t trial_iters, int32_t* tile_warps,
+                                         int32_t* i_per_lane, float* ms_per_iter);
 
 /* Cached tile for the current membership's key, 0 if none was tuned yet. */
 tsgne_status tsgne_batch_cached_tile(tsgne_batch* b, int32_t* tile_warps);

@@ -147,6 +147,8 @@ EXPORTS = {
     "tsgne_kernel_times": (_st, [_p, _p, _p, _i32, _i32]),
     "tsgne_repulsion_shape": (_st, [_p] + [ctypes.POINTER(_i32)] * 6),
     "tsgne_sync": (_st, [_p]),
+    "tsgne_set_repulsion_shape": (_st, [_p, _i32, _i32, _i32]),
+    "tsgne_autotune": (_st, [_p, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32), _p]),
     "tsgne_repulsion_noalloc": (_st, [_i32, _p, _p, _p, _p]),
     "tsgne_shard_set": (_st, [_p, _i32, _i32]),
     "tsgne_shard_repulsion": (_st, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
@@ -171,6 +173,9 @@ EXPORTS = {
     "tsgne_batch_reset": (_st, [_p]),
     "tsgne_batch_autotune": (_st, [_p, _i32, ctypes.POINTER(_i32), _p]),
     "tsgne_batch_cached_tile": (_st, [_p, ctypes.POINTER(_i32)]),
+    "tsgne_batch_set_shape": (_st, [_p, _i32, _i32]),
+    "tsgne_batch_shape": (_st, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "tsgne_batch_autotune_shapes": (_st, [_p, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _p]),
     "tsgne_shortest_path_embedding": (_st, [_i32, _p, _p, _p, _i32, _i32, _p, _i32, _p]),
     "tsgne_build_P_shortest_path": (_st, [_p, _i32, _p, _p, _p, _i32, _i32, _i32]),
     "tsgne_set_device_memory_limit": (None, [_i64]),
@@ -582,6 +587,22 @@ class Layout:
     def gradient(self, alpha=1.0, out=None):
         return tsgne_gradient(self.ctx, alpha, out)
 
+    REPULSION_SHAPES = ((2, 16, 1), (1, 16, 1), (2, 8, 1), (1, 8, 1), (0, 0, 0))
+
+    def set_repulsion_shape(self, tile_warps: int, i_per_lane: int, symmetric: bool = True):
+        _check(self.ctx, lib().tsgne_set_repulsion_shape(self.ctx, int(tile_warps), int(i_per_lane),
+                                                         1 if symmetric else 0))
+
+    def autotune(self, trial_passes: int = 3):
+        """Times each shape of the exact pass; keeps the fastest.  Returns
+        ((warps, i-points per lane, symmetric), {shape name: ms per pass})."""
+        w, ri, sym = _i32(), _i32(), _i32()
+        ms = np.zeros(5, np.float32)
+        _check(self.ctx, lib().tsgne_autotune(self.ctx, int(trial_passes), ctypes.byref(w), ctypes.byref(ri),
+                                              ctypes.byref(sym), ms.ctypes.data_as(_p)))
+        names = [f"sym_{a}x{b}" if c else "ordered" for a, b, c in self.REPULSION_SHAPES]
+        return (w.value, ri.value, sym.value), {k: float(v) for k, v in zip(names, ms)}
+
     def get_Y(self, out=None):
         return tsgne_get_Y(self.ctx, out)
 
@@ -707,12 +728,31 @@ class Batch:
     def reset(self):
         self._check(lib().tsgne_batch_reset(self.h))
 
+    BATCH_SHAPES = ((1, 16), (2, 16), (4, 16), (1, 8), (2, 8), (4, 8))
+
     def autotune(self, trial_iters: int = 3):
+        """Tile warps only (16 i-points per lane): (chosen warps, {warps: ms})."""
         chosen = _i32()
         ms = np.zeros(3, np.float32)
         self._check(lib().tsgne_batch_autotune(self.h, int(trial_iters), ctypes.byref(chosen),
                                                ms.ctypes.data_as(_p)))
         return chosen.value, dict(zip((1, 2, 4), ms.tolist()))
+
+    def autotune_shapes(self, trial_iters: int = 3):
+        """Every compiled shape: ((warps, i-points per lane), {"WxRI": ms})."""
+        w, ri = _i32(), _i32()
+        ms = np.zeros(6, np.float32)
+        self._check(lib().tsgne_batch_autotune_shapes(self.h, int(trial_iters), ctypes.byref(w), ctypes.byref(ri),
+                                                      ms.ctypes.data_as(_p)))
+        return (w.value, ri.value), {f"{a}x{b}": float(t) for (a, b), t in zip(self.BATCH_SHAPES, ms)}
+
+    def set_shape(self, tile_warps: int, i_per_lane: int):
+        self._check(lib().tsgne_batch_set_shape(self.h, int(tile_warps), int(i_per_lane)))
+
+    def shape(self):
+        w, ri = _i32(), _i32()
+        self._check(lib().tsgne_batch_shape(self.h, ctypes.byref(w), ctypes.byref(ri)))
+        return w.value, ri.value
 
     def cached_tile(self) -> int:
         w = _i32()

@@ -4,6 +4,9 @@
 // structure.cu, affinity.cu, repulsion.cu and iterate.cu.
 #include <atomic>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstddef>
 #include <cstring>
 #include <new>
@@ -115,6 +118,12 @@ struct tsgne_ctx {
   DevBuf<Sched> sched;
   // sharding of the exact repulsion over several contexts (tsgne_shard_*):
   // this context evaluates tile-pair units [shard_u0, shard_u1)
+  // shape of the exact pass: symmetric (shape) or the ordered-pair kernel
+  // (oshape, its per-chunk partial forces in oslots); tsgne_autotune picks
+  bool ordered = false;
+  RepShape oshape;
+  DevBuf<float2> oslots;
+  int n_pad_alloc = 0;
   int shard_rank = 0, shard_world = 1;
   int shard_u0 = 0, shard_u1 = 0;
   bool shard_pending = false;  // a share was enqueued and awaits its finish call
@@ -270,6 +279,17 @@ tsgne_status enqueue_repulsion(tsgne_ctx* ctx, int advance) {
     return prof_end(ctx, &pr);
   }
   TS_TRY(prof_begin(ctx, 0, &pr));
+  if (ctx->ordered) {  // every ordered pair, partial forces per j-chunk
+    TS_TRY(launch_repulsion(ctx->oshape, ctx->n, ctx->Y[ctx->cur].get(), ctx->oslots.get(), ctx->zpart.get(),
+                            ctx->sched.get(), advance, c.early_exag, c.ee_iters, c.momentum0, c.momentum1,
+                            ctx->stream));
+    TS_TRY(prof_end(ctx, &pr));
+    ProfRec pr2;
+    TS_TRY(prof_begin(ctx, 5, &pr2));
+    TS_TRY(launch_reduce_slots(ctx->n, ctx->oslots.get(), ctx->oshape.chunks, ctx->oshape.n_pad, ctx->fsum.get(),
+                               ctx->stream));
+    return prof_end(ctx, &pr2);
+  }
   TS_TRY(launch_repulsion_sym(ctx->shape, ctx->n, ctx->Yread(ctx->cur), ctx->bf16 ? 1 : 0, ctx->facc.get(),
                               ctx->zpart.get(), ctx->sched.get(), advance, c.early_exag, c.ee_iters, c.momentum0,
                               c.momentum1, ctx->stream));
@@ -303,7 +323,7 @@ AttractArgs attract_args(tsgne_ctx* ctx) {
 tsgne_status sync_shadow(tsgne_ctx* ctx, int k) {
   if (!ctx->bf16) return TSGNE_OK;
   return launch_to_bf16(reinterpret_cast<const float*>(ctx->Y[k].get()), ctx->Y16[k].get(),
-                        2 * (int64_t)ctx->shape.n_pad, ctx->stream);
+                        2 * (int64_t)ctx->n_pad_alloc, ctx->stream);
 }
 
 // Attraction + update of every row from the forces of the last repulsion
@@ -406,8 +426,11 @@ tsgne_status ensure_graph(tsgne_ctx* ctx, int start) {
 // Allocates the per-layout buffers for n points (after P is known).
 tsgne_status alloc_layout(tsgne_ctx* ctx) {
   ctx->shape = repulsion_shape_sym(ctx->n, ctx->sms);
+  ctx->ordered = false;
   TS_TRY(repulsion_sym_prepare(ctx->shape));
-  const size_t np = (size_t)ctx->shape.n_pad;
+  // padded for every shape of the exact pass (tiles of 256 ... 2048 points)
+  const size_t np = (size_t)((ctx->n + 2047) / 2048) * 2048;
+  ctx->n_pad_alloc = (int)np;
   TS_TRY(ctx->Y[0].alloc(np));
   TS_TRY(ctx->Y[1].alloc(np));
   TS_TRY(ctx->upd.alloc(np));
@@ -469,8 +492,8 @@ tsgne_status install(tsgne_ctx* ctx, int n, int64_t nnz, DevBuf<int64_t>& rp, De
 }
 
 tsgne_status reset_optimizer(tsgne_ctx* ctx, int32_t t) {
-  TS_TRY(launch_fill2(ctx->upd.get(), ctx->shape.n_pad, 0.f, ctx->stream));
-  TS_TRY(launch_fill2(ctx->gains.get(), ctx->shape.n_pad, 1.f, ctx->stream));
+  TS_TRY(launch_fill2(ctx->upd.get(), ctx->n_pad_alloc, 0.f, ctx->stream));
+  TS_TRY(launch_fill2(ctx->gains.get(), ctx->n_pad_alloc, 1.f, ctx->stream));
   Sched h{};
   h.t = t;
   TS_CUDA(cudaMemcpyAsync(ctx->sched.get(), &h, sizeof(Sched), cudaMemcpyHostToDevice, ctx->stream));
@@ -875,12 +898,121 @@ tsgne_status tsgne_repulsion_shape(tsgne_ctx* ctx, int32_t* grid, int32_t* block
                                    int32_t* j_tile, int32_t* j_chunks, int32_t* n_pad) {
   TS_TRY(enter(ctx));
   if (!ctx->have_P) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P first");
-  if (grid) *grid = ctx->shape.grid;
-  if (block) *block = ctx->shape.block;
-  if (i_per_thread) *i_per_thread = ctx->shape.R;
-  if (j_tile) *j_tile = ctx->shape.jtile;
-  if (j_chunks) *j_chunks = ctx->shape.chunks;
-  if (n_pad) *n_pad = ctx->shape.n_pad;
+  const RepShape& sh = ctx->ordered ? ctx->oshape : ctx->shape;
+  if (grid) *grid = sh.grid;
+  if (block) *block = sh.block;
+  if (i_per_thread) *i_per_thread = sh.R;
+  if (j_tile) *j_tile = sh.jtile;
+  if (j_chunks) *j_chunks = sh.chunks;
+  if (n_pad) *n_pad = sh.n_pad;
+  return TSGNE_OK;
+}
+
+namespace {
+std::mutex g_shape_mu;
+std::map<std::tuple<int, int, int>, int> g_shape_cache;  // (SMs, ceil log2 n, bf16) -> candidate index
+
+// Candidate shapes of the exact pass: (warps per CTA, i-points per lane,
+// symmetric); the last is the ordered-pair kernel (FP32 storage only).
+constexpr int kCtxShapes[5][3] = {{2, 16, 1}, {1, 16, 1}, {2, 8, 1}, {1, 8, 1}, {0, 0, 0}};
+
+tsgne_status set_shape(tsgne_ctx* ctx, int warps, int ri, int symmetric) {
+  if (symmetric) {
+    if (!((warps == 1 || warps == 2) && (ri == 8 || ri == 16))) {
+      last_msg() = "symmetric shapes: warps 1 or 2, i_per_lane 8 or 16";
+      return TSGNE_ERR_INVALID_ARG;
+    }
+    const RepShape sh = repulsion_shape_sym_fixed(ctx->n, ctx->sms, warps, ri);
+    TS_TRY(repulsion_sym_prepare(sh));
+    if ((size_t)sh.units > ctx->zpart.n) TS_TRY(ctx->zpart.alloc((size_t)sh.units));
+    ctx->shape = sh;
+    ctx->ordered = false;
+    ctx->oslots = DevBuf<float2>();
+  } else {
+    if (ctx->bf16) {
+      last_msg() = "the ordered-pair kernel reads FP32 layouts only";
+      return TSGNE_ERR_INVALID_ARG;
+    }
+    const RepShape sh = repulsion_shape(ctx->n, ctx->sms);
+    if (sh.n_pad > ctx->n_pad_alloc) {
+      last_msg() = "ordered shape exceeds the layout padding";
+      return TSGNE_ERR_INVALID_ARG;
+    }
+    TS_TRY(ctx->oslots.alloc((size_t)sh.chunks * (size_t)sh.n_pad));
+    if (repulsion_zpart_count(sh) > ctx->zpart.n) TS_TRY(ctx->zpart.alloc(repulsion_zpart_count(sh)));
+    ctx->oshape = sh;
+    ctx->ordered = true;
+  }
+  ctx->reset_graphs();
+  return TSGNE_OK;
+}
+}  // namespace
+
+tsgne_status tsgne_set_repulsion_shape(tsgne_ctx* ctx, int32_t tile_warps, int32_t i_per_lane, int32_t symmetric) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (!ctx->have_P) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P first");
+  if (ctx->use_tree) return fail(ctx, TSGNE_ERR_INVALID_ARG, "the tree code has no exact-pass shape");
+  if (ctx->shard_pending) return fail(ctx, TSGNE_ERR_INVALID_ARG, "a share is awaiting its finish call");
+  API_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  API_TRY(ctx, set_shape(ctx, tile_warps, i_per_lane, symmetric ? 1 : 0));
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_autotune(tsgne_ctx* ctx, int32_t trial_passes, int32_t* tile_warps, int32_t* i_per_lane,
+                            int32_t* symmetric, float* ms_per_pass) {
+  TS_TRY(enter(ctx));
+  DeviceGuard dg(ctx->device);
+  if (trial_passes < 1) return fail(ctx, TSGNE_ERR_INVALID_ARG, "trial_passes < 1");
+  if (!ctx->have_P || !ctx->have_Y) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P and set Y first");
+  if (ctx->use_tree) return fail(ctx, TSGNE_ERR_INVALID_ARG, "the tree code has no exact-pass shape");
+  if (ctx->shard_pending) return fail(ctx, TSGNE_ERR_INVALID_ARG, "a share is awaiting its finish call");
+  int lg = 0;
+  while ((1LL << lg) < (long long)ctx->n) ++lg;
+  const auto key = std::make_tuple(ctx->sms, lg, ctx->bf16 ? 1 : 0);
+  const bool prof = ctx->cfg.profile != 0;
+  ctx->cfg.profile = 0;  // candidate passes are timed here, not by the kernel profile
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  API_CUDA(ctx, cudaEventCreate(&e0));
+  API_CUDA(ctx, cudaEventCreate(&e1));
+  int best = -1;
+  float best_ms = 0.f;
+  tsgne_status st = TSGNE_OK;
+  for (int k = 0; k < 5 && st == TSGNE_OK; ++k) {
+    const int* c = kCtxShapes[k];
+    float ms = -1.f;
+    if (!c[2] && ctx->bf16) {
+      if (ms_per_pass) ms_per_pass[k] = ms;  // not a candidate with BF16 storage
+      continue;
+    }
+    st = cudaStreamSynchronize(ctx->stream) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
+    if (st == TSGNE_OK) st = set_shape(ctx, c[0], c[1], c[2]);
+    if (st == TSGNE_OK) st = enqueue_repulsion(ctx, 0);  // warm-up; passes do not advance the iteration
+    if (st == TSGNE_OK) st = cudaEventRecord(e0, ctx->stream) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
+    for (int t = 0; t < trial_passes && st == TSGNE_OK; ++t) st = enqueue_repulsion(ctx, 0);
+    if (st == TSGNE_OK) st = cudaEventRecord(e1, ctx->stream) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
+    if (st == TSGNE_OK) st = cudaEventSynchronize(e1) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
+    if (st == TSGNE_OK) st = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
+    if (st != TSGNE_OK) break;
+    ms /= (float)trial_passes;
+    if (ms_per_pass) ms_per_pass[k] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = k;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->cfg.profile = prof ? 1 : 0;
+  if (st != TSGNE_OK) return fail(ctx, st);
+  API_TRY(ctx, set_shape(ctx, kCtxShapes[best][0], kCtxShapes[best][1], kCtxShapes[best][2]));
+  {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shape_cache[key] = best;
+  }
+  if (tile_warps) *tile_warps = kCtxShapes[best][0];
+  if (i_per_lane) *i_per_lane = kCtxShapes[best][1];
+  if (symmetric) *symmetric = kCtxShapes[best][2];
   return TSGNE_OK;
 }
 
@@ -903,7 +1035,8 @@ tsgne_status tsgne_shard_repulsion(tsgne_ctx* ctx, int64_t* units, int32_t* u0, 
   TS_TRY(enter(ctx));
   DeviceGuard dg(ctx->device);
   if (!ctx->have_P || !ctx->have_Y) return fail(ctx, TSGNE_ERR_NOT_BUILT, "build P and set Y first");
-  if (ctx->use_tree) return fail(ctx, TSGNE_ERR_INVALID_ARG, "sharding applies to the exact repulsion");
+  if (ctx->use_tree || ctx->ordered)
+    return fail(ctx, TSGNE_ERR_INVALID_ARG, "sharding applies to the symmetric exact repulsion");
   if (ctx->shard_pending) return fail(ctx, TSGNE_ERR_INVALID_ARG, "the previous share has not been finished");
   const int64_t U = ctx->shape.units;
   ctx->shard_u0 = (int)(U * ctx->shard_rank / ctx->shard_world);

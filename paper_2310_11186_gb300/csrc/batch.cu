@@ -89,11 +89,11 @@ __device__ __forceinline__ int find_owner(const int* __restrict__ off, int count
   return lo;
 }
 
-template <int W>
-__global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
+template <int W, int RI>
+__global__ void __launch_bounds__(W * 32, warps_per_sm(RI) / W)
     k_batch_repulsion(const GraphDesc* __restrict__ descs, const int* __restrict__ unit_off, int members, int U,
                       BatchCtr* ctr) {
-  constexpr int T = W * 32 * kRI;
+  constexpr int T = W * 32 * RI;
   extern __shared__ float4 smem[];
   float4* sj = smem;
   float2* sacc = reinterpret_cast<float2*>(smem + T);
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
       continue;
     }
     const float2* Y = d.Y[d.sched->t & 1];
-    const double zt = sym_unit<W>(Y, d.n, d.acc, d.fscale, a, b, sj, sacc);
+    const double zt = sym_unit<W, RI>(Y, d.n, d.acc, d.fscale, a, b, sj, sacc);
     const double zb = block_sum_d(zt);
     if (tid == 0) d.zunit[u - unit_off[g]] = zb;
     __syncthreads();
@@ -240,27 +240,27 @@ __global__ void __launch_bounds__(256) k_batch_attract(const GraphDesc* __restri
   if (!isfinite(y.x) || !isfinite(y.y)) atomicOr(&d.sched->flags, kFlagNonfiniteY);
 }
 
-template <int W>
-size_t batch_smem() {
-  return (size_t)(W * 32 * kRI) * (sizeof(float4) + sizeof(float2));
-}
+// The compiled shapes of the batched pass: (warps per CTA, i-points per lane).
+constexpr int kShapes[6][2] = {{1, 16}, {2, 16}, {4, 16}, {1, 8}, {2, 8}, {4, 8}};
 
-size_t smem_for(int W) {
-  switch (W) {
-    case 4: return batch_smem<4>();
-    case 2: return batch_smem<2>();
-    default: return batch_smem<1>();
-  }
-}
+size_t smem_for(int W, int RI) { return (size_t)(W * 32 * RI) * (sizeof(float4) + sizeof(float2)); }
 
-tsgne_status prepare_w(int W) {
-  const int bytes = (int)smem_for(W);
-  switch (W) {
-    case 4: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
-    case 2: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
-    default: TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)); break;
-  }
+template <int W, int RI>
+tsgne_status prepare_shape() {
+  TS_CUDA(cudaFuncSetAttribute(k_batch_repulsion<W, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_for(W, RI)));
   return TSGNE_OK;
+}
+
+tsgne_status prepare_w(int W, int RI) {
+  if (RI == 16) {
+    if (W == 4) return prepare_shape<4, 16>();
+    if (W == 2) return prepare_shape<2, 16>();
+    return prepare_shape<1, 16>();
+  }
+  if (W == 4) return prepare_shape<4, 8>();
+  if (W == 2) return prepare_shape<2, 8>();
+  return prepare_shape<1, 8>();
 }
 
 // One member: affinities, layout, optimiser state and repulsion scratch.
@@ -287,7 +287,7 @@ struct Member {
 };
 
 std::mutex g_cache_mu;
-std::map<std::tuple<int, int, int>, int> g_tile_cache;  // (SMs, log2 pairs, log2 members) -> W
+std::map<std::tuple<int, int, int>, int> g_tile_cache;  // (SMs, log2 pairs, log2 members) -> 100 W + RI
 
 }  // namespace
 }  // namespace tsgne
@@ -304,6 +304,7 @@ struct tsgne_batch {
   bool own_stream = false;
   int device = 0, sms = 1;
   int W = 1;
+  int RI = kRI;  // i-points per lane of the batched pass
   std::string err;
   int next_id = 0;
   std::vector<std::unique_ptr<Member>> members;
@@ -344,19 +345,19 @@ tsgne_status bfail(tsgne_batch* b, tsgne_status st, const std::string& msg = std
     if (e__ != cudaSuccess) return bfail((b), cuda_fail(e__, #call, __FILE__, __LINE__));  \
   } while (0)
 
-// The kernels' tile (sym_unit: 32 lanes x kRI i-points x W warps); every
+// The kernels' tile (sym_unit: 32 lanes x RI i-points x W warps); every
 // tile size divides kMaxT, so a member's n_pad never exceeds its buffers'.
-static_assert(kMaxT % (32 * kRI) == 0 && 32 * kRI * 4 <= kMaxT, "tiles of 1, 2 and 4 warps must divide kMaxT");
+static_assert(kMaxT % (32 * 8) == 0 && 32 * 16 * 4 <= kMaxT, "tiles of 1, 2 and 4 warps must divide kMaxT");
 
-void shape_member(Member& m, int W) {
-  const int T = 32 * kRI * W;
+void shape_member(Member& m, int W, int RI) {
+  const int T = 32 * RI * W;
   m.nt = (m.n + T - 1) / T;
   m.n_pad = m.nt * T;
   m.units = m.tree ? 0 : m.nt * (m.nt + 1) / 2;
 }
 
-tsgne_status alloc_scratch(Member& m, int W) {
-  shape_member(m, W);
+tsgne_status alloc_scratch(Member& m, int W, int RI) {
+  shape_member(m, W, RI);
   TS_TRY(m.zunit.alloc((size_t)m.units));
   return TSGNE_OK;
 }
@@ -468,14 +469,23 @@ tsgne_status enqueue_iteration(tsgne_batch* b) {
       TS_CUDA(cudaEventRecord(b->ev[1 + k], s));
     }
   }
-  const int W = b->W;
-  const int slots = b->sms * (kWarpsPerSm / W);
+  const int W = b->W, RI = b->RI;
+  const int slots = b->sms * (warps_per_sm(RI) / W);
   const int grid = b->U < slots ? b->U : slots;
-  const size_t sm = smem_for(W);
-  if (b->U > 0) switch (W) {
-    case 4: k_batch_repulsion<4><<<grid, 128, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
-    case 2: k_batch_repulsion<2><<<grid, 64, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
-    default: k_batch_repulsion<1><<<grid, 32, sm, b->stream>>>(b->d_desc.get(), b->d_unit_off.get(), G, b->U, b->d_ctr.get()); break;
+  const size_t sm = smem_for(W, RI);
+  if (b->U > 0) {
+    const GraphDesc* dd = b->d_desc.get();
+    const int* uo = b->d_unit_off.get();
+    BatchCtr* ctr = b->d_ctr.get();
+    if (RI == 16) {
+      if (W == 4) k_batch_repulsion<4, 16><<<grid, 128, sm, b->stream>>>(dd, uo, G, b->U, ctr);
+      else if (W == 2) k_batch_repulsion<2, 16><<<grid, 64, sm, b->stream>>>(dd, uo, G, b->U, ctr);
+      else k_batch_repulsion<1, 16><<<grid, 32, sm, b->stream>>>(dd, uo, G, b->U, ctr);
+    } else {
+      if (W == 4) k_batch_repulsion<4, 8><<<grid, 128, sm, b->stream>>>(dd, uo, G, b->U, ctr);
+      else if (W == 2) k_batch_repulsion<2, 8><<<grid, 64, sm, b->stream>>>(dd, uo, G, b->U, ctr);
+      else k_batch_repulsion<1, 8><<<grid, 32, sm, b->stream>>>(dd, uo, G, b->U, ctr);
+    }
   }
   // 32 W threads: the same reduction tree as the single-layout pass's last CTA
   k_batch_finalize<<<G, 32 * W, 0, b->stream>>>(b->d_desc.get(), c.early_exag, c.ee_iters, c.momentum0, c.momentum1);
@@ -626,7 +636,7 @@ tsgne_status prepare_member(const tsgne_config& cfg, int sms, int32_t n, const i
 // Adds a prepared member to the batch (its per-tile scratch for the current
 // tile); the membership changes at the next run.
 tsgne_status attach_member(tsgne_batch* b, std::unique_ptr<Member> mem, int32_t* id_out) {
-  TS_TRY(alloc_scratch(*mem, b->W));
+  TS_TRY(alloc_scratch(*mem, b->W, b->RI));
   mem->id = b->next_id++;
   if (id_out) *id_out = mem->id;
   b->members.push_back(std::move(mem));
@@ -669,8 +679,8 @@ tsgne_status tsgne_batch_create(tsgne_batch** out, const tsgne_config* cfg, int3
   if (st == TSGNE_OK) st = b->d_ctr.alloc(1);
   if (st == TSGNE_OK && cudaMemsetAsync(b->d_ctr.get(), 0, sizeof(BatchCtr), b->stream) != cudaSuccess)
     st = TSGNE_ERR_CUDA;
-  for (int w : {1, 2, 4})
-    if (st == TSGNE_OK) st = prepare_w(w);
+  for (const auto& sh : kShapes)
+    if (st == TSGNE_OK) st = prepare_w(sh[0], sh[1]);
   if (st == TSGNE_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = TSGNE_ERR_CUDA;
   if (st != TSGNE_OK) {
     delete b;
@@ -803,15 +813,28 @@ tsgne_status tsgne_batch_set_active(tsgne_batch* b, int32_t id, int32_t active) 
   return TSGNE_OK;
 }
 
+tsgne_status tsgne_batch_set_shape(tsgne_batch* b, int32_t tile_warps, int32_t i_per_lane) {
+  if (!b) return TSGNE_ERR_INVALID_ARG;
+  if (!(tile_warps == 1 || tile_warps == 2 || tile_warps == 4) || !(i_per_lane == 8 || i_per_lane == 16))
+    return bfail(b, TSGNE_ERR_INVALID_ARG, "tile_warps must be 1, 2 or 4 and i_per_lane 8 or 16");
+  if (tile_warps == b->W && i_per_lane == b->RI) return TSGNE_OK;
+  B_CUDA(b, cudaStreamSynchronize(b->stream));
+  for (auto& m : b->members) B_TRY(b, alloc_scratch(*m, tile_warps, i_per_lane));
+  b->W = tile_warps;
+  b->RI = i_per_lane;
+  invalidate(b);
+  return TSGNE_OK;
+}
+
 tsgne_status tsgne_batch_set_tile(tsgne_batch* b, int32_t tile_warps) {
   if (!b) return TSGNE_ERR_INVALID_ARG;
-  if (!(tile_warps == 1 || tile_warps == 2 || tile_warps == 4))
-    return bfail(b, TSGNE_ERR_INVALID_ARG, "tile_warps must be 1, 2 or 4");
-  if (tile_warps == b->W) return TSGNE_OK;
-  B_CUDA(b, cudaStreamSynchronize(b->stream));
-  for (auto& m : b->members) B_TRY(b, alloc_scratch(*m, tile_warps));
-  b->W = tile_warps;
-  invalidate(b);
+  return tsgne_batch_set_shape(b, tile_warps, b->RI);
+}
+
+tsgne_status tsgne_batch_shape(tsgne_batch* b, int32_t* tile_warps, int32_t* i_per_lane) {
+  if (!b) return TSGNE_ERR_INVALID_ARG;
+  if (tile_warps) *tile_warps = b->W;
+  if (i_per_lane) *i_per_lane = b->RI;
   return TSGNE_OK;
 }
 
@@ -822,22 +845,24 @@ tsgne_status tsgne_batch_reset(tsgne_batch* b) {
   return TSGNE_OK;
 }
 
-tsgne_status tsgne_batch_autotune(tsgne_batch* b, int32_t trial_iters, int32_t* chosen, float* ms_per_iter) {
-  if (!b || trial_iters < 1) return TSGNE_ERR_INVALID_ARG;
-  b->err.clear();
-  B_TRY(b, refresh(b));
+namespace {
+// Times trial_iters iterations of each candidate shape from the members'
+// initial state, keeps the fastest (the members are reset to their initial
+// state afterwards) and caches it per (SM count, log2 pairs, log2 members).
+tsgne_status autotune(tsgne_batch* b, int32_t trial_iters, const int (*cand)[2], int ncand, float* ms_out,
+                      int* best_w, int* best_ri) {
+  TS_TRY(refresh(b));
   double pairs = 0.0;
   for (auto& m : b->members) pairs += 0.5 * (double)m->n * (double)m->n;
   const auto key = std::make_tuple(b->sms, (int)std::log2(pairs + 1.0), (int)std::log2((double)b->members.size() + 1.0));
-  int best = -1;
+  int bw = -1, bri = -1;
   float best_ms = 0.f;
-  const int cand[3] = {1, 2, 4};
   cudaEvent_t e0, e1;
-  B_CUDA(b, cudaEventCreate(&e0));
-  B_CUDA(b, cudaEventCreate(&e1));
-  for (int k = 0; k < 3; ++k) {
-    const int w = cand[k];
-    tsgne_status st = tsgne_batch_set_tile(b, w);
+  TS_CUDA(cudaEventCreate(&e0));
+  TS_CUDA(cudaEventCreate(&e1));
+  tsgne_status st = TSGNE_OK;
+  for (int k = 0; k < ncand && st == TSGNE_OK; ++k) {
+    st = tsgne_batch_set_shape(b, cand[k][0], cand[k][1]);
     if (st == TSGNE_OK) st = run_iterations(b, 1, false);  // warm-up
     if (st == TSGNE_OK) st = cudaEventRecord(e0, b->stream) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
     if (st == TSGNE_OK) st = run_iterations(b, trial_iters, false);
@@ -845,27 +870,48 @@ tsgne_status tsgne_batch_autotune(tsgne_batch* b, int32_t trial_iters, int32_t* 
     if (st == TSGNE_OK) st = cudaEventSynchronize(e1) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
     float ms = 0.f;
     if (st == TSGNE_OK) st = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess ? TSGNE_OK : TSGNE_ERR_CUDA;
-    if (st != TSGNE_OK) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return bfail(b, st);
-    }
+    if (st != TSGNE_OK) break;
     ms /= (float)trial_iters;
-    if (ms_per_iter) ms_per_iter[k] = ms;
-    if (best < 0 || ms < best_ms) {
-      best = w;
+    if (ms_out) ms_out[k] = ms;
+    if (bw < 0 || ms < best_ms) {
+      bw = cand[k][0];
+      bri = cand[k][1];
       best_ms = ms;
     }
-    B_TRY(b, tsgne_batch_reset(b));
+    st = tsgne_batch_reset(b);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  B_TRY(b, tsgne_batch_set_tile(b, best));
+  TS_TRY(st);
+  TS_TRY(tsgne_batch_set_shape(b, bw, bri));
   {
     std::lock_guard<std::mutex> lk(g_cache_mu);
-    g_tile_cache[key] = best;
+    g_tile_cache[key] = 100 * bw + bri;
   }
-  if (chosen) *chosen = best;
+  *best_w = bw;
+  *best_ri = bri;
+  return TSGNE_OK;
+}
+}  // namespace
+
+tsgne_status tsgne_batch_autotune(tsgne_batch* b, int32_t trial_iters, int32_t* chosen, float* ms_per_iter) {
+  if (!b || trial_iters < 1) return TSGNE_ERR_INVALID_ARG;
+  b->err.clear();
+  const int cand[3][2] = {{1, 16}, {2, 16}, {4, 16}};
+  int w = 0, ri = 0;
+  B_TRY(b, autotune(b, trial_iters, cand, 3, ms_per_iter, &w, &ri));
+  if (chosen) *chosen = w;
+  return TSGNE_OK;
+}
+
+tsgne_status tsgne_batch_autotune_shapes(tsgne_batch* b, int32_t trial_iters, int32_t* tile_warps,
+                                         int32_t* i_per_lane, float* ms_per_iter) {
+  if (!b || trial_iters < 1) return TSGNE_ERR_INVALID_ARG;
+  b->err.clear();
+  int w = 0, ri = 0;
+  B_TRY(b, autotune(b, trial_iters, kShapes, 6, ms_per_iter, &w, &ri));
+  if (tile_warps) *tile_warps = w;
+  if (i_per_lane) *i_per_lane = ri;
   return TSGNE_OK;
 }
 
@@ -876,7 +922,7 @@ tsgne_status tsgne_batch_cached_tile(tsgne_batch* b, int32_t* tile_warps) {
   const auto key = std::make_tuple(b->sms, (int)std::log2(pairs + 1.0), (int)std::log2((double)b->members.size() + 1.0));
   std::lock_guard<std::mutex> lk(g_cache_mu);
   auto it = g_tile_cache.find(key);
-  *tile_warps = it == g_tile_cache.end() ? 0 : it->second;
+  *tile_warps = it == g_tile_cache.end() ? 0 : it->second / 100;
   return TSGNE_OK;
 }
 

@@ -282,6 +282,22 @@ __global__ void __launch_bounds__(kAttrCta)
   }
 }
 
+// F^r_i = the ordered-pair kernel's partial forces added in chunk order
+// (fixed order: bit-reproducible); one thread per point.
+__global__ void __launch_bounds__(kAttrCta)
+    k_reduce_slots(int n, const float2* __restrict__ part, int slots, int n_pad, float2* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    float fx = 0.f, fy = 0.f;
+    for (int k = 0; k < slots; ++k) {
+      const float2 f = part[(size_t)k * n_pad + i];
+      fx += f.x;
+      fy += f.y;
+    }
+    out[i] = make_float2(fx, fy);
+  }
+}
+
 // Pulls the layout into L2 (one sequential read) so that the neighbour
 // gathers of the attraction hit L2 rather than DRAM sectors.
 __global__ void k_prefetch_l2(const char* __restrict__ p, int64_t bytes) {
@@ -371,6 +387,12 @@ int grid_rows(int64_t n, int per_cta) {
 }  // namespace
 
 int kl_partial_count(int sm_count) { return sm_count * 4; }
+
+tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad, float2* out, cudaStream_t s) {
+  k_reduce_slots<<<grid_rows(n, kAttrCta), kAttrCta, 0, s>>>(n, part, slots, n_pad, out);
+  TS_CUDA(cudaGetLastError());
+  return TSGNE_OK;
+}
 
 tsgne_status launch_fix_forces(int n, unsigned long long* acc, float2* out, cudaStream_t s) {
   const int g = grid_rows(n, kAttrCta);

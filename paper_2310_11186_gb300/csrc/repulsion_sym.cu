@@ -65,12 +65,12 @@ __device__ __forceinline__ void finalize_z(const double* zunit, int units, int n
 // one rank's share when the pass is sharded).  finalize != 0: the last CTA
 // also sets Z and the schedule (one GPU); else the caller sums the unit
 // partials over the ranks and launches k_finalize_z.
-template <int W, class YT>
-__global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
+template <int W, int RI, class YT>
+__global__ void __launch_bounds__(W * 32, warps_per_sm(RI) / W)
     k_repulsion_sym(const YT* __restrict__ Y, int n, int nt, unsigned long long* __restrict__ acc, float fscale,
                     double* __restrict__ zunit, Sched* sched, int u0, int u1, int finalize, int advance, float ee,
                     int ee_iters, float mom0, float mom1) {
-  constexpr int T = W * 32 * kRI;
+  constexpr int T = W * 32 * RI;
   extern __shared__ float4 smem[];
   float4* sj = smem;                                   // T x {-x, -x, -y, -y}
   float2* sacc = reinterpret_cast<float2*>(smem + T);  // T x force accumulator
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSm / W)
       __syncthreads();
       continue;
     }
-    const double zt = sym_unit<W, YT>(Y, n, acc, fscale, a, b, sj, sacc);
+    const double zt = sym_unit<W, RI, YT>(Y, n, acc, fscale, a, b, sj, sacc);
     const double zb = block_sum_d(zt);
     if (tid == 0) zunit[u] = zb;
     __syncthreads();  // shared tiles are rewritten by the next unit
@@ -114,44 +114,82 @@ __global__ void k_finalize_z(const double* __restrict__ zunit, int units, int n,
   finalize_z(zunit, units, n, sched, advance, ee, ee_iters, mom0, mom1);
 }
 
-template <int W>
+template <int W, int RI>
 size_t smem_bytes() {
-  constexpr int T = W * 32 * kRI;
+  constexpr int T = W * 32 * RI;
   return (size_t)T * (sizeof(float4) + sizeof(float2));
 }
 
-template <int W>
+template <int W, int RI>
 tsgne_status prepare() {
-  TS_CUDA(cudaFuncSetAttribute(k_repulsion_sym<W, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_bytes<W>()));
-  TS_CUDA(cudaFuncSetAttribute(k_repulsion_sym<W, bf162>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_bytes<W>()));
+  TS_CUDA(cudaFuncSetAttribute(k_repulsion_sym<W, RI, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_bytes<W, RI>()));
+  TS_CUDA(cudaFuncSetAttribute(k_repulsion_sym<W, RI, bf162>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_bytes<W, RI>()));
   return TSGNE_OK;
 }
 
-template <int W>
+template <int W, int RI>
 tsgne_status launch(const RepShape& sh, int grid, int n, const void* Y, int y_bf16, unsigned long long* acc,
                     double* zunit, Sched* sched, int u0, int u1, int finalize, int advance, float ee, int ee_iters,
                     float mom0, float mom1, cudaStream_t s) {
   const float fs = fix_scale(n);
   if (y_bf16)
-    k_repulsion_sym<W, bf162><<<grid, W * 32, sh.smem, s>>>(static_cast<const bf162*>(Y), n, sh.chunks, acc, fs,
-                                                            zunit, sched, u0, u1, finalize, advance, ee, ee_iters,
-                                                            mom0, mom1);
+    k_repulsion_sym<W, RI, bf162><<<grid, W * 32, sh.smem, s>>>(static_cast<const bf162*>(Y), n, sh.chunks, acc, fs,
+                                                                zunit, sched, u0, u1, finalize, advance, ee,
+                                                                ee_iters, mom0, mom1);
   else
-    k_repulsion_sym<W, float2><<<grid, W * 32, sh.smem, s>>>(static_cast<const float2*>(Y), n, sh.chunks, acc, fs,
-                                                             zunit, sched, u0, u1, finalize, advance, ee, ee_iters,
-                                                             mom0, mom1);
+    k_repulsion_sym<W, RI, float2><<<grid, W * 32, sh.smem, s>>>(static_cast<const float2*>(Y), n, sh.chunks, acc,
+                                                                 fs, zunit, sched, u0, u1, finalize, advance, ee,
+                                                                 ee_iters, mom0, mom1);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }
 
+// The four compiled shapes: (warps per CTA, i-points per lane).
+tsgne_status dispatch(const RepShape& sh, int grid, int n, const void* Y, int y_bf16, unsigned long long* acc,
+                      double* zunit, Sched* sched, int u0, int u1, int finalize, int advance, float ee, int ee_iters,
+                      float mom0, float mom1, cudaStream_t s) {
+  if (sh.warps == 2 && sh.R == 16)
+    return launch<2, 16>(sh, grid, n, Y, y_bf16, acc, zunit, sched, u0, u1, finalize, advance, ee, ee_iters, mom0,
+                         mom1, s);
+  if (sh.warps == 1 && sh.R == 16)
+    return launch<1, 16>(sh, grid, n, Y, y_bf16, acc, zunit, sched, u0, u1, finalize, advance, ee, ee_iters, mom0,
+                         mom1, s);
+  if (sh.warps == 2 && sh.R == 8)
+    return launch<2, 8>(sh, grid, n, Y, y_bf16, acc, zunit, sched, u0, u1, finalize, advance, ee, ee_iters, mom0,
+                        mom1, s);
+  if (sh.warps == 1 && sh.R == 8)
+    return launch<1, 8>(sh, grid, n, Y, y_bf16, acc, zunit, sched, u0, u1, finalize, advance, ee, ee_iters, mom0,
+                        mom1, s);
+  last_msg() = "no compiled repulsion shape with these warps / i-points per lane";
+  return TSGNE_ERR_INVALID_ARG;
+}
+
 }  // namespace
 
-RepShape repulsion_shape_sym(int n, int sm_count) {
+RepShape repulsion_shape_sym_fixed(int n, int sm_count, int W, int RI) {
   RepShape sh;
+  const int T = 32 * RI * W;
+  const int nt = (n + T - 1) / T;
+  sh.warps = W;
+  sh.block = 32 * W;
+  sh.R = RI;
+  sh.jtile = T;
+  sh.chunks = nt;
+  sh.n_pad = nt * T;
+  sh.n_iblk = nt;
+  sh.n_jtiles = nt;
+  sh.units = nt * (nt + 1) / 2;
+  const int slots = sm_count * (warps_per_sm(RI) / W);
+  sh.grid = sh.units < slots ? sh.units : slots;
+  sh.smem = (size_t)T * (sizeof(float4) + sizeof(float2));
+  return sh;
+}
+
+RepShape repulsion_shape_sym(int n, int sm_count) {
   int W = 2;
-  for (int w : {2, 1}) {
+  for (int w : {2, 1}) {  // 2-warp CTAs once the units fill 4 waves of the grid
     W = w;
     const long T = 32L * kRI * w;
     const long nt = (n + T - 1) / T;
@@ -159,35 +197,23 @@ RepShape repulsion_shape_sym(int n, int sm_count) {
     const long slots = (long)sm_count * (kWarpsPerSm / w);
     if (units >= 4 * slots) break;
   }
-  const int T = 32 * kRI * W;
-  const int nt = (n + T - 1) / T;
-  sh.warps = W;
-  sh.block = 32 * W;
-  sh.R = kRI;
-  sh.jtile = T;
-  sh.chunks = nt;
-  sh.n_pad = nt * T;
-  sh.n_iblk = nt;
-  sh.n_jtiles = nt;
-  sh.units = nt * (nt + 1) / 2;
-  const int slots = sm_count * (kWarpsPerSm / W);
-  sh.grid = sh.units < slots ? sh.units : slots;
-  sh.smem = W == 2 ? smem_bytes<2>() : smem_bytes<1>();
-  return sh;
+  return repulsion_shape_sym_fixed(n, sm_count, W, kRI);
 }
 
 tsgne_status repulsion_sym_prepare(const RepShape& sh) {
-  return sh.warps == 2 ? prepare<2>() : prepare<1>();
+  if (sh.warps == 2 && sh.R == 16) return prepare<2, 16>();
+  if (sh.warps == 1 && sh.R == 16) return prepare<1, 16>();
+  if (sh.warps == 2 && sh.R == 8) return prepare<2, 8>();
+  if (sh.warps == 1 && sh.R == 8) return prepare<1, 8>();
+  last_msg() = "no compiled repulsion shape with these warps / i-points per lane";
+  return TSGNE_ERR_INVALID_ARG;
 }
 
 tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, unsigned long long* acc,
                                   double* zpart, Sched* sched, int advance, float ee, int ee_iters, float mom0,
                                   float mom1, cudaStream_t s) {
-  if (sh.warps == 2)
-    return launch<2>(sh, sh.grid, n, Y, y_bf16, acc, zpart, sched, 0, sh.units, 1, advance, ee, ee_iters, mom0, mom1,
-                     s);
-  return launch<1>(sh, sh.grid, n, Y, y_bf16, acc, zpart, sched, 0, sh.units, 1, advance, ee, ee_iters, mom0, mom1,
-                   s);
+  return dispatch(sh, sh.grid, n, Y, y_bf16, acc, zpart, sched, 0, sh.units, 1, advance, ee, ee_iters, mom0, mom1,
+                  s);
 }
 
 tsgne_status launch_repulsion_sym_units(const RepShape& sh, int n, const void* Y, int y_bf16,
@@ -196,8 +222,7 @@ tsgne_status launch_repulsion_sym_units(const RepShape& sh, int n, const void* Y
   if (u1 <= u0) return TSGNE_OK;
   const int slots = sh.grid > 0 ? sh.grid : 1;  // persistent grid of the full pass: one CTA per slot
   const int grid = (u1 - u0) < slots ? (u1 - u0) : slots;
-  if (sh.warps == 2) return launch<2>(sh, grid, n, Y, y_bf16, acc, zpart, sched, u0, u1, 0, 0, 1.f, 0, 0.f, 0.f, s);
-  return launch<1>(sh, grid, n, Y, y_bf16, acc, zpart, sched, u0, u1, 0, 0, 1.f, 0, 0.f, 0.f, s);
+  return dispatch(sh, grid, n, Y, y_bf16, acc, zpart, sched, u0, u1, 0, 0, 1.f, 0, 0.f, 0.f, s);
 }
 
 tsgne_status launch_finalize_z(const RepShape& sh, int n, const double* zpart, Sched* sched, int advance, float ee,

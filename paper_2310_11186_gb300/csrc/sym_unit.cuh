@@ -24,15 +24,19 @@
 
 namespace tsgne {
 
-constexpr int kRI = 16;             // i-points per lane
-constexpr int kH = kRI / 2;         // FP32x2 pairs of i-points per lane
-constexpr int kWarpsPerSm = 8;      // resident warps per SM the grid is sized for
+constexpr int kRI = 16;             // i-points per lane (default shape)
+constexpr int kWarpsPerSm = 8;      // resident warps per SM the grid is sized for (16 i-points per lane)
 constexpr int kGroup = 64;          // j-points per ring group (32 lanes x 2)
+
+// Resident warps per SM the grid is sized for, by i-points per lane: 16
+// i-points need about 200 registers a thread (8 warps), 8 about half.
+__host__ __device__ constexpr int warps_per_sm(int RI) { return RI >= 16 ? 8 : 16; }
 
 __device__ __forceinline__ int row_start(int a, int nt) { return a * nt - (a * (a - 1)) / 2; }
 
 // One j-point against the lane's 8 i-points; acc (x, y) is the running sum
 // of w^2 (y_i - y_j) over i for this j.
+template <int kH>
 __device__ __forceinline__ void ring_pair(const float4 q, float& accx, float& accy, const u64 (&X2)[kH],
                                           const u64 (&Y2)[kH], u64 (&FX)[kH], u64 (&FY)[kH], u64 (&Z2)[kH],
                                           const u64 one2) {
@@ -75,11 +79,13 @@ __device__ __forceinline__ void red_fix(unsigned long long* p, float v, float sc
 // diagonal unit includes the w_ii = 1 terms of its real points).  Every
 // thread of the CTA must call it; it ends with the shared tiles free for reuse
 // only after a __syncthreads by the caller.
-template <int W, class YT = float2>
+template <int W, int RI = kRI, class YT = float2>
 __device__ __forceinline__ double sym_unit(const YT* __restrict__ Y, int n, unsigned long long* __restrict__ acc,
                                            float fscale, int a, int b, float4* sj, float2* sacc) {
-  constexpr int T = W * 32 * kRI;
-  constexpr int G = T / kGroup;  // = 4W groups
+  constexpr int kH = RI / 2;  // FP32x2 pairs of i-points per lane
+  constexpr int T = W * 32 * RI;
+  constexpr int G = T / kGroup;  // = W RI / 2 groups (a power of two)
+  static_assert((G & (G - 1)) == 0, "ring groups are picked modulo G");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u64 one2 = pk(1.f, 1.f);
 
@@ -89,8 +95,8 @@ __device__ __forceinline__ double sym_unit(const YT* __restrict__ Y, int n, unsi
     sj[k] = make_float4(-p.x, -p.x, -p.y, -p.y);
     sacc[k] = make_float2(0.f, 0.f);
   }
-  // i points of tile a: lane holds i = a*T + warp*256 + r*32 + lane, r = 0..7
-  const int ibase = a * T + warp * (32 * kRI) + lane;
+  // i points of tile a: lane holds i = a*T + warp*32*RI + r*32 + lane, r < RI
+  const int ibase = a * T + warp * (32 * RI) + lane;
   u64 X2[kH], Y2[kH], FX[kH], FY[kH], Z2[kH], ZG[kH];
 #pragma unroll
   for (int h = 0; h < kH; ++h) {
@@ -116,8 +122,8 @@ __device__ __forceinline__ double sym_unit(const YT* __restrict__ Y, int n, unsi
         const int jj = (lane + s) & 31;
         const float4 q0 = gj[2 * jj];
         const float4 q1 = gj[2 * jj + 1];
-        ring_pair(q0, ax0, ay0, X2, Y2, FX, FY, Z2, one2);
-        ring_pair(q1, ax1, ay1, X2, Y2, FX, FY, Z2, one2);
+        ring_pair<kH>(q0, ax0, ay0, X2, Y2, FX, FY, Z2, one2);
+        ring_pair<kH>(q1, ax1, ay1, X2, Y2, FX, FY, Z2, one2);
         ax0 = __shfl_sync(0xffffffffu, ax0, src);
         ay0 = __shfl_sync(0xffffffffu, ay0, src);
         ax1 = __shfl_sync(0xffffffffu, ax1, src);

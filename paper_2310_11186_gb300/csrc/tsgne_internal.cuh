@@ -224,6 +224,8 @@ tsgne_status launch_repulsion(const RepShape& sh, int n, const float2* Y, float2
 // repulsion_sym_prepare sets kernel attributes (call it outside stream
 // capture, once per shape).
 RepShape repulsion_shape_sym(int n, int sm_count);
+// A given shape: W warps per CTA (1 or 2), RI i-points per lane (8 or 16).
+RepShape repulsion_shape_sym_fixed(int n, int sm_count, int W, int RI);
 tsgne_status repulsion_sym_prepare(const RepShape& sh);
 // Y is float2[n_pad] (y_bf16 = 0) or __nv_bfloat162[n_pad] (y_bf16 = 1).
 tsgne_status launch_repulsion_sym(const RepShape& sh, int n, const void* Y, int y_bf16, unsigned long long* acc,
@@ -240,6 +242,9 @@ tsgne_status launch_repulsion_sym_units(const RepShape& sh, int n, const void* Y
 // CTA of a whole pass sets them (same block size, so the same bits).
 tsgne_status launch_finalize_z(const RepShape& sh, int n, const double* zpart, Sched* sched, int advance, float ee,
                                int ee_iters, float mom0, float mom1, cudaStream_t s);
+// F^r[i] = sum_k part[k * n_pad + i] for k < slots, in slot order (the
+// ordered-pair kernel's partial forces).
+tsgne_status launch_reduce_slots(int n, const float2* part, int slots, int n_pad, float2* out, cudaStream_t s);
 // F^r[i] = acc[2 i .. 2 i + 1] / fix_scale(n) (one FP32 rounding of the exact
 // integer sum), and the accumulators back to zero for the next pass.
 tsgne_status launch_fix_forces(int n, unsigned long long* acc, float2* out, cudaStream_t s);

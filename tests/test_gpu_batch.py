@@ -109,6 +109,37 @@ def test_members_in_a_mix_equal_alone(tile):
     assert np.array_equal(late_Y, _alone(*late, tile, 15))
 
 
+def test_batch_shapes_and_their_autotuner():
+    """Every shape of the batched pass (1, 2, 4 warps x 8, 16 i-points per
+    lane) keeps members independent (a member alone equals it in a mix at
+    that shape); the shape autotuner picks one of them, resets the members,
+    and a later run equals a fresh batch set to the same shape."""
+    gs = _graphs([2600, 900, 4100], seed=140)
+    for w, ri in ((1, 8), (4, 8), (2, 16)):
+        with pkg.Batch() as b:
+            b.set_shape(w, ri)
+            ids = [b.add(g.row_ptr, g.col, X, Y0) for g, X, Y0 in gs]
+            b.run(12)
+            mixed = [b.get_Y(i)[0] for i in ids]
+        for (g, X, Y0), Ym in zip(gs, mixed):
+            with pkg.Batch() as b1:
+                b1.set_shape(w, ri)
+                i = b1.add(g.row_ptr, g.col, X, Y0)
+                b1.run(12)
+                assert np.array_equal(b1.get_Y(i)[0], Ym)
+    with pkg.Batch() as b:
+        ids = [b.add(g.row_ptr, g.col, X, Y0) for g, X, Y0 in gs]
+        chosen, ms = b.autotune_shapes(trial_iters=2)
+        assert chosen in pkg.Batch.BATCH_SHAPES and b.shape() == chosen and len(ms) == 6
+        b.run(12)
+        tuned = [b.get_Y(i)[0] for i in ids]
+    with pkg.Batch() as b:
+        b.set_shape(*chosen)
+        ids = [b.add(g.row_ptr, g.col, X, Y0) for g, X, Y0 in gs]
+        b.run(12)
+        assert all(np.array_equal(b.get_Y(i)[0], t) for i, t in zip(ids, tuned))
+
+
 def test_remove_keeps_others_unchanged():
     gs = _graphs([900, 1500, 2600], seed=20)
     with pkg.Batch(tile_warps=2) as b:

@@ -195,6 +195,64 @@ def test_Z_in_a_tight_cloud(sigma):
     assert abs(Z - oZ) / oZ < 1e-6, (Z, oZ, abs(Z - oZ) / oZ)
 
 
+@pytest.mark.parametrize("shape", [(2, 16, 1), (1, 16, 1), (2, 8, 1), (1, 8, 1), (0, 0, 0)])
+def test_every_repulsion_shape_matches_the_oracle(shape):
+    """Each shape the autotuner can pick (symmetric with 1 or 2 warps and 8
+    or 16 i-points per lane, or the ordered-pair kernel) gives the oracle's
+    gradient and Z, and 10 iterations stay within the short-horizon bound."""
+    n = 5003
+    g = synth.random_graph(n, 6.0, seed=41)
+    X = synth.block_embedding((np.arange(n) % 7).astype(np.int32), 16, seed=41)
+    rp, col, P = _oracle_case(g, X, 3.0)
+    Y = synth.spread_layout((np.arange(n) % 7).astype(np.int32), scale=20.0, seed=42)
+    oG, oZ = oracle.gradient(n, rp, col, P, Y.astype(np.float64), 1.0)
+    Y0 = synth.y_init(n, seed=43)
+    oY, _, _ = oracle.optimize(n, rp, col, P, Y0, 10)
+    with pkg.Layout() as lay:
+        lay.set_P(rp, col, P.astype(np.float32))
+        lay.set_repulsion_shape(*shape)
+        lay.init_Y(Y)
+        G, Z = lay.gradient(1.0)
+        lay.init_Y(Y0)
+        lay.run(10)
+        Y10 = lay.get_Y()
+    assert abs(Z - oZ) / oZ < 1e-5, (shape, Z, oZ)
+    assert rel_l2(G, oG) < 1e-4, (shape, rel_l2(G, oG))
+    assert rel_l2(Y10, oY) < 1e-4, (shape, rel_l2(Y10, oY))
+
+
+def test_autotune_keeps_the_layout_and_picks_a_shape():
+    g, X = synth.workload("sbm2k")
+    Y0 = synth.y_init(g.n, seed=5)
+    with pkg.Layout() as lay:
+        lay.build_P(g.row_ptr, g.col, X)
+        lay.init_Y(Y0)
+        lay.run(4)
+        Yb, Ub, Gb, itb = lay.get_state()
+        chosen, ms = lay.autotune(2)
+        Ya, Ua, Ga, ita = lay.get_state()
+        assert np.array_equal(Ya, Yb) and np.array_equal(Ua, Ub) and ita == itb == 4
+        assert chosen in pkg.Layout.REPULSION_SHAPES and min(v for v in ms.values() if v > 0) > 0
+        lay.run(6)
+        Yt = lay.get_Y()
+    with pkg.Layout() as ref:  # the same shape set by hand gives the same bits
+        ref.build_P(g.row_ptr, g.col, X)
+        ref.set_repulsion_shape(*chosen)
+        ref.init_Y(Y0)
+        ref.run(4)
+        ref.run(6)
+        assert np.array_equal(ref.get_Y(), Yt)
+    with pkg.Layout() as lay:
+        lay.build_P(g.row_ptr, g.col, X)
+        for bad in ((3, 16, 1), (2, 4, 1)):
+            with pytest.raises(pkg.TsgneError):
+                lay.set_repulsion_shape(*bad)
+    with pkg.Layout(precision=1) as lay:  # the ordered kernel reads FP32 layouts only
+        lay.build_P(g.row_ptr, g.col, X)
+        with pytest.raises(pkg.TsgneError):
+            lay.set_repulsion_shape(0, 0, False)
+
+
 def test_gradient_two_nodes_vanishes():
     """2-node graph: p = q, the KL gradient is 0 for any layout."""
     with pkg.Layout() as lay:
