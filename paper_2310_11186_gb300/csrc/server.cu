@@ -25,7 +25,7 @@
 // stream-ordered allocations (cudaFree would wait for the whole device),
 // while the tick launches the resident layouts' iterations; prepared members
 // are attached at the start of the next tick.  A tick with nothing resident
-// waits for the first prepared member instead of running nothing.
+// waits for all admitted requests to be prepared instead of running nothing.
 // Every member's arithmetic is independent of the others (batch.cu), so a
 // request's layout is the same whatever else is resident.  Cancelling a
 // queued or resident request frees it at once; its result reports
@@ -175,15 +175,19 @@ void worker_main(tsgne_server* s) {
   }
 }
 
-// Attaches the members the worker has prepared (waiting for one if nothing
-// is resident and some are being prepared).
-tsgne_status attach_ready(tsgne_server* s, bool wait_for_one) {
+// Attaches the members the worker has prepared.  wait_all: first wait until
+// every admitted request has come back (used when nothing is resident: the
+// GPU has nothing else to do, and the selection then sees every admitted
+// request, as it would without the worker).
+tsgne_status attach_ready(tsgne_server* s, bool wait_all) {
   std::vector<std::pair<int64_t, tsgne_member*>> got;
   std::vector<std::pair<int64_t, std::string>> bad;
   {
     std::unique_lock<std::mutex> lk(s->mu);
-    if (wait_for_one)
-      s->cv_ready.wait(lk, [s] { return !s->ready.empty() || !s->failed.empty(); });
+    if (wait_all) {
+      const size_t want = (size_t)s->preparing;
+      s->cv_ready.wait(lk, [s, want] { return s->ready.size() + s->failed.size() >= want; });
+    }
     got.swap(s->ready);
     bad.swap(s->failed);
   }
@@ -348,7 +352,7 @@ tsgne_status tsgne_server_tick(tsgne_server* s, int32_t* resident, int32_t* queu
     if (st != TSGNE_OK) return st;
     int32_t nres = 0;
     for (const auto& kv : s->reqs) nres += kv.second.state == kResident;
-    if (nres == 0 && s->preparing > 0) st = attach_ready(s, true);  // nothing to run meanwhile
+    if (nres == 0 && s->preparing > 0) st = attach_ready(s, true);  // nothing else to run meanwhile
     if (st != TSGNE_OK) return st;
   }
   // (aged first, -ticks waited, remaining work, id): the overdue layouts
