@@ -260,13 +260,16 @@ def run_reference(args):
         t = time.perf_counter()
         oracle.repulsion_all(Yd, threads=cores, i0=0, i1=rows)
         times.append(time.perf_counter() - t)
-    s_per_iter = statistics.mean(times) * g.n / rows
-    value = 1.0 / s_per_iter
+    step_s = statistics.mean(times)
+    frac = rows / g.n  # one step is this fraction of an iteration's repulsion
+    value = frac / step_s
     sample = (f"FP64 oracle repulsion rows 0..{rows} of {g.n} (F_rep and row Z sums, {rows * g.n:.3g} pair "
-              f"evaluations per step), rows split over {cores} host threads, extrapolated to all rows")
+              f"evaluations per step = {frac:.4f} of an iteration), rows split over {cores} host threads; "
+              f"value = iterations/s = that fraction / the measured step time")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_per_iter * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "iteration_fraction_per_step": frac, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOAD_DESC if args.workload == WORKLOAD else
                    args.workload, "nodes": g.n, "edges": g.m // 2},
