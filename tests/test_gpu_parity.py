@@ -235,11 +235,11 @@ def test_autotune_keeps_the_layout_and_picks_a_shape():
         assert chosen in pkg.Layout.REPULSION_SHAPES and min(v for v in ms.values() if v > 0) > 0
         lay.run(6)
         Yt = lay.get_Y()
-    with pkg.Layout() as ref:  # the same shape set by hand gives the same bits
+    with pkg.Layout() as ref:  # the same shapes set by hand give the same bits
         ref.build_P(g.row_ptr, g.col, X)
-        ref.set_repulsion_shape(*chosen)
         ref.init_Y(Y0)
-        ref.run(4)
+        ref.run(4)  # the default shape, as before the autotuner ran
+        ref.set_repulsion_shape(*chosen)
         ref.run(6)
         assert np.array_equal(ref.get_Y(), Yt)
     with pkg.Layout() as lay:
