@@ -1,9 +1,11 @@
 // Per-iteration kernels other than the repulsion.
 //
-// k_attract (S3 + S5 fused): the attraction of a CTA's rows (short rows as
-//   G slot partials per row computed by (row, slot) pairs packed over the
-//   CTA; long rows in 1024-entry warp chunks), then one thread per row
-//   applies the update:
+// k_attract (S3, with S5 in update mode): the attraction of a CTA's rows
+//   (short rows as G slot partials per row computed by (row, slot) pairs
+//   packed over the CTA; long rows in 1024-entry warp chunks), then one
+//   thread per row forms the gradient.  It defines the order of every row's
+//   sum; the gradient export runs it, and the update pass runs
+//   k_attract_plan (attract_plan.cu), which gives the same sums.  Per row:
 //     F^a_i = sum_{j in N(i)} p_ij w_ij (y_i - y_j),  w = (1 + ||y_i-y_j||^2)^-1,
 //   add the repulsion forces of the row (chunk order), and form the
 //   gradient of Eq. 5 with P scaled by alpha (early exaggeration):
@@ -21,7 +23,6 @@
 //   fixed-order totals; KL = first + second * ln Z on the host (Eq. 5 with
 //   q = w / Z).
 #include <cmath>
-#include <type_traits>
 #include <vector>
 
 #include "reduce.cuh"
@@ -68,58 +69,24 @@ __device__ __forceinline__ void block_excl_scan(int v, int* off, int* wsum) {
 // the optimiser state and Y_i and writes the update (coalesced).  The sums
 // are the bits G lanes per row with group_sum<G> produce.
 //
-// FUSED (update only): the first heavy_blocks CTAs instead take the chunks
-// of the long rows (more than kHeavyDeg entries), one warp per chunk; the
-// warp that completes a row's last chunk adds the row's chunk sums in chunk
-// order and applies that row's update, and the row CTAs skip long rows.  The
-// hub rows' gathers then overlap with the short rows' in one launch, and the
-// results are bit-identical to the two-launch form (k_attract_heavy, then
-// chunk sums added in the row CTA).
-template <int G, bool EXPORT, class PT, class YT, bool FUSED = false>
+// This is the definition of every row's summation order; the gradient
+// export runs it (rows above kHeavyDeg entries take their chunk sums from
+// k_attract_heavy), and the update pass (k_attract_plan, attract_plan.cu)
+// reproduces the same sums bit for bit on a schedule fixed with P.
+template <int G, bool EXPORT, class PT, class YT>
 __global__ void __launch_bounds__(kAttrCta, 6)
     k_attract(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const PT* __restrict__ P,
               const YT* __restrict__ Ycur, const float2* __restrict__ Ym, float2* __restrict__ Ynext,
               bf162* __restrict__ Ynext16, float2* __restrict__ upd, float2* __restrict__ gains,
               const float2* __restrict__ frep_part, int chunks, int n_pad, Sched* sched, float eta, float min_gain,
-              float alpha_export, float2* __restrict__ g_out, HeavyRows hv, int heavy_blocks) {
+              float alpha_export, float2* __restrict__ g_out, HeavyRows hv) {
   __shared__ float2 spart[kAttrCta][G];
   __shared__ int64_t srp[kAttrCta + 1];
   __shared__ int soff[kAttrCta + 1];
   __shared__ int swarp[kAttrCta / 32];
   __shared__ uint8_t srow[kAttrCta * G];  // (row, slot) pair -> row
   __shared__ int slevels;
-  if (FUSED && (int)blockIdx.x < heavy_blocks) {
-    const int lane = threadIdx.x & 31;
-    const int stride = heavy_blocks * (kAttrCta / 32);
-    for (int c = blockIdx.x * (kAttrCta / 32) + (threadIdx.x >> 5); c < hv.chunks; c += stride) {
-      const int64_t i = hv.chunk_row[c];
-      float ax = 0.f, ay = 0.f;
-      attract_entries<32, PT, YT>(hv.chunk_begin[c], hv.chunk_end[c], col, P, Ycur, i, lane, ld_y(Ycur, i), ax,
-                                  ay);
-      ax = group_sum<32>(ax);
-      ay = group_sum<32>(ay);
-      if (lane == 0) {
-        hv.fa[c] = make_float2(ax, ay);
-        const int h = hv.chunk_heavy[c];
-        const int c0 = hv.chunk_off[h], c1 = hv.chunk_off[h + 1];
-        // acquire-release arrival: the chunk sums stored before it are
-        // visible to the last chunk's warp after its own (no separate fences)
-        if (atom_add_acq_rel_u32(&hv.arrivals[h], 1u) == (unsigned)(c1 - c0 - 1)) {  // last chunk of the row
-          hv.arrivals[h] = 0u;
-          float sx = 0.f, sy = 0.f;
-          for (int q = c0; q < c1; ++q) {
-            const float2 f = __ldcg(hv.fa + q);
-            sx += f.x;
-            sy += f.y;
-          }
-          finish_row<false>(i, make_float2(sx, sy), frep_part, chunks, n_pad, sched, 0.f, nullptr, Ym, Ynext,
-                            Ynext16, upd, gains, eta, min_gain);
-        }
-      }
-    }
-    return;
-  }
-  const int64_t row0 = (int64_t)(blockIdx.x - (FUSED ? heavy_blocks : 0)) * kAttrCta;
+  const int64_t row0 = (int64_t)blockIdx.x * kAttrCta;
   const int tid = threadIdx.x;
   for (int t = tid; t <= kAttrCta; t += kAttrCta) srp[t] = row0 + t <= n ? rp[row0 + t] : 0;
   if (tid == 0) slevels = 0;
@@ -135,7 +102,7 @@ __global__ void __launch_bounds__(kAttrCta, 6)
     if (d <= kHeavyDeg) {
       ns = (int)(d < G ? d : G);
       if (d > 0) atomicMax(&slevels, (int)((d + G - 1) / G));  // entries per slot, at most
-    } else if (!FUSED) {  // chunk sums from k_attract_heavy, in chunk order
+    } else {  // chunk sums from k_attract_heavy, in chunk order
       int lo = 0, hi = hv.count - 1;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -206,7 +173,6 @@ __global__ void __launch_bounds__(kAttrCta, 6)
     }
   __syncthreads();
   if (i >= n) return;
-  if (FUSED && srp[tid + 1] - srp[tid] > kHeavyDeg) return;  // updated by its last chunk
   // (3) the row's sum in the order of group_sum<G> (xor butterfly: slot l
   // plus slot l ^ o for o = G/2, ..., 1), then the update
   static_assert(G == 8, "the butterfly below is written out for 8 slots");
@@ -492,25 +458,10 @@ namespace {
 
 template <bool EXPORT, class PT, class YT>
 tsgne_status attract_t(const AttractArgs& a, float alpha, float2* g, cudaStream_t s) {
-  const int grid = grid_rows(a.n, kAttrCta);
-  // FP32 storage: hub chunks and short rows in one launch.  The BF16 variant
-  // of the fused kernel spills under the 6-CTA register cap and runs slower
-  // than two launches, so BF16 keeps k_attract_heavy first.
-  constexpr bool kFuse = std::is_same<PT, float>::value;
-  if (!EXPORT && !kFuse && a.hv.chunks > 0) TS_TRY(launch_attract_heavy(a, s));
-  if (!EXPORT && kFuse && a.hv.chunks > 0) {
-    int heavy = (a.hv.chunks + kAttrCta / 32 - 1) / (kAttrCta / 32);
-    if (heavy > 4096) heavy = 4096;
-    k_attract<kG, false, PT, YT, true><<<heavy + grid, kAttrCta, 0, s>>>(
-        a.n, a.rp, a.col, static_cast<const PT*>(a.P), static_cast<const YT*>(a.Yr), a.Ym, a.Ynext,
-        static_cast<bf162*>(a.Ynext16), a.upd, a.gains, a.frep, a.chunks, a.n_pad, a.sched, a.eta, a.min_gain, alpha,
-        g, a.hv, heavy);
-  } else {
-    k_attract<kG, EXPORT, PT, YT><<<grid, kAttrCta, 0, s>>>(
-        a.n, a.rp, a.col, static_cast<const PT*>(a.P), static_cast<const YT*>(a.Yr), a.Ym, a.Ynext,
-        static_cast<bf162*>(a.Ynext16), a.upd, a.gains, a.frep, a.chunks, a.n_pad, a.sched, a.eta, a.min_gain, alpha,
-        g, a.hv, 0);
-  }
+  k_attract<kG, EXPORT, PT, YT><<<grid_rows(a.n, kAttrCta), kAttrCta, 0, s>>>(
+      a.n, a.rp, a.col, static_cast<const PT*>(a.P), static_cast<const YT*>(a.Yr), a.Ym, a.Ynext,
+      static_cast<bf162*>(a.Ynext16), a.upd, a.gains, a.frep, a.chunks, a.n_pad, a.sched, a.eta, a.min_gain, alpha,
+      g, a.hv);
   TS_CUDA(cudaGetLastError());
   return TSGNE_OK;
 }
@@ -533,8 +484,6 @@ tsgne_status heavy_t(const AttractArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
-
-tsgne_status launch_attract_update(const AttractArgs& a, cudaStream_t s) { return attract_dispatch<false>(a, 0.f, nullptr, s); }
 
 tsgne_status launch_attract_heavy(const AttractArgs& a, cudaStream_t s) {
   if (a.hv.chunks <= 0) return TSGNE_OK;

@@ -320,7 +320,6 @@ struct AttractArgs {
   float min_gain = 0.f;
   HeavyRows hv;
 };
-tsgne_status launch_attract_update(const AttractArgs& a, cudaStream_t s);
 // Schedule of the attraction + update pass fixed when P is installed
 // (attract_plan.cu): rows of at most 32 entries in CTAs of 256 consecutive
 // rows, rows of 33..128 entries in CTAs of 64 listed rows, their slot chains
@@ -363,7 +362,7 @@ struct AttractPlan {
 tsgne_status build_attract_plan(int n, const int64_t* rp, const int32_t* col, const float* P,
                                 const __nv_bfloat16* P16, const HeavyStore& hs, AttractPlan& plan, cudaStream_t s);
 // The attraction + update pass on the plan (the update mode of
-// launch_attract_update: same results, bit for bit).
+// k_attract: same results, bit for bit).
 tsgne_status launch_attract_plan(const AttractArgs& a, const PlanView& pv, cudaStream_t s);
 // Gradient export g = 4 (alpha F^a - F^r / Z) without state change.
 tsgne_status launch_gradient(const AttractArgs& a, float alpha, float2* g, cudaStream_t s);
