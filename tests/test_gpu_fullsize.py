@@ -92,3 +92,35 @@ def test_full_size_rmat21(record_property):
     oG = oracle.gradient_rows(g.n, orp, ocol, oP, Y, 12.0, Z, rows)
     record_property("grad_rel_l2_sample", rel_l2(G[rows], oG))
     assert rel_l2(G[rows], oG) < 1e-4, rel_l2(G[rows], oG)
+
+
+def test_full_size_batched_config2(record_property):
+    """The batched workload as bench.py runs it: 256 block models (500 to
+    50,000 nodes, 2.8M nodes in all) in one batch, its shape chosen by the
+    shape autotuner; after one iteration the largest member and four others
+    equal the oracle's optimiser within the short-horizon bound (1e-4
+    relative L2), and every sampled member equals itself run alone."""
+    graphs = synth.sbm_mixed_batch(256, 500, 50_000, 4, 12, 5, 40, 64, seed=0)
+    Y0s = [synth.y_init(g.n, seed=k) for k, (g, _) in enumerate(graphs)]
+    with pkg.Batch() as b:
+        ids = [b.add(g.row_ptr, g.col, X, Y0) for (g, X), Y0 in zip(graphs, Y0s)]
+        shape, _ = b.autotune_shapes(trial_iters=1)
+        b.run(1)
+        sizes = np.array([g.n for g, _ in graphs])
+        rng = np.random.default_rng(7)
+        pick = [int(np.argmax(sizes))] + rng.choice(len(graphs), 4, replace=False).tolist()
+        got = {k: b.get_Y(ids[k]) for k in pick}
+    for k in pick:
+        g, X = graphs[k]
+        Y, it = got[k]
+        assert it == 1
+        rp, col, P = oracle.build_P(g.n, g.row_ptr, g.col, X, 30.0)
+        oY, _, _ = oracle.optimize(g.n, rp, col, P, Y0s[k], 1)
+        err = rel_l2(Y, oY)
+        record_property(f"member{k}_n{g.n}_rel_l2", err)
+        assert err < 1e-4, (k, g.n, err)
+        with pkg.Batch() as b1:
+            b1.set_shape(*shape)
+            i = b1.add(g.row_ptr, g.col, X, Y0s[k])
+            b1.run(1)
+            assert np.array_equal(b1.get_Y(i)[0], Y)
