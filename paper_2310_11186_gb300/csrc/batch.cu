@@ -138,6 +138,7 @@ __global__ void k_batch_finalize(const GraphDesc* __restrict__ descs, float ee, 
   if (threadIdx.x == 0) {
     Sched* s = d.sched;
     s->Z = total - (double)d.n;
+    s->inv_z = (float)(1.0 / s->Z);
     const int t = s->t;
     s->alpha = t < ee_iters ? ee : 1.0f;
     s->mu = t < ee_iters ? mom0 : mom1;
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(256) k_batch_attract(const GraphDesc* __restri
   if (!valid || lane != 0) return;
   const Sched* s = d.sched;
   const float2 fr = d.fsum[i];
-  const float invZ = (float)(1.0 / s->Z);
+  const float invZ = s->inv_z;
   const float gx = 4.0f * (s->alpha * ax - fr.x * invZ);
   const float gy = 4.0f * (s->alpha * ay - fr.y * invZ);
   float2 u = d.upd[i], gn = d.gains[i];

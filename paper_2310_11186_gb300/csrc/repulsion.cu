@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(BLOCK, kCtasPerSm)
     const double total = sum_partials(zpart, gridDim.x);
     if (tid == 0) {
       sched->Z = total - (double)n;
+      sched->inv_z = (float)(1.0 / sched->Z);
       const int t = sched->t;
       sched->alpha = t < ee_iters ? ee : 1.0f;
       sched->mu = t < ee_iters ? mom0 : mom1;

@@ -54,6 +54,7 @@ __device__ __forceinline__ void finalize_z(const double* zunit, int units, int n
   if (threadIdx.x == 0) {
     sched->work_next = 0u;
     sched->Z = total - (double)n;
+    sched->inv_z = (float)(1.0 / sched->Z);
     const int t = sched->t;
     sched->alpha = t < ee_iters ? ee : 1.0f;
     sched->mu = t < ee_iters ? mom0 : mom1;

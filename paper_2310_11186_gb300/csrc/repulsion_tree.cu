@@ -665,8 +665,10 @@ __global__ void __launch_bounds__(32 * kWalkWarps, 4)
       st->next_group = 0u;
       if (stalled)
         atomicOr(&sched->flags, kFlagWaitTimeout);
-      else
+      else {
         sched->Z = total;
+        sched->inv_z = (float)(1.0 / total);
+      }
       const int t = sched->t;
       sched->alpha = t < ee_iters ? ee : 1.0f;
       sched->mu = t < ee_iters ? mom0 : mom1;

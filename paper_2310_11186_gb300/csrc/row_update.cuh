@@ -156,7 +156,7 @@ __device__ __forceinline__ void finish_row(int64_t i, float2 fa, const float2* _
     rx += f.x;
     ry += f.y;
   }
-  const float invZ = (float)(1.0 / sched->Z);
+  const float invZ = sched->inv_z;
   const float alpha = EXPORT ? alpha_export : sched->alpha;
   const float gx = 4.0f * (alpha * fa.x - rx * invZ);
   const float gy = 4.0f * (alpha * fa.y - ry * invZ);

@@ -40,6 +40,7 @@ struct Sched {
   uint32_t rep_done;   // last-CTA counter of the repulsion pass
   uint32_t red_done;   // last-CTA counter of the generic reductions
   uint32_t work_next;  // work-queue head of the symmetric repulsion pass
+  float inv_z;         // (float)(1 / Z), written with Z: the rows read it instead of dividing in FP64
   double red[4];       // results of the generic reductions
 };
 
