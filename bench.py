@@ -976,6 +976,7 @@ def main():
     ap.add_argument("--rmat-scale", type=int, default=21)
     ap.add_argument("--only-rmat", action="store_true", help="run only the R-MAT section (profiling)")
     ap.add_argument("--only-tree", action="store_true", help="run only the tree-code section (profiling)")
+    ap.add_argument("--only-batched", action="store_true", help="run only the batched section (profiling)")
     ap.add_argument("--scale", action="store_true", help="also lay out 3M- and 4M-node graphs with the tree code (a few minutes)")
     ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOAD,
                     help="zipf300k is the benchmark; the others are smaller cases for profiling")
@@ -993,6 +994,16 @@ def main():
         torch.cuda.set_device(0)
         pbuild.build()
         print(json.dumps({"rmat": bench_rmat(args, pkg)}), flush=True)
+        return 0
+    if args.only_batched:
+        import torch
+
+        from paper_2310_11186_gb300 import build as pbuild
+        import paper_2310_11186_gb300 as pkg
+
+        torch.cuda.set_device(0)
+        pbuild.build()
+        print(json.dumps({"batched": bench_batched(args, pkg)}), flush=True)
         return 0
     if args.only_tree:
         import torch

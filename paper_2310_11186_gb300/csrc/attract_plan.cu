@@ -32,7 +32,9 @@
 // still running at level k are a prefix [0, cnt[k]) of the list and entry k
 // of chain q sits at ent + off[k] + q in copies of col and P made in that
 // order: every level's loads are coalesced, and each thread issues the loads
-// of all entries of its chain before the first gather returns.
+// of all entries of its chain before the first gather returns.  A CTA starts
+// by prefetching into L2 the streams it reads (chain codes, col and P in chain
+// order, its rows' optimiser state; a hub chunk's col and P).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -52,6 +54,17 @@ constexpr int kSlotsShort = 8;
 constexpr int kSlotsMed = 32;
 static_assert(kShortRowsPerCta * kSlotsShort == kMedRowsPerCta * kSlotsMed, "one shared partial array");
 constexpr int kPartials = kShortRowsPerCta * kSlotsShort;  // 2048
+
+// L2 prefetch of the 128-byte lines of [lo, hi), spread over nt threads; every
+// address touched lies inside the range.  A hint: the CTA's streams (chain
+// codes, col and P in chain order, the rows' optimiser state; a hub chunk's
+// col and P) are on their way from DRAM while its first gathers run.
+template <class T>
+__device__ __forceinline__ void prefetch_range(const T* lo, const T* hi, int t, int nt) {
+  const uintptr_t a = (uintptr_t)lo, b = (uintptr_t)hi;
+  for (uintptr_t q = (a & ~(uintptr_t)127) + (uintptr_t)t * 128; q < b; q += (uintptr_t)nt * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(q < a ? a : q));
+}
 
 // One entry's term of F^a, as attract_entries adds it.
 template <class PT, class YT>
@@ -83,6 +96,8 @@ __global__ void __launch_bounds__(kPlanThreads, 6)
       if (!TS_IN(c, 0, hv.chunks, dbg)) continue;
       const int64_t i = hv.chunk_row[c];
       if (!TS_IN(i, 0, a.n, dbg)) continue;
+      prefetch_range(a.col + hv.chunk_begin[c], a.col + hv.chunk_end[c], lane, 32);
+      prefetch_range(P + hv.chunk_begin[c], P + hv.chunk_end[c], lane, 32);
       float ax = 0.f, ay = 0.f;
       attract_entries<32, PT, YT>(hv.chunk_begin[c], hv.chunk_end[c], a.col, P, Y, i, lane, ld_y(Y, i), ax, ay,
                                   a.n, dbg);
@@ -113,6 +128,21 @@ __global__ void __launch_bounds__(kPlanThreads, 6)
   const PlanCta m = med ? pv.med[cb] : pv.shorts[cb - pv.n_med];
   const int shift = med ? 5 : 3;
   const int64_t row0 = med ? 0 : (int64_t)(cb - pv.n_med) * kShortRowsPerCta;
+  {
+    const int64_t tot = (int64_t)m.cnt[0] + m.cnt[1] + m.cnt[2] + m.cnt[3];
+    prefetch_range(pv.code + m.pair, pv.code + m.pair + m.cnt[0], tid, kPlanThreads);
+    prefetch_range(pv.colS + m.ent, pv.colS + m.ent + tot, tid, kPlanThreads);
+    const PT* PS = static_cast<const PT*>(pv.PS);
+    prefetch_range(PS + m.ent, PS + m.ent + tot, tid, kPlanThreads);
+  }
+  if (!med) {
+    const int64_t r1 = row0 + kShortRowsPerCta < a.n ? row0 + kShortRowsPerCta : a.n;
+    prefetch_range(a.rp + row0, a.rp + r1 + 1, tid, kPlanThreads);
+    prefetch_range(a.frep + row0, a.frep + r1, tid, kPlanThreads);
+    prefetch_range(a.upd + row0, a.upd + r1, tid, kPlanThreads);
+    prefetch_range(a.gains + row0, a.gains + r1, tid, kPlanThreads);
+    prefetch_range(a.Ym + row0, a.Ym + r1, tid, kPlanThreads);
+  }
   for (int k = tid; k < kPartials; k += kPlanThreads) spart[k] = make_float2(0.f, 0.f);
   __syncthreads();
 
