@@ -158,7 +158,7 @@ void worker_main(tsgne_server* s) {
       if (s->stop) return;
       id = s->prep_q.front();
       s->prep_q.pop_front();
-      r = &s->reqs[id];  // not erased while preparing; its inputs are not touched by the ticks
+      r = &s->reqs.find(id)->second;  // present and not erased while preparing; its inputs are not touched by the ticks
     }
     tsgne_member* m = nullptr;
     const tsgne_status st = tsgne_batch_prepare(s->batch, r->n, r->rp.data(), r->col.empty() ? nullptr : r->col.data(),
