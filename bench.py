@@ -427,7 +427,7 @@ def run_ours(args):
     rmat_res = bench_rmat(args, pkg) if (rank == 0 and not args.no_rmat) else None
     tree_res = bench_tree(args, pkg, g, X, Y0, Yt) if (rank == 0 and not args.no_tree) else None
     rw_res = bench_random_walk(args, pkg, g, X) if (rank == 0 and not args.no_tree) else None
-    scale_res = bench_scale(args, pkg) if (rank == 0 and args.scale) else None
+    scale_res = bench_scale(args, pkg) if (rank == 0 and not args.no_scale) else None
     cfg0_res = bench_config0(args, pkg) if (rank == 0 and not args.no_config0) else None
 
     if rank != 0:
@@ -980,7 +980,8 @@ def main():
     ap.add_argument("--only-rmat", action="store_true", help="run only the R-MAT section (profiling)")
     ap.add_argument("--only-tree", action="store_true", help="run only the tree-code section (profiling)")
     ap.add_argument("--only-batched", action="store_true", help="run only the batched section (profiling)")
-    ap.add_argument("--scale", action="store_true", help="also lay out 3M- and 4M-node graphs with the tree code (a few minutes)")
+    ap.add_argument("--no-scale", action="store_true",
+                    help="skip the 3M- and 4M-node tree-code layouts (about a minute, most of it building the graphs)")
     ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOAD,
                     help="zipf300k is the benchmark; the others are smaller cases for profiling")
     args = ap.parse_args()
