@@ -484,9 +484,11 @@ tsgne_status install(tsgne_ctx* ctx, int n, int64_t nnz, DevBuf<int64_t>& rp, De
   } else {
     ctx->P16 = DevBuf<tsgne::bf16>();
   }
-  TS_TRY(find_heavy_rows(n, ctx->rp.get(), ctx->hub, ctx->stream));
-  TS_TRY(build_attract_plan(n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->bf16 ? ctx->P16.get() : nullptr,
-                            ctx->hub, ctx->plan, ctx->stream));
+  TS_TRY(host_guard([&] { return find_heavy_rows(n, ctx->rp.get(), ctx->hub, ctx->stream); }));
+  TS_TRY(host_guard([&] {
+    return build_attract_plan(n, ctx->rp.get(), ctx->col.get(), ctx->P.get(), ctx->bf16 ? ctx->P16.get() : nullptr,
+                              ctx->hub, ctx->plan, ctx->stream);
+  }));
   ctx->have_P = true;
   return TSGNE_OK;
 }

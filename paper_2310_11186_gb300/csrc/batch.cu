@@ -372,7 +372,7 @@ void invalidate(tsgne_batch* b) {
 }
 
 // Uploads descriptors and prefix offsets for the current membership.
-tsgne_status refresh(tsgne_batch* b) {
+tsgne_status refresh_impl(tsgne_batch* b) {
   if (!b->dirty) return TSGNE_OK;
   std::vector<Member*> act;
   b->trees.clear();
@@ -428,6 +428,8 @@ tsgne_status refresh(tsgne_batch* b) {
   b->dirty = false;
   return TSGNE_OK;
 }
+
+tsgne_status refresh(tsgne_batch* b) { return host_guard([&] { return refresh_impl(b); }); }
 
 constexpr int kAuxStreams = 8;
 
@@ -712,7 +714,9 @@ tsgne_status tsgne_batch_add_ex(tsgne_batch* b, int32_t n, const int64_t* row_pt
   b->err.clear();
   last_msg().clear();
   std::unique_ptr<Member> mem;
-  B_TRY(b, prepare_member(b->cfg, b->sms, n, row_ptr, col_idx, X, d, Y0, ptr_kind, repulsion, b->stream, mem));
+  B_TRY(b, host_guard([&] {
+          return prepare_member(b->cfg, b->sms, n, row_ptr, col_idx, X, d, Y0, ptr_kind, repulsion, b->stream, mem);
+        }));
   B_TRY(b, attach_member(b, std::move(mem), id_out));
   return TSGNE_OK;
 }
@@ -731,7 +735,8 @@ tsgne_status tsgne_batch_prepare(tsgne_batch* b, int32_t n, const int64_t* row_p
   const cudaStream_t saved = as;
   as = s;  // stream-ordered allocations: no device-wide wait in cudaFree
   std::unique_ptr<Member> mem;
-  const tsgne_status st = prepare_member(b->cfg, b->sms, n, row_ptr, col_idx, X, d, Y0, ptr_kind, repulsion, s, mem);
+  const tsgne_status st = host_guard(
+      [&] { return prepare_member(b->cfg, b->sms, n, row_ptr, col_idx, X, d, Y0, ptr_kind, repulsion, s, mem); });
   as = saved;
   if (st != TSGNE_OK) return st;
   tsgne_member* h = new (std::nothrow) tsgne_member();

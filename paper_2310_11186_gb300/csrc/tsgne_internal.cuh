@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
+#include <new>
 #include <string>
 
 #include "tsgne.h"
@@ -83,6 +84,19 @@ struct RepShape {
 
 // Last error message of the calling thread (copied into the context by the API layer).
 std::string& last_msg();
+
+// Runs f (which returns a status) and turns a failed host allocation into
+// TSGNE_ERR_OOM, so that no C++ exception crosses the C ABI or ends a thread
+// of the library.
+template <class F>
+tsgne_status host_guard(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    last_msg() = "out of host memory";
+    return TSGNE_ERR_OOM;
+  }
+}
 
 // Returns TSGNE_ERR_OOM or TSGNE_ERR_CUDA for e and records a message.
 tsgne_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
