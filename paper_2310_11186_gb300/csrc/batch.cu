@@ -319,6 +319,10 @@ struct tsgne_batch {
   std::vector<cudaStream_t> aux;  // branches of the tree members' launches
   std::vector<cudaEvent_t> ev;    // fork event, then one join event per tree member
   ~tsgne_batch() {
+    // work still queued may read the members' buffers, and a buffer from the
+    // admission worker is freed on the worker's stream, not on these
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto a : aux) cudaStreamSynchronize(a);
     members.clear();  // stream-ordered frees need their streams
     if (graph) cudaGraphExecDestroy(graph);
     for (auto e : ev) cudaEventDestroy(e);
