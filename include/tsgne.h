@@ -98,8 +98,10 @@ typedef struct {
                               and centre at distance d from the group's box as one
                               interaction when r < theta * d; opened nodes of <= 4 points
                               are summed exactly.  Z and the forces are both approximated;
-                              n must be below 2^30 (else INVALID_ARG when P is built); the
-                              batch API accepts 0 only */
+                              n must be below 2^30 (else INVALID_ARG when P is built).  The
+                              exact sums take at most 2^24 - 2048 points (else INVALID_ARG
+                              when P is built).  In the batch API it is the default of the
+                              members (tsgne_batch_add_ex chooses per member) */
   float theta;             /* opening angle of the tree code, [0, 1] (default 0.5; 0 sums
                               every pair exactly through the tree) */
   int32_t p_walks;         /* 0: p_{j|i} by the perplexity bisection of Eq. 2 (default);

@@ -425,6 +425,10 @@ tsgne_status ensure_graph(tsgne_ctx* ctx, int start) {
 
 // Allocates the per-layout buffers for n points (after P is known).
 tsgne_status alloc_layout(tsgne_ctx* ctx) {
+  if (ctx->cfg.repulsion == 0 && ctx->n > kMaxExactPoints) {
+    last_msg() = "the exact repulsion takes at most 2^24 - 2048 points (cfg.repulsion = 1: the tree code)";
+    return TSGNE_ERR_INVALID_ARG;
+  }
   ctx->shape = repulsion_shape_sym(ctx->n, ctx->sms);
   ctx->ordered = false;
   TS_TRY(repulsion_sym_prepare(ctx->shape));

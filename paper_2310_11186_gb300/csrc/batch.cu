@@ -389,6 +389,16 @@ tsgne_status refresh_impl(tsgne_batch* b) {
   b->G = G;
   std::vector<GraphDesc> h(G > 0 ? G : 1);
   std::vector<int> uo(G + 1, 0), ro(G + 1, 0), co(G + 1, 0);
+  int64_t tu = 0, tr = 0, tc = 0;  // the totals are 32-bit in the kernels
+  for (const Member* m : act) {
+    tu += m->units;
+    tr += m->n;
+    tc += m->hv.chunks;
+  }
+  if (tu > INT32_MAX || tr * kBG > INT32_MAX || tc > INT32_MAX) {
+    last_msg() = "the active members' tile pairs, rows or hub chunks exceed the batch's 32-bit counts";
+    return TSGNE_ERR_INVALID_ARG;
+  }
   for (int k = 0; k < G; ++k) {
     Member& m = *act[k];
     GraphDesc d{};
@@ -573,6 +583,9 @@ tsgne_status prepare_member(const tsgne_config& cfg, int sms, int32_t n, const i
   if (!(repulsion == 0 || repulsion == 1)) return fail_(TSGNE_ERR_INVALID_ARG, "repulsion must be 0 or 1");
   if (n < 2 || d < 1 || !row_ptr || !X || !(ptr_kind == TSGNE_PTR_HOST || ptr_kind == TSGNE_PTR_DEVICE))
     return fail_(TSGNE_ERR_INVALID_ARG, "need n >= 2, d >= 1, row_ptr, X and a valid ptr_kind");
+  if (repulsion == 0 && n > kMaxExactPoints)
+    return fail_(TSGNE_ERR_INVALID_ARG, "an exact member takes at most 2^24 - 2048 points (repulsion = 1: the tree code)");
+  if (repulsion == 1 && n >= (1 << 30)) return fail_(TSGNE_ERR_INVALID_ARG, "the tree code takes fewer than 2^30 points");
   const cudaMemcpyKind kin = ptr_kind == TSGNE_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   int64_t first = 0, m = 0;
   if (ptr_kind == TSGNE_PTR_HOST) {

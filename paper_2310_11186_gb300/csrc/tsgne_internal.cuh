@@ -85,6 +85,12 @@ struct RepShape {
 // Last error message of the calling thread (copied into the context by the API layer).
 std::string& last_msg();
 
+// Largest layout of the exact pass: its tile pairs are numbered in 32-bit
+// ints, nt (nt + 1) / 2 for nt tiles, and the smallest tile (256 points)
+// gives nt = 65,528 here.  An exact iteration at this size takes about a
+// minute; the tree code takes up to 2^30 points.
+constexpr int kMaxExactPoints = (1 << 24) - 2048;
+
 // Runs f (which returns a status) and turns a failed host allocation into
 // TSGNE_ERR_OOM, so that no C++ exception crosses the C ABI or ends a thread
 // of the library.

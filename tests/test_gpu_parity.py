@@ -497,3 +497,23 @@ def test_layout_after_10_iterations_with_hub_rows():
             out.append(lay.get_Y())
     assert np.array_equal(out[0], out[1])
     assert rel_l2(out[0], oY) < 1e-4, rel_l2(out[0], oY)
+
+
+def test_exact_pass_size_limit_is_reported():
+    """Above 2^24 - 2048 points the exact pass's tile-pair count would leave
+    its 32-bit range: P builds, the layout is refused with INVALID_ARG and the
+    context stays usable; a batch refuses such an exact member before any
+    device work."""
+    n = (1 << 24) - 2048 + 1
+    rp = np.zeros(n + 1, np.int64)
+    X = np.zeros((n, 1), np.float32)
+    with pkg.Layout() as lay:
+        with pytest.raises(pkg.TsgneError) as e:
+            lay.build_P(rp, np.zeros(0, np.int32), X)
+        assert e.value.status == 1
+        lay.build_P(np.array([0, 1, 2, 2], np.int64), np.array([1, 0], np.int32), np.zeros((3, 2), np.float32))
+        assert lay.sizes() == (3, 2)
+    with pkg.Batch() as b:
+        with pytest.raises(pkg.TsgneError) as e:
+            b.add(rp, np.zeros(0, np.int32), X)
+        assert e.value.status == 1
