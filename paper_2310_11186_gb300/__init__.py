@@ -313,9 +313,13 @@ def tsgne_shortest_path_embedding(row_ptr, col_idx, targets, l0: int = 0, out=No
             out = torch.empty((n, d), dtype=torch.float32, device=row_ptr.device)
         else:
             out = np.zeros((n, d), np.float32)
+    if _numel(out) != n * d:
+        raise ValueError(f"out must hold n x d = {n * d} float32 values, not {_numel(out)}")
     ob = _as_buffer(out, np.float32)
     if ob[1] != kind:
         raise ValueError("out must live where the inputs live")
+    if ob[2] is not out and not (hasattr(out, "data_ptr") and ob[2].data_ptr() == out.data_ptr()):
+        raise ValueError("out must be a contiguous float32 array")
     s = None if stream is None else ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
     st = lib().tsgne_shortest_path_embedding(n, rp[0], ci[0], tg[0], d, int(l0), ob[0], kind, s)
     if st != 0:
@@ -376,9 +380,15 @@ def tsgne_kl(ctx) -> float:
     return v.value
 
 
+def _numel(a) -> int:
+    return int(a.numel()) if hasattr(a, "numel") else int(np.size(a))
+
+
 def _out(n, out):
     if out is None:
         out = np.zeros((n, 2), np.float32)
+    if _numel(out) != 2 * n:
+        raise ValueError(f"output must hold n x 2 = {2 * n} float32 values, not {_numel(out)}")
     buf = _as_buffer(out, np.float32)
     if buf[2] is not out and not (hasattr(out, "data_ptr") and buf[2].data_ptr() == out.data_ptr()):
         raise ValueError("output must be a contiguous float32 array")

@@ -7,6 +7,7 @@ import re
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_2310_11186_gb300 as pkg
@@ -140,3 +141,20 @@ def test_a_c_program_links_and_calls_the_library(built, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stderr)
+
+
+def test_outputs_of_the_wrong_size_are_refused_before_the_library_writes(built):
+    # _out runs before any call into the library: a short or long buffer never
+    # reaches it
+    with pytest.raises(ValueError):
+        pkg._out(10, np.zeros((9, 2), np.float32))
+    with pytest.raises(ValueError):
+        pkg._out(10, np.zeros(21, np.float32))
+    with pytest.raises(ValueError):  # a dtype that would need a copy
+        pkg._out(10, np.zeros((10, 2), np.float64))
+    out, buf = pkg._out(10, np.zeros((10, 2), np.float32))
+    assert out.shape == (10, 2) and buf[2] is out
+    rp = np.array([0, 1, 2], np.int64)
+    col = np.array([1, 0], np.int32)
+    with pytest.raises(ValueError):
+        pkg.tsgne_shortest_path_embedding(rp, col, np.array([0], np.int32), out=np.zeros((2, 2), np.float32))
