@@ -290,6 +290,9 @@ def _same_kind(*bufs):
 
 
 def tsgne_build_P(ctx, n, row_ptr, col_idx, X):
+    _graph(int(n), row_ptr, col_idx)
+    if len(X.shape) != 2 or int(X.shape[0]) != int(n):
+        raise ValueError("X must be an n x d array")
     rp = _as_buffer(row_ptr, np.int64)
     ci = _as_buffer(col_idx, np.int32)
     x = _as_buffer(X, np.float32)
@@ -302,6 +305,7 @@ def tsgne_shortest_path_embedding(row_ptr, col_idx, targets, l0: int = 0, out=No
     """ShortestPath embedding (Sec. 2.3, Eq. 8): float32 n x d BFS distances to
     the targets, capped at l0 + 1 (l0 <= 0: floor(sqrt(|E|)))."""
     n = len(row_ptr) - 1
+    _graph(n, row_ptr, col_idx)
     rp = _as_buffer(row_ptr, np.int64)
     ci = _as_buffer(col_idx, np.int32)
     tg = _as_buffer(targets, np.int32)
@@ -328,6 +332,7 @@ def tsgne_shortest_path_embedding(row_ptr, col_idx, targets, l0: int = 0, out=No
 
 
 def tsgne_build_P_shortest_path(ctx, n, row_ptr, col_idx, targets, l0: int = 0):
+    _graph(int(n), row_ptr, col_idx)
     rp = _as_buffer(row_ptr, np.int64)
     ci = _as_buffer(col_idx, np.int32)
     tg = _as_buffer(targets, np.int32)
@@ -336,6 +341,9 @@ def tsgne_build_P_shortest_path(ctx, n, row_ptr, col_idx, targets, l0: int = 0):
 
 
 def tsgne_set_P(ctx, n, row_ptr, col_idx, P):
+    _graph(int(n), row_ptr, col_idx)
+    if _numel(P) != _numel(col_idx):
+        raise ValueError("P must hold one value per entry of col")
     rp = _as_buffer(row_ptr, np.int64)
     ci = _as_buffer(col_idx, np.int32)
     pv = _as_buffer(P, np.float32)
@@ -362,6 +370,8 @@ def tsgne_get_P(ctx):
 
 
 def tsgne_init_Y(ctx, Y0=None):
+    if Y0 is not None:
+        _rows(Y0, tsgne_get_sizes(ctx)[0], 2, "Y0")
     y = _as_buffer(Y0, np.float32)
     _check(ctx, lib().tsgne_init_Y(ctx, y[0], y[1]))
 
@@ -393,6 +403,26 @@ def _out(n, out):
     if buf[2] is not out and not (hasattr(out, "data_ptr") and buf[2].data_ptr() == out.data_ptr()):
         raise ValueError("output must be a contiguous float32 array")
     return out, buf
+
+
+def _rows(a, n: int, k: int, name: str):
+    """Checks that an input holds n x k values (k = 0: n values) before the
+    library reads it."""
+    if a is None:
+        return
+    want = n * k if k else n
+    if _numel(a) != want:
+        raise ValueError(f"{name} must hold {want} values ({n} x {k or 1}), not {_numel(a)}")
+
+
+def _graph(n: int, row_ptr, col):
+    """row_ptr must hold n + 1 values and col at least row_ptr[n] (the
+    library reads that many; it validates the values themselves)."""
+    if n < 0 or _numel(row_ptr) != n + 1:
+        raise ValueError("row_ptr must hold n + 1 values")
+    m = int(row_ptr[-1]) if n >= 0 and _numel(row_ptr) > 0 else 0
+    if m > 0 and (col is None or _numel(col) < m):
+        raise ValueError(f"col must hold at least row_ptr[n] = {m} values")
 
 
 def tsgne_gradient(ctx, alpha: float = 1.0, out=None):
@@ -469,6 +499,10 @@ def tsgne_get_state(ctx):
 
 
 def tsgne_set_state(ctx, Y, update=None, gains=None, iteration=0):
+    n = tsgne_get_sizes(ctx)[0]
+    _rows(Y, n, 2, "Y")
+    _rows(update, n, 2, "update")
+    _rows(gains, n, 2, "gains")
     y = _as_buffer(Y, np.float32)
     u = _as_buffer(update, np.float32)
     g = _as_buffer(gains, np.float32)
@@ -691,6 +725,11 @@ class Batch:
     def add(self, row_ptr, col, X, Y0=None, repulsion=None) -> int:
         """Adds a member; repulsion 0 (exact) or 1 (tree code), default the
         batch configuration's."""
+        n = len(row_ptr) - 1
+        _graph(n, row_ptr, col)
+        if len(X.shape) != 2 or int(X.shape[0]) != n:
+            raise ValueError("X must be an n x d array")
+        _rows(Y0, n, 2, "Y0")
         rp = _as_buffer(row_ptr, np.int64)
         ci = _as_buffer(col, np.int32)
         x = _as_buffer(X, np.float32)
@@ -864,6 +903,10 @@ class Server:
         y = None if Y0 is None else np.ascontiguousarray(Y0, np.float32)
         rid = _i64()
         n = rp.size - 1
+        _graph(n, rp, ci)
+        if x.ndim != 2 or x.shape[0] != n:
+            raise ValueError("X must be an n x d array")
+        _rows(y, n, 2, "Y0")
         self._check(lib().tsgne_server_submit(self.h, n, rp.ctypes.data_as(_p), ci.ctypes.data_as(_p) if ci.size else None,
                                               x.ctypes.data_as(_p), int(x.shape[1]),
                                               None if y is None else y.ctypes.data_as(_p), ctypes.byref(rid)))

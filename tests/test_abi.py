@@ -158,3 +158,19 @@ def test_outputs_of_the_wrong_size_are_refused_before_the_library_writes(built):
     col = np.array([1, 0], np.int32)
     with pytest.raises(ValueError):
         pkg.tsgne_shortest_path_embedding(rp, col, np.array([0], np.int32), out=np.zeros((2, 2), np.float32))
+
+
+def test_inputs_of_the_wrong_size_are_refused_before_the_library_reads(built):
+    rp = np.array([0, 2, 3, 4], np.int64)
+    pkg._graph(3, rp, np.array([1, 2, 0, 0], np.int32))
+    with pytest.raises(ValueError):  # col shorter than row_ptr[n]
+        pkg._graph(3, rp, np.array([1, 2, 0], np.int32))
+    with pytest.raises(ValueError):  # row_ptr of the wrong length
+        pkg._graph(4, rp, np.array([1, 2, 0, 0], np.int32))
+    pkg._rows(np.zeros((3, 2), np.float32), 3, 2, "Y0")
+    with pytest.raises(ValueError):
+        pkg._rows(np.zeros((2, 2), np.float32), 3, 2, "Y0")
+    with pytest.raises(ValueError):  # X with the wrong row count, before any call into the library
+        pkg.tsgne_build_P(None, 3, rp, np.array([1, 2, 0, 0], np.int32), np.zeros((2, 4), np.float32))
+    with pytest.raises(ValueError):  # P with the wrong length
+        pkg.tsgne_set_P(None, 3, rp, np.array([1, 2, 0, 0], np.int32), np.zeros(3, np.float32))
