@@ -389,6 +389,20 @@ def test_device_layout_io():
         G = torch.empty_like(out)
         lay.gradient(1.0, out=G)
         assert np.array_equal(G.cpu().numpy(), lay.gradient(1.0)[0])
+        # device buffers of the wrong size never reach the library
+        with pytest.raises(ValueError):
+            lay.get_Y(torch.empty((g.n - 1, 2), dtype=torch.float32, device="cuda"))
+        with pytest.raises(ValueError):
+            lay.init_Y(Y0[:-1])
+        with pytest.raises(ValueError):
+            lay.set_state(Y0, update=torch.zeros((g.n, 1), dtype=torch.float32, device="cuda"))
+        rp = torch.from_numpy(g.row_ptr).cuda()
+        col = torch.from_numpy(g.col).cuda()
+        with pytest.raises(ValueError):
+            lay.build_P(rp, col[:-1], torch.from_numpy(X).cuda())
+        with pytest.raises(ValueError):
+            lay.build_P(rp, col, torch.from_numpy(X[:-1]).cuda())
+        assert np.array_equal(out.cpu().numpy(), lay.get_Y())  # the layout is untouched
 
 
 def test_gradient_parity_with_hub_rows():
