@@ -198,7 +198,15 @@ __global__ void __launch_bounds__(256) k_batch_attract(const GraphDesc* __restri
   const int64_t r = gt / G;
   const int lane = (int)(gt % G);
   const bool valid = r < R;
-  const int g = valid ? find_owner(row_off, members, (int)r) : 0;
+  __shared__ int s_g0;  // owner of the CTA's first row; the CTA's rows span few members
+  if (threadIdx.x == 0) {
+    const int64_t r0 = (int64_t)blockIdx.x * blockDim.x / G;
+    s_g0 = r0 < R ? find_owner(row_off, members, (int)r0) : 0;
+  }
+  __syncthreads();
+  int g = s_g0;
+  if (valid)
+    while (g + 1 < members && row_off[g + 1] <= (int)r) ++g;
   const GraphDesc& d = descs[g];
   const int64_t i = valid ? r - row_off[g] : 0;
   float ax = 0.f, ay = 0.f;
